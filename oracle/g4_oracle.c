@@ -1,0 +1,982 @@
+/*
+ * g4_oracle.c -- plain, slow, FP64 CPU reference for the short-range tree/FMM gravity path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA path is checked against.
+ * Only the test-suite, the smoke check and the CPU-baseline leg of the benchmark may load it.
+ * It shares no code, header, table or constant generator with the CUDA library.
+ *
+ * Every function follows the definition or the algorithm steps of GADGET-4 (Springel et al.
+ * 2021) in the paper's order and notation, with no blocking, fusion or reordering beyond
+ * what that definition states:
+ *   - integer coordinates ................ Sec. 2.10 "Integer coordinates", Sec. 2.11
+ *   - Peano-Hilbert keys / oct-tree ....... Sec. 2.2.1 "Geometry of the tree"
+ *   - multipole moments Q_n ............... Sec. 2.2.2, definition below Eq. (eqonesidetreepotential)
+ *   - derivative tensors D_n, g_n ......... Eqs. (eqngderiv0)-(eqngderiv), Appendix A
+ *   - softening law ....................... Eq. (eqnsoft), Sec. 2.1
+ *   - TreePM short-range kernel ........... Eq. (eqnpo4), Sec. 2.3
+ *   - one-sided walk, opening criteria .... Eqs. (eqonesidetreepotential), (eqonesidetreeacc),
+ *                                           (eqnrelcriterion), Sec. 2.2.3
+ *   - FMM expansion, dual walk, L2L/L2P ... Sec. 2.4 and Appendix A
+ *
+ * Readings of places where the paper is silent are listed in the header of each function.
+ * Parity pins (tests/test_oracle_*.py) tie each function to closed forms, invariants and
+ * brute force, independent of this code.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (no fast-math).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXP 5
+#define OR_KEYBITS 21
+
+typedef struct {
+    double box;        /* L: the integer unit is L / 2^32 */
+    int periodic;      /* 1: nearest periodic image (Sec. 2.1, Eq. eqnpo1) */
+    double r_s;        /* TreePM split scale; <= 0 means plain Newtonian kernel */
+    double r_cut;      /* absolute short-range cutoff radius (Sec. 2.3); ignored when r_s <= 0 */
+    int pp_cut;        /* 1: particle pairs at r >= r_cut are dropped */
+    double alpha;      /* relative opening parameter, Eq. (eqnrelcriterion) */
+    double theta;      /* geometric opening angle theta_c */
+    int criterion;     /* 0 = relative, 1 = geometric */
+    int order;         /* expansion order p (1..5) */
+    int exclusion;     /* 1: exclusion zone around node centres (Sec. 2.2.3) */
+    double G;          /* gravitational constant */
+    int n_eps;         /* number of softening classes */
+    const double *eps; /* softening length eps_0 per class (Sec. 2.9) */
+    int keep_qp;       /* FMM: 1 keeps Q_p in the potential (Sec. 2.4 drops it by default) */
+} or_params;
+
+/* ===================================================================================== */
+/* a1: integer coordinates (Sec. 2.10, Sec. 2.11)                                         */
+/* ===================================================================================== */
+
+/* Periodic box: x_int = floor(x / L * 2^32) mod 2^32.  Out is SoA 3 x n. */
+void or_int_coords_periodic(const double *pos, int64_t n, double L, uint32_t *out)
+{
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) {
+            double t = floor(pos[3 * i + k] / L * 4294967296.0);
+            int64_t v = (int64_t)t;
+            out[k * n + i] = (uint32_t)(v & 0xFFFFFFFFLL);
+        }
+}
+
+/* Isolated system (Sec. 2.11): the particles are shrink-wrapped and mapped into the central
+ * half of the integer cube, so that integer differences never wrap.  Reading: cube side S is
+ * the smallest power of two >= 2 * (largest bounding-box extent); the cube is centred on the
+ * bounding-box midpoint.  frame = {origin_x, origin_y, origin_z, S}, with physical position =
+ * origin + x_int * S / 2^32. */
+void or_int_coords_isolated(const double *pos, int64_t n, uint32_t *out, double *frame)
+{
+    double lo[3], hi[3], c[3];
+    for (int k = 0; k < 3; k++) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) {
+            double x = pos[3 * i + k];
+            if (x < lo[k]) lo[k] = x;
+            if (x > hi[k]) hi[k] = x;
+        }
+    double ext = 0.0;
+    for (int k = 0; k < 3; k++) {
+        c[k] = 0.5 * (lo[k] + hi[k]);
+        if (hi[k] - lo[k] > ext) ext = hi[k] - lo[k];
+    }
+    /* smallest power of two S with S >= 2 * ext (S = 1 for a single point) */
+    double S = 1.0;
+    if (ext > 0.0) {
+        int e;
+        double f = frexp(2.0 * ext, &e);   /* 2*ext = f * 2^e, f in [0.5, 1) */
+        S = (f == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+    }
+    double scale = 4294967296.0 / S;
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) {
+            double t = floor((pos[3 * i + k] - c[k]) * scale) + 2147483648.0;
+            out[k * n + i] = (uint32_t)(int64_t)t;
+        }
+    for (int k = 0; k < 3; k++) frame[k] = c[k] - 0.5 * S;
+    frame[3] = S;
+}
+
+/* ===================================================================================== */
+/* a2: Peano-Hilbert key (Sec. 2.2.1; curve construction after Skilling 2004,             */
+/*     "Programming the Hilbert curve", restated here in plain C)                         */
+/* ===================================================================================== */
+
+/* Key of the cell (x, y, z), each given with `bits` bits.  The three coordinates are first
+ * turned into the "transposed" Hilbert index: walking from the most significant bit down, a
+ * set bit at level q inverts the lower bits of the first axis, a clear bit swaps the lower
+ * bits of the first axis with those of the current axis; afterwards the axes are Gray-coded.
+ * The key interleaves the transposed bits, x first, most significant level first. */
+uint64_t or_hilbert_key(uint32_t x, uint32_t y, uint32_t z, int bits)
+{
+    uint32_t X[3] = {x, y, z};
+    uint32_t top = 1u << (bits - 1);
+    for (uint32_t q = top; q > 1; q >>= 1) {
+        uint32_t low = q - 1;
+        for (int ax = 0; ax < 3; ax++) {
+            if (X[ax] & q) {
+                X[0] ^= low;
+            } else {
+                uint32_t t = (X[0] ^ X[ax]) & low;
+                X[0] ^= t;
+                X[ax] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t flip = 0;
+    for (uint32_t q = top; q > 1; q >>= 1)
+        if (X[2] & q) flip ^= q - 1;
+    for (int ax = 0; ax < 3; ax++) X[ax] ^= flip;
+    uint64_t key = 0;
+    for (int b = bits - 1; b >= 0; b--)
+        for (int ax = 0; ax < 3; ax++)
+            key = (key << 1) | ((X[ax] >> b) & 1u);
+    return key;
+}
+
+/* 63-bit key from the top 21 bits of each 32-bit coordinate. */
+void or_keys(const uint32_t *pos, int64_t n, uint64_t *keys)
+{
+    for (int64_t i = 0; i < n; i++)
+        keys[i] = or_hilbert_key(pos[i] >> 11, pos[n + i] >> 11, pos[2 * n + i] >> 11,
+                                 OR_KEYBITS);
+}
+
+/* a3: stable sort of (key, original index); perm[sorted] = original index. */
+typedef struct { uint64_t key; int64_t idx; } or_kv;
+static int or_kv_cmp(const void *a, const void *b)
+{
+    const or_kv *p = (const or_kv *)a, *q = (const or_kv *)b;
+    if (p->key != q->key) return p->key < q->key ? -1 : 1;
+    return p->idx < q->idx ? -1 : (p->idx > q->idx ? 1 : 0);
+}
+
+void or_sort(const uint64_t *keys, int64_t n, uint64_t *keys_sorted, int64_t *perm)
+{
+    or_kv *a = (or_kv *)malloc(sizeof(or_kv) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; i++) { a[i].key = keys[i]; a[i].idx = i; }
+    qsort(a, (size_t)n, sizeof(or_kv), or_kv_cmp);
+    for (int64_t i = 0; i < n; i++) { keys_sorted[i] = a[i].key; perm[i] = a[i].idx; }
+    free(a);
+}
+
+/* ===================================================================================== */
+/* a4: oct-tree with a leaf threshold (Sec. 2.2.1)                                        */
+/* ===================================================================================== */
+
+typedef struct {
+    int64_t nn, cap;
+    int32_t *level;
+    int64_t *first, *count, *next;  /* next = index after the node's subtree (DFS pre-order) */
+    uint32_t *center;               /* nn x 3 geometric centre in integer units */
+    /* filled by or_multipoles */
+    int order;
+    double *mass;                   /* nn */
+    double *com;                    /* nn x 3: (s - c) in physical units */
+    double *mono;                   /* nn x nmono: monomial moments of orders 0..order */
+    double *eps_max, *amin;         /* nn */
+} or_tree;
+
+static int64_t or_nmono(int order) { return (int64_t)(order + 1) * (order + 2) * (order + 3) / 6; }
+
+/* offset of multi-index (a, b, c), a + b + c = n, within all monomials of orders 0..n */
+static int or_mono_index(int a, int b, int c)
+{
+    int n = a + b + c;
+    return n * (n + 1) * (n + 2) / 6 + (n - a) * (n - a + 1) / 2 + (n - a - b);
+}
+
+static void or_tree_push(or_tree *t, int level, int64_t first, int64_t count,
+                         const uint32_t *pos, int64_t np)
+{
+    if (t->nn == t->cap) {
+        t->cap = t->cap * 2 + 64;
+        t->level = (int32_t *)realloc(t->level, sizeof(int32_t) * t->cap);
+        t->first = (int64_t *)realloc(t->first, sizeof(int64_t) * t->cap);
+        t->count = (int64_t *)realloc(t->count, sizeof(int64_t) * t->cap);
+        t->next = (int64_t *)realloc(t->next, sizeof(int64_t) * t->cap);
+        t->center = (uint32_t *)realloc(t->center, sizeof(uint32_t) * 3 * t->cap);
+    }
+    int64_t k = t->nn++;
+    t->level[k] = level;
+    t->first[k] = first;
+    t->count[k] = count;
+    t->next[k] = -1;
+    /* the cell of a level-l node is the common top-l-bit prefix of its particles' coordinates */
+    for (int ax = 0; ax < 3; ax++) {
+        uint32_t x = pos[ax * np + first];
+        uint32_t corner = (level == 0) ? 0u : (x & ~((1u << (32 - level)) - 1u));
+        uint32_t half = (level == 0) ? 0x80000000u : (1u << (31 - level));
+        t->center[3 * k + ax] = corner + half;
+    }
+}
+
+/* Recursive subdivision in depth-first pre-order, children in PH order.  A node is split
+ * when it holds more than leaf_max particles and has not reached the key resolution. */
+static void or_build_rec(or_tree *t, const uint64_t *keys, const uint32_t *pos, int64_t np,
+                         int level, int64_t first, int64_t count, int leaf_max)
+{
+    int64_t me = t->nn;
+    or_tree_push(t, level, first, count, pos, np);
+    if (count > leaf_max && level < OR_KEYBITS) {
+        int shift = 3 * (OR_KEYBITS - level - 1);
+        int64_t i = first, end = first + count;
+        while (i < end) {
+            uint64_t digit = (keys[i] >> shift) & 7u;
+            int64_t j = i;
+            while (j < end && ((keys[j] >> shift) & 7u) == digit) j++;
+            or_build_rec(t, keys, pos, np, level + 1, i, j - i, leaf_max);
+            i = j;
+        }
+    }
+    t->next[me] = t->nn;
+}
+
+or_tree *or_tree_build(const uint64_t *keys_sorted, const uint32_t *pos_sorted, int64_t n,
+                       int leaf_max)
+{
+    or_tree *t = (or_tree *)calloc(1, sizeof(or_tree));
+    if (n > 0) or_build_rec(t, keys_sorted, pos_sorted, n, 0, 0, n, leaf_max);
+    return t;
+}
+
+int64_t or_tree_nnodes(const or_tree *t) { return t->nn; }
+
+void or_tree_export(const or_tree *t, int32_t *level, int64_t *first, int64_t *count,
+                    int64_t *next, uint32_t *center)
+{
+    memcpy(level, t->level, sizeof(int32_t) * t->nn);
+    memcpy(first, t->first, sizeof(int64_t) * t->nn);
+    memcpy(count, t->count, sizeof(int64_t) * t->nn);
+    memcpy(next, t->next, sizeof(int64_t) * t->nn);
+    memcpy(center, t->center, sizeof(uint32_t) * 3 * t->nn);
+}
+
+void or_tree_free(or_tree *t)
+{
+    if (!t) return;
+    free(t->level); free(t->first); free(t->count); free(t->next); free(t->center);
+    free(t->mass); free(t->com); free(t->mono); free(t->eps_max); free(t->amin);
+    free(t);
+}
+
+/* ===================================================================================== */
+/* a5: node moments by definition (Sec. 2.2.2): M, centre of mass s, and                  */
+/*     Q_n = sum_j m_j (x_j - s)^(n), stored as monomials sum m dx^a dy^b dz^c.            */
+/* ===================================================================================== */
+
+static double or_isep(uint32_t a, uint32_t b, int periodic)
+{
+    /* signed integer difference a - b: two's complement gives the nearest image (Sec. 2.10) */
+    if (periodic) return (double)(int32_t)(a - b);
+    return (double)((int64_t)a - (int64_t)b);
+}
+
+static double or_ipow(double x, int k)
+{
+    double r = 1.0;
+    for (int i = 0; i < k; i++) r *= x;
+    return r;
+}
+
+void or_multipoles(or_tree *t, const uint32_t *pos, int64_t np, const double *mass,
+                   const uint8_t *cls, const double *aold, const or_params *P)
+{
+    int order = P->order;
+    int64_t nm = or_nmono(order);
+    double scale = P->box / 4294967296.0;
+    t->order = order;
+    t->mass = (double *)realloc(t->mass, sizeof(double) * (t->nn ? t->nn : 1));
+    t->com = (double *)realloc(t->com, sizeof(double) * 3 * (t->nn ? t->nn : 1));
+    t->mono = (double *)realloc(t->mono, sizeof(double) * nm * (t->nn ? t->nn : 1));
+    t->eps_max = (double *)realloc(t->eps_max, sizeof(double) * (t->nn ? t->nn : 1));
+    t->amin = (double *)realloc(t->amin, sizeof(double) * (t->nn ? t->nn : 1));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < t->nn; k++) {
+        int64_t f = t->first[k], e = f + t->count[k];
+        double M = 0.0, d[3] = {0, 0, 0}, em = 0.0, am = INFINITY;
+        for (int64_t j = f; j < e; j++) {
+            M += mass[j];
+            for (int ax = 0; ax < 3; ax++)
+                d[ax] += mass[j] * or_isep(pos[ax * np + j], t->center[3 * k + ax], 0) * scale;
+            double ej = P->eps[cls ? cls[j] : 0];
+            if (ej > em) em = ej;
+            double aj = aold ? aold[j] : 0.0;
+            if (aj < am) am = aj;
+        }
+        double s[3];
+        for (int ax = 0; ax < 3; ax++) s[ax] = (M > 0) ? d[ax] / M : 0.0;
+        t->mass[k] = M;
+        for (int ax = 0; ax < 3; ax++) t->com[3 * k + ax] = s[ax];
+        t->eps_max[k] = em;
+        t->amin[k] = am;
+        double *q = t->mono + nm * k;
+        for (int64_t c = 0; c < nm; c++) q[c] = 0.0;
+        for (int64_t j = f; j < e; j++) {
+            double dx[3];
+            for (int ax = 0; ax < 3; ax++)
+                dx[ax] = or_isep(pos[ax * np + j], t->center[3 * k + ax], 0) * scale - s[ax];
+            for (int n = 0; n <= order; n++)
+                for (int a = n; a >= 0; a--)
+                    for (int b = n - a; b >= 0; b--) {
+                        int c = n - a - b;
+                        q[or_mono_index(a, b, c)] +=
+                            mass[j] * or_ipow(dx[0], a) * or_ipow(dx[1], b) * or_ipow(dx[2], c);
+                    }
+        }
+    }
+}
+
+void or_tree_export_moments(const or_tree *t, double *mass, double *com, double *mono,
+                            double *eps_max, double *amin)
+{
+    int64_t nm = or_nmono(t->order);
+    memcpy(mass, t->mass, sizeof(double) * t->nn);
+    memcpy(com, t->com, sizeof(double) * 3 * t->nn);
+    memcpy(mono, t->mono, sizeof(double) * nm * t->nn);
+    if (eps_max) memcpy(eps_max, t->eps_max, sizeof(double) * t->nn);
+    if (amin) memcpy(amin, t->amin, sizeof(double) * t->nn);
+}
+
+/* ===================================================================================== */
+/* a7: interaction kernels                                                                 */
+/* ===================================================================================== */
+
+/* Cubic-spline softened inverse distance g_soft(r) = 1/(r + eps(r)) = -W_2(u)/h with
+ * h = 2.8 eps_0, u = r/h (Eq. eqnsoft).  W_2 is the potential of the cubic spline kernel
+ * (Springel et al. 2001, eq. 71, not printed in the paper; reading: the standard form).
+ * Returns g0 = g_soft and g1 = (1/r) d g_soft / dr. */
+void or_soft_kernel(double r, double h, double *g0, double *g1)
+{
+    if (r >= h) {
+        *g0 = 1.0 / r;
+        *g1 = -1.0 / (r * r * r);
+        return;
+    }
+    double u = r / h, u2 = u * u;
+    double W, dWu; /* W_2(u) and W_2'(u)/u */
+    if (u < 0.5) {
+        W = 16.0 / 3.0 * u2 - 48.0 / 5.0 * u2 * u2 + 32.0 / 5.0 * u2 * u2 * u - 14.0 / 5.0;
+        dWu = 32.0 / 3.0 - 192.0 / 5.0 * u2 + 32.0 * u2 * u;
+    } else {
+        W = 1.0 / (15.0 * u) + 32.0 / 3.0 * u2 - 16.0 * u2 * u + 48.0 / 5.0 * u2 * u2
+            - 32.0 / 15.0 * u2 * u2 * u - 16.0 / 5.0;
+        dWu = -1.0 / (15.0 * u2 * u) + 64.0 / 3.0 - 48.0 * u + 192.0 / 5.0 * u2
+              - 32.0 / 3.0 * u2 * u;
+    }
+    *g0 = -W / h;
+    *g1 = -dWu / (h * h * h);
+}
+
+/* Pair kernel of the short-range potential, Eq. (eqnpo4):
+ *   g(r) = g_soft(r) - 1/r + erfc(r / 2 r_s) / r = g_soft(r) - erf(r / 2 r_s) / r
+ * (the constant pi/(alpha^2 V) is dropped, as in Sec. 2.3).  Plain Newtonian softened kernel
+ * when r_s <= 0.  g1 = g'(r)/r.  h = 2.8 eps_ij with eps_ij = max(eps_i, eps_j). */
+void or_pair_kernel(double r, double h, double r_s, double *g0, double *g1)
+{
+    or_soft_kernel(r, h, g0, g1);
+    if (r_s <= 0.0) return;
+    double al = 0.5 / r_s, x = al * r;
+    const double tsp = 1.1283791670955126; /* 2/sqrt(pi) */
+    if (x < 1e-3) {
+        /* series of erf(x)/x and of its r-derivative term near the origin */
+        *g0 -= al * tsp * (1.0 - x * x / 3.0 + x * x * x * x / 10.0);
+        *g1 += al * al * al * tsp * (2.0 / 3.0 - 0.4 * x * x + x * x * x * x / 7.0);
+        return;
+    }
+    double ef = erf(x);
+    *g0 -= ef / r;
+    /* -(1/r) d/dr [erf(al r)/r] = erf(al r)/r^3 - (2 al/sqrt(pi)) exp(-al^2 r^2) / r^2 */
+    *g1 += ef / (r * r * r) - al * tsp * exp(-x * x) / (r * r);
+}
+
+/* g_n(r) = (r^-1 d/dr)^n g(r) for n = 0..nmax (Eq. above eqngderiv0), for the unsoftened
+ * multipole kernel g = 1/r (r_s <= 0) or g = erfc(r / 2 r_s) / r.  The ordinary derivatives
+ * g^(k) come from Leibniz' rule on erfc(al r) * (1/r) with
+ *   d^j/dr^j erfc(al r) = -(2 al / sqrt(pi)) (-al)^(j-1) H_{j-1}(al r) exp(-al^2 r^2),
+ * H the physicists' Hermite polynomials; g_n then follows from the Appendix A formulas. */
+void or_gn(double r, double r_s, int nmax, double *g)
+{
+    double E[8], R[8], gd[8];
+    int kmax = nmax;
+    if (r_s > 0.0) {
+        double al = 0.5 / r_s, x = al * r, ex = exp(-x * x);
+        double H[8];
+        H[0] = 1.0;
+        H[1] = 2.0 * x;
+        for (int m = 1; m < 7; m++) H[m + 1] = 2.0 * x * H[m] - 2.0 * m * H[m - 1];
+        E[0] = erfc(x);
+        double alp = 1.0; /* (-al)^(j-1) */
+        for (int j = 1; j <= kmax; j++) {
+            E[j] = -1.1283791670955126 * al * alp * H[j - 1] * ex;
+            alp *= -al;
+        }
+    } else {
+        E[0] = 1.0;
+        for (int j = 1; j <= kmax; j++) E[j] = 0.0;
+    }
+    double fact = 1.0, rp = 1.0 / r;
+    for (int i = 0; i <= kmax; i++) {
+        R[i] = ((i & 1) ? -1.0 : 1.0) * fact * rp; /* d^i/dr^i (1/r) = (-1)^i i! / r^(i+1) */
+        fact *= (double)(i + 1);
+        rp /= r;
+    }
+    for (int k = 0; k <= kmax; k++) {
+        double s = 0.0, binom = 1.0;
+        for (int j = 0; j <= k; j++) {
+            s += binom * E[j] * R[k - j];
+            binom = binom * (double)(k - j) / (double)(j + 1);
+        }
+        gd[k] = s;
+    }
+    /* Appendix A: g_n = r^-n sum_j c_{n,j} g^(n-j) / r^j */
+    static const double C[8][7] = {
+        {0},
+        {1},
+        {1, -1},
+        {1, -3, 3},
+        {1, -6, 15, -15},
+        {1, -10, 45, -105, 105},
+        {1, -15, 105, -420, 945, -945},
+        {1, -21, 210, -1260, 4725, -10395, 10395},
+    };
+    g[0] = gd[0];
+    for (int n = 1; n <= nmax; n++) {
+        double s = 0.0, rj = 1.0;
+        for (int j = 0; j < n; j++) {
+            s += C[n][j] * gd[n - j] * rj;
+            rj /= r;
+        }
+        g[n] = s * or_ipow(1.0 / r, n);
+    }
+}
+
+/* Full derivative tensor D_m = grad^(m) g(|r|) (3^m entries, index digit k of the flat index
+ * is the k-th tensor index, little-endian in base 3).  Eqs. (eqngderiv0)-(eqngderiv): each
+ * component is a sum over all partial pairings of its m index slots; a pairing with j pairs
+ * contributes g_{m-j} times one Kronecker delta per pair and one r component per unpaired
+ * slot. */
+static double or_pairings(int m, const int *idx, const double *r, const double *g,
+                          unsigned used, double prod, int pairs)
+{
+    int k = 0;
+    while (k < m && (used & (1u << k))) k++;
+    if (k == m) return g[m - pairs] * prod;
+    used |= 1u << k;
+    double s = or_pairings(m, idx, r, g, used, prod * r[idx[k]], pairs);
+    for (int v = k + 1; v < m; v++)
+        if (!(used & (1u << v)) && idx[v] == idx[k])
+            s += or_pairings(m, idx, r, g, used | (1u << v), prod, pairs + 1);
+    return s;
+}
+
+static int or_pow3(int m)
+{
+    int p = 1;
+    for (int i = 0; i < m; i++) p *= 3;
+    return p;
+}
+
+void or_D_full(int m, const double *r, const double *g, double *out)
+{
+    int n3 = or_pow3(m), idx[16];
+    for (int t = 0; t < n3; t++) {
+        int v = t;
+        for (int k = 0; k < m; k++) { idx[k] = v % 3; v /= 3; }
+        out[t] = or_pairings(m, idx, r, g, 0u, 1.0, 0);
+    }
+}
+
+/* full-tensor component of a symmetric moment tensor: the monomial of its index counts */
+static double or_Q_full(const double *mono, int m, int t)
+{
+    int cnt[3] = {0, 0, 0};
+    for (int k = 0; k < m; k++) { cnt[t % 3]++; t /= 3; }
+    return mono[or_mono_index(cnt[0], cnt[1], cnt[2])];
+}
+
+static double or_factorial(int n)
+{
+    double f = 1.0;
+    for (int i = 2; i <= n; i++) f *= i;
+    return f;
+}
+
+/* ===================================================================================== */
+/* a6: one-sided tree walk (Sec. 2.2.2-2.2.3, Sec. 2.3)                                   */
+/* ===================================================================================== */
+
+/* Particle-node term with r = s - x:
+ *   phi += -G sum_{n=0}^{p}   (1/n!) Q_n . D_n        (Eq. eqonesidetreepotential)
+ *   a   += -G sum_{n=0}^{p-1} (1/n!) Q_n . D_{n+1}    (Eq. eqonesidetreeacc)            */
+static void or_pn(const double *mono, const double *rv, int p, double r_s, double G,
+                  double *acc, double *pot)
+{
+    double r = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+    double g[OR_MAXP + 2];
+    or_gn(r, r_s, p, g);
+    double D[OR_MAXP + 1][729];
+    for (int m = 0; m <= p; m++) or_D_full(m, rv, g, D[m]);
+    double phi = 0.0, a[3] = {0, 0, 0};
+    for (int n = 0; n <= p; n++) {
+        double inv = 1.0 / or_factorial(n);
+        int n3 = or_pow3(n);
+        for (int t = 0; t < n3; t++) {
+            double q = or_Q_full(mono, n, t);
+            phi += inv * q * D[n][t];
+            if (n <= p - 1)
+                for (int i = 0; i < 3; i++) a[i] += inv * q * D[n + 1][i + 3 * t];
+        }
+    }
+    *pot += -G * phi;
+    for (int i = 0; i < 3; i++) acc[i] += -G * a[i];
+}
+
+static double or_sep(uint32_t a, uint32_t b, const or_params *P)
+{
+    return or_isep(a, b, P->periodic) * (P->box / 4294967296.0);
+}
+
+/* Walk for the particle at sorted index i.  Node handling, in this order:
+ *   - TreePM: the node is dropped when the nearest point of its (nearest-image) cube is
+ *     further than r_cut (Sec. 2.3, reading: Euclidean distance to the cube);
+ *   - a leaf is opened into particle-particle terms (pairs at r >= r_cut are dropped when
+ *     pp_cut is set);
+ *   - an internal node is opened if the particle lies inside the node's cube, or inside the
+ *     exclusion cube of half-width l around the geometric centre (Sec. 2.2.3, reading of
+ *     Fig. FigTREESketch), or if r < 2.8 max(eps_i, eps_max(node)) (multipoles are always
+ *     unsoftened, reading of Sec. 2.9), or if the opening criterion fails:
+ *       relative  G M / r^2 (l / r)^p < alpha |a_old|     (Eq. eqnrelcriterion)
+ *       geometric l / r < theta_c;
+ *     otherwise its multipole expansion is used.                                          */
+static void or_walk_one(const or_tree *t, const uint32_t *pos, int64_t np, const double *mass,
+                        const uint8_t *cls, const double *aold, int64_t i, const or_params *P,
+                        double *acc, double *pot, int64_t *cnt)
+{
+    double scale = P->box / 4294967296.0;
+    int p = P->order;
+    int64_t nm = or_nmono(p);
+    int treepm = P->r_s > 0.0;
+    double rc2 = P->r_cut * P->r_cut;
+    double eps_i = P->eps[cls ? cls[i] : 0];
+    double a_i = aold ? aold[i] : 0.0;
+    uint32_t xi[3] = {pos[i], pos[np + i], pos[2 * np + i]};
+    acc[0] = acc[1] = acc[2] = 0.0;
+    *pot = 0.0;
+    cnt[0] = cnt[1] = 0;
+    int64_t k = 0;
+    while (k < t->nn) {
+        double side = ldexp(P->box, -t->level[k]);
+        double dc[3];
+        for (int ax = 0; ax < 3; ax++) dc[ax] = or_sep(t->center[3 * k + ax], xi[ax], P);
+        if (treepm) {
+            double e2 = 0.0;
+            for (int ax = 0; ax < 3; ax++) {
+                double e = fabs(dc[ax]) - 0.5 * side;
+                if (e > 0) e2 += e * e;
+            }
+            if (e2 > rc2) { k = t->next[k]; continue; }
+        }
+        int leaf = (t->next[k] == k + 1);
+        if (leaf) {
+            for (int64_t j = t->first[k]; j < t->first[k] + t->count[k]; j++) {
+                if (j == i) continue;
+                double d[3];
+                for (int ax = 0; ax < 3; ax++) d[ax] = or_sep(pos[ax * np + j], xi[ax], P);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (treepm && P->pp_cut && r2 >= rc2) continue;
+                double eps_j = P->eps[cls ? cls[j] : 0];
+                double h = 2.8 * (eps_i > eps_j ? eps_i : eps_j);
+                double g0, g1;
+                or_pair_kernel(sqrt(r2), h, P->r_s, &g0, &g1);
+                *pot += -P->G * mass[j] * g0;
+                for (int ax = 0; ax < 3; ax++) acc[ax] += -P->G * mass[j] * g1 * d[ax];
+                cnt[0]++;
+            }
+            k = t->next[k];
+            continue;
+        }
+        double rv[3];
+        for (int ax = 0; ax < 3; ax++) rv[ax] = dc[ax] + t->com[3 * k + ax];
+        double r2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+        double dmax = fmax(fabs(dc[0]), fmax(fabs(dc[1]), fabs(dc[2])));
+        int open = 0;
+        if (dmax <= 0.5 * side) open = 1;                     /* particle inside the node */
+        if (P->exclusion && dmax < side) open = 1;             /* exclusion zone */
+        double epsn = t->eps_max[k];
+        double h = 2.8 * (eps_i > epsn ? eps_i : epsn);
+        if (r2 < h * h) open = 1;                              /* softened: open */
+        if (!open) {
+            if (P->criterion == 1) {
+                if (side * side >= P->theta * P->theta * r2) open = 1;
+            } else {
+                double r = sqrt(r2);
+                double lhs = P->G * t->mass[k] * or_ipow(side, p);
+                double rhs = P->alpha * a_i * or_ipow(r, p + 2);
+                if (!(lhs < rhs)) open = 1;
+            }
+        }
+        if (open) { k = k + 1; continue; }
+        or_pn(t->mono + nm * k, rv, p, P->r_s, P->G, acc, pot);
+        cnt[1]++;
+        k = t->next[k];
+    }
+}
+
+void or_tree_walk(const or_tree *t, const uint32_t *pos, int64_t np, const double *mass,
+                  const uint8_t *cls, const double *aold, const int64_t *sinks, int64_t ns,
+                  const or_params *P, double *acc, double *pot, int64_t *cnt)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t s = 0; s < ns; s++)
+        or_walk_one(t, pos, np, mass, cls, aold, sinks[s], P, acc + 3 * s, pot + s, cnt + 2 * s);
+}
+
+/* ===================================================================================== */
+/* Direct summation (validation reference, Sec. 3): every pair, nearest periodic image.   */
+/* r_max > 0 restricts the sum to pairs with r < r_max (cell list when periodic).          */
+/* ===================================================================================== */
+
+static void or_pair_acc(const uint32_t *pos, int64_t np, const double *mass, const uint8_t *cls,
+                        int64_t i, int64_t j, const or_params *P, double *acc, double *pot,
+                        double r2max)
+{
+    double d[3];
+    for (int ax = 0; ax < 3; ax++) d[ax] = or_sep(pos[ax * np + j], pos[ax * np + i], P);
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (r2max > 0 && r2 >= r2max) return;
+    double ei = P->eps[cls ? cls[i] : 0], ej = P->eps[cls ? cls[j] : 0];
+    double h = 2.8 * (ei > ej ? ei : ej), g0, g1;
+    or_pair_kernel(sqrt(r2), h, P->r_s, &g0, &g1);
+    *pot += -P->G * mass[j] * g0;
+    for (int ax = 0; ax < 3; ax++) acc[ax] += -P->G * mass[j] * g1 * d[ax];
+}
+
+void or_direct(const uint32_t *pos, int64_t np, const double *mass, const uint8_t *cls,
+               const int64_t *sinks, int64_t ns, const or_params *P, double r_max,
+               double *acc, double *pot)
+{
+    double r2max = r_max > 0 ? r_max * r_max : 0.0;
+    int use_cells = P->periodic && r_max > 0 && r_max * 3.0 <= P->box;
+    if (!use_cells) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t s = 0; s < ns; s++) {
+            int64_t i = sinks[s];
+            double a[3] = {0, 0, 0}, ph = 0.0;
+            for (int64_t j = 0; j < np; j++)
+                if (j != i) or_pair_acc(pos, np, mass, cls, i, j, P, a, &ph, r2max);
+            for (int ax = 0; ax < 3; ax++) acc[3 * s + ax] = a[ax];
+            pot[s] = ph;
+        }
+        return;
+    }
+    /* cell list: cells of side >= r_max, sources bucketed by cell (a filter only) */
+    int nc = (int)floor(P->box / r_max);
+    if (nc > 512) nc = 512;
+    int64_t ncell = (int64_t)nc * nc * nc;
+    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * (ncell + 1));
+    int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (np > 0 ? np : 1));
+    int64_t *cell_of = (int64_t *)malloc(sizeof(int64_t) * (np > 0 ? np : 1));
+    for (int64_t c = 0; c <= ncell; c++) head[c] = 0;
+    for (int64_t j = 0; j < np; j++) {
+        int64_t c[3];
+        for (int ax = 0; ax < 3; ax++) {
+            c[ax] = (int64_t)((double)pos[ax * np + j] / 4294967296.0 * nc);
+            if (c[ax] >= nc) c[ax] = nc - 1;
+        }
+        cell_of[j] = (c[0] * nc + c[1]) * nc + c[2];
+        head[cell_of[j] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; c++) head[c + 1] += head[c];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (ncell > 0 ? ncell : 1));
+    for (int64_t c = 0; c < ncell; c++) fill[c] = head[c];
+    for (int64_t j = 0; j < np; j++) list[fill[cell_of[j]]++] = j;
+    free(fill);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t s = 0; s < ns; s++) {
+        int64_t i = sinks[s];
+        double a[3] = {0, 0, 0}, ph = 0.0;
+        int64_t ci[3];
+        for (int ax = 0; ax < 3; ax++) {
+            ci[ax] = (int64_t)((double)pos[ax * np + i] / 4294967296.0 * nc);
+            if (ci[ax] >= nc) ci[ax] = nc - 1;
+        }
+        for (int dx = -1; dx <= 1; dx++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dz = -1; dz <= 1; dz++) {
+                    int64_t cx = (ci[0] + dx + nc) % nc, cy = (ci[1] + dy + nc) % nc,
+                            cz = (ci[2] + dz + nc) % nc;
+                    int64_t c = (cx * nc + cy) * nc + cz;
+                    for (int64_t q = head[c]; q < head[c + 1]; q++) {
+                        int64_t j = list[q];
+                        if (j != i) or_pair_acc(pos, np, mass, cls, i, j, P, a, &ph, r2max);
+                    }
+                }
+        for (int ax = 0; ax < 3; ax++) acc[3 * s + ax] = a[ax];
+        pot[s] = ph;
+    }
+    free(head); free(list); free(cell_of);
+}
+
+/* ===================================================================================== */
+/* a8: Cartesian FMM (Sec. 2.4, Appendix A)                                                */
+/* ===================================================================================== */
+
+/* Field tensors T_k (k = 0..p, full 3^k components) per node: the potential near the node's
+ * centre of mass is Phi(s + a) = sum_k (1/k!) T_k . a^(k). */
+typedef struct {
+    const or_tree *t;
+    const uint32_t *pos;
+    int64_t np;
+    const double *mass;
+    const uint8_t *cls;
+    const or_params *P;
+    double *T;      /* nn x ntens */
+    int ntens;
+    int toff[OR_MAXP + 2];
+    double *acc, *pot;
+    int64_t n_m2l, n_p2p;
+} or_fmm_ctx;
+
+static int or_is_leaf(const or_tree *t, int64_t k) { return t->next[k] == k + 1; }
+
+static void or_node_dc(const or_fmm_ctx *C, int64_t A, int64_t B, double *dc)
+{
+    /* geometric-centre separation c_B - c_A (nearest image when periodic) */
+    for (int ax = 0; ax < 3; ax++)
+        dc[ax] = or_sep(C->t->center[3 * B + ax], C->t->center[3 * A + ax], C->P);
+}
+
+/* symmetric particle-particle interactions between leaves A and B (A == B: pairs i < j) */
+static void or_p2p(or_fmm_ctx *C, int64_t A, int64_t B)
+{
+    const or_tree *t = C->t;
+    const or_params *P = C->P;
+    double rc2 = P->r_cut * P->r_cut;
+    int treepm = P->r_s > 0.0;
+    for (int64_t i = t->first[A]; i < t->first[A] + t->count[A]; i++) {
+        int64_t j0 = (A == B) ? i + 1 : t->first[B];
+        for (int64_t j = j0; j < t->first[B] + t->count[B]; j++) {
+            double d[3];
+            for (int ax = 0; ax < 3; ax++)
+                d[ax] = or_sep(C->pos[ax * C->np + j], C->pos[ax * C->np + i], P);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (treepm && P->pp_cut && r2 >= rc2) continue;
+            double ei = P->eps[C->cls ? C->cls[i] : 0], ej = P->eps[C->cls ? C->cls[j] : 0];
+            double h = 2.8 * (ei > ej ? ei : ej), g0, g1;
+            or_pair_kernel(sqrt(r2), h, P->r_s, &g0, &g1);
+            C->pot[i] += -P->G * C->mass[j] * g0;
+            C->pot[j] += -P->G * C->mass[i] * g0;
+            for (int ax = 0; ax < 3; ax++) {
+                C->acc[3 * i + ax] += -P->G * C->mass[j] * g1 * d[ax];
+                C->acc[3 * j + ax] += P->G * C->mass[i] * g1 * d[ax];
+            }
+            C->n_p2p++;
+        }
+    }
+}
+
+/* Node-node expansion, both directions, with r = s_B - s_A (Sec. 2.4):
+ *   T^A_k += -G (-1)^k sum_{n=0}^{p-k} (1/n!) D_{n+k}(r) . Q^B_n
+ *   T^B_k += -G        sum_{n=0}^{p-k} ((-1)^n/n!) D_{n+k}(r) . Q^A_n
+ * Q_p is dropped unless keep_qp is set (it only shifts the potential by a constant).     */
+static void or_m2l(or_fmm_ctx *C, int64_t A, int64_t B, const double *rv)
+{
+    const or_tree *t = C->t;
+    const or_params *P = C->P;
+    int p = P->order;
+    int64_t nm = or_nmono(t->order);
+    double r = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+    double g[OR_MAXP + 2];
+    or_gn(r, P->r_s, p, g);
+    static __thread double D[OR_MAXP + 1][729];
+    for (int m = 0; m <= p; m++) or_D_full(m, rv, g, D[m]);
+    double *TA = C->T + (int64_t)C->ntens * A, *TB = C->T + (int64_t)C->ntens * B;
+    const double *QA = t->mono + nm * A, *QB = t->mono + nm * B;
+    for (int k = 0; k <= p; k++) {
+        int k3 = or_pow3(k);
+        double sk = (k & 1) ? -1.0 : 1.0;
+        for (int I = 0; I < k3; I++) {
+            double fa = 0.0, fb = 0.0;
+            for (int n = 0; n <= p - k; n++) {
+                if (n == p && !P->keep_qp) continue;
+                double inv = 1.0 / or_factorial(n), sn = (n & 1) ? -1.0 : 1.0;
+                int n3 = or_pow3(n);
+                for (int J = 0; J < n3; J++) {
+                    double d = D[n + k][I + k3 * J];
+                    fa += inv * d * or_Q_full(QB, n, J);
+                    fb += inv * sn * d * or_Q_full(QA, n, J);
+                }
+            }
+            TA[C->toff[k] + I] += -P->G * sk * fa;
+            TB[C->toff[k] + I] += -P->G * fb;
+        }
+    }
+    C->n_m2l++;
+}
+
+/* Dual tree walk (Sec. 2.4): a pair of nodes either interacts through a symmetric multipole
+ * expansion, or both nodes are opened ("open both", so interacting nodes have equal sizes);
+ * if one of them is a leaf only the other is opened; two leaves interact particle by
+ * particle.  A node interacting with itself is replaced by all pairs of its daughters.
+ * Readings: leaves are the finest cells (they are not opened into single particles);
+ * pairs whose nearest faces are further apart than r_cut are dropped (Sec. 2.5); touching
+ * nodes never interact when the exclusion zone is on; a pair with r < 2.8 max(eps_max) is
+ * opened (multipoles unsoftened); the relative criterion is
+ *   G M_max / r^2 (l_max / r)^(p-1) < alpha min(|a|_min,A, |a|_min,B)
+ * and the geometric one (l_A + l_B) / r < theta_c (Eq. eqnNodeDec).                       */
+static void or_interact(or_fmm_ctx *C, int64_t A, int64_t B)
+{
+    const or_tree *t = C->t;
+    const or_params *P = C->P;
+    if (A == B) {
+        if (or_is_leaf(t, A)) { or_p2p(C, A, A); return; }
+        for (int64_t c1 = A + 1; c1 < t->next[A]; c1 = t->next[c1])
+            for (int64_t c2 = c1; c2 < t->next[A]; c2 = t->next[c2]) or_interact(C, c1, c2);
+        return;
+    }
+    double lA = ldexp(P->box, -t->level[A]), lB = ldexp(P->box, -t->level[B]);
+    double dc[3];
+    or_node_dc(C, A, B, dc);
+    if (P->r_s > 0.0) {
+        double e2 = 0.0;
+        for (int ax = 0; ax < 3; ax++) {
+            double e = fabs(dc[ax]) - 0.5 * (lA + lB);
+            if (e > 0) e2 += e * e;
+        }
+        if (e2 > P->r_cut * P->r_cut) return;
+    }
+    double rv[3];
+    for (int ax = 0; ax < 3; ax++) rv[ax] = dc[ax] + t->com[3 * B + ax] - t->com[3 * A + ax];
+    double r2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+    int accept = 1;
+    double dmax = fmax(fabs(dc[0]), fmax(fabs(dc[1]), fabs(dc[2])));
+    if (P->exclusion && dmax <= 0.5 * (lA + lB)) accept = 0;   /* touching */
+    if (dmax < 0.5 * (lA + lB)) accept = 0;                     /* overlapping cubes */
+    double em = fmax(t->eps_max[A], t->eps_max[B]);
+    if (r2 < (2.8 * em) * (2.8 * em)) accept = 0;
+    if (accept) {
+        if (P->criterion == 1) {
+            if ((lA + lB) * (lA + lB) >= P->theta * P->theta * r2) accept = 0;
+        } else {
+            double r = sqrt(r2);
+            double Mmax = fmax(t->mass[A], t->mass[B]), lmax = fmax(lA, lB);
+            double amin = fmin(t->amin[A], t->amin[B]);
+            double lhs = P->G * Mmax * or_ipow(lmax, P->order - 1);
+            double rhs = P->alpha * amin * or_ipow(r, P->order + 1);
+            if (!(lhs < rhs)) accept = 0;
+        }
+    }
+    if (accept) { or_m2l(C, A, B, rv); return; }
+    int la = or_is_leaf(t, A), lb = or_is_leaf(t, B);
+    if (la && lb) { or_p2p(C, A, B); return; }
+    if (la) {
+        for (int64_t c = B + 1; c < t->next[B]; c = t->next[c]) or_interact(C, A, c);
+    } else if (lb) {
+        for (int64_t c = A + 1; c < t->next[A]; c = t->next[c]) or_interact(C, c, B);
+    } else {
+        for (int64_t ca = A + 1; ca < t->next[A]; ca = t->next[ca])
+            for (int64_t cb = B + 1; cb < t->next[B]; cb = t->next[cb]) or_interact(C, ca, cb);
+    }
+}
+
+/* contraction of a full order-(k+j) tensor with v^(j) over its last j slots */
+static double or_contract_tail(const double *Tkj, int k, int j, int I, const double *v)
+{
+    int k3 = or_pow3(k), j3 = or_pow3(j);
+    double s = 0.0;
+    for (int J = 0; J < j3; J++) {
+        double vp = 1.0;
+        int w = J;
+        for (int u = 0; u < j; u++) { vp *= v[w % 3]; w /= 3; }
+        s += Tkj[I + k3 * J] * vp;
+    }
+    return s;
+}
+
+/* Downward pass (Sec. 2.4, phase 3): the parent field is shifted to each daughter's centre
+ * of mass, T^C_k += sum_j (1/j!) T^P_{k+j} . d^(j) with d = s_C - s_P, and at the leaves
+ * evaluated at the particles: Phi = sum_k (1/k!) T_k . a^(k),
+ * acc = -sum_{k>=1} (1/(k-1)!) T_k . a^(k-1) with a = x - s.                             */
+static void or_down(or_fmm_ctx *C, int64_t k)
+{
+    const or_tree *t = C->t;
+    const or_params *P = C->P;
+    int p = P->order;
+    double scale = P->box / 4294967296.0;
+    double *Tp = C->T + (int64_t)C->ntens * k;
+    if (or_is_leaf(t, k)) {
+        for (int64_t i = t->first[k]; i < t->first[k] + t->count[k]; i++) {
+            double a[3];
+            for (int ax = 0; ax < 3; ax++)
+                a[ax] = or_isep(C->pos[ax * C->np + i], t->center[3 * k + ax], 0) * scale
+                        - t->com[3 * k + ax];
+            double phi = 0.0;
+            for (int q = 0; q <= p; q++) {
+                int q3 = or_pow3(q);
+                double inv = 1.0 / or_factorial(q);
+                for (int I = 0; I < q3; I++) {
+                    double ap = 1.0;
+                    int w = I;
+                    for (int u = 0; u < q; u++) { ap *= a[w % 3]; w /= 3; }
+                    phi += inv * Tp[C->toff[q] + I] * ap;
+                }
+            }
+            C->pot[i] += phi;
+            for (int ax = 0; ax < 3; ax++) {
+                double s = 0.0;
+                for (int q = 1; q <= p; q++)
+                    s += or_contract_tail(Tp + C->toff[q], 1, q - 1, ax, a) / or_factorial(q - 1);
+                C->acc[3 * i + ax] += -s;
+            }
+        }
+        return;
+    }
+    for (int64_t c = k + 1; c < t->next[k]; c = t->next[c]) {
+        double d[3];
+        for (int ax = 0; ax < 3; ax++)
+            d[ax] = or_isep(t->center[3 * c + ax], t->center[3 * k + ax], 0) * scale
+                    + t->com[3 * c + ax] - t->com[3 * k + ax];
+        double *Tc = C->T + (int64_t)C->ntens * c;
+        for (int q = 0; q <= p; q++) {
+            int q3 = or_pow3(q);
+            for (int I = 0; I < q3; I++) {
+                double s = 0.0;
+                for (int j = 0; j <= p - q; j++)
+                    s += or_contract_tail(Tp + C->toff[q + j], q, j, I, d) / or_factorial(j);
+                Tc[C->toff[q] + I] += s;
+            }
+        }
+        or_down(C, c);
+    }
+}
+
+/* Full FMM force computation for all particles (sorted order).  acc: n x 3, pot: n.
+ * counts[0] = number of node-node expansions (each pair once), counts[1] = particle pairs. */
+void or_fmm(const or_tree *t, const uint32_t *pos, int64_t np, const double *mass,
+            const uint8_t *cls, const or_params *P, double *acc, double *pot, int64_t *counts)
+{
+    or_fmm_ctx C;
+    memset(&C, 0, sizeof(C));
+    C.t = t; C.pos = pos; C.np = np; C.mass = mass; C.cls = cls; C.P = P;
+    C.acc = acc; C.pot = pot;
+    int off = 0;
+    for (int k = 0; k <= P->order; k++) { C.toff[k] = off; off += or_pow3(k); }
+    C.ntens = off;
+    C.T = (double *)calloc((size_t)C.ntens * (size_t)(t->nn ? t->nn : 1), sizeof(double));
+    for (int64_t i = 0; i < 3 * np; i++) acc[i] = 0.0;
+    for (int64_t i = 0; i < np; i++) pot[i] = 0.0;
+    if (t->nn > 0) {
+        or_interact(&C, 0, 0);
+        or_down(&C, 0);
+    }
+    counts[0] = C.n_m2l;
+    counts[1] = C.n_p2p;
+    free(C.T);
+}

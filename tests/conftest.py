@@ -1,0 +1,14 @@
+"""Shared pytest configuration: the ``gpu`` marker and a few cached workloads."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the sm_103a library)")
+    config.addinivalue_line("markers", "slow: long-running CPU test")
