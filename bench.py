@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark: short-range tree-gravity forces/s at N = 256^3 on one GB300.
+
+Workload (the headline configuration): periodic box L = 500 with 256^3 equal-mass particles,
+lattice plus Zel'dovich displacements from a seeded Gaussian field with P(k) ~ k^-2 and rms
+displacement 2 grid spacings (strongly clustered), 32-bit integer coordinates, TreePM split
+r_s = 1.25 L / 512, cutoff 4.5 r_s, softening eps = L / 256 / 30, one-sided tree of order
+p = 3 with the relative opening criterion alpha = 0.0025, leaf threshold 8.
+
+One step = one complete force computation through the C ABI: Peano-Hilbert keys + radix sort,
+PH-order gather, oct-tree build, upward moments, tree walk (with |a_old| of the previous step),
+scatter back to input order.  |a_old| comes from one geometric-criterion walk before timing
+(the paper's first-step bootstrap).  Inputs (about 335 MB) are larger than the 129 MB L2.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tree-gravity forces/sec at N=256^3 (FP32 vs FP64-judged, 99% err<=1e-3)"
+UNIT = "forces/s"
+N_SIDE = 256
+L_BOX = 500.0
+RMS = 2.0
+SEED = 1003
+# algorithmic work per interaction (operations of the kernel formulas; erfc, exp and rsqrt
+# count as one operation each)
+FLOPS_PP = 35
+FLOPS_PN = {1: 40, 2: 110, 3: 170, 4: 300, 5: 480}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA x max clock
+
+
+def workload_params(n_side=N_SIDE, L=L_BOX):
+    d = L / n_side
+    return dict(box_size=L, periodic=1, r_s=1.25 * L / (2 * n_side), r_cut_factor=4.5,
+                eps=[d / 30.0], alpha=0.0025, order_p=3, leaf_max=8)
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------------------------
+def oracle_sample_run(n_side=64):
+    """The FP64 oracle's full pipeline on a 64^3 box with the same spacing, split, softening
+    and clustering recipe as the headline workload (a bounded sample of it)."""
+    import oracle
+    from paper_2010_03567_gb300 import synth
+    L = L_BOX * n_side / N_SIDE
+    ps = synth.zeldovich(n_side, L, RMS, SEED)
+    wp = workload_params(n_side, L)
+    OP = oracle.OracleParams(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
+                             r_cut_factor=4.5, alpha=wp["alpha"], order=3)
+    q = oracle.int_coords_periodic(ps.pos, L)
+    OB = oracle.OracleParams(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
+                             r_cut_factor=4.5, criterion=1, theta=0.5, order=3)
+    run = oracle.prepare(q, ps.mass, None, None, OB, 8)
+    ab, _, _ = oracle.tree_forces(run, np.arange(ps.n))
+    aold = np.linalg.norm(ab, axis=1)
+
+    def step():
+        t0 = time.perf_counter()
+        r = oracle.prepare(q, ps.mass, None, aold, OP, 8)
+        oracle.tree_forces(r, np.arange(ps.n))
+        return time.perf_counter() - t0
+
+    return ps.n, step
+
+
+def cpu_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n, step = oracle_sample_run()
+    for _ in range(max(0, min(args.warmup, 1))):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    t = sum(ts)
+    val = n * args.steps / t
+    sample = f"FP64 oracle, full pipeline on a 64^3 (L=125) box of the same recipe, {n} forces per step"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(world),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_block(world):
+    return {"workload": "periodic Zel'dovich box, 256^3 particles, L=500, rms displacement 2 "
+                        "spacings, TreePM short range r_s=1.25L/512, R_cut=4.5, eps=L/7680, "
+                        "tree p=3, alpha=0.0025, leaf 8",
+            "n_particles": N_SIDE ** 3, "order_p": 3, "alpha": 0.0025, "leaf_max": 8,
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "l2": "inputs (335 MB) larger than L2 (129 MB); no flush"}
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2010_03567_gb300 import g4, synth
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ps = synth.zeldovich(N_SIDE, L_BOX, RMS, SEED + rank)
+    n = ps.n
+    wp = workload_params()
+    P = g4.params(**wp)
+    PB = g4.params(**{**wp, "criterion": 1, "theta": 0.5})
+    pos = torch.from_numpy(ps.pos).cuda()
+    pos_int, _ = g4.g4_int_coords(pos, True, L_BOX)
+    del pos
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    tg = g4.TreeGravity(n, P)
+    # bootstrap |a_old| (geometric criterion), then the relative-criterion steps
+    acc0, _ = tg.forces(pos_int, mass, None, None, PB)
+    aold = torch.linalg.vector_norm(acc0, dim=0).contiguous()
+    torch.cuda.synchronize()
+    nn, ml = tg.tree.status()
+
+    stream = torch.cuda.current_stream()
+    ev_walk = []
+
+    def step(record=False):
+        tg.prepare(pos_int, mass, None, aold, P)
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        tg.walk(P)
+        if record:
+            e1.record(stream)
+            ev_walk.append((e0, e1))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    tg.tree.status()
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    l0 = g4.launch_count()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = g4.launch_count() - l0
+    ms = t0.elapsed_time(t1) / args.steps
+    walk_ms = sum(a.elapsed_time(b) for a, b in ev_walk) / len(ev_walk)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        ms = float(tt.item())
+    clk = clocks.stop()
+    counts = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+    flops = counts[0] * FLOPS_PP + counts[1] * FLOPS_PN[3]
+    achieved = flops / (walk_ms * 1e-3) / 1e12
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
+    h_pos = pos_int.cpu().pin_memory()
+    h_mass = mass.cpu().pin_memory()
+    h_aold = aold.cpu().pin_memory()
+    h_acc = torch.empty((3, n), dtype=torch.float32).pin_memory()
+    h_pot = torch.empty(n, dtype=torch.float32).pin_memory()
+    d_pos, d_mass, d_aold = torch.empty_like(pos_int), torch.empty_like(mass), torch.empty_like(aold)
+
+    def e2e_step():
+        d_pos.copy_(h_pos, non_blocking=True)
+        d_mass.copy_(h_mass, non_blocking=True)
+        d_aold.copy_(h_aold, non_blocking=True)
+        acc, pot = tg.forces(d_pos, d_mass, None, d_aold, P)
+        h_acc.copy_(acc, non_blocking=True)
+        h_pot.copy_(pot, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    # ---- accuracy on a sample against the FP64 direct sum (pairs with r < r_cut)
+    accuracy = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        sinks = synth.subset(n, 4096, 2002)
+        q = pos_int.cpu().numpy().view(np.uint32)
+        OP = oracle.OracleParams(box=L_BOX, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
+                                 r_cut_factor=4.5)
+        ad, _ = oracle.direct(q, ps.mass, None, sinks, OP, r_max=OP.r_cut)
+        ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
+        e = np.linalg.norm(ag - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        accuracy = {"reference": "FP64 direct sum over pairs with r < r_cut (oracle)",
+                    "sample": int(len(sinks)), "p50": float(np.percentile(e, 50)),
+                    "p99": float(np.percentile(e, 99)), "max": float(np.max(e))}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        nb, cstep = oracle_sample_run()
+        tcpu = cstep()
+        cpu = {"value": nb / tcpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": "FP64 oracle, full pipeline on a 64^3 (L=125) box of the same recipe "
+                         f"({nb} forces, {tcpu:.1f} s)"}
+
+    if rank == 0:
+        value = world * n / (ms * 1e-3)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": config_block(world), "clocks": clk,
+                "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT,
+                        "h2d_bytes_per_step": int(n * (12 + 4 + 4)),
+                        "d2h_bytes_per_step": int(n * (12 + 4))},
+                "gpu_launches": int(launches),
+                "roofline": {"bound": "alu", "kernel": "k_walk (tree walk, p=3, TreePM)",
+                             "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
+                             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                             "walk_ms": walk_ms,
+                             "interactions_per_step": {"pp": int(counts[0]), "pn": int(counts[1])}},
+                "tree": {"nodes": nn, "max_level": ml},
+                "interactions_per_s": float((counts[0] + counts[1]) / (walk_ms * 1e-3)),
+                "accuracy": accuracy, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist:
+        tdist.barrier()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "gb300":
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,226 @@
+/*
+ * g4.h -- C ABI of the GB300 short-range tree / FMM gravity library (libg4.so).
+ *
+ * The library computes the short-range gravitational accelerations and potentials of the
+ * GADGET-4 method (Springel, Pakmor, Zier & Reinecke 2021) on one GPU:
+ *   integer coordinates (Sec. 2.10, 2.11) -> Peano-Hilbert keys and radix sort (Sec. 2.2.1)
+ *   -> oct-tree with leaf threshold (Sec. 2.2.1) -> node moments (Sec. 2.2.2)
+ *   -> one-sided tree walk with the relative opening criterion (Eq. eqnrelcriterion) and the
+ *      TreePM short-range kernel (Eq. eqnpo4), or the symmetric Cartesian FMM (Sec. 2.4).
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers owned by the caller, unless stated otherwise.
+ *     Only a g4_tree handle is library-owned (create with g4_tree_create, release with
+ *     g4_tree_free).
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *     default stream).  The returned status reports argument and launch errors synchronously.
+ *     Errors detected by kernels (capacity overflow, bounded waits running out) are recorded
+ *     in the tree handle and reported by g4_tree_status(), which synchronises the stream.
+ *   - Integer positions are uint32 per axis in SoA layout [x[0..n), y[0..n), z[0..n)]; the
+ *     physical unit of one integer step is box_size / 2^32 (Sec. 2.10).
+ *   - Potential sign convention: pot = phi = -G sum m g(r); acc = -grad phi (Sec. 2.2.2).
+ *     The constant pi/(alpha^2 V) of Eq. (eqnpo4) is omitted and the self-potential of a
+ *     particle is not included.
+ *   - On failure a thread-local message is available from g4_last_error().
+ *   - The library never falls back to a CPU path: without a usable CUDA device every call
+ *     that launches work returns G4_ERR_CUDA.
+ */
+#ifndef G4_H
+#define G4_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    G4_OK = 0,
+    G4_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter */
+    G4_ERR_OOM = 2,         /* device allocation failed */
+    G4_ERR_CUDA = 3,        /* CUDA launch or runtime error */
+    G4_ERR_TIMEOUT = 4,     /* a bounded device wait ran out */
+    G4_ERR_DEPTH = 5,       /* key resolution exceeded */
+    G4_ERR_STATE = 6,       /* handle used in the wrong order (e.g. walk before moments) */
+    G4_ERR_CAPACITY = 7     /* a library-owned buffer was too small; retry with more */
+} g4_status;
+
+#define G4_MAX_EPS_CLASSES 8
+#define G4_MAX_ORDER 5
+
+/* Parameters of one force computation (plain values, copied by every call). */
+typedef struct g4_params {
+    double box_size;       /* L; physical size of the 2^32 integer range (Sec. 2.10) */
+    int periodic;          /* 1: nearest periodic image via two's complement (Sec. 2.10) */
+    double r_s;            /* TreePM split scale (Sec. 2.3); <= 0: plain Newtonian kernel */
+    double r_cut_factor;   /* R_cut; r_cut = max(R_cut * r_s, 2.8 eps_max) (Sec. 2.3) */
+    int pp_cut;            /* 1: particle pairs with r >= r_cut are dropped (TreePM only) */
+    double alpha;          /* relative opening parameter of Eq. (eqnrelcriterion) */
+    double theta;          /* geometric opening angle theta_c (criterion 1, bootstrap) */
+    int criterion;         /* 0: relative criterion (needs a_old), 1: geometric l/r < theta */
+    int order_p;           /* expansion order p, 1..5 (Sec. 2.2.2) */
+    int leaf_max;          /* split threshold: a node with more particles is split (1..64) */
+    int exclusion_zone;    /* 1: no multipole use within the cube of half-width l around the
+                              node's geometric centre (Sec. 2.2.3) */
+    int precision;         /* 0: FP32 interactions, FP64 moments for big nodes; 1: all FP64 */
+    double G;              /* gravitational constant */
+    int n_eps_classes;     /* number of softening classes (1..G4_MAX_EPS_CLASSES) */
+    double eps_table[G4_MAX_EPS_CLASSES]; /* softening length eps_0 per class (Sec. 2.9) */
+    int group_size;        /* sinks per warp group of the walk (8, 16 or 32; 0 = 32) */
+    int fp64_count;        /* nodes holding >= fp64_count particles accumulate moments in
+                              FP64 (0 = 4096) */
+    int keep_qp;           /* FMM: 1 keeps Q_p in the potential (Sec. 2.4 drops it) */
+} g4_params;
+
+typedef struct g4_tree_s *g4_tree;
+
+/* Library version string (static storage). */
+const char *g4_version(void);
+
+/* Thread-local description of the last error returned on this thread (static storage). */
+const char *g4_last_error(void);
+
+/* Number of kernel launches the library has issued since it was loaded (all threads).
+ * Diagnostic only; host-side, never fails. */
+int64_t g4_launch_count(void);
+
+/* Fills *p with the defaults: periodic=0, r_s=0, R_cut=4.5, pp_cut=1, alpha=0.0025,
+ * theta=0.5, criterion=0, p=3, leaf_max=8, exclusion=1, precision=0, G=1, one class with
+ * eps=0.01, group_size=32, fp64_count=4096, keep_qp=0.  Host-only, never fails for p!=NULL. */
+g4_status g4_params_default(g4_params *p);
+
+/* ---- a1: integer coordinates (Sec. 2.10, Sec. 2.11) ----------------------------------- */
+
+/* Converts n physical positions pos[n][3] (FP64, row-major, device) to uint32 SoA
+ * pos_int[3][n] (device).
+ *   periodic = 1: x_int = floor(x / L * 2^32) mod 2^32, L = box_size; frame = {0,0,0,L}.
+ *   periodic = 0: the bounding box is shrink-wrapped into the central half of the integer
+ *     cube: S = smallest power of two >= 2 * (largest extent), centred on the bounding-box
+ *     midpoint c: x_int = floor((x - c) * 2^32 / S) + 2^31; frame = {c - S/2 (3), S}
+ *     (box_size is ignored).
+ * frame: 4 doubles of device memory receiving {origin_x, origin_y, origin_z, side}; the
+ * isolated case needs `side` as params.box_size of the later calls.
+ * Errors: G4_ERR_INVALID_ARG for NULL pointers, n < 0 or box_size <= 0 when periodic. */
+g4_status g4_int_coords(const double *pos, int64_t n, int periodic, double box_size,
+                        uint32_t *pos_int, double *frame, void *stream);
+
+/* ---- a2 + a3: Peano-Hilbert keys and stable radix sort (Sec. 2.2.1) -------------------- */
+
+/* Bytes of device workspace g4_keys_sort needs for n particles. */
+g4_status g4_keys_sort_workspace(int64_t n, size_t *bytes);
+
+/* 63-bit Peano-Hilbert keys from the top 21 bits of each coordinate, then a stable sort:
+ *   keys_sorted[k] = key of particle perm[k], ascending; equal keys keep input order.
+ * pos_int: 3 x n SoA (device); keys_sorted: n uint64 (device); perm: n int32 (device,
+ * sorted -> original index).  workspace: >= g4_keys_sort_workspace(n) bytes of device
+ * memory, 256-byte aligned, not used concurrently by another call.
+ * Errors: G4_ERR_INVALID_ARG for NULL pointers, n < 0, n >= 2^31, small workspace. */
+g4_status g4_keys_sort(const uint32_t *pos_int, int64_t n, uint64_t *keys_sorted,
+                       int32_t *perm, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Gathers particle arrays into PH order: out[k] = in[perm[k]].  cls/aold may be NULL (both
+ * in and out).  pos arrays are 3 x n SoA. */
+g4_status g4_gather(const int32_t *perm, int64_t n, const uint32_t *pos_in,
+                    const float *mass_in, const uint8_t *cls_in, const float *aold_in,
+                    uint32_t *pos_out, float *mass_out, uint8_t *cls_out, float *aold_out,
+                    void *stream);
+
+/* Scatters PH-ordered results back to input order: out[perm[k]] = in[k].  acc arrays are
+ * 3 x n SoA; pot may be NULL (both). */
+g4_status g4_scatter(const int32_t *perm, int64_t n, const float *acc_sorted,
+                     const float *pot_sorted, float *acc_out, float *pot_out, void *stream);
+
+/* ---- a4: oct-tree (Sec. 2.2.1) ---------------------------------------------------------- */
+
+/* Allocates a tree handle for up to n_max particles and node_capacity nodes (0 = a default
+ * that suffices for ordinary particle sets).  All device memory is allocated here, none in
+ * later calls, so build/moments/walk sequences can be captured in a CUDA graph.
+ * Errors: G4_ERR_INVALID_ARG, G4_ERR_OOM. */
+g4_status g4_tree_create(int64_t n_max, int64_t node_capacity, g4_tree *out);
+
+/* Releases the handle and its device memory (synchronises the device first). */
+void g4_tree_free(g4_tree tree);
+
+/* Builds the oct-tree over PH-sorted keys: a node is split when it holds more than
+ * leaf_max particles and lies above the 21-level key resolution; children are in PH order;
+ * nodes are numbered in depth-first pre-order.  pos_sorted (3 x n SoA, PH order) gives the
+ * node cells.  Requires n <= n_max of the handle.  Capacity overflow is reported by
+ * g4_tree_status (G4_ERR_CAPACITY). */
+g4_status g4_tree_build(g4_tree tree, const uint64_t *keys_sorted, const uint32_t *pos_sorted,
+                        int64_t n, const g4_params *params, void *stream);
+
+/* Synchronises `stream`, then reports the node count, deepest level and the device error
+ * flags of the last build/walk.  Returns G4_ERR_CAPACITY / G4_ERR_TIMEOUT when a kernel
+ * recorded that condition (flags are cleared by the next g4_tree_build). */
+g4_status g4_tree_status(g4_tree tree, int64_t *n_nodes, int32_t *max_level, void *stream);
+
+/* Copies the node topology (depth-first order) into caller device buffers of at least
+ * n_nodes entries: level, first particle, particle count, next (index after the subtree),
+ * centre (n_nodes x 3 uint32, geometric centre in integer units).  Any pointer may be NULL. */
+g4_status g4_tree_nodes(g4_tree tree, int32_t *level, int32_t *first, int32_t *count,
+                        int32_t *next, uint32_t *center, void *stream);
+
+/* ---- a5: node moments (Sec. 2.2.2) ------------------------------------------------------ */
+
+/* Mass M, centre of mass s, multipole moments Q_2..Q_p about s (Q_1 = 0), per-node maximum
+ * softening and minimum |a_old| (FMM).  Inputs in PH order; cls and aold may be NULL (class
+ * 0 / |a| = 0).  Nodes with >= fp64_count particles accumulate in FP64. */
+g4_status g4_multipoles(g4_tree tree, const uint32_t *pos_sorted, const float *mass_sorted,
+                        const uint8_t *cls_sorted, const float *aold_sorted,
+                        const g4_params *params, void *stream);
+
+/* Copies node moments into caller device buffers (n_nodes entries each): mass, com
+ * (n_nodes x 3, s minus geometric centre, physical units), mono (n_nodes x nmono, monomial
+ * moments sum m dx^a dy^b dz^c of orders 0..p about s, multi-indices ordered by order, then
+ * a descending, then b descending).  Any pointer may be NULL. */
+g4_status g4_tree_moments(g4_tree tree, double *mass, double *com, double *mono, void *stream);
+
+/* ---- a6/a7: one-sided tree walk (Sec. 2.2.3, Sec. 2.3) ---------------------------------- */
+
+/* Accelerations and potentials of the sinks from all particles of the tree.
+ *   sinks: active == NULL -> all n particles; otherwise active[0..n_active) lists sorted-order
+ *          indices (ascending PH order recommended for coherent groups).
+ *   opening: relative criterion G M / r^2 (l/r)^p < alpha |a_old| (criterion 0; aold_sorted
+ *          required) or geometric l/r < theta (criterion 1); plus the exclusion zone, and
+ *          nodes closer than 2.8 max(eps_i, eps_max(node)) are always opened.
+ *   TreePM (r_s > 0): nodes whose nearest (periodic-image) edge is beyond r_cut are dropped;
+ *          pairs use g = g_soft - erf(r / 2 r_s) / r (Eq. eqnpo4).
+ * Outputs (sorted order, written only at sink indices): acc 3 x n SoA float, pot n float
+ * (nullable), counts 2 x n uint32 (PP interactions, PN interactions; nullable).
+ * Requires g4_tree_build and g4_multipoles on the same handle with the same order_p. */
+g4_status g4_gravity_tree(g4_tree tree, const uint32_t *pos_sorted, const float *mass_sorted,
+                          const uint8_t *cls_sorted, const float *aold_sorted,
+                          const int32_t *active, int64_t n_active, const g4_params *params,
+                          float *acc, float *pot, uint32_t *counts, void *stream);
+
+/* ---- a8: symmetric Cartesian FMM (Sec. 2.4, Sec. 2.5) ----------------------------------- */
+
+/* Bytes of device workspace g4_gravity_fmm needs for the tree's current size. */
+g4_status g4_fmm_workspace(g4_tree tree, const g4_params *params, size_t *bytes);
+
+/* Forces for all n particles by the dual tree walk: node pairs either interact by the
+ * symmetric expansion (field added to both nodes) or both are opened ("open both"; a leaf is
+ * never opened, two leaves interact particle by particle; a node paired with itself is
+ * replaced by all pairs of its daughters).  Criterion G M_max / r^2 (l_max/r)^(p-1) <
+ * alpha min |a|_min (or (l_A + l_B)/r < theta), touching nodes never interact, pairs whose
+ * nearest faces are beyond r_cut are dropped.  Fields are passed down (L2L) and evaluated
+ * at the particles (L2P).  Outputs as for g4_gravity_tree (counts: PP, node-node);
+ * momentum_out (3 doubles of device memory, nullable) receives sum m a in FP64. */
+g4_status g4_gravity_fmm(g4_tree tree, const uint32_t *pos_sorted, const float *mass_sorted,
+                         const uint8_t *cls_sorted, const g4_params *params, float *acc,
+                         float *pot, uint32_t *counts, double *momentum_out, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
+/* ---- helper: direct summation on the GPU --------------------------------------------------- */
+
+/* O(n * n_sinks) direct sum with the same pair kernel (nearest image when periodic, pair
+ * cutoff when TreePM and pp_cut).  sinks == NULL -> all particles.  acc 3 x n SoA, pot n. */
+g4_status g4_direct(const uint32_t *pos, const float *mass, const uint8_t *cls, int64_t n,
+                    const int32_t *sinks, int64_t n_sinks, const g4_params *params, float *acc,
+                    float *pot, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* G4_H */

@@ -1,0 +1,177 @@
+// g4_kernels.cuh -- interaction kernels shared by the walk, FMM and direct-sum kernels:
+//   * pair kernel of the short-range potential (Eq. eqnpo4) with cubic-spline softening
+//     (Eq. eqnsoft), g = g_soft - erf(r / 2 r_s) / r, returning g0 = g and g1 = g'/r;
+//   * g_n = (r^-1 d/dr)^n g for the unsoftened multipole kernel (1/r or erfc(r/2r_s)/r),
+//     from the upward recursion B_n = ((2n-1) B_{n-1} + (2a^2)^(n-1) t) / r^2, g_n = (-1)^n B_n
+//     (a = 1/(2 r_s), t = (2a/sqrt(pi)) exp(-a^2 r^2); t = 0 for the Newtonian kernel);
+//   * Cartesian derivative tensors D_{abc} = d^a_x d^b_y d^c_z g(|r|) for a symmetric
+//     multi-index, D_{abc} = sum_{i,j,k} K(a,i) K(b,j) K(c,k) g_{n-i-j-k} x^(a-2i) y^(b-2j)
+//     z^(c-2k) with K(a,i) = a! / (2^i i! (a-2i)!) -- the count of ways to pair 2i of the a
+//     equal index slots by Kronecker deltas (Eqs. eqngderiv0-eqngderiv).
+#pragma once
+#include "g4_internal.cuh"
+
+namespace g4k {
+
+__host__ __device__ constexpr int fact(int n) { return n <= 1 ? 1 : n * fact(n - 1); }
+__host__ __device__ constexpr int pairk(int a, int i)
+{
+    // a! / (2^i i! (a-2i)!)
+    return fact(a) / ((1 << i) * fact(i) * fact(a - 2 * i));
+}
+
+template <typename T> struct Math;
+template <> struct Math<float> {
+    static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float erfc(float x) { return erfcf(x); }
+    static __device__ __forceinline__ float erf(float x) { return erff(x); }
+    static __device__ __forceinline__ float exp(float x) { return expf(x); }
+};
+template <> struct Math<double> {
+    static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double erfc(double x) { return ::erfc(x); }
+    static __device__ __forceinline__ double erf(double x) { return ::erf(x); }
+    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+};
+
+// Pair kernel.  r2: squared separation, h: 2.8 eps_ij, as = 1/(2 r_s) (TREEPM only).
+// Returns g0 = g(r), g1 = g'(r)/r.  At r = 0 (coincident particles) g1 is irrelevant.
+template <typename T, bool TREEPM>
+__device__ __forceinline__ void pair_kernel(T r2, T h, T as, T &g0, T &g1)
+{
+    const T two_over_sqrtpi = T(1.1283791670955126);
+    if (r2 >= h * h) {
+        const T rinv = Math<T>::rsqrt(r2);
+        if (TREEPM) {
+            const T r = r2 * rinv, x = r * as;
+            const T e = Math<T>::erfc(x);
+            const T t = two_over_sqrtpi * as * Math<T>::exp(-x * x);
+            g0 = e * rinv;
+            g1 = -(g0 + t) * rinv * rinv;
+        } else {
+            g0 = rinv;
+            g1 = -rinv * rinv * rinv;
+        }
+        return;
+    }
+    const T r = Math<T>::sqrt(r2);
+    const T hinv = T(1) / h;
+    const T u = r * hinv, u2 = u * u;
+    T W, dWu;   // W_2(u) and W_2'(u)/u of the cubic-spline potential
+    if (u < T(0.5)) {
+        W = u2 * (T(16.0 / 3.0) + u2 * (T(-48.0 / 5.0) + u * T(32.0 / 5.0))) - T(14.0 / 5.0);
+        dWu = T(32.0 / 3.0) + u2 * (T(-192.0 / 5.0) + u * T(32.0));
+    } else {
+        const T uinv = T(1) / u;
+        W = T(1.0 / 15.0) * uinv +
+            u2 * (T(32.0 / 3.0) + u * (T(-16.0) + u * (T(48.0 / 5.0) + u * T(-32.0 / 15.0)))) -
+            T(16.0 / 5.0);
+        dWu = T(-1.0 / 15.0) * uinv * uinv * uinv + T(64.0 / 3.0) +
+              u * (T(-48.0) + u * (T(192.0 / 5.0) + u * T(-32.0 / 3.0)));
+    }
+    g0 = -W * hinv;
+    g1 = -dWu * hinv * hinv * hinv;
+    if (TREEPM) {
+        if (r2 > T(0)) {
+            const T rinv = T(1) / r, x = r * as;
+            const T ef = Math<T>::erf(x);
+            const T t = two_over_sqrtpi * as * Math<T>::exp(-x * x);
+            g0 -= ef * rinv;
+            g1 += (ef * rinv - t) * rinv * rinv;
+        } else {
+            g0 -= two_over_sqrtpi * as;
+        }
+    }
+}
+
+// g_0..g_N of the unsoftened multipole kernel at squared distance r2 (r2 > 0).
+template <int N, typename T, bool TREEPM>
+__device__ __forceinline__ void gn_kernel(T r2, T as, T *g)
+{
+    const T rinv = Math<T>::rsqrt(r2), rinv2 = rinv * rinv;
+    T B = rinv, t = T(0), tw = T(0);
+    if (TREEPM) {
+        const T r = r2 * rinv, x = r * as;
+        B = Math<T>::erfc(x) * rinv;
+        t = T(1.1283791670955126) * as * Math<T>::exp(-x * x);
+        tw = T(2) * as * as;
+    }
+    g[0] = B;
+#pragma unroll
+    for (int n = 1; n <= N; n++) {
+        B = (T(2 * n - 1) * B + t) * rinv2;
+        if (TREEPM) t *= tw;
+        g[n] = (n & 1) ? -B : B;
+    }
+}
+
+// All D_{abc} with a+b+c <= N into D[g4_midx(a,b,c)].
+template <int N, typename T>
+__device__ __forceinline__ void dtensors(T x, T y, T z, const T *g, T *D)
+{
+    T px[N + 1], py[N + 1], pz[N + 1];
+    px[0] = py[0] = pz[0] = T(1);
+#pragma unroll
+    for (int k = 1; k <= N; k++) {
+        px[k] = px[k - 1] * x;
+        py[k] = py[k - 1] * y;
+        pz[k] = pz[k - 1] * z;
+    }
+#pragma unroll
+    for (int n = 0; n <= N; n++)
+#pragma unroll
+        for (int bc = 0; bc <= n; bc++)
+#pragma unroll
+            for (int c = 0; c <= bc; c++) {
+                const int a = n - bc, b = bc - c;
+                T s = T(0);
+#pragma unroll
+                for (int i = 0; 2 * i <= a; i++)
+#pragma unroll
+                    for (int j = 0; 2 * j <= b; j++)
+#pragma unroll
+                        for (int k = 0; 2 * k <= c; k++)
+                            s += T(pairk(a, i) * pairk(b, j) * pairk(c, k)) * g[n - i - j - k] *
+                                 px[a - 2 * i] * py[b - 2 * j] * pz[c - 2 * k];
+                D[g4_midx(a, b, c)] = s;
+            }
+}
+
+// Particle-node term of the one-sided expansion with r = s - x (Eqs. eqonesidetreepotential,
+// eqonesidetreeacc): sacc += sum_{n<P} Q_n . D_{n+1} / n!,  spot += sum_{n<=P} Q_n . D_n / n!
+// (the caller multiplies both by -G).  Qs holds moments of orders 2..P at g4_midx - 4.
+template <int P, typename T, bool TREEPM>
+__device__ __forceinline__ void pn_term(const T *Qs, T M, T x, T y, T z, T as, T &sx, T &sy,
+                                        T &sz, T &sp)
+{
+    const T r2 = x * x + y * y + z * z;
+    T g[P + 1];
+    gn_kernel<P, T, TREEPM>(r2, as, g);
+    T D[g4_nmono(P)];
+    dtensors<P, T>(x, y, z, g, D);
+    T ax = M * D[g4_midx(1, 0, 0)], ay = M * D[g4_midx(0, 1, 0)], az = M * D[g4_midx(0, 0, 1)];
+    T ph = M * D[0];
+#pragma unroll
+    for (int n = 2; n <= P; n++)
+#pragma unroll
+        for (int bc = 0; bc <= n; bc++)
+#pragma unroll
+            for (int c = 0; c <= bc; c++) {
+                const int a = n - bc, b = bc - c;
+                const T w = Qs[g4_midx(a, b, c) - 4] * T(1.0 / double(fact(a) * fact(b) * fact(c)));
+                ph += w * D[g4_midx(a, b, c)];
+                if (n <= P - 1) {
+                    ax += w * D[g4_midx(a + 1, b, c)];
+                    ay += w * D[g4_midx(a, b + 1, c)];
+                    az += w * D[g4_midx(a, b, c + 1)];
+                }
+            }
+    sx += ax;
+    sy += ay;
+    sz += az;
+    sp += ph;
+}
+
+}  // namespace g4k

@@ -1,0 +1,433 @@
+// g4_walk.cu -- one-sided tree walk (Sec. 2.2.3) with the relative opening criterion
+// (Eq. eqnrelcriterion) and the TreePM short-range kernel (Sec. 2.3), plus a GPU direct sum.
+//
+// Work decomposition: a warp owns a group of 32 PH-consecutive sinks (one per lane) and walks
+// the depth-first node array once for the whole group.  Each lane keeps its own walk exact:
+// `resume` is the next node index the lane still has to look at; the warp visits node
+// min(resume) over its lanes, so every lane sees precisely the nodes a single-particle walk
+// would see, while node records are fetched once per warp (broadcast loads).  Per node and
+// lane the decision is one of: skip (TreePM cutoff), open (descend: resume = k + 1), use the
+// multipole (particle-node term), or -- for a leaf -- particle-particle terms with the
+// leaf's particles.  Groups are handed out by a device work counter, so warps that finish
+// early pull more groups (persistent kernel).
+#include "g4_internal.cuh"
+#include "g4_kernels.cuh"
+
+namespace {
+
+using namespace g4k;
+
+struct WalkArgs {
+    const uint32_t *pos;
+    const float *mass;
+    const uint8_t *cls;
+    const float *aold;
+    const int32_t *active;
+    int n, n_sinks;
+    const int32_t *lvl;        // lvl[G4_NLEVELS] = node count
+    const G4Node *node;
+    const float *q;
+    const double *qd;          // FP64 node data (precision 1)
+    int nq;
+    float *acc, *pot;
+    uint32_t *counts;
+    int *work;                 // group counter
+    const int32_t *flags;      // tree error flags
+    double scale;
+    double G, alpha, theta2, rcut2, as;
+    double box;
+    float h_cls[G4_MAX_EPS_CLASSES];
+    int exclusion, pp_cut;
+};
+
+enum : int { ACT_NONE = 0, ACT_SKIP = 1, ACT_OPEN = 2, ACT_ACCEPT = 3, ACT_LEAF = 4 };
+
+template <int P, typename T> __device__ __forceinline__ T ipow(T x)
+{
+    T r = T(1);
+#pragma unroll
+    for (int i = 0; i < P; i++) r *= x;
+    return r;
+}
+
+__device__ __forceinline__ G4Node load_node(const G4Node *p)
+{
+    const int4 *v = reinterpret_cast<const int4 *>(p);
+    int4 a = __ldg(v), b = __ldg(v + 1), c = __ldg(v + 2);
+    G4Node nd;
+    nd.cx = (uint32_t)a.x;
+    nd.cy = (uint32_t)a.y;
+    nd.cz = (uint32_t)a.z;
+    nd.meta = (uint32_t)a.w;
+    nd.sx = __int_as_float(b.x);
+    nd.sy = __int_as_float(b.y);
+    nd.sz = __int_as_float(b.z);
+    nd.mass = __int_as_float(b.w);
+    nd.first = c.x;
+    nd.count = c.y;
+    nd.next = c.z;
+    nd.parent = c.w;
+    int4 d = __ldg(v + 3);
+    nd.amin = __int_as_float(d.x);
+    nd.hmax = __int_as_float(d.y);
+    nd.bfs = d.z;
+    nd.pad = d.w;
+    return nd;
+}
+
+template <int P, typename T, bool TREEPM, bool GEOM>
+__global__ void __launch_bounds__(256) k_walk(const WalkArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    if (*A.flags & G4_FLAG_CAPACITY) return;   // incomplete tree: outputs left untouched
+    const int nn = A.lvl[G4_NLEVELS];
+    const T scale = (T)A.scale, G = (T)A.G, as = (T)A.as, rcut2 = (T)A.rcut2;
+    const T theta2 = (T)A.theta2, alpha = (T)A.alpha;
+    const int ngroups = (A.n_sinks + 31) >> 5;
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(A.work, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ngroups) break;
+        const int s = g * 32 + lane;
+        const bool valid = s < A.n_sinks;
+        const int i = valid ? (A.active ? A.active[s] : s) : 0;
+        const uint32_t xi = A.pos[i], yi = A.pos[A.n + i], zi = A.pos[2 * A.n + i];
+        const T hi = (T)A.h_cls[A.cls ? A.cls[i] : 0];
+        const T crit = GEOM ? T(0) : alpha * (T)(A.aold ? A.aold[i] : 0.f);
+        T sx = T(0), sy = T(0), sz = T(0), sp = T(0);
+        uint32_t npp = 0, npn = 0;
+        int resume = valid ? 0 : 0x7fffffff;
+        int k = __reduce_min_sync(0xffffffffu, resume);
+        while (k < nn) {
+            const G4Node nd = load_node(A.node + k);
+            const int lv = nd.meta & 31u;
+            const bool leaf = nd.meta & 32u;
+            const T side = ldexp((T)A.box, -lv), half = T(0.5) * side;
+            int act = ACT_NONE;
+            if (resume <= k) {
+                const T dcx = (T)(int32_t)(nd.cx - xi) * scale;
+                const T dcy = (T)(int32_t)(nd.cy - yi) * scale;
+                const T dcz = (T)(int32_t)(nd.cz - zi) * scale;
+                bool skip = false;
+                if (TREEPM) {
+                    const T ex = fmax(fabs(dcx) - half, T(0));
+                    const T ey = fmax(fabs(dcy) - half, T(0));
+                    const T ez = fmax(fabs(dcz) - half, T(0));
+                    skip = ex * ex + ey * ey + ez * ez > rcut2;
+                }
+                if (skip) {
+                    act = ACT_SKIP;
+                } else if (leaf) {
+                    act = ACT_LEAF;
+                } else {
+                    T ox, oy, oz, M;
+                    if (sizeof(T) == 8 && A.qd) {
+                        const double *dd = A.qd + (size_t)k * (4 + A.nq);
+                        ox = (T)dd[0]; oy = (T)dd[1]; oz = (T)dd[2]; M = (T)dd[3];
+                    } else {
+                        ox = (T)nd.sx; oy = (T)nd.sy; oz = (T)nd.sz; M = (T)nd.mass;
+                    }
+                    const T rx = dcx + ox, ry = dcy + oy, rz = dcz + oz;
+                    const T r2 = rx * rx + ry * ry + rz * rz;
+                    const T dmax = fmax(fabs(dcx), fmax(fabs(dcy), fabs(dcz)));
+                    const T h = fmax(hi, (T)nd.hmax);
+                    bool open = (dmax <= half) || (A.exclusion && dmax < side) || (r2 < h * h);
+                    if (!open) {
+                        if (GEOM) {
+                            open = side * side >= theta2 * r2;
+                        } else {
+                            const T r = sqrt(r2);
+                            open = !(G * M * ipow<P>(side) < crit * ipow<P + 2>(r));
+                        }
+                    }
+                    act = open ? ACT_OPEN : ACT_ACCEPT;
+                }
+                resume = (act == ACT_OPEN) ? k + 1 : max(nd.next, k + 1);
+            }
+            if (__any_sync(0xffffffffu, act == ACT_ACCEPT) && act == ACT_ACCEPT) {
+                T Qs[g4_nq(P) > 0 ? g4_nq(P) : 1];
+                T ox, oy, oz, M;
+                if (sizeof(T) == 8 && A.qd) {
+                    const double *dd = A.qd + (size_t)k * (4 + A.nq);
+                    ox = (T)dd[0]; oy = (T)dd[1]; oz = (T)dd[2]; M = (T)dd[3];
+#pragma unroll
+                    for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)dd[4 + c];
+                } else {
+                    ox = (T)nd.sx; oy = (T)nd.sy; oz = (T)nd.sz; M = (T)nd.mass;
+                    const float *qq = A.q + (size_t)k * A.nq;
+#pragma unroll
+                    for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)__ldg(qq + c);
+                }
+                const T rx = (T)(int32_t)(nd.cx - xi) * scale + ox;
+                const T ry = (T)(int32_t)(nd.cy - yi) * scale + oy;
+                const T rz = (T)(int32_t)(nd.cz - zi) * scale + oz;
+                pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, as, sx, sy, sz, sp);
+                npn++;
+            }
+            if (__any_sync(0xffffffffu, act == ACT_LEAF)) {
+                const int f = max(nd.first, 0), e = min(nd.first + nd.count, A.n);
+                for (int j = f; j < e; j++) {
+                    const uint32_t xj = __ldg(A.pos + j), yj = __ldg(A.pos + A.n + j),
+                                   zj = __ldg(A.pos + 2 * A.n + j);
+                    const T mj = (T)__ldg(A.mass + j);
+                    const T hj = (T)A.h_cls[A.cls ? __ldg(A.cls + j) : 0];
+                    if (act == ACT_LEAF && j != i) {
+                        const T dx = (T)(int32_t)(xj - xi) * scale;
+                        const T dy = (T)(int32_t)(yj - yi) * scale;
+                        const T dz = (T)(int32_t)(zj - zi) * scale;
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        if (!(TREEPM && A.pp_cut && r2 >= rcut2)) {
+                            T g0, g1;
+                            pair_kernel<T, TREEPM>(r2, fmax(hi, hj), as, g0, g1);
+                            sx += mj * g1 * dx;
+                            sy += mj * g1 * dy;
+                            sz += mj * g1 * dz;
+                            sp += mj * g0;
+                            npp++;
+                        }
+                    }
+                }
+            }
+            k = __reduce_min_sync(0xffffffffu, resume);
+        }
+        if (valid) {
+            A.acc[i] = (float)(-G * sx);
+            A.acc[A.n + i] = (float)(-G * sy);
+            A.acc[2 * A.n + i] = (float)(-G * sz);
+            if (A.pot) A.pot[i] = (float)(-G * sp);
+            if (A.counts) {
+                A.counts[i] = npp;
+                A.counts[A.n + i] = npn;
+            }
+        }
+    }
+}
+
+// -------------------------------------------------------------------------------------------
+// direct summation on the GPU (validation helper): one thread per sink, sources through
+// shared memory tiles.
+// -------------------------------------------------------------------------------------------
+struct DirectArgs {
+    const uint32_t *pos;
+    const float *mass;
+    const uint8_t *cls;
+    int n;
+    const int32_t *sinks;
+    int n_sinks;
+    float *acc, *pot;
+    double scale, G, rcut2, as;
+    float h_cls[G4_MAX_EPS_CLASSES];
+    int pp_cut;
+};
+
+template <typename T, bool TREEPM>
+__global__ void __launch_bounds__(256) k_direct(const DirectArgs A)
+{
+    __shared__ uint32_t sxp[256], syp[256], szp[256];
+    __shared__ float sm[256], sh[256];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = s < A.n_sinks;
+    const int i = valid ? (A.sinks ? A.sinks[s] : s) : 0;
+    const uint32_t xi = A.pos[i], yi = A.pos[A.n + i], zi = A.pos[2 * A.n + i];
+    const T hi = (T)A.h_cls[A.cls ? A.cls[i] : 0];
+    const T scale = (T)A.scale, as = (T)A.as, rcut2 = (T)A.rcut2;
+    T ax = 0, ay = 0, az = 0, ph = 0;
+    for (int base = 0; base < A.n; base += 256) {
+        int j = base + threadIdx.x;
+        if (j < A.n) {
+            sxp[threadIdx.x] = A.pos[j];
+            syp[threadIdx.x] = A.pos[A.n + j];
+            szp[threadIdx.x] = A.pos[2 * A.n + j];
+            sm[threadIdx.x] = A.mass[j];
+            sh[threadIdx.x] = A.h_cls[A.cls ? A.cls[j] : 0];
+        }
+        __syncthreads();
+        const int m = min(256, A.n - base);
+        if (valid)
+            for (int t = 0; t < m; t++) {
+                if (base + t == i) continue;
+                const T dx = (T)(int32_t)(sxp[t] - xi) * scale;
+                const T dy = (T)(int32_t)(syp[t] - yi) * scale;
+                const T dz = (T)(int32_t)(szp[t] - zi) * scale;
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                if (TREEPM && A.pp_cut && r2 >= rcut2) continue;
+                T g0, g1;
+                pair_kernel<T, TREEPM>(r2, fmax(hi, (T)sh[t]), as, g0, g1);
+                const T mj = (T)sm[t];
+                ax += mj * g1 * dx;
+                ay += mj * g1 * dy;
+                az += mj * g1 * dz;
+                ph += mj * g0;
+            }
+        __syncthreads();
+    }
+    if (valid) {
+        const T G = (T)A.G;
+        A.acc[i] = (float)(-G * ax);
+        A.acc[A.n + i] = (float)(-G * ay);
+        A.acc[2 * A.n + i] = (float)(-G * az);
+        if (A.pot) A.pot[i] = (float)(-G * ph);
+    }
+}
+
+__global__ void k_zero_int(int *p) { *p = 0; }
+
+template <int P, typename T, bool TREEPM, bool GEOM>
+void launch_walk(const WalkArgs &A, cudaStream_t st)
+{
+    // residency: 8 warps per block; enough blocks to fill every SM several times
+    int nb = g4_num_sms() * 6;
+    k_walk<P, T, TREEPM, GEOM><<<nb, 256, 0, st>>>(A);
+}
+
+template <int P, typename T>
+void dispatch_walk2(const WalkArgs &A, bool treepm, bool geom, cudaStream_t st)
+{
+    if (treepm) {
+        if (geom) launch_walk<P, T, true, true>(A, st);
+        else launch_walk<P, T, true, false>(A, st);
+    } else {
+        if (geom) launch_walk<P, T, false, true>(A, st);
+        else launch_walk<P, T, false, false>(A, st);
+    }
+}
+
+template <typename T>
+void dispatch_walk(int p, const WalkArgs &A, bool treepm, bool geom, cudaStream_t st)
+{
+    switch (p) {
+    case 1: dispatch_walk2<1, T>(A, treepm, geom, st); break;
+    case 2: dispatch_walk2<2, T>(A, treepm, geom, st); break;
+    case 3: dispatch_walk2<3, T>(A, treepm, geom, st); break;
+    case 4: dispatch_walk2<4, T>(A, treepm, geom, st); break;
+    default: dispatch_walk2<5, T>(A, treepm, geom, st); break;
+    }
+}
+
+}  // namespace
+
+double g4_r_cut(const g4_params *P)
+{
+    double emax = 0.0;
+    for (int k = 0; k < P->n_eps_classes; k++) emax = fmax(emax, P->eps_table[k]);
+    return fmax(P->r_cut_factor * P->r_s, 2.8 * emax);
+}
+
+g4_status g4_check_params(const g4_params *P, const char *who)
+{
+    if (!P) return g4_fail(G4_ERR_INVALID_ARG, "%s: NULL params", who);
+    if (!(P->box_size > 0)) return g4_fail(G4_ERR_INVALID_ARG, "%s: box_size must be > 0", who);
+    if (P->order_p < 1 || P->order_p > G4_MAX_ORDER)
+        return g4_fail(G4_ERR_INVALID_ARG, "%s: order_p=%d out of [1,5]", who, P->order_p);
+    if (P->n_eps_classes < 1 || P->n_eps_classes > G4_MAX_EPS_CLASSES)
+        return g4_fail(G4_ERR_INVALID_ARG, "%s: n_eps_classes=%d", who, P->n_eps_classes);
+    if (P->criterion != 0 && P->criterion != 1)
+        return g4_fail(G4_ERR_INVALID_ARG, "%s: criterion=%d", who, P->criterion);
+    if (P->precision != 0 && P->precision != 1)
+        return g4_fail(G4_ERR_INVALID_ARG, "%s: precision=%d", who, P->precision);
+    return G4_OK;
+}
+
+extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
+                                     const float *mass_sorted, const uint8_t *cls_sorted,
+                                     const float *aold_sorted, const int32_t *active,
+                                     int64_t n_active, const g4_params *P, float *acc, float *pot,
+                                     uint32_t *counts, void *stream)
+{
+    g4_status s = g4_check_params(P, "g4_gravity_tree");
+    if (s != G4_OK) return s;
+    if (!t || !pos_sorted || !mass_sorted || !acc)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_tree: NULL argument");
+    if (t->built_n < 0 || t->moments_order < 0)
+        return g4_fail(G4_ERR_STATE, "g4_gravity_tree: build and multipoles must run first");
+    if (t->moments_order != P->order_p)
+        return g4_fail(G4_ERR_STATE, "g4_gravity_tree: moments of order %d, walk order %d",
+                       t->moments_order, P->order_p);
+    if (P->precision == 1 && !t->moments_fp64)
+        return g4_fail(G4_ERR_STATE, "g4_gravity_tree: FP64 walk needs FP64 multipoles");
+    if (P->criterion == 0 && !aold_sorted)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_tree: relative criterion needs a_old");
+    const int n = t->built_n;
+    if (active && (n_active < 0 || n_active > n))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_tree: n_active=%lld", (long long)n_active);
+    const int ns = active ? (int)n_active : n;
+    if (n == 0 || ns == 0) return G4_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    WalkArgs A;
+    A.pos = pos_sorted;
+    A.mass = mass_sorted;
+    A.cls = cls_sorted;
+    A.aold = aold_sorted;
+    A.active = active;
+    A.n = n;
+    A.n_sinks = ns;
+    A.lvl = t->lvl;
+    A.node = t->node;
+    A.q = t->q;
+    A.qd = P->precision == 1 ? t->qd : nullptr;
+    A.nq = g4_nq(P->order_p);
+    A.acc = acc;
+    A.pot = pot;
+    A.counts = counts;
+    A.work = t->d_flags + 1;
+    A.flags = t->d_flags;
+    A.scale = P->box_size / 4294967296.0;
+    A.G = P->G;
+    A.alpha = P->alpha;
+    A.theta2 = P->theta * P->theta;
+    const bool treepm = P->r_s > 0.0;
+    const double rc = treepm ? g4_r_cut(P) : 0.0;
+    A.rcut2 = rc * rc;
+    A.as = treepm ? 0.5 / P->r_s : 0.0;
+    A.box = P->box_size;
+    for (int k = 0; k < G4_MAX_EPS_CLASSES; k++)
+        A.h_cls[k] = k < P->n_eps_classes ? (float)(2.8 * P->eps_table[k]) : 0.f;
+    A.exclusion = P->exclusion_zone;
+    A.pp_cut = P->pp_cut;
+    k_zero_int<<<1, 1, 0, st>>>(A.work);
+    const bool geom = P->criterion == 1;
+    if (P->precision == 1) dispatch_walk<double>(P->order_p, A, treepm, geom, st);
+    else dispatch_walk<float>(P->order_p, A, treepm, geom, st);
+    return g4_launch_check("tree walk", 2);
+}
+
+extern "C" g4_status g4_direct(const uint32_t *pos, const float *mass, const uint8_t *cls,
+                               int64_t n, const int32_t *sinks, int64_t n_sinks,
+                               const g4_params *P, float *acc, float *pot, void *stream)
+{
+    g4_status s = g4_check_params(P, "g4_direct");
+    if (s != G4_OK) return s;
+    if (n < 0 || n >= ((int64_t)1 << 31) || !pos || !mass || !acc || (sinks && n_sinks < 0))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_direct: bad arguments");
+    const int ns = sinks ? (int)n_sinks : (int)n;
+    if (n == 0 || ns == 0) return G4_OK;
+    DirectArgs A;
+    A.pos = pos;
+    A.mass = mass;
+    A.cls = cls;
+    A.n = (int)n;
+    A.sinks = sinks;
+    A.n_sinks = ns;
+    A.acc = acc;
+    A.pot = pot;
+    A.scale = P->box_size / 4294967296.0;
+    A.G = P->G;
+    const bool treepm = P->r_s > 0.0;
+    const double rc = treepm ? g4_r_cut(P) : 0.0;
+    A.rcut2 = rc * rc;
+    A.as = treepm ? 0.5 / P->r_s : 0.0;
+    for (int k = 0; k < G4_MAX_EPS_CLASSES; k++)
+        A.h_cls[k] = k < P->n_eps_classes ? (float)(2.8 * P->eps_table[k]) : 0.f;
+    A.pp_cut = P->pp_cut;
+    cudaStream_t st = (cudaStream_t)stream;
+    int nb = (ns + 255) / 256;
+    if (P->precision == 1) {
+        if (treepm) k_direct<double, true><<<nb, 256, 0, st>>>(A);
+        else k_direct<double, false><<<nb, 256, 0, st>>>(A);
+    } else {
+        if (treepm) k_direct<float, true><<<nb, 256, 0, st>>>(A);
+        else k_direct<float, false><<<nb, 256, 0, st>>>(A);
+    }
+    return g4_launch_check("direct sum", 1);
+}

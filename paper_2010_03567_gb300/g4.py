@@ -1,0 +1,350 @@
+"""Thin Python binding of libg4.so (include/g4.h): argument marshalling only.
+
+Every function here forwards torch CUDA tensors (device pointers) and the current CUDA stream
+to the C entry point of the same name; all arithmetic runs in the sm_103a kernels.  There is
+no CPU fallback: if the library cannot be loaded, or no CUDA device is present, the calls
+raise.
+
+uint32 / uint64 device arrays are carried in int32 / int64 tensors (same bits).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+_lib = None
+
+
+class G4Error(RuntimeError):
+    pass
+
+
+MAX_EPS = 8
+
+
+class G4Params(C.Structure):
+    _fields_ = [("box_size", C.c_double), ("periodic", C.c_int), ("r_s", C.c_double),
+                ("r_cut_factor", C.c_double), ("pp_cut", C.c_int), ("alpha", C.c_double),
+                ("theta", C.c_double), ("criterion", C.c_int), ("order_p", C.c_int),
+                ("leaf_max", C.c_int), ("exclusion_zone", C.c_int), ("precision", C.c_int),
+                ("G", C.c_double), ("n_eps_classes", C.c_int),
+                ("eps_table", C.c_double * MAX_EPS), ("group_size", C.c_int),
+                ("fp64_count", C.c_int), ("keep_qp", C.c_int)]
+
+    def copy(self) -> "G4Params":
+        p = G4Params()
+        C.memmove(C.byref(p), C.byref(self), C.sizeof(G4Params))
+        return p
+
+
+def lib():
+    """Loads the in-tree libg4.so (building it with nvcc when it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if _build.needs_build():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise G4Error("libg4.so is missing and could not be built")
+        L = C.CDLL(path)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    P = C.POINTER(G4Params)
+    sig = {
+        "g4_version": ([], C.c_char_p),
+        "g4_last_error": ([], C.c_char_p),
+        "g4_launch_count": ([], C.c_int64),
+        "g4_params_default": ([P], i32),
+        "g4_int_coords": ([vp, i64, i32, d, vp, vp, vp], i32),
+        "g4_keys_sort_workspace": ([i64, C.POINTER(C.c_size_t)], i32),
+        "g4_keys_sort": ([vp, i64, vp, vp, vp, C.c_size_t, vp], i32),
+        "g4_gather": ([vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
+        "g4_scatter": ([vp, i64, vp, vp, vp, vp, vp], i32),
+        "g4_tree_create": ([i64, i64, C.POINTER(vp)], i32),
+        "g4_tree_free": ([vp], None),
+        "g4_tree_build": ([vp, vp, vp, i64, P, vp], i32),
+        "g4_tree_status": ([vp, C.POINTER(i64), C.POINTER(C.c_int32), vp], i32),
+        "g4_tree_nodes": ([vp, vp, vp, vp, vp, vp, vp], i32),
+        "g4_multipoles": ([vp, vp, vp, vp, vp, P, vp], i32),
+        "g4_tree_moments": ([vp, vp, vp, vp, vp], i32),
+        "g4_gravity_tree": ([vp, vp, vp, vp, vp, vp, i64, P, vp, vp, vp, vp], i32),
+        "g4_fmm_workspace": ([vp, P, C.POINTER(C.c_size_t)], i32),
+        "g4_gravity_fmm": ([vp, vp, vp, vp, P, vp, vp, vp, vp, vp, C.c_size_t, vp], i32),
+        "g4_direct": ([vp, vp, vp, i64, vp, i64, P, vp, vp, vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        msg = lib().g4_last_error().decode(errors="replace")
+        raise G4Error(f"{what} failed (status {st}): {msg}")
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise G4Error("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise G4Error("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def params(**kw) -> G4Params:
+    """g4_params with the library defaults, overridden by keyword arguments.  ``eps`` may be
+    a sequence of softening lengths (one per class)."""
+    p = G4Params()
+    _check(lib().g4_params_default(C.byref(p)), "g4_params_default")
+    eps = kw.pop("eps", None)
+    if eps is not None:
+        eps = [float(e) for e in (eps if hasattr(eps, "__len__") else [eps])]
+        if not 1 <= len(eps) <= MAX_EPS:
+            raise G4Error("1..8 softening classes supported")
+        p.n_eps_classes = len(eps)
+        for k, e in enumerate(eps):
+            p.eps_table[k] = e
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise G4Error(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def version() -> str:
+    return lib().g4_version().decode()
+
+
+def launch_count() -> int:
+    """Kernel launches issued by libg4 since it was loaded."""
+    return int(lib().g4_launch_count())
+
+
+# ---- a1..a3 ----------------------------------------------------------------------------------
+
+def g4_int_coords(pos: torch.Tensor, periodic: bool, box_size: float = 0.0, out=None, frame=None,
+                  stream=None):
+    """pos: (n,3) float64 CUDA -> (pos_int (3,n) int32 holding uint32 bits, frame (4,) f64)."""
+    n = pos.shape[0]
+    out = out if out is not None else torch.empty((3, n), dtype=torch.int32, device=pos.device)
+    frame = frame if frame is not None else torch.empty(4, dtype=torch.float64, device=pos.device)
+    _check(lib().g4_int_coords(_ptr(pos), n, int(periodic), float(box_size), _ptr(out),
+                               _ptr(frame), _stream(stream)), "g4_int_coords")
+    return out, frame
+
+
+def g4_keys_sort_workspace(n: int) -> int:
+    b = C.c_size_t()
+    _check(lib().g4_keys_sort_workspace(n, C.byref(b)), "g4_keys_sort_workspace")
+    return int(b.value)
+
+
+def g4_keys_sort(pos_int: torch.Tensor, keys=None, perm=None, workspace=None, stream=None):
+    """pos_int (3,n) -> (keys (n,) int64 holding uint64 keys, perm (n,) int32)."""
+    n = pos_int.shape[1]
+    dev = pos_int.device
+    keys = keys if keys is not None else torch.empty(n, dtype=torch.int64, device=dev)
+    perm = perm if perm is not None else torch.empty(n, dtype=torch.int32, device=dev)
+    if workspace is None:
+        workspace = torch.empty(g4_keys_sort_workspace(n) + 256, dtype=torch.uint8, device=dev)
+    wp = workspace.data_ptr()
+    off = (-wp) % 256
+    _check(lib().g4_keys_sort(_ptr(pos_int), n, _ptr(keys), _ptr(perm), C.c_void_p(wp + off),
+                              workspace.numel() - off, _stream(stream)), "g4_keys_sort")
+    return keys, perm
+
+
+def g4_gather(perm, pos, mass, cls=None, aold=None, out=None, stream=None):
+    n = perm.shape[0]
+    if out is None:
+        out = (torch.empty_like(pos), torch.empty_like(mass),
+               None if cls is None else torch.empty_like(cls),
+               None if aold is None else torch.empty_like(aold))
+    po, mo, co, ao = out
+    _check(lib().g4_gather(_ptr(perm), n, _ptr(pos), _ptr(mass), _ptr(cls), _ptr(aold), _ptr(po),
+                           _ptr(mo), _ptr(co), _ptr(ao), _stream(stream)), "g4_gather")
+    return po, mo, co, ao
+
+
+def g4_scatter(perm, acc_sorted, pot_sorted=None, out=None, stream=None):
+    n = perm.shape[0]
+    if out is None:
+        out = (torch.empty_like(acc_sorted), None if pot_sorted is None else torch.empty_like(pot_sorted))
+    ao, po = out
+    _check(lib().g4_scatter(_ptr(perm), n, _ptr(acc_sorted), _ptr(pot_sorted), _ptr(ao), _ptr(po),
+                            _stream(stream)), "g4_scatter")
+    return ao, po
+
+
+# ---- a4..a8 -----------------------------------------------------------------------------------
+
+class Tree:
+    """Library-owned tree handle (g4_tree): node arrays for up to n_max particles."""
+
+    def __init__(self, n_max: int, node_capacity: int = 0):
+        h = C.c_void_p()
+        _check(lib().g4_tree_create(int(n_max), int(node_capacity), C.byref(h)), "g4_tree_create")
+        self.h = h
+        self.n_max = n_max
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().g4_tree_free(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, keys_sorted, pos_sorted, p: G4Params, stream=None):
+        _check(lib().g4_tree_build(self.h, _ptr(keys_sorted), _ptr(pos_sorted),
+                                   int(pos_sorted.shape[1]), C.byref(p), _stream(stream)),
+               "g4_tree_build")
+
+    def status(self, stream=None):
+        nn = C.c_int64()
+        ml = C.c_int32()
+        _check(lib().g4_tree_status(self.h, C.byref(nn), C.byref(ml), _stream(stream)), "g4_tree_status")
+        return int(nn.value), int(ml.value)
+
+    def nodes(self, stream=None) -> dict:
+        nn, _ = self.status(stream)
+        dev = torch.device("cuda")
+        out = {k: torch.empty(nn, dtype=torch.int32, device=dev) for k in ("level", "first", "count", "next")}
+        out["center"] = torch.empty((nn, 3), dtype=torch.int32, device=dev)
+        _check(lib().g4_tree_nodes(self.h, _ptr(out["level"]), _ptr(out["first"]), _ptr(out["count"]),
+                                   _ptr(out["next"]), _ptr(out["center"]), _stream(stream)), "g4_tree_nodes")
+        return out
+
+    def multipoles(self, pos_sorted, mass_sorted, cls_sorted, aold_sorted, p: G4Params, stream=None):
+        _check(lib().g4_multipoles(self.h, _ptr(pos_sorted), _ptr(mass_sorted), _ptr(cls_sorted),
+                                   _ptr(aold_sorted), C.byref(p), _stream(stream)), "g4_multipoles")
+
+    def moments(self, order: int, stream=None) -> dict:
+        nn, _ = self.status(stream)
+        nm = (order + 1) * (order + 2) * (order + 3) // 6
+        dev = torch.device("cuda")
+        out = {"mass": torch.empty(nn, dtype=torch.float64, device=dev),
+               "com": torch.empty((nn, 3), dtype=torch.float64, device=dev),
+               "mono": torch.empty((nn, nm), dtype=torch.float64, device=dev)}
+        _check(lib().g4_tree_moments(self.h, _ptr(out["mass"]), _ptr(out["com"]), _ptr(out["mono"]),
+                                     _stream(stream)), "g4_tree_moments")
+        return out
+
+    def gravity_tree(self, pos_sorted, mass_sorted, cls_sorted, aold_sorted, p: G4Params,
+                     active=None, acc=None, pot=None, counts=None, stream=None):
+        n = pos_sorted.shape[1]
+        dev = pos_sorted.device
+        acc = acc if acc is not None else torch.zeros((3, n), dtype=torch.float32, device=dev)
+        pot = pot if pot is not None else torch.zeros(n, dtype=torch.float32, device=dev)
+        counts = counts if counts is not None else torch.zeros((2, n), dtype=torch.int32, device=dev)
+        na = 0 if active is None else int(active.shape[0])
+        _check(lib().g4_gravity_tree(self.h, _ptr(pos_sorted), _ptr(mass_sorted), _ptr(cls_sorted),
+                                     _ptr(aold_sorted), _ptr(active), na, C.byref(p), _ptr(acc),
+                                     _ptr(pot), _ptr(counts), _stream(stream)), "g4_gravity_tree")
+        return acc, pot, counts
+
+    def fmm_workspace(self, p: G4Params) -> int:
+        b = C.c_size_t()
+        _check(lib().g4_fmm_workspace(self.h, C.byref(p), C.byref(b)), "g4_fmm_workspace")
+        return int(b.value)
+
+    def gravity_fmm(self, pos_sorted, mass_sorted, cls_sorted, p: G4Params, workspace=None,
+                    acc=None, pot=None, counts=None, momentum=None, stream=None):
+        n = pos_sorted.shape[1]
+        dev = pos_sorted.device
+        acc = acc if acc is not None else torch.zeros((3, n), dtype=torch.float32, device=dev)
+        pot = pot if pot is not None else torch.zeros(n, dtype=torch.float32, device=dev)
+        counts = counts if counts is not None else torch.zeros((2, n), dtype=torch.int32, device=dev)
+        momentum = momentum if momentum is not None else torch.zeros(3, dtype=torch.float64, device=dev)
+        if workspace is None:
+            workspace = torch.empty(self.fmm_workspace(p) + 256, dtype=torch.uint8, device=dev)
+        wp = workspace.data_ptr()
+        off = (-wp) % 256
+        _check(lib().g4_gravity_fmm(self.h, _ptr(pos_sorted), _ptr(mass_sorted), _ptr(cls_sorted),
+                                    C.byref(p), _ptr(acc), _ptr(pot), _ptr(counts), _ptr(momentum),
+                                    C.c_void_p(wp + off), workspace.numel() - off, _stream(stream)),
+               "g4_gravity_fmm")
+        return acc, pot, counts, momentum
+
+
+def g4_direct(pos, mass, cls, p: G4Params, sinks=None, acc=None, pot=None, stream=None):
+    n = pos.shape[1]
+    dev = pos.device
+    acc = acc if acc is not None else torch.zeros((3, n), dtype=torch.float32, device=dev)
+    pot = pot if pot is not None else torch.zeros(n, dtype=torch.float32, device=dev)
+    ns = 0 if sinks is None else int(sinks.shape[0])
+    _check(lib().g4_direct(_ptr(pos), _ptr(mass), _ptr(cls), n, _ptr(sinks), ns, C.byref(p),
+                           _ptr(acc), _ptr(pot), _stream(stream)), "g4_direct")
+    return acc, pot
+
+
+# ---- whole pipeline ------------------------------------------------------------------------------
+
+class TreeGravity:
+    """Preallocated pipeline: keys + sort -> gather -> tree -> moments -> walk -> scatter.
+
+    All buffers are allocated once (torch, on the current device), so ``forces`` performs no
+    allocation and no host synchronisation and can be captured in a CUDA graph.
+    """
+
+    def __init__(self, n: int, p: G4Params, node_capacity: int = 0, with_cls: bool = False):
+        dev = torch.device("cuda")
+        self.n = n
+        self.p = p
+        if node_capacity == 0:
+            node_capacity = 4096 + int(n * max(1.5, 3.5 / max(1, int(p.leaf_max))))
+        self.tree = Tree(n, node_capacity)
+        self.keys = torch.empty(n, dtype=torch.int64, device=dev)
+        self.perm = torch.empty(n, dtype=torch.int32, device=dev)
+        self.ws = torch.empty(g4_keys_sort_workspace(n) + 256, dtype=torch.uint8, device=dev)
+        self.pos_s = torch.empty((3, n), dtype=torch.int32, device=dev)
+        self.mass_s = torch.empty(n, dtype=torch.float32, device=dev)
+        self.cls_s = torch.empty(n, dtype=torch.uint8, device=dev) if with_cls else None
+        self.aold_s = torch.empty(n, dtype=torch.float32, device=dev)
+        self.acc_s = torch.zeros((3, n), dtype=torch.float32, device=dev)
+        self.pot_s = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.counts = torch.zeros((2, n), dtype=torch.int32, device=dev)
+        self.acc = torch.zeros((3, n), dtype=torch.float32, device=dev)
+        self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
+
+    def prepare(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None):
+        p = p or self.p
+        g4_keys_sort(pos_int, self.keys, self.perm, self.ws, stream)
+        g4_gather(self.perm, pos_int, mass, cls if self.cls_s is not None else None, aold,
+                  out=(self.pos_s, self.mass_s, self.cls_s if cls is not None else None,
+                       self.aold_s if aold is not None else None), stream=stream)
+        self.tree.build(self.keys, self.pos_s, p, stream)
+        self.tree.multipoles(self.pos_s, self.mass_s, self.cls_s if cls is not None else None,
+                             self.aold_s if aold is not None else None, p, stream)
+
+    def walk(self, p: G4Params | None = None, use_aold: bool = True, stream=None):
+        p = p or self.p
+        self.tree.gravity_tree(self.pos_s, self.mass_s, self.cls_s,
+                               self.aold_s if use_aold else None, p, acc=self.acc_s, pot=self.pot_s,
+                               counts=self.counts, stream=stream)
+        g4_scatter(self.perm, self.acc_s, self.pot_s, out=(self.acc, self.pot), stream=stream)
+        return self.acc, self.pot
+
+    def forces(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None):
+        self.prepare(pos_int, mass, cls, aold, p, stream)
+        return self.walk(p, use_aold=aold is not None, stream=stream)

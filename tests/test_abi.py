@@ -1,0 +1,49 @@
+"""The C-ABI library builds for sm_103a, loads on a CPU-only host and exports every entry
+point that include/g4.h declares.  Only host-side calls are made (no kernels)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "g4.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(g4_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2010_03567_gb300 import build
+    path = build.build()
+    lib = C.CDLL(path)
+    names = _declared()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_side_calls():
+    from paper_2010_03567_gb300 import g4
+    assert "sm_103a" in g4.version()
+    p = g4.params(alpha=0.01, eps=[0.1, 0.2])
+    assert p.alpha == 0.01 and p.n_eps_classes == 2 and p.eps_table[1] == 0.2
+    assert p.leaf_max == 8 and p.order_p == 3 and p.r_cut_factor == 4.5
+    # argument errors are reported synchronously with a message, without touching a GPU
+    b = C.c_size_t()
+    st = g4.lib().g4_keys_sort_workspace(-1, C.byref(b))
+    assert st == 1 and b"bad args" in g4.lib().g4_last_error()
+    assert g4.g4_keys_sort_workspace(1 << 20) > 12 * (1 << 20)
+    with pytest.raises(g4.G4Error):
+        g4.params(no_such_field=1)
+
+
+def test_oracle_and_library_share_no_code():
+    # the oracle is plain C under oracle/, the library CUDA under the package: no includes across
+    import glob
+    for f in glob.glob(os.path.join(ROOT, "paper_2010_03567_gb300", "csrc", "*")):
+        assert "oracle" not in open(f).read().lower().replace("oracle-free", "")
+    txt = open(os.path.join(ROOT, "oracle", "g4_oracle.c")).read()
+    assert "g4.h" not in txt and "g4_internal" not in txt

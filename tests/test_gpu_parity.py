@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Integer work (coordinates, keys, sort permutation, tree topology, dyadic node masses)
+must be bit-exact; forces must meet the 99th-percentile relative error 1e-5 against the
+same-algorithm oracle (a few particles may differ where an FP32 opening decision lands on
+the other side of the threshold than the FP64 one -- several results are then valid).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_2010_03567_gb300 import g4, synth  # noqa: E402
+
+from _helpers import (gpu_forces, gpu_params, int_coords, oracle_params, relerr, to_dev,  # noqa: E402
+                      u32_dev, u32_host, u64_host)
+
+pytestmark = pytest.mark.gpu
+
+PARITY_P99 = 1e-5
+
+
+def _treepm_box(n_side=32, rms=2.0, seed=1003):
+    L = n_side * 1.953125          # same mean spacing as the 256^3, L = 500 workload
+    ps = synth.zeldovich(n_side, L, rms, seed)
+    return ps, dict(r_s=1.25 * L / (2 * n_side), r_cut_factor=4.5)
+
+
+# ---- a1 / a2 / a3 ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["periodic", "isolated"])
+def test_int_coords_bit_exact(kind):
+    ps = synth.zeldovich(20, 7.0, 1.0, 3) if kind == "periodic" else synth.plummer(5000, 9)
+    pos = torch.from_numpy(ps.pos).cuda()
+    qg, frame = g4.g4_int_coords(pos, ps.periodic, ps.box_size)
+    torch.cuda.synchronize()
+    if ps.periodic:
+        q = oracle.int_coords_periodic(ps.pos, ps.box_size)
+        fr = np.array([0, 0, 0, ps.box_size])
+    else:
+        q, fr = oracle.int_coords_isolated(ps.pos)
+    assert np.array_equal(u32_host(qg), q)
+    assert np.array_equal(frame.cpu().numpy(), fr)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 4095, 4096, 4097, 100003])
+def test_keys_sort_bit_exact(n):
+    g = np.random.default_rng(n)
+    q = g.integers(0, 2 ** 32, size=(3, n), dtype=np.uint64).astype(np.uint32)
+    if n > 10:
+        q[:, n // 3: n // 3 + 50] = q[:, n // 3: n // 3 + 1]     # equal keys: stability
+    keys, perm = g4.g4_keys_sort(u32_dev(torch, q))
+    torch.cuda.synchronize()
+    ko = oracle.keys(q)
+    kso, permo = oracle.sort(ko)
+    assert np.array_equal(u64_host(keys), kso)
+    assert np.array_equal(perm.cpu().numpy().astype(np.int64), permo)
+
+
+def test_keys_clustered_workload():
+    ps, _ = _treepm_box(64)
+    q, _ = int_coords(ps)
+    keys, perm = g4.g4_keys_sort(u32_dev(torch, q))
+    kso, permo = oracle.sort(oracle.keys(q))
+    assert np.array_equal(u64_host(keys), kso)
+    assert np.array_equal(perm.cpu().numpy().astype(np.int64), permo)
+
+
+# ---- a4 / a5 ----------------------------------------------------------------------------------
+
+def _tree_case(ps, leaf_max, order=3):
+    q, box = int_coords(ps)
+    P = gpu_params(g4, ps, box, leaf_max=leaf_max, order_p=order)
+    tg = g4.TreeGravity(ps.n, P, with_cls=True)
+    tg.prepare(u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32),
+               to_dev(torch, ps.eps_class, torch.uint8), None)
+    torch.cuda.synchronize()
+    OP = oracle_params(ps, box, order=order)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, None, OP, leaf_max)
+    return tg, run, box
+
+
+@pytest.mark.parametrize("case", ["plummer-8", "plummer-1", "box-4", "box-16", "tiny-3"])
+def test_tree_topology_bit_exact(case):
+    if case.startswith("plummer"):
+        ps = synth.plummer_16k()
+    elif case == "tiny-3":
+        ps = synth.plummer(5, 2)
+    else:
+        ps, _ = _treepm_box(24)
+    leaf = int(case.split("-")[1])
+    tg, run, _ = _tree_case(ps, leaf)
+    nd = {k: v.cpu().numpy() for k, v in tg.tree.nodes().items()}
+    ot = run.tree.export()
+    assert len(nd["level"]) == len(ot["level"])
+    assert np.array_equal(nd["level"], ot["level"])
+    assert np.array_equal(nd["first"], ot["first"])
+    assert np.array_equal(nd["count"], ot["count"])
+    assert np.array_equal(nd["next"], ot["next"])
+    assert np.array_equal(nd["center"].view(np.uint32), ot["center"])
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_moments_parity(order):
+    ps = synth.plummer_16k()
+    tg, run, box = _tree_case(ps, 8, order)
+    gm = {k: v.cpu().numpy() for k, v in tg.tree.moments(order).items()}
+    om = run.tree.export_moments()
+    # node masses are dyadic sums: bit-exact
+    assert np.array_equal(gm["mass"], om["mass"])
+    lv = run.tree.export()["level"]
+    side = box / 2.0 ** lv
+    assert np.max(np.abs(gm["com"] - om["com"]) / side[:, None]) < 2e-6
+    for n in range(2, order + 1):
+        for a in range(n, -1, -1):
+            for b in range(n - a, -1, -1):
+                k = oracle.mono_index(a, b, n - a - b)
+                scale = om["mass"] * side ** n
+                err = np.abs(gm["mono"][:, k] - om["mono"][:, k]) / scale
+                assert np.max(err) < 1e-5, (a, b, n - a - b, np.max(err))
+
+
+# ---- a6 / a7: walk --------------------------------------------------------------------------
+
+def _plummer_c1():
+    ps = synth.plummer_16k()
+    q, box = int_coords(ps)
+    OP = oracle_params(ps, box)
+    ad, _ = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP)
+    aold = np.linalg.norm(ad, axis=1).astype(np.float32)    # prior direct-sum pass, FP32
+    return ps, q, box, aold, ad
+
+
+def test_walk_parity_plummer_relative():
+    ps, q, box, aold, ad = _plummer_c1()
+    kw = dict(alpha=0.0025, order_p=3)
+    P = gpu_params(g4, ps, box, **kw)
+    ag, pg, cg, _ = gpu_forces(torch, g4, ps, q, P, aold)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, aold.astype(np.float64), oracle_params(ps, box, **kw), 8)
+    ao, po, co = oracle.tree_forces(run, np.arange(ps.n))
+    e = relerr(ag, ao)
+    assert np.percentile(e, 99) < PARITY_P99, np.percentile(e, [50, 99, 100])
+    ep = np.abs(pg - po) / np.abs(po)
+    assert np.percentile(ep, 99) < PARITY_P99
+    same = np.all(cg == co, axis=1)
+    assert same.mean() > 0.99, same.mean()
+    # accuracy against the FP64 direct sum (the method's own error at alpha = 0.0025)
+    assert np.percentile(relerr(ag, ad), 99) < 1e-2
+
+
+@pytest.mark.parametrize("order", [1, 2, 4, 5])
+def test_walk_parity_orders(order):
+    ps, q, box, aold, _ = _plummer_c1()
+    kw = dict(alpha=0.0025, order_p=order)
+    P = gpu_params(g4, ps, box, **kw)
+    ag, pg, cg, _ = gpu_forces(torch, g4, ps, q, P, aold)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, aold.astype(np.float64), oracle_params(ps, box, **kw), 8)
+    sinks = np.arange(0, ps.n, 4)
+    ao, po, co = oracle.tree_forces(run, sinks)
+    assert np.percentile(relerr(ag[sinks], ao), 99) < PARITY_P99
+
+
+def test_walk_parity_treepm_relative():
+    ps, tp = _treepm_box(32)
+    q, box = int_coords(ps)
+    kw = dict(alpha=0.0025, **tp)
+    OP = oracle_params(ps, box, **kw)
+    ad, _ = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP, r_max=OP.r_cut)
+    aold = np.linalg.norm(ad, axis=1).astype(np.float32)
+    P = gpu_params(g4, ps, box, **kw)
+    ag, pg, cg, _ = gpu_forces(torch, g4, ps, q, P, aold)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, aold.astype(np.float64), OP, 8)
+    ao, po, co = oracle.tree_forces(run, np.arange(ps.n))
+    e = relerr(ag, ao)
+    assert np.percentile(e, 99) < PARITY_P99, np.percentile(e, [50, 99, 100])
+    assert np.mean(np.all(cg == co, axis=1)) > 0.99
+    # against the hard-cutoff FP64 direct sum: the headline accuracy target
+    assert np.percentile(relerr(ag, ad), 99) < 1e-3
+
+
+def test_walk_parity_geometric_bootstrap():
+    ps, tp = _treepm_box(24)
+    q, box = int_coords(ps)
+    kw = dict(criterion=1, theta=0.5, **tp)
+    P = gpu_params(g4, ps, box, **kw)
+    ag, pg, cg, _ = gpu_forces(torch, g4, ps, q, P, None)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, None, oracle_params(ps, box, **kw), 8)
+    ao, po, co = oracle.tree_forces(run, np.arange(ps.n))
+    assert np.percentile(relerr(ag, ao), 99) < PARITY_P99
+
+
+def test_walk_alpha0_is_direct_sum():
+    ps, tp = _treepm_box(16)
+    q, box = int_coords(ps)
+    kw = dict(alpha=0.0, **tp)
+    P = gpu_params(g4, ps, box, **kw)
+    ag, pg, cg, _ = gpu_forces(torch, g4, ps, q, P, np.ones(ps.n, np.float32))
+    assert np.all(cg[:, 1] == 0)
+    OP = oracle_params(ps, box, **kw)
+    ad, pd = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP, r_max=OP.r_cut)
+    assert np.percentile(relerr(ag, ad), 99) < PARITY_P99
+    # GPU direct-sum helper, same kernel
+    acc, pot = g4.g4_direct(u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32), None, P)
+    assert np.percentile(relerr(acc.cpu().numpy().T, ad), 99) < PARITY_P99
+
+
+def test_walk_fp64_mode():
+    ps, q, box, aold, _ = _plummer_c1()
+    kw = dict(alpha=0.0025, order_p=3)
+    P = gpu_params(g4, ps, box, precision=1, **kw)
+    ag, pg, cg, _ = gpu_forces(torch, g4, ps, q, P, aold)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, aold.astype(np.float64), oracle_params(ps, box, **kw), 8)
+    ao, po, co = oracle.tree_forces(run, np.arange(ps.n))
+    e = relerr(ag, ao)
+    # FP64 arithmetic; the outputs are FP32, so the comparison floor is FP32 rounding
+    assert np.percentile(e, 99) < 2e-7
+    assert np.mean(np.all(cg == co, axis=1)) > 0.999
+
+
+def test_active_subset_bitwise_equal_and_deterministic():
+    ps, q, box, aold, _ = _plummer_c1()
+    P = gpu_params(g4, ps, box, alpha=0.0025)
+    tg = g4.TreeGravity(ps.n, P)
+    pos = u32_dev(torch, q)
+    mass = to_dev(torch, ps.mass, torch.float32)
+    a = to_dev(torch, aold, torch.float32)
+    tg.prepare(pos, mass, None, a)
+    acc_s, pot_s, cnt = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P)
+    acc2, pot2, _ = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P)
+    assert torch.equal(acc_s, acc2) and torch.equal(pot_s, pot2)
+    active = torch.arange(5, ps.n, 37, dtype=torch.int32, device="cuda")
+    acc3, pot3, _ = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, active=active)
+    idx = active.long()
+    assert torch.equal(acc3[:, idx], acc_s[:, idx])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 33])
+def test_small_and_degenerate_sets(n):
+    ps = synth.plummer(max(n, 1), 77 + n)
+    if n == 33:   # many coincident particles: leaves at key resolution above leaf_max
+        ps.pos[1:20] = ps.pos[0]
+    q, box = int_coords(ps)
+    P = gpu_params(g4, ps, box, criterion=1, theta=0.5)
+    ag, pg, cg, _ = gpu_forces(torch, g4, ps, q, P, None)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, None, oracle_params(ps, box, criterion=1, theta=0.5), 8)
+    ao, po, co = oracle.tree_forces(run, np.arange(ps.n))
+    if n == 1:
+        assert np.all(ag == 0) and np.all(pg == 0)
+    else:
+        assert np.allclose(ag, ao, rtol=1e-5, atol=1e-6 * np.abs(ao).max())
+        assert np.allclose(pg, po, rtol=1e-5)
