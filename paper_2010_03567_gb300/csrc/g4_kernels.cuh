@@ -13,6 +13,31 @@
 
 namespace g4k {
 
+// one 64-byte node record through the read-only path (4 x 16-byte loads)
+__device__ __forceinline__ G4Node load_node(const G4Node *p)
+{
+    const int4 *v = reinterpret_cast<const int4 *>(p);
+    const int4 a = __ldg(v), b = __ldg(v + 1), c = __ldg(v + 2), d = __ldg(v + 3);
+    G4Node nd;
+    nd.cx = (uint32_t)a.x;
+    nd.cy = (uint32_t)a.y;
+    nd.cz = (uint32_t)a.z;
+    nd.meta = (uint32_t)a.w;
+    nd.sx = __int_as_float(b.x);
+    nd.sy = __int_as_float(b.y);
+    nd.sz = __int_as_float(b.z);
+    nd.mass = __int_as_float(b.w);
+    nd.first = c.x;
+    nd.count = c.y;
+    nd.next = c.z;
+    nd.parent = c.w;
+    nd.amin = __int_as_float(d.x);
+    nd.hmax = __int_as_float(d.y);
+    nd.bfs = d.z;
+    nd.nchild = d.w;
+    return nd;
+}
+
 __host__ __device__ constexpr int fact(int n) { return n <= 1 ? 1 : n * fact(n - 1); }
 __host__ __device__ constexpr int pairk(int a, int i)
 {

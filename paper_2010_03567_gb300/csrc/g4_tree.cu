@@ -175,6 +175,7 @@ __global__ void k_build_dfs(int level, const int32_t *__restrict__ lvl,
 __global__ void k_build_emit(const int32_t *__restrict__ lvl, const uint32_t *__restrict__ pos,
                              int n, const int32_t *__restrict__ b_first,
                              const int32_t *__restrict__ b_count, const int32_t *__restrict__ b_child,
+                             const int32_t *__restrict__ b_nchild,
                              const int32_t *__restrict__ b_size, const int32_t *__restrict__ b_dfs,
                              const int32_t *__restrict__ b_parent, G4Node *__restrict__ node)
 {
@@ -205,7 +206,7 @@ __global__ void k_build_emit(const int32_t *__restrict__ lvl, const uint32_t *__
         nd.amin = 0.f;
         nd.hmax = 0.f;
         nd.bfs = b;
-        nd.pad = 0;
+        nd.nchild = b_child[b] < 0 ? 0 : b_nchild[b];
         node[d] = nd;
     }
 }
@@ -317,7 +318,8 @@ extern "C" g4_status g4_tree_build(g4_tree t, const uint64_t *keys_sorted,
         k_build_dfs<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->b_child, t->b_nchild, t->b_size,
                                                   t->b_dfs);
     k_build_emit<<<nb, BUILD_THREADS, 0, st>>>(t->lvl, pos_sorted, (int)n, t->b_first, t->b_count,
-                                               t->b_child, t->b_size, t->b_dfs, t->b_parent, t->node);
+                                               t->b_child, t->b_nchild, t->b_size, t->b_dfs,
+                                               t->b_parent, t->node);
     t->built_n = (int)n;
     t->moments_order = -1;
     return g4_launch_check("tree build", 4 + G4_MAXLEVEL + 2 * (G4_MAXLEVEL + 1));

@@ -50,31 +50,6 @@ template <int P, typename T> __device__ __forceinline__ T ipow(T x)
     return r;
 }
 
-__device__ __forceinline__ G4Node load_node(const G4Node *p)
-{
-    const int4 *v = reinterpret_cast<const int4 *>(p);
-    int4 a = __ldg(v), b = __ldg(v + 1), c = __ldg(v + 2);
-    G4Node nd;
-    nd.cx = (uint32_t)a.x;
-    nd.cy = (uint32_t)a.y;
-    nd.cz = (uint32_t)a.z;
-    nd.meta = (uint32_t)a.w;
-    nd.sx = __int_as_float(b.x);
-    nd.sy = __int_as_float(b.y);
-    nd.sz = __int_as_float(b.z);
-    nd.mass = __int_as_float(b.w);
-    nd.first = c.x;
-    nd.count = c.y;
-    nd.next = c.z;
-    nd.parent = c.w;
-    int4 d = __ldg(v + 3);
-    nd.amin = __int_as_float(d.x);
-    nd.hmax = __int_as_float(d.y);
-    nd.bfs = d.z;
-    nd.pad = d.w;
-    return nd;
-}
-
 template <int P, typename T, bool TREEPM, bool GEOM>
 __global__ void __launch_bounds__(256) k_walk(const WalkArgs A)
 {
