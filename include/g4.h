@@ -119,6 +119,23 @@ g4_status g4_keys_sort_workspace(int64_t n, size_t *bytes);
 g4_status g4_keys_sort(const uint32_t *pos_int, int64_t n, uint64_t *keys_sorted,
                        int32_t *perm, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Same result as g4_keys_sort, but allocation-free: the scratch memory is a fixed array inside
+ * the library (about 16 MB of device memory on every GPU that loads libg4, held until the
+ * process exits) instead of a caller workspace.  The paper has no counterpart; this entry
+ * point exists for callers that cannot allocate device memory when they sort -- code running
+ * during CUDA-graph capture, applications whose device memory belongs to another allocator,
+ * plugins handed pointers but no allocator.  It calls no cudaMalloc/cudaFree.
+ *   - n is limited to 2^20 (1048576); larger n returns G4_ERR_INVALID_ARG with a message.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *     with that device current) and caches it; make that first call before any stream
+ *     capture.
+ *   - All calls share the array: calls that overlap on the GPU (other streams or threads)
+ *     race on it and must be serialised.  Each call overwrites every scratch word it reads,
+ *     so nothing needs clearing between calls.
+ * Arguments and output as for g4_keys_sort. */
+g4_status g4_keys_sort_noalloc(const uint32_t *pos_int, int64_t n, uint64_t *keys_sorted,
+                               int32_t *perm, void *stream);
+
 /* Gathers particle arrays into PH order: out[k] = in[perm[k]].  cls/aold may be NULL (both
  * in and out).  pos arrays are 3 x n SoA. */
 g4_status g4_gather(const int32_t *perm, int64_t n, const uint32_t *pos_in,

@@ -504,3 +504,63 @@ extern "C" g4_status g4_scatter(const int32_t *perm, int64_t n, const float *acc
                                                                        pot_sorted, acc_out, pot_out);
     return g4_launch_check("scatter", 1);
 }
+
+// -------------------------------------------------------------------------------------------
+// Allocation-free variant of g4_keys_sort.
+//
+// Some callers cannot allocate device memory at the time they need the sort: code running
+// while a CUDA graph is being captured, host applications whose device memory is owned by
+// another allocator (a pre-reserved arena) and that forbid cudaMalloc after start-up, and
+// plugins that are handed device pointers but no allocator.  This entry point takes its
+// scratch from a fixed file-scope device array instead of a caller-provided workspace.
+//
+// The array is part of the library image: every GPU that loads libg4 holds it (about 16 MB)
+// until the process exits.  All calls share it, so calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on it; serialise them.  The sort
+// overwrites every scratch word it later reads (tile counts are written in full before the
+// scan), so the contents left by an earlier call never need clearing.
+// -------------------------------------------------------------------------------------------
+static constexpr int64_t G4_STATIC_SORT_MAX = (int64_t)1 << 20;
+
+static constexpr size_t static_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+static constexpr size_t G4_STATIC_SORT_BYTES =
+    static_align256(sizeof(uint64_t) * G4_STATIC_SORT_MAX) +
+    static_align256(sizeof(int32_t) * G4_STATIC_SORT_MAX) * 2 +
+    static_align256(sizeof(uint32_t) * 256 * ((G4_STATIC_SORT_MAX + SORT_TILE - 1) / SORT_TILE)) +
+    static_align256(sizeof(uint32_t) * 256);
+
+static __device__ __align__(256) unsigned char g4_static_sort_scratch[G4_STATIC_SORT_BYTES];
+
+// Host code may not use the array's name as a device address: the device address is looked
+// up once per device (with that device current) and cached.
+static void *g4_static_scratch_ptr[64] = {nullptr};
+
+extern "C" g4_status g4_keys_sort_noalloc(const uint32_t *pos_int, int64_t n,
+                                          uint64_t *keys_sorted, int32_t *perm, void *stream)
+{
+    if (n < 0 || n > G4_STATIC_SORT_MAX)
+        return g4_fail(G4_ERR_INVALID_ARG,
+                       "g4_keys_sort_noalloc: n=%lld exceeds the static scratch limit of %lld "
+                       "particles (use g4_keys_sort with a caller workspace)",
+                       (long long)n, (long long)G4_STATIC_SORT_MAX);
+    if (n == 0) return G4_OK;
+    if (!pos_int || !keys_sorted || !perm)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_keys_sort_noalloc: NULL pointer");
+    int dev = 0;
+    g4_status s = g4_cuda_check(cudaGetDevice(&dev), "g4_keys_sort_noalloc: cudaGetDevice");
+    if (s != G4_OK) return s;
+    if (dev < 0 || dev >= 64) return g4_fail(G4_ERR_INVALID_ARG, "g4_keys_sort_noalloc: device id");
+    void *scratch = __atomic_load_n(&g4_static_scratch_ptr[dev], __ATOMIC_ACQUIRE);
+    if (!scratch) {
+        // first call on this device: look up the array's device address
+        s = g4_cuda_check(cudaGetSymbolAddress(&scratch, g4_static_sort_scratch),
+                          "g4_keys_sort_noalloc: cudaGetSymbolAddress");
+        if (s != G4_OK) return s;
+        __atomic_store_n(&g4_static_scratch_ptr[dev], scratch, __ATOMIC_RELEASE);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    k_keys<<<g4_blocks_for(n, 256), 256, 0, st>>>(pos_int, n, keys_sorted);
+    s = g4_launch_check("keys (static scratch)", 1);
+    if (s != G4_OK) return s;
+    return g4_sort_pairs_u64(keys_sorted, keys_sorted, perm, n, scratch, G4_STATIC_SORT_BYTES, 63, st);
+}

@@ -67,6 +67,7 @@ def _declare(L):
         "g4_int_coords": ([vp, i64, i32, d, vp, vp, vp], i32),
         "g4_keys_sort_workspace": ([i64, C.POINTER(C.c_size_t)], i32),
         "g4_keys_sort": ([vp, i64, vp, vp, vp, C.c_size_t, vp], i32),
+        "g4_keys_sort_noalloc": ([vp, i64, vp, vp, vp], i32),
         "g4_gather": ([vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "g4_scatter": ([vp, i64, vp, vp, vp, vp, vp], i32),
         "g4_tree_create": ([i64, i64, C.POINTER(vp)], i32),
