@@ -158,11 +158,12 @@ def run_reference(args, rank, world):
     return 0
 
 
-def config_block(world):
-    return {"workload": "periodic Zel'dovich box, 256^3 particles, L=500, rms displacement 2 "
-                        "spacings, TreePM short range r_s=1.25L/512, R_cut=4.5, eps=L/7680, "
+def config_block(world, n_side=N_SIDE):
+    L = L_BOX * n_side / N_SIDE
+    return {"workload": f"periodic Zel'dovich box, {n_side}^3 particles, L={L:g}, rms displacement 2 "
+                        f"spacings, TreePM short range r_s=1.25L/{2 * n_side}, R_cut=4.5, eps=L/{30 * n_side}, "
                         "tree p=3, alpha=0.0025, leaf 8",
-            "n_particles": N_SIDE ** 3, "order_p": 3, "alpha": 0.0025, "leaf_max": 8,
+            "n_particles": n_side ** 3, "order_p": 3, "alpha": 0.0025, "leaf_max": 8,
             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
             "l2": "inputs (335 MB) larger than L2 (129 MB); no flush"}
 
@@ -176,13 +177,15 @@ def run_gpu(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    ps = synth.zeldovich(N_SIDE, L_BOX, RMS, SEED + rank)
+    n_side = args.n_side
+    L = L_BOX * n_side / N_SIDE          # same spacing, split and softening at any size
+    ps = synth.zeldovich(n_side, L, RMS, SEED + rank)
     n = ps.n
-    wp = workload_params()
+    wp = workload_params(n_side, L)
     P = g4.params(**wp)
     PB = g4.params(**{**wp, "criterion": 1, "theta": 0.5})
     pos = torch.from_numpy(ps.pos).cuda()
-    pos_int, _ = g4.g4_int_coords(pos, True, L_BOX)
+    pos_int, _ = g4.g4_int_coords(pos, True, L)
     del pos
     mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
     tg = g4.TreeGravity(n, P)
@@ -274,7 +277,7 @@ def run_gpu(args, rank, world):
         import oracle
         sinks = synth.subset(n, 4096, 2002)
         q = pos_int.cpu().numpy().view(np.uint32)
-        OP = oracle.OracleParams(box=L_BOX, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
+        OP = oracle.OracleParams(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
                                  r_cut_factor=4.5)
         ad, _ = oracle.direct(q, ps.mass, None, sinks, OP, r_max=OP.r_cut)
         ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
@@ -296,7 +299,7 @@ def run_gpu(args, rank, world):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic", "config": config_block(world), "clocks": clk,
+                "data": "synthetic", "config": config_block(world, n_side), "clocks": clk,
                 "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": int(n * (12 + 4 + 4)),
                         "d2h_bytes_per_step": int(n * (12 + 4))},
@@ -324,6 +327,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--n-side", type=int, default=N_SIDE,
+                    help="particles per side (default 256: the headline workload; smaller sizes "
+                         "keep the spacing, split and softening, for profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

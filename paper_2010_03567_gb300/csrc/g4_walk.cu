@@ -50,14 +50,139 @@ template <int P, typename T> __device__ __forceinline__ T ipow(T x)
     return r;
 }
 
-template <int P, typename T, bool TREEPM, bool GEOM>
-__global__ void __launch_bounds__(256) k_walk(const WalkArgs A)
+constexpr int WALK_THREADS = 256;
+constexpr int WALK_WARPS = WALK_THREADS / 32;
+constexpr int LEAF_BUF = 128;
+
+// per-warp shared state: the pending leaf list of the group and a staging area of 32 sources
+struct WalkSmem {
+    int first[LEAF_BUF], count[LEAF_BUF], pref[LEAF_BUF];
+    unsigned mask[LEAF_BUF];
+    uint32_t x[32], y[32], z[32];
+    float m[32], h[32];
+    unsigned smask[32];
+    int j[32];
+};
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane)
 {
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x - v;
+}
+
+// Per-lane decision for an internal node (the single-particle walk's rule): skip beyond the
+// TreePM cutoff, open when inside the node / its exclusion zone / the softening range or
+// when the opening criterion fails, otherwise accept the multipole.
+template <int P, typename T, bool TREEPM, bool GEOM>
+__device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &nd, int k,
+                                              uint32_t xi, uint32_t yi, uint32_t zi, T hi, T crit)
+{
+    const T scale = (T)A.scale;
+    const T side = ldexp((T)A.box, -(int)(nd.meta & 31u)), half = T(0.5) * side;
+    const T dcx = (T)(int32_t)(nd.cx - xi) * scale;
+    const T dcy = (T)(int32_t)(nd.cy - yi) * scale;
+    const T dcz = (T)(int32_t)(nd.cz - zi) * scale;
+    if (TREEPM) {
+        const T ex = fmax(fabs(dcx) - half, T(0));
+        const T ey = fmax(fabs(dcy) - half, T(0));
+        const T ez = fmax(fabs(dcz) - half, T(0));
+        if (ex * ex + ey * ey + ez * ez > (T)A.rcut2) return ACT_SKIP;
+    }
+    T ox, oy, oz, M;
+    if (sizeof(T) == 8 && A.qd) {
+        const double *dd = A.qd + (size_t)k * (4 + A.nq);
+        ox = (T)dd[0]; oy = (T)dd[1]; oz = (T)dd[2]; M = (T)dd[3];
+    } else {
+        ox = (T)nd.sx; oy = (T)nd.sy; oz = (T)nd.sz; M = (T)nd.mass;
+    }
+    const T rx = dcx + ox, ry = dcy + oy, rz = dcz + oz;
+    const T r2 = rx * rx + ry * ry + rz * rz;
+    const T dmax = fmax(fabs(dcx), fmax(fabs(dcy), fabs(dcz)));
+    const T h = fmax(hi, (T)nd.hmax);
+    bool open = (dmax <= half) || (A.exclusion && dmax < side) || (r2 < h * h);
+    if (!open) {
+        if (GEOM) open = side * side >= (T)A.theta2 * r2;
+        else open = !((T)A.G * M * ipow<P>(side) < crit * ipow<P + 2>(sqrt(r2)));
+    }
+    return open ? ACT_OPEN : ACT_ACCEPT;
+}
+
+// particle-particle terms of the group's sinks with the particles of the pending leaves;
+// every lane takes the sources in the list order, masked by the lanes that reach each leaf
+template <typename T, bool TREEPM>
+__device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nleaf, int total,
+                                         int lane, int i, uint32_t xi, uint32_t yi, uint32_t zi,
+                                         T hi, T &ax, T &ay, T &az, T &ap, uint32_t &npp)
+{
+    const T scale = (T)A.scale, as = (T)A.as, rcut2 = (T)A.rcut2;
+    for (int b = 0; b < total; b += 32) {
+        const int t = b + lane;
+        if (t < total) {
+            int lo = 0, hi_ = nleaf - 1;
+            while (lo < hi_) {
+                const int mid = (lo + hi_ + 1) >> 1;
+                if (S.pref[mid] <= t) lo = mid;
+                else hi_ = mid - 1;
+            }
+            const int j = S.first[lo] + (t - S.pref[lo]);
+            S.x[lane] = __ldg(A.pos + j);
+            S.y[lane] = __ldg(A.pos + A.n + j);
+            S.z[lane] = __ldg(A.pos + 2 * A.n + j);
+            S.m[lane] = __ldg(A.mass + j);
+            S.h[lane] = A.h_cls[A.cls ? __ldg(A.cls + j) : 0];
+            S.smask[lane] = S.mask[lo];
+            S.j[lane] = j;
+        }
+        __syncwarp();
+        const int nb = min(32, total - b);
+        for (int u = 0; u < nb; u++) {
+            const unsigned mk = S.smask[u];
+            const int j = S.j[u];
+            if (((mk >> lane) & 1u) && j != i) {
+                const T dx = (T)(int32_t)(S.x[u] - xi) * scale;
+                const T dy = (T)(int32_t)(S.y[u] - yi) * scale;
+                const T dz = (T)(int32_t)(S.z[u] - zi) * scale;
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                if (!(TREEPM && A.pp_cut && r2 >= rcut2)) {
+                    T g0, g1;
+                    pair_kernel<T, TREEPM>(r2, fmax(hi, (T)S.h[u]), as, g0, g1);
+                    const T mj = (T)S.m[u];
+                    const T mg1 = mj * g1;
+                    ax += mg1 * dx;
+                    ay += mg1 * dy;
+                    az += mg1 * dz;
+                    ap += mj * g0;
+                    npp++;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// The group walk.  Nodes are scanned in depth-first order in windows of 32 (one node per lane,
+// coalesced loads).  A node is visited unless an earlier node of the window that the group
+// skipped covers it (prefix maximum of the skipped subtrees' ends).  Group-level tests are
+// conservative: a node is skipped only if its cube is beyond r_cut of the group's bounding
+// box, and it needs per-lane decisions ("maybe") only if some sink could possibly accept its
+// multipole.  Leaves go to the pending list with the mask of lanes that reach them; "maybe"
+// nodes get the exact per-lane decision, and a lane that accepts or skips one resumes after
+// its subtree, exactly as a single-particle walk would.
+template <int P, typename T, bool TREEPM, bool GEOM>
+__global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
+{
+    __shared__ WalkSmem smem[WALK_WARPS];
+    WalkSmem &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     if (*A.flags & G4_FLAG_CAPACITY) return;   // incomplete tree: outputs left untouched
     const int nn = A.lvl[G4_NLEVELS];
-    const T scale = (T)A.scale, G = (T)A.G, as = (T)A.as, rcut2 = (T)A.rcut2;
-    const T theta2 = (T)A.theta2, alpha = (T)A.alpha;
+    const float fscale = (float)A.scale, fbox = (float)A.box;
     const int ngroups = (A.n_sinks + 31) >> 5;
     for (;;) {
         int g = 0;
@@ -66,111 +191,178 @@ __global__ void __launch_bounds__(256) k_walk(const WalkArgs A)
         if (g >= ngroups) break;
         const int s = g * 32 + lane;
         const bool valid = s < A.n_sinks;
-        const int i = valid ? (A.active ? A.active[s] : s) : 0;
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        const int i = valid ? (A.active ? A.active[s] : s) : (A.active ? A.active[g * 32] : g * 32);
         const uint32_t xi = A.pos[i], yi = A.pos[A.n + i], zi = A.pos[2 * A.n + i];
         const T hi = (T)A.h_cls[A.cls ? A.cls[i] : 0];
-        const T crit = GEOM ? T(0) : alpha * (T)(A.aold ? A.aold[i] : 0.f);
-        T sx = T(0), sy = T(0), sz = T(0), sp = T(0);
+        const T crit = GEOM ? T(0) : (T)A.alpha * (T)(A.aold ? A.aold[i] : 0.f);
+        // group bounding box, in integer offsets from lane 0's sink
+        const uint32_t x0 = __shfl_sync(0xffffffffu, xi, 0), y0 = __shfl_sync(0xffffffffu, yi, 0),
+                       z0 = __shfl_sync(0xffffffffu, zi, 0);
+        const int ox = (int32_t)(xi - x0), oy = (int32_t)(yi - y0), oz = (int32_t)(zi - z0);
+        const int lox = __reduce_min_sync(0xffffffffu, ox), hix = __reduce_max_sync(0xffffffffu, ox);
+        const int loy = __reduce_min_sync(0xffffffffu, oy), hiy = __reduce_max_sync(0xffffffffu, oy);
+        const int loz = __reduce_min_sync(0xffffffffu, oz), hiz = __reduce_max_sync(0xffffffffu, oz);
+        const uint32_t gcx = x0 + (uint32_t)(int)(((long long)lox + hix) >> 1);
+        const uint32_t gcy = y0 + (uint32_t)(int)(((long long)loy + hiy) >> 1);
+        const uint32_t gcz = z0 + (uint32_t)(int)(((long long)loz + hiz) >> 1);
+        const float ghx = (0.5f * (float)((long long)hix - lox) + 2.f) * fscale;
+        const float ghy = (0.5f * (float)((long long)hiy - loy) + 2.f) * fscale;
+        const float ghz = (0.5f * (float)((long long)hiz - loz) + 2.f) * fscale;
+        float critmax = (float)crit;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) critmax = fmaxf(critmax, __shfl_xor_sync(0xffffffffu, critmax, o));
+        critmax *= 1.001f;
+
+        T ax = T(0), ay = T(0), az = T(0), ap = T(0);     // particle-particle sums
+        T bx = T(0), by = T(0), bz = T(0), bp = T(0);     // particle-node sums
         uint32_t npp = 0, npn = 0;
         int resume = valid ? 0 : 0x7fffffff;
-        int k = __reduce_min_sync(0xffffffffu, resume);
+        int nleaf = 0, total = 0;
+        int k = 0;
         while (k < nn) {
-            const G4Node nd = load_node(A.node + k);
-            const int lv = nd.meta & 31u;
-            const bool leaf = nd.meta & 32u;
-            const T side = ldexp((T)A.box, -lv), half = T(0.5) * side;
-            int act = ACT_NONE;
-            if (resume <= k) {
-                const T dcx = (T)(int32_t)(nd.cx - xi) * scale;
-                const T dcy = (T)(int32_t)(nd.cy - yi) * scale;
-                const T dcz = (T)(int32_t)(nd.cz - zi) * scale;
-                bool skip = false;
+            const int j = k + lane;
+            const bool vj = j < nn;
+            G4Node nd;
+            if (vj) nd = load_node(A.node + j);
+            const bool leaf = vj && (nd.meta & 32u);
+            bool gskip = false, maybe = false;
+            if (vj) {
+                const float side = ldexpf(fbox, -(int)(nd.meta & 31u)), half = 0.5f * side;
+                const float dcx = (float)(int32_t)(nd.cx - gcx) * fscale;
+                const float dcy = (float)(int32_t)(nd.cy - gcy) * fscale;
+                const float dcz = (float)(int32_t)(nd.cz - gcz) * fscale;
                 if (TREEPM) {
-                    const T ex = fmax(fabs(dcx) - half, T(0));
-                    const T ey = fmax(fabs(dcy) - half, T(0));
-                    const T ez = fmax(fabs(dcz) - half, T(0));
-                    skip = ex * ex + ey * ey + ez * ez > rcut2;
+                    const float ex = fmaxf(fabsf(dcx) - half - ghx, 0.f);
+                    const float ey = fmaxf(fabsf(dcy) - half - ghy, 0.f);
+                    const float ez = fmaxf(fabsf(dcz) - half - ghz, 0.f);
+                    gskip = ex * ex + ey * ey + ez * ez > 1.0001f * (float)A.rcut2;
                 }
-                if (skip) {
-                    act = ACT_SKIP;
-                } else if (leaf) {
-                    act = ACT_LEAF;
-                } else {
-                    T ox, oy, oz, M;
-                    if (sizeof(T) == 8 && A.qd) {
-                        const double *dd = A.qd + (size_t)k * (4 + A.nq);
-                        ox = (T)dd[0]; oy = (T)dd[1]; oz = (T)dd[2]; M = (T)dd[3];
+                if (!gskip && !leaf) {
+                    // can any sink of the group accept this node's multipole?
+                    bool none = false;
+                    if (A.exclusion && fmaxf(fabsf(dcx) + ghx, fmaxf(fabsf(dcy) + ghy, fabsf(dcz) + ghz)) < 0.999f * side)
+                        none = true;
+                    const float fx = fabsf(dcx + nd.sx) + ghx, fy = fabsf(dcy + nd.sy) + ghy,
+                                fz = fabsf(dcz + nd.sz) + ghz;
+                    const float rmax2 = (fx * fx + fy * fy + fz * fz) * 1.001f;
+                    if (rmax2 < nd.hmax * nd.hmax) none = true;
+                    if (GEOM) {
+                        if (side * side >= (float)A.theta2 * rmax2) none = true;
                     } else {
-                        ox = (T)nd.sx; oy = (T)nd.sy; oz = (T)nd.sz; M = (T)nd.mass;
+                        const float rmax = sqrtf(rmax2);
+                        if (!((float)A.G * nd.mass * ipow<P>(side) < critmax * ipow<P + 2>(rmax))) none = true;
                     }
-                    const T rx = dcx + ox, ry = dcy + oy, rz = dcz + oz;
-                    const T r2 = rx * rx + ry * ry + rz * rz;
-                    const T dmax = fmax(fabs(dcx), fmax(fabs(dcy), fabs(dcz)));
-                    const T h = fmax(hi, (T)nd.hmax);
-                    bool open = (dmax <= half) || (A.exclusion && dmax < side) || (r2 < h * h);
-                    if (!open) {
-                        if (GEOM) {
-                            open = side * side >= theta2 * r2;
-                        } else {
-                            const T r = sqrt(r2);
-                            open = !(G * M * ipow<P>(side) < crit * ipow<P + 2>(r));
-                        }
-                    }
-                    act = open ? ACT_OPEN : ACT_ACCEPT;
+                    maybe = !none;
                 }
-                resume = (act == ACT_OPEN) ? k + 1 : max(nd.next, k + 1);
             }
-            if (__any_sync(0xffffffffu, act == ACT_ACCEPT) && act == ACT_ACCEPT) {
-                T Qs[g4_nq(P) > 0 ? g4_nq(P) : 1];
-                T ox, oy, oz, M;
-                if (sizeof(T) == 8 && A.qd) {
-                    const double *dd = A.qd + (size_t)k * (4 + A.nq);
-                    ox = (T)dd[0]; oy = (T)dd[1]; oz = (T)dd[2]; M = (T)dd[3];
+            // depth-first coverage inside the window by skipped subtrees
+            int e = (vj && gskip) ? nd.next : 0;
+            int pm = e;
 #pragma unroll
-                    for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)dd[4 + c];
-                } else {
-                    ox = (T)nd.sx; oy = (T)nd.sy; oz = (T)nd.sz; M = (T)nd.mass;
-                    const float *qq = A.q + (size_t)k * A.nq;
-#pragma unroll
-                    for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)__ldg(qq + c);
-                }
-                const T rx = (T)(int32_t)(nd.cx - xi) * scale + ox;
-                const T ry = (T)(int32_t)(nd.cy - yi) * scale + oy;
-                const T rz = (T)(int32_t)(nd.cz - zi) * scale + oz;
-                pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, as, sx, sy, sz, sp);
-                npn++;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, pm, o);
+                if (lane >= o) pm = max(pm, y);
             }
-            if (__any_sync(0xffffffffu, act == ACT_LEAF)) {
-                const int f = max(nd.first, 0), e = min(nd.first + nd.count, A.n);
-                for (int j = f; j < e; j++) {
-                    const uint32_t xj = __ldg(A.pos + j), yj = __ldg(A.pos + A.n + j),
-                                   zj = __ldg(A.pos + 2 * A.n + j);
-                    const T mj = (T)__ldg(A.mass + j);
-                    const T hj = (T)A.h_cls[A.cls ? __ldg(A.cls + j) : 0];
-                    if (act == ACT_LEAF && j != i) {
-                        const T dx = (T)(int32_t)(xj - xi) * scale;
-                        const T dy = (T)(int32_t)(yj - yi) * scale;
-                        const T dz = (T)(int32_t)(zj - zi) * scale;
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        if (!(TREEPM && A.pp_cut && r2 >= rcut2)) {
-                            T g0, g1;
-                            pair_kernel<T, TREEPM>(r2, fmax(hi, hj), as, g0, g1);
-                            sx += mj * g1 * dx;
-                            sy += mj * g1 * dy;
-                            sz += mj * g1 * dz;
-                            sp += mj * g0;
-                            npp++;
+            int excl = __shfl_up_sync(0xffffffffu, pm, 1);
+            if (lane == 0) excl = 0;
+            const bool visited = vj && excl <= j && !gskip;
+            int knext = max(k + 32, __shfl_sync(0xffffffffu, pm, 31));
+            const unsigned leafm = __ballot_sync(0xffffffffu, visited && leaf);
+            const unsigned maybem = __ballot_sync(0xffffffffu, visited && maybe);
+            const bool all_active = __all_sync(0xffffffffu, !valid || resume <= k);
+            if (maybem == 0 && all_active) {
+                const int nnew = __popc(leafm);
+                if (nnew > 0) {
+                    if (nleaf + nnew > LEAF_BUF) {
+                        pp_flush<T, TREEPM>(A, S, nleaf, total, lane, i, xi, yi, zi, hi, ax, ay, az, ap, npp);
+                        nleaf = 0;
+                        total = 0;
+                    }
+                    const bool me = (leafm >> lane) & 1u;
+                    const int cnt = me ? nd.count : 0;
+                    const int pre = warp_excl_scan(cnt, lane);
+                    if (me) {
+                        const int pos = nleaf + __popc(leafm & lt);
+                        S.first[pos] = nd.first;
+                        S.count[pos] = nd.count;
+                        S.mask[pos] = vmask;
+                        S.pref[pos] = total + pre;
+                    }
+                    total += __shfl_sync(0xffffffffu, pre + cnt, 31);
+                    nleaf += nnew;
+                    __syncwarp();
+                }
+            } else {
+                // events in depth-first order: leaves get the mask of lanes still walking
+                // there; "maybe" nodes get exact per-lane decisions
+                unsigned ev = leafm | maybem;
+                int skip_until = 0;
+                while (ev) {
+                    const int src = __ffs(ev) - 1;
+                    ev &= ev - 1u;
+                    const int jj = k + src;
+                    if (jj < skip_until) continue;
+                    const G4Node n2 = load_node(A.node + jj);
+                    if ((leafm >> src) & 1u) {
+                        const unsigned m = __ballot_sync(0xffffffffu, resume <= jj);
+                        if (m) {
+                            if (nleaf + 1 > LEAF_BUF) {
+                                pp_flush<T, TREEPM>(A, S, nleaf, total, lane, i, xi, yi, zi, hi, ax, ay, az, ap, npp);
+                                nleaf = 0;
+                                total = 0;
+                            }
+                            if (lane == 0) {
+                                S.first[nleaf] = n2.first;
+                                S.count[nleaf] = n2.count;
+                                S.mask[nleaf] = m;
+                                S.pref[nleaf] = total;
+                            }
+                            __syncwarp();
+                            nleaf++;
+                            total += n2.count;
                         }
+                    } else {
+                        int act = ACT_NONE;
+                        if (resume <= jj) {
+                            act = exact_decision<P, T, TREEPM, GEOM>(A, n2, jj, xi, yi, zi, hi, crit);
+                            if (act != ACT_OPEN) resume = max(n2.next, jj + 1);
+                        }
+                        if (__any_sync(0xffffffffu, act == ACT_ACCEPT) && act == ACT_ACCEPT) {
+                            T Qs[g4_nq(P) > 0 ? g4_nq(P) : 1];
+                            T mx, my, mz, M;
+                            if (sizeof(T) == 8 && A.qd) {
+                                const double *dd = A.qd + (size_t)jj * (4 + A.nq);
+                                mx = (T)dd[0]; my = (T)dd[1]; mz = (T)dd[2]; M = (T)dd[3];
+#pragma unroll
+                                for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)dd[4 + c];
+                            } else {
+                                mx = (T)n2.sx; my = (T)n2.sy; mz = (T)n2.sz; M = (T)n2.mass;
+                                const float *qq = A.q + (size_t)jj * A.nq;
+#pragma unroll
+                                for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)__ldg(qq + c);
+                            }
+                            const T rx = (T)(int32_t)(n2.cx - xi) * (T)A.scale + mx;
+                            const T ry = (T)(int32_t)(n2.cy - yi) * (T)A.scale + my;
+                            const T rz = (T)(int32_t)(n2.cz - zi) * (T)A.scale + mz;
+                            pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, (T)A.as, bx, by, bz, bp);
+                            npn++;
+                        }
+                        if (__all_sync(0xffffffffu, resume > jj + 1 || !valid)) skip_until = max(n2.next, jj + 1);
                     }
                 }
+                knext = max(knext, skip_until);
             }
-            k = __reduce_min_sync(0xffffffffu, resume);
+            k = knext;
         }
+        if (nleaf > 0)
+            pp_flush<T, TREEPM>(A, S, nleaf, total, lane, i, xi, yi, zi, hi, ax, ay, az, ap, npp);
         if (valid) {
-            A.acc[i] = (float)(-G * sx);
-            A.acc[A.n + i] = (float)(-G * sy);
-            A.acc[2 * A.n + i] = (float)(-G * sz);
-            if (A.pot) A.pot[i] = (float)(-G * sp);
+            const T G = (T)A.G;
+            A.acc[i] = (float)(-G * (ax + bx));
+            A.acc[A.n + i] = (float)(-G * (ay + by));
+            A.acc[2 * A.n + i] = (float)(-G * (az + bz));
+            if (A.pot) A.pot[i] = (float)(-G * (ap + bp));
             if (A.counts) {
                 A.counts[i] = npp;
                 A.counts[A.n + i] = npn;
