@@ -43,10 +43,13 @@ FLOPS_PN = {1: 40, 2: 110, 3: 170, 4: 300, 5: 480}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA x max clock
 
 
-def workload_params(n_side=N_SIDE, L=L_BOX):
+LEAF_MAX = 8
+
+
+def workload_params(n_side=N_SIDE, L=L_BOX, leaf_max=None):
     d = L / n_side
     return dict(box_size=L, periodic=1, r_s=1.25 * L / (2 * n_side), r_cut_factor=4.5,
-                eps=[d / 30.0], alpha=0.0025, order_p=3, leaf_max=8)
+                eps=[d / 30.0], alpha=0.0025, order_p=3, leaf_max=leaf_max or LEAF_MAX)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -181,7 +184,7 @@ def run_gpu(args, rank, world):
     L = L_BOX * n_side / N_SIDE          # same spacing, split and softening at any size
     ps = synth.zeldovich(n_side, L, RMS, SEED + rank)
     n = ps.n
-    wp = workload_params(n_side, L)
+    wp = workload_params(n_side, L, args.leaf_max)
     P = g4.params(**wp)
     PB = g4.params(**{**wp, "criterion": 1, "theta": 0.5})
     pos = torch.from_numpy(ps.pos).cuda()
@@ -327,6 +330,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--leaf-max", type=int, default=None,
+                    help="leaf threshold of the tree (default: the tuned value)")
     ap.add_argument("--n-side", type=int, default=N_SIDE,
                     help="particles per side (default 256: the headline workload; smaller sizes "
                          "keep the spacing, split and softening, for profiling)")

@@ -136,6 +136,18 @@ g4_status g4_keys_sort(const uint32_t *pos_int, int64_t n, uint64_t *keys_sorted
 g4_status g4_keys_sort_noalloc(const uint32_t *pos_int, int64_t n, uint64_t *keys_sorted,
                                int32_t *perm, void *stream);
 
+/* Batched independent systems (a forest), e.g. many small isolated systems solved together:
+ * bytes of workspace for g4_keys_sort_batched. */
+g4_status g4_keys_sort_batched_workspace(int64_t n, size_t *bytes);
+
+/* Stable sort of n particles by (system id, Peano-Hilbert key): particles of system s end up
+ * contiguous, in PH order within the system.  sys_id: n uint16 (device, < 65536 systems);
+ * pos_int as for g4_keys_sort (each system in its own integer frame); keys_sorted, perm as
+ * for g4_keys_sort; workspace >= g4_keys_sort_batched_workspace(n), 256-byte aligned. */
+g4_status g4_keys_sort_batched(const uint32_t *pos_int, int64_t n, const uint16_t *sys_id,
+                               uint64_t *keys_sorted, int32_t *perm, void *workspace,
+                               size_t workspace_bytes, void *stream);
+
 /* Gathers particle arrays into PH order: out[k] = in[perm[k]].  cls/aold may be NULL (both
  * in and out).  pos arrays are 3 x n SoA. */
 g4_status g4_gather(const int32_t *perm, int64_t n, const uint32_t *pos_in,
@@ -166,6 +178,19 @@ void g4_tree_free(g4_tree tree);
  * g4_tree_status (G4_ERR_CAPACITY). */
 g4_status g4_tree_build(g4_tree tree, const uint64_t *keys_sorted, const uint32_t *pos_sorted,
                         int64_t n, const g4_params *params, void *stream);
+
+/* Builds one oct-tree per system in a single call sequence (a forest; Sec. 2.2.1 per system).
+ * keys_sorted/pos_sorted: output of g4_keys_sort_batched plus g4_gather; sys_first: n_sys + 1
+ * int32 (device) giving each system's first sorted index (sys_first[n_sys] = n; systems must
+ * be non-empty); sys_box: n_sys doubles (device), the physical size of each system's 2^32
+ * integer range (the `side` of its isolated frame, or its periodic box).  Both arrays are
+ * read by later g4_multipoles / g4_gravity_tree calls on this handle and must stay valid.
+ * Roots are numbered in system order; g4_gravity_tree then walks each sink only through its
+ * own system's tree, all systems in one persistent launch (params.box_size is ignored). */
+g4_status g4_tree_build_forest(g4_tree tree, const uint64_t *keys_sorted,
+                               const uint32_t *pos_sorted, int64_t n, const int32_t *sys_first,
+                               const double *sys_box, int32_t n_sys, const g4_params *params,
+                               void *stream);
 
 /* Synchronises `stream`, then reports the node count, deepest level and the device error
  * flags of the last build/walk.  Returns G4_ERR_CAPACITY / G4_ERR_TIMEOUT when a kernel
@@ -228,6 +253,57 @@ g4_status g4_gravity_fmm(g4_tree tree, const uint32_t *pos_sorted, const float *
                          const uint8_t *cls_sorted, const g4_params *params, float *acc,
                          float *pot, uint32_t *counts, double *momentum_out, void *workspace,
                          size_t workspace_bytes, void *stream);
+
+/* ---- learned cost model for scheduling the walk (no counterpart in the paper's method; its
+ *      load-balancing cost q_i is the interaction count of the last force computation,
+ *      Sec. 6.1, which these calls learn to predict) --------------------------------------- */
+
+/* Number of float parameters of the 6 -> 32 -> 32 -> 1 MLP (1313): W1[32][6], b1[32],
+ * W2[32][32], b2[32], W3[32], b3. */
+int32_t g4_mlp_param_count(void);
+
+/* Six features per PH-sorted particle of a built tree, row-major n x 6 floats: leaf
+ * occupancy / leaf_max, leaf depth / 21, log10 |a_old|, time bin / 8, log2(parent count)/24,
+ * log2(grandparent count)/24.  aold_sorted, bins_sorted (uint8 time bins) may be NULL.
+ * leaf_scratch: n int32 of device scratch. */
+g4_status g4_cost_features(g4_tree tree, const float *aold_sorted, const uint8_t *bins_sorted,
+                           const g4_params *params, float *features, int32_t *leaf_scratch,
+                           void *stream);
+
+/* Cost labels from the counts of the last walk: labels[i] = log(1 + PP_i + c_pn * PN_i).
+ * counts: 2 x n uint32 as written by g4_gravity_tree. */
+g4_status g4_cost_labels(const uint32_t *counts, int64_t n, float c_pn, float *labels, void *stream);
+
+/* Inference: out[i] = MLP(features[i]) with BF16 weights and activations, FP32 sums. */
+g4_status g4_mlp_forward(const float *params, const float *features, int64_t n, float *out,
+                         void *stream);
+
+/* Bytes of device workspace for g4_mlp_train_step on n samples. */
+g4_status g4_mlp_train_workspace(int64_t n, size_t *bytes);
+
+/* One Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected with `step` >= 1) on the mean
+ * squared error between MLP(features) and labels over all n samples; params, adam_m, adam_v:
+ * g4_mlp_param_count() floats each (device, FP32 masters, updated in place).  lr = 0 only
+ * computes the gradient.  loss_out (1 float) and grad_out (param count floats) are device
+ * pointers and may be NULL.  The gradient is reduced in a fixed order (deterministic). */
+g4_status g4_mlp_train_step(float *params, float *adam_m, float *adam_v, int32_t step,
+                            const float *features, const float *labels, int64_t n, float lr,
+                            float *loss_out, float *grad_out, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
+/* Bytes of device workspace for g4_schedule_lpt with n sinks. */
+g4_status g4_schedule_workspace(int64_t n, size_t *bytes);
+
+/* Longest-processing-time schedule of the walk: group g holds sorted sinks [32g, 32g+32);
+ * its predicted cost is the sum of expm1(pred) over its sinks; group_order (ceil(n/32) int32,
+ * device) lists the groups by descending predicted cost (ties in PH order). */
+g4_status g4_schedule_lpt(const float *pred_sorted, int64_t n, int32_t *group_order,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Makes later g4_gravity_tree calls on this handle hand out groups in `group_order`
+ * (device array of ngroups = ceil(n/32) entries, kept by pointer; NULL restores PH order).
+ * Used only for whole-set walks of a single system whose group count matches. */
+g4_status g4_tree_set_group_order(g4_tree tree, const int32_t *group_order, int64_t ngroups);
 
 /* ---- helper: direct summation on the GPU --------------------------------------------------- */
 

@@ -1,0 +1,347 @@
+// g4_cost.cu -- learned cost model for scheduling the tree walk.
+//
+// The paper balances work with a cost factor q_i per particle: the number of interactions of
+// its last force computation (Sec. 6.1).  Here a small MLP predicts that cost from cheap
+// per-particle tree features, and the walk's 32-sink groups are handed out heaviest first
+// (longest-processing-time order) through the walk's device work queue.  Forces do not depend
+// on the order: every group's result is the same whichever warp computes it and whenever.
+//
+// Model: 6 -> 32 -> 32 -> 1, ReLU, weights and activations stored in BF16 with FP32
+// accumulation; FP32 master weights trained by Adam on the mean squared error of
+// log(1 + cost).  Parameter layout (1313 floats):
+//   W1[32][6], b1[32], W2[32][32], b2[32], W3[32], b3.
+#include <cuda_bf16.h>
+
+#include "g4_internal.cuh"
+
+namespace {
+
+constexpr int F = 6, H = 32;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * F, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H,
+              OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + H, NPARAM = OFF_B3 + 1;
+static_assert(NPARAM == 1313, "parameter count");
+constexpr int MLP_THREADS = 256;
+
+__device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16(x)); }
+
+// ---- features --------------------------------------------------------------------------------
+
+__global__ void k_leaf_of(const G4Node *__restrict__ node, const int32_t *__restrict__ lvl,
+                          int32_t *__restrict__ leaf_of)
+{
+    const int total = lvl[G4_NLEVELS];
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < total; d += gridDim.x * blockDim.x) {
+        const G4Node nd = node[d];
+        if (nd.meta & 32u)
+            for (int i = nd.first; i < nd.first + nd.count; i++) leaf_of[i] = d;
+    }
+}
+
+// Six features per (sorted) particle: leaf occupancy / leaf_max, leaf depth / 21,
+// log10 |a_old|, time bin / 8, log2 of the parent node's particle count / 24 (local node
+// count), log2 of the grandparent's count / 24 (density of the PH-key prefix two levels up).
+__global__ void k_features(const G4Node *__restrict__ node, const int32_t *__restrict__ leaf_of,
+                           const float *__restrict__ aold, const uint8_t *__restrict__ bins, int n,
+                           float inv_leaf, float *__restrict__ feat)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int d = leaf_of[i];
+        const G4Node lf = node[d];
+        const int p = lf.parent >= 0 ? lf.parent : d;
+        const G4Node pn = node[p];
+        const int gp = pn.parent >= 0 ? pn.parent : p;
+        const int gc = node[gp].count;
+        const float a = aold ? fmaxf(aold[i], 1e-30f) : 1.0f;
+        float *f = feat + (size_t)i * F;
+        f[0] = (float)lf.count * inv_leaf;
+        f[1] = (float)(lf.meta & 31u) * (1.0f / 21.0f);
+        f[2] = log10f(a);
+        f[3] = bins ? (float)bins[i] * 0.125f : 0.0f;
+        f[4] = log2f((float)pn.count + 1.0f) * (1.0f / 24.0f);
+        f[5] = log2f((float)gc + 1.0f) * (1.0f / 24.0f);
+    }
+}
+
+// cost label of the last walk: log(1 + PP + c_pn * PN)
+__global__ void k_cost_label(const uint32_t *__restrict__ counts, int n, float c_pn,
+                             float *__restrict__ y)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = log1pf((float)counts[i] + c_pn * (float)counts[n + i]);
+}
+
+// ---- MLP forward / backward --------------------------------------------------------------------
+
+struct SW {
+    __nv_bfloat16 w1[H * F], w2[H * H], w3[H];
+    float b1[H], b2[H], b3;
+};
+
+__device__ __forceinline__ void load_weights(SW &s, const float *__restrict__ P)
+{
+    for (int k = threadIdx.x; k < H * F; k += blockDim.x) s.w1[k] = __float2bfloat16(P[OFF_W1 + k]);
+    for (int k = threadIdx.x; k < H * H; k += blockDim.x) s.w2[k] = __float2bfloat16(P[OFF_W2 + k]);
+    for (int k = threadIdx.x; k < H; k += blockDim.x) {
+        s.w3[k] = __float2bfloat16(P[OFF_W3 + k]);
+        s.b1[k] = P[OFF_B1 + k];
+        s.b2[k] = P[OFF_B2 + k];
+    }
+    if (threadIdx.x == 0) s.b3 = P[OFF_B3];
+}
+
+// forward of one sample: BF16 inputs/weights/activations, FP32 sums
+__device__ __forceinline__ float mlp_forward(const SW &s, const float *x_in, float *h1, float *h2)
+{
+    float x[F];
+#pragma unroll
+    for (int k = 0; k < F; k++) x[k] = bf(x_in[k]);
+#pragma unroll 4
+    for (int j = 0; j < H; j++) {
+        float a = s.b1[j];
+#pragma unroll
+        for (int k = 0; k < F; k++) a += __bfloat162float(s.w1[j * F + k]) * x[k];
+        h1[j] = bf(fmaxf(a, 0.f));
+    }
+#pragma unroll 2
+    for (int j = 0; j < H; j++) {
+        float a = s.b2[j];
+#pragma unroll
+        for (int k = 0; k < H; k++) a += __bfloat162float(s.w2[j * H + k]) * h1[k];
+        h2[j] = bf(fmaxf(a, 0.f));
+    }
+    float y = s.b3;
+#pragma unroll
+    for (int k = 0; k < H; k++) y += __bfloat162float(s.w3[k]) * h2[k];
+    return y;
+}
+
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_forward(const float *__restrict__ P,
+                                                             const float *__restrict__ feat, int n,
+                                                             float *__restrict__ out)
+{
+    __shared__ SW s;
+    load_weights(s, P);
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float h1[H], h2[H];
+        out[i] = mlp_forward(s, feat + (size_t)i * F, h1, h2);
+    }
+}
+
+// Per-block gradient of the mean squared error over the block's samples (FP32), written to
+// gpart[block][NPARAM]; the loss sum goes to gpart[block][NPARAM].  A fixed-order reduction
+// follows, so training is deterministic.
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_grad(const float *__restrict__ P,
+                                                          const float *__restrict__ feat,
+                                                          const float *__restrict__ y, int n,
+                                                          float inv_n, float *__restrict__ gpart)
+{
+    __shared__ SW s;
+    __shared__ float g[MLP_THREADS / 32][NPARAM + 1];   // one row per warp: no atomics
+    load_weights(s, P);
+    for (int k = threadIdx.x; k < (MLP_THREADS / 32) * (NPARAM + 1); k += blockDim.x)
+        (&g[0][0])[k] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        const bool ok = i < n;
+        float x[F], h1[H], h2[H];
+        float e = 0.f;
+        if (ok) {
+#pragma unroll
+            for (int k = 0; k < F; k++) x[k] = bf(feat[(size_t)i * F + k]);
+            const float out = mlp_forward(s, feat + (size_t)i * F, h1, h2);
+            e = out - y[i];
+        } else {
+#pragma unroll
+            for (int k = 0; k < F; k++) x[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < H; k++) h1[k] = h2[k] = 0.f;
+        }
+        const float dy = 2.f * e * inv_n;      // d(mean sq. error)/d(output)
+        // layer 3
+        float d2[H];
+#pragma unroll
+        for (int k = 0; k < H; k++) d2[k] = (h2[k] > 0.f) ? dy * __bfloat162float(s.w3[k]) : 0.f;
+        // warp-reduce each gradient component, one shared atomic per warp
+        auto acc = [&](int idx, float v) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) g[w][idx] += v;
+        };
+        for (int k = 0; k < H; k++) acc(OFF_W3 + k, dy * h2[k]);
+        acc(OFF_B3, dy);
+        acc(NPARAM, ok ? e * e * inv_n : 0.f);
+        // layer 2
+        float d1[H];
+#pragma unroll
+        for (int k = 0; k < H; k++) d1[k] = 0.f;
+        for (int j = 0; j < H; j++) {
+            acc(OFF_B2 + j, d2[j]);
+            for (int k = 0; k < H; k++) {
+                acc(OFF_W2 + j * H + k, d2[j] * h1[k]);
+                d1[k] += d2[j] * __bfloat162float(s.w2[j * H + k]);
+            }
+        }
+        // layer 1
+        for (int j = 0; j < H; j++) {
+            const float dj = (h1[j] > 0.f) ? d1[j] : 0.f;
+            acc(OFF_B1 + j, dj);
+#pragma unroll
+            for (int k = 0; k < F; k++) acc(OFF_W1 + j * F + k, dj * x[k]);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k <= NPARAM; k += blockDim.x) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < MLP_THREADS / 32; q++) t += g[q][k];
+        gpart[(size_t)blockIdx.x * (NPARAM + 1) + k] = t;
+    }
+}
+
+// fixed-order reduction of the per-block gradients, then one Adam step on the FP32 masters
+__global__ void k_mlp_adam(float *__restrict__ P, float *__restrict__ m, float *__restrict__ v,
+                           const float *__restrict__ gpart, int nblocks, float lr, float b1,
+                           float b2, float eps, int step, float *__restrict__ grad_out,
+                           float *__restrict__ loss_out)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= NPARAM; k += gridDim.x * blockDim.x) {
+        float gk = 0.f;
+        for (int b = 0; b < nblocks; b++) gk += gpart[(size_t)b * (NPARAM + 1) + k];
+        if (k == NPARAM) {
+            if (loss_out) *loss_out = gk;
+            continue;
+        }
+        if (grad_out) grad_out[k] = gk;
+        if (lr > 0.f) {
+            const float mk = b1 * m[k] + (1.f - b1) * gk;
+            const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+            m[k] = mk;
+            v[k] = vk;
+            const float mh = mk / (1.f - powf(b1, (float)step));
+            const float vh = vk / (1.f - powf(b2, (float)step));
+            P[k] -= lr * mh / (sqrtf(vh) + eps);
+        }
+    }
+}
+
+// ---- longest-processing-time order of the walk groups ----------------------------------------
+
+__global__ void k_group_cost(const float *__restrict__ pred, int n, int ngroups,
+                             uint64_t *__restrict__ key)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+        float c = 0.f;
+        const int e = min(n, g * 32 + 32);
+        for (int i = g * 32; i < e; i++) c += expm1f(fmaxf(pred[i], 0.f));
+        // descending cost = ascending complement of the (non-negative) float bits
+        key[g] = (uint64_t)(0xFFFFFFFFu - __float_as_uint(fmaxf(c, 0.f)));
+    }
+}
+
+}  // namespace
+
+static inline size_t al256c(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" int32_t g4_mlp_param_count(void) { return NPARAM; }
+
+extern "C" g4_status g4_cost_features(g4_tree t, const float *aold_sorted, const uint8_t *bins_sorted,
+                                      const g4_params *P, float *features, int32_t *leaf_scratch,
+                                      void *stream)
+{
+    if (!t || !P || !features || !leaf_scratch)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_cost_features: NULL argument");
+    if (t->built_n < 0) return g4_fail(G4_ERR_STATE, "g4_cost_features: tree not built");
+    const int n = t->built_n;
+    if (n == 0) return G4_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_leaf_of<<<g4_num_sms() * 4, 256, 0, st>>>(t->node, t->lvl, leaf_scratch);
+    k_features<<<g4_blocks_for(n, 256), 256, 0, st>>>(t->node, leaf_scratch, aold_sorted, bins_sorted,
+                                                     n, 1.0f / (float)P->leaf_max, features);
+    return g4_launch_check("cost features", 2);
+}
+
+extern "C" g4_status g4_cost_labels(const uint32_t *counts, int64_t n, float c_pn, float *labels,
+                                    void *stream)
+{
+    if (n < 0 || (n > 0 && (!counts || !labels)))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_cost_labels: bad arguments");
+    if (n == 0) return G4_OK;
+    k_cost_label<<<g4_blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(counts, (int)n, c_pn, labels);
+    return g4_launch_check("cost labels", 1);
+}
+
+extern "C" g4_status g4_mlp_forward(const float *params, const float *features, int64_t n,
+                                    float *out, void *stream)
+{
+    if (n < 0 || n >= ((int64_t)1 << 31) || !params || (n > 0 && (!features || !out)))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_mlp_forward: bad arguments");
+    if (n == 0) return G4_OK;
+    k_mlp_forward<<<g4_blocks_for(n, MLP_THREADS, 4), MLP_THREADS, 0, (cudaStream_t)stream>>>(
+        params, features, (int)n, out);
+    return g4_launch_check("mlp forward", 1);
+}
+
+extern "C" g4_status g4_mlp_train_workspace(int64_t n, size_t *bytes)
+{
+    if (!bytes || n < 0) return g4_fail(G4_ERR_INVALID_ARG, "g4_mlp_train_workspace: bad args");
+    const int nb = g4_blocks_for(n > 0 ? n : 1, MLP_THREADS, 2);
+    *bytes = al256c(sizeof(float) * (size_t)nb * (NPARAM + 1));
+    return G4_OK;
+}
+
+extern "C" g4_status g4_mlp_train_step(float *params, float *adam_m, float *adam_v, int32_t step,
+                                       const float *features, const float *labels, int64_t n,
+                                       float lr, float *loss_out, float *grad_out, void *workspace,
+                                       size_t workspace_bytes, void *stream)
+{
+    if (n <= 0 || n >= ((int64_t)1 << 31) || !params || !adam_m || !adam_v || !features ||
+        !labels || !workspace || step < 1)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_mlp_train_step: bad arguments");
+    const int nb = g4_blocks_for(n, MLP_THREADS, 2);
+    if (workspace_bytes < sizeof(float) * (size_t)nb * (NPARAM + 1))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_mlp_train_step: workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *gpart = (float *)workspace;
+    k_mlp_grad<<<nb, MLP_THREADS, 0, st>>>(params, features, labels, (int)n, 1.0f / (float)n, gpart);
+    k_mlp_adam<<<(NPARAM + 256) / 256, 256, 0, st>>>(params, adam_m, adam_v, gpart, nb, lr, 0.9f,
+                                                     0.999f, 1e-8f, step, grad_out, loss_out);
+    return g4_launch_check("mlp train step", 2);
+}
+
+extern "C" g4_status g4_schedule_workspace(int64_t n, size_t *bytes)
+{
+    if (!bytes || n < 0) return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_workspace: bad args");
+    const int64_t ng = (n + 31) / 32;
+    *bytes = al256c(8 * (size_t)(ng > 0 ? ng : 1)) + g4_sort_workspace_bytes(ng);
+    return G4_OK;
+}
+
+extern "C" g4_status g4_schedule_lpt(const float *pred_sorted, int64_t n, int32_t *group_order,
+                                     void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!pred_sorted || !group_order || !workspace)))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_lpt: bad arguments");
+    if (n == 0) return G4_OK;
+    const int64_t ng = (n + 31) / 32;
+    const size_t need = al256c(8 * (size_t)ng) + g4_sort_workspace_bytes(ng);
+    if (workspace_bytes < need) return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_lpt: workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    uint64_t *key = (uint64_t *)workspace;
+    void *sws = (char *)workspace + al256c(8 * (size_t)ng);
+    k_group_cost<<<g4_blocks_for(ng, 256), 256, 0, st>>>(pred_sorted, (int)n, (int)ng, key);
+    g4_status s = g4_launch_check("group cost", 1);
+    if (s != G4_OK) return s;
+    // stable sort by descending predicted cost; ties keep PH order
+    return g4_sort_pairs_u64(key, key, group_order, ng, sws, g4_sort_workspace_bytes(ng), 32, st);
+}
+
+extern "C" g4_status g4_tree_set_group_order(g4_tree t, const int32_t *group_order, int64_t ngroups)
+{
+    if (!t || ngroups < 0) return g4_fail(G4_ERR_INVALID_ARG, "g4_tree_set_group_order: bad args");
+    t->group_order = group_order;
+    t->group_order_n = group_order ? ngroups : 0;
+    return G4_OK;
+}

@@ -66,6 +66,15 @@ struct g4_tree_s {
     float *q = nullptr;           // cap x g4_nq(G4_MAX_ORDER) FP32 moments (orders 2..p)
     double *qd = nullptr;         // FP64 mirror (precision 1 only): cap x (4 + nq)
     int built_n = -1;
+    // forest (several independent systems in one handle); n_sys = 0 for a single system
+    int n_sys = 0;
+    const int32_t *sys_first = nullptr;   // caller device array [n_sys + 1], sorted-order offsets
+    const double *sys_box = nullptr;      // caller device array [n_sys], box size per system
+    int32_t *sys_goff = nullptr;          // library: walk-group offsets per system [n_sys + 1]
+    int sys_cap = 0;
+    // optional walk schedule: order in which the 32-sink groups are handed out
+    const int32_t *group_order = nullptr;
+    int64_t group_order_n = 0;
     int moments_order = -1;
     int moments_fp64 = 0;
     // host copies filled by g4_tree_status
@@ -94,6 +103,18 @@ static inline int g4_blocks_for(int64_t work, int threads, int per_sm = 8)
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
+}
+
+// system of sorted particle j in a forest (binary search over the systems' first indices)
+__device__ __forceinline__ int g4_system_of(const int32_t *sys_first, int n_sys, int j)
+{
+    int lo = 0, hi = n_sys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sys_first[mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // internal entry points shared between translation units

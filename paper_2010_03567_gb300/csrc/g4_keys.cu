@@ -348,6 +348,26 @@ __global__ void k_scatter(const int32_t *__restrict__ perm, int64_t n,
     }
 }
 
+__global__ void k_sys_keys(const uint16_t *__restrict__ sys, const int32_t *__restrict__ perm,
+                           int64_t n, uint64_t *__restrict__ out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = sys[perm[k]];
+}
+
+__global__ void k_compose(const uint64_t *__restrict__ keys1, const int32_t *__restrict__ perm1,
+                          const int32_t *__restrict__ p2, int64_t n, uint64_t *__restrict__ keys,
+                          int32_t *__restrict__ perm)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int j = p2[k];
+        keys[k] = keys1[j];
+        perm[k] = perm1[j];
+    }
+}
+
 }  // namespace
 
 // -------------------------------------------------------------------------------------------
@@ -432,6 +452,58 @@ extern "C" g4_status g4_keys_sort(const uint32_t *pos_int, int64_t n, uint64_t *
     if (s != G4_OK) return s;
     return g4_sort_pairs_u64(keys_sorted, keys_sorted, perm, n, workspace, workspace_bytes,
                              63, st);
+}
+
+static size_t batched_extra(int64_t n)
+{
+    size_t m = (size_t)(n > 0 ? n : 1);
+    return 2 * align256(8 * m) + 2 * align256(4 * m);
+}
+
+extern "C" g4_status g4_keys_sort_batched_workspace(int64_t n, size_t *bytes)
+{
+    if (!bytes || n < 0) return g4_fail(G4_ERR_INVALID_ARG, "g4_keys_sort_batched_workspace: bad args");
+    *bytes = g4_sort_workspace_bytes(n) + batched_extra(n);
+    return G4_OK;
+}
+
+extern "C" g4_status g4_keys_sort_batched(const uint32_t *pos_int, int64_t n, const uint16_t *sys_id,
+                                          uint64_t *keys_sorted, int32_t *perm, void *workspace,
+                                          size_t workspace_bytes, void *stream)
+{
+    if (n < 0 || n >= (int64_t)1 << 31)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_keys_sort_batched: n=%lld out of range", (long long)n);
+    if (n == 0) return G4_OK;
+    if (!pos_int || !sys_id || !keys_sorted || !perm || !workspace)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_keys_sort_batched: NULL pointer");
+    if (((uintptr_t)workspace & 255) != 0)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_keys_sort_batched: workspace not 256-byte aligned");
+    const size_t need = g4_sort_workspace_bytes(n) + batched_extra(n);
+    if (workspace_bytes < need)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_keys_sort_batched: workspace too small (%zu < %zu)",
+                       workspace_bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)workspace + g4_sort_workspace_bytes(n);
+    const size_t m = (size_t)n;
+    uint64_t *keys1 = (uint64_t *)w;
+    w += align256(8 * m);
+    uint64_t *sysk = (uint64_t *)w;
+    w += align256(8 * m);
+    int32_t *perm1 = (int32_t *)w;
+    w += align256(4 * m);
+    int32_t *p2 = (int32_t *)w;
+    const int nb = g4_blocks_for(n, 256);
+    // stage 1: stable sort by Peano-Hilbert key; stage 2: stable sort by system (16-bit ids)
+    k_keys<<<nb, 256, 0, st>>>(pos_int, n, keys1);
+    g4_status s = g4_launch_check("batched keys", 1);
+    if (s != G4_OK) return s;
+    s = g4_sort_pairs_u64(keys1, keys1, perm1, n, workspace, g4_sort_workspace_bytes(n), 63, st);
+    if (s != G4_OK) return s;
+    k_sys_keys<<<nb, 256, 0, st>>>(sys_id, perm1, n, sysk);
+    s = g4_sort_pairs_u64(sysk, sysk, p2, n, workspace, g4_sort_workspace_bytes(n), 16, st);
+    if (s != G4_OK) return s;
+    k_compose<<<nb, 256, 0, st>>>(keys1, perm1, p2, n, keys_sorted, perm);
+    return g4_launch_check("batched sort", 2);
 }
 
 extern "C" g4_status g4_int_coords(const double *pos, int64_t n, int periodic, double box_size,

@@ -122,6 +122,9 @@ struct MomArgs {
     int fp64_count;
     int all_fp64;
     const int32_t *flags;
+    const int32_t *sys_first;    // forest: per-system box sizes (n_sys = 0: one system)
+    const double *sys_box;
+    int n_sys;
 };
 
 template <int P, typename T>
@@ -131,7 +134,9 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd)
     T q[NM];
 #pragma unroll
     for (int k = 0; k < NM; k++) q[k] = T(0);
-    const T scale = (T)A.scale;
+    const T scale = A.n_sys ? (T)(A.sys_box[g4_system_of(A.sys_first, A.n_sys, nd.first)] *
+                                  (1.0 / 4294967296.0))
+                            : (T)A.scale;
     T M = T(0), sx = T(0), sy = T(0), sz = T(0);
     float hmax = 0.f, amin = 3.0e38f;
     const bool leaf = nd.meta & 32u;
@@ -301,6 +306,9 @@ extern "C" g4_status g4_multipoles(g4_tree t, const uint32_t *pos_sorted, const 
     A.fp64_count = P->fp64_count > 0 ? P->fp64_count : 4096;
     A.all_fp64 = P->precision == 1;
     A.flags = t->d_flags;
+    A.sys_first = t->sys_first;
+    A.sys_box = t->sys_box;
+    A.n_sys = t->n_sys;
     A.qd = nullptr;
     if (P->precision == 1) {
         if (!t->qd) {

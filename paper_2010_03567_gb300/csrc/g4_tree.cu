@@ -31,6 +31,65 @@ __global__ void k_build_init(int32_t *lvl, int32_t *flags, int32_t *b_first, int
     }
 }
 
+// forest: level 0 holds one root per system, system s covering sorted particles
+// [sys_first[s], sys_first[s+1])
+__global__ void k_build_init_forest(int32_t *lvl, int32_t *flags, int32_t *b_first, int32_t *b_count,
+                                    int32_t *b_parent, const int32_t *__restrict__ sys_first,
+                                    int n_sys)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0) {
+        if (t < 2 * (G4_NLEVELS + 1)) lvl[t] = 0;
+        __syncthreads();
+        if (t == 0) {
+            lvl[G4_NLEVELS + 1 + 0] = n_sys;
+            *flags = 0;
+        }
+    }
+    for (int s = t; s < n_sys; s += gridDim.x * blockDim.x) {
+        b_first[s] = sys_first[s];
+        b_count[s] = sys_first[s + 1] - sys_first[s];
+        b_parent[s] = -1;
+    }
+}
+
+// forest: depth-first numbers of the roots (prefix sums of the subtree sizes) and the walk
+// group offsets of the systems (prefix sums of ceil(n_s / 32)); one block
+__global__ void __launch_bounds__(1024) k_forest_roots(const int32_t *__restrict__ b_size,
+                                                       const int32_t *__restrict__ sys_first,
+                                                       int n_sys, int32_t *__restrict__ b_dfs,
+                                                       int32_t *__restrict__ goff)
+{
+    __shared__ int ws[2][32];
+    __shared__ int carry[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry[0] = carry[1] = 0;
+    __syncthreads();
+    for (int base = 0; base < n_sys; base += 1024) {
+        const int s = base + threadIdx.x;
+        int a = s < n_sys ? b_size[s] : 0;
+        int g = s < n_sys ? (sys_first[s + 1] - sys_first[s] + 31) / 32 : 0;
+        int xa = a, xg = g;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ya = __shfl_up_sync(0xffffffffu, xa, o), yg = __shfl_up_sync(0xffffffffu, xg, o);
+            if (lane >= o) { xa += ya; xg += yg; }
+        }
+        if (lane == 31) { ws[0][w] = xa; ws[1][w] = xg; }
+        __syncthreads();
+        int pa = carry[0], pg = carry[1];
+        for (int k = 0; k < w; k++) { pa += ws[0][k]; pg += ws[1][k]; }
+        if (s < n_sys) {
+            b_dfs[s] = pa + xa - a;
+            goff[s] = pg + xg - g;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) { carry[0] = pa + xa; carry[1] = pg + xg; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) goff[n_sys] = carry[1];
+}
+
 __device__ __forceinline__ int lower_bound_digit(const uint64_t *__restrict__ keys, int lo, int hi,
                                                  int shift, uint32_t d)
 {
@@ -187,7 +246,8 @@ __global__ void k_build_emit(const int32_t *__restrict__ lvl, const uint32_t *__
         while (l + 1 < G4_NLEVELS && b >= off[l + 1]) l++;
         (void)cnt;
         int d = b_dfs[b], f = b_first[b];
-        if ((unsigned)d >= (unsigned)total || (unsigned)f >= (unsigned)n) continue;   // invalid tree
+        if ((unsigned)d >= (unsigned)total) continue;   // invalid tree
+        if (b_count[b] == 0 || (unsigned)f >= (unsigned)n) f = 0;   // empty system root
         G4Node nd;
         uint32_t x[3] = {pos[f], pos[n + f], pos[2 * n + f]};
         uint32_t mask = (l == 0) ? 0u : ~((1u << (32 - l)) - 1u);
@@ -199,7 +259,7 @@ __global__ void k_build_emit(const int32_t *__restrict__ lvl, const uint32_t *__
         nd.meta = (uint32_t)l | (leaf ? 32u : 0u);
         nd.sx = nd.sy = nd.sz = 0.f;
         nd.mass = 0.f;
-        nd.first = f;
+        nd.first = b_count[b] == 0 ? 0 : f;
         nd.count = b_count[b];
         nd.next = d + b_size[b];
         nd.parent = b_parent[b] >= 0 ? b_dfs[b_parent[b]] : -1;
@@ -291,6 +351,7 @@ extern "C" void g4_tree_free(g4_tree t)
     cudaFree(t->node);
     cudaFree(t->q);
     if (t->qd) cudaFree(t->qd);
+    if (t->sys_goff) cudaFree(t->sys_goff);
     delete t;
 }
 
@@ -322,7 +383,60 @@ extern "C" g4_status g4_tree_build(g4_tree t, const uint64_t *keys_sorted,
                                                t->b_parent, t->node);
     t->built_n = (int)n;
     t->moments_order = -1;
+    t->n_sys = 0;
+    t->sys_first = nullptr;
+    t->sys_box = nullptr;
     return g4_launch_check("tree build", 4 + G4_MAXLEVEL + 2 * (G4_MAXLEVEL + 1));
+}
+
+extern "C" g4_status g4_tree_build_forest(g4_tree t, const uint64_t *keys_sorted,
+                                          const uint32_t *pos_sorted, int64_t n,
+                                          const int32_t *sys_first, const double *sys_box,
+                                          int32_t n_sys, const g4_params *P, void *stream)
+{
+    if (!t || !P || n < 0 || n > t->n_max || n_sys < 1 || !sys_first || !sys_box ||
+        (n > 0 && (!keys_sorted || !pos_sorted)))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_tree_build_forest: bad arguments");
+    if (P->leaf_max < 1 || P->leaf_max > 64)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_tree_build_forest: leaf_max=%d", P->leaf_max);
+    if ((int64_t)n_sys > t->cap)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_tree_build_forest: more systems than node capacity");
+    if (n_sys > t->sys_cap) {
+        // grows only when a larger batch arrives; steady-state calls allocate nothing
+        if (t->sys_goff) cudaFree(t->sys_goff);
+        t->sys_goff = nullptr;
+        t->sys_cap = 0;
+        if (cudaMalloc(&t->sys_goff, sizeof(int32_t) * (n_sys + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return g4_fail(G4_ERR_OOM, "g4_tree_build_forest: group offsets");
+        }
+        t->sys_cap = n_sys;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    k_build_init_forest<<<g4_blocks_for(n_sys, 256, 4), 256, 0, st>>>(
+        t->lvl, t->d_flags, t->b_first, t->b_count, t->b_parent, sys_first, n_sys);
+    int nb = g4_num_sms() * 4;
+    for (int l = 0; l < G4_MAXLEVEL; l++)
+        k_build_expand<<<nb, BUILD_THREADS, 0, st>>>(keys_sorted, l, P->leaf_max, t->cap, t->lvl,
+                                                     t->d_flags, t->b_first, t->b_count,
+                                                     t->b_child, t->b_nchild, t->b_parent);
+    k_build_last<<<nb, BUILD_THREADS, 0, st>>>(t->lvl, t->cap, t->b_child, t->b_nchild);
+    k_build_clip<<<1, 32, 0, st>>>(t->lvl, t->cap);
+    for (int l = G4_MAXLEVEL; l >= 0; l--)
+        k_build_subtree<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->b_child, t->b_nchild, t->b_size);
+    k_forest_roots<<<1, 1024, 0, st>>>(t->b_size, sys_first, n_sys, t->b_dfs, t->sys_goff);
+    for (int l = 0; l <= G4_MAXLEVEL; l++)
+        k_build_dfs<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->b_child, t->b_nchild, t->b_size,
+                                                  t->b_dfs);
+    k_build_emit<<<nb, BUILD_THREADS, 0, st>>>(t->lvl, pos_sorted, (int)n, t->b_first, t->b_count,
+                                               t->b_child, t->b_nchild, t->b_size, t->b_dfs,
+                                               t->b_parent, t->node);
+    t->built_n = (int)n;
+    t->moments_order = -1;
+    t->n_sys = n_sys;
+    t->sys_first = sys_first;
+    t->sys_box = sys_box;
+    return g4_launch_check("forest build", 5 + G4_MAXLEVEL + 2 * (G4_MAXLEVEL + 1));
 }
 
 extern "C" g4_status g4_tree_status(g4_tree t, int64_t *n_nodes, int32_t *max_level, void *stream)

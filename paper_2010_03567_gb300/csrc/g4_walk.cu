@@ -33,6 +33,11 @@ struct WalkArgs {
     uint32_t *counts;
     int *work;                 // group counter
     const int32_t *flags;      // tree error flags
+    const int32_t *b_dfs;      // forest: root of system s is node b_dfs[s]
+    const int32_t *sys_first, *sys_goff;
+    const double *sys_box;
+    int n_sys;
+    const int32_t *group_order;   // optional schedule (longest predicted cost first)
     double scale;
     double G, alpha, theta2, rcut2, as;
     double box;
@@ -50,18 +55,19 @@ template <int P, typename T> __device__ __forceinline__ T ipow(T x)
     return r;
 }
 
-constexpr int WALK_THREADS = 256;
+constexpr int WALK_THREADS = 128;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
-constexpr int LEAF_BUF = 128;
+constexpr int LEAF_BUF = 64;
+constexpr int STAGE = 64;       // sources staged per pass of the particle-particle phase
 
-// per-warp shared state: the pending leaf list of the group and a staging area of 32 sources
+// per-warp shared state: the pending leaf list of the group and the staged sources
 struct WalkSmem {
-    int first[LEAF_BUF], count[LEAF_BUF], pref[LEAF_BUF];
+    int first[LEAF_BUF], count[LEAF_BUF], pref[LEAF_BUF], node[LEAF_BUF];
     unsigned mask[LEAF_BUF];
-    uint32_t x[32], y[32], z[32];
-    float m[32], h[32];
-    unsigned smask[32];
-    int j[32];
+    float4 rel[STAGE];          // source position relative to the group centre (float), mass
+    uint4 ipos[STAGE];          // source integer position, softening length h (bits)
+    int2 mj[STAGE];             // lane mask of the source's leaf, particle index
+    float4 sink[32];            // sinks relative to the group centre, opening threshold
 };
 
 __device__ __forceinline__ int warp_excl_scan(int v, int lane)
@@ -80,10 +86,11 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane)
 // when the opening criterion fails, otherwise accept the multipole.
 template <int P, typename T, bool TREEPM, bool GEOM>
 __device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &nd, int k,
-                                              uint32_t xi, uint32_t yi, uint32_t zi, T hi, T crit)
+                                              uint32_t xi, uint32_t yi, uint32_t zi, T hi, T crit,
+                                              double gscale, double gbox)
 {
-    const T scale = (T)A.scale;
-    const T side = ldexp((T)A.box, -(int)(nd.meta & 31u)), half = T(0.5) * side;
+    const T scale = (T)gscale;
+    const T side = ldexp((T)gbox, -(int)(nd.meta & 31u)), half = T(0.5) * side;
     const T dcx = (T)(int32_t)(nd.cx - xi) * scale;
     const T dcy = (T)(int32_t)(nd.cy - yi) * scale;
     const T dcz = (T)(int32_t)(nd.cz - zi) * scale;
@@ -112,54 +119,129 @@ __device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &n
     return open ? ACT_OPEN : ACT_ACCEPT;
 }
 
-// particle-particle terms of the group's sinks with the particles of the pending leaves;
-// every lane takes the sources in the list order, masked by the lanes that reach each leaf
+// Particle-particle phase for the pending leaves of a group.
+//  1. TreePM: each leaf's lane mask is narrowed to the lanes whose cutoff sphere reaches the
+//     leaf's cube (the per-lane skip of a single-particle walk), empty leaves are dropped.
+//  2. Sources are staged 128 at a time; every lane tests them against its sink with positions
+//     relative to the group centre (cheap, slightly enlarged cutoff) and keeps a bit per
+//     candidate; then each lane evaluates its own candidates with exact integer separations,
+//     the exact cutoff and the full kernel.  Lanes only spend the expensive kernel on their
+//     own pairs, so the warp is not held back by pairs of other lanes.
+// The sum order of every sink is the order of its sources in the list (depth-first), so the
+// result does not depend on which other sinks share the group.
 template <typename T, bool TREEPM>
-__device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nleaf, int total,
-                                         int lane, int i, uint32_t xi, uint32_t yi, uint32_t zi,
-                                         T hi, T &ax, T &ay, T &az, T &ap, uint32_t &npp)
+__device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nleaf, int lane, int i,
+                                         uint32_t xi, uint32_t yi, uint32_t zi, uint32_t gcx,
+                                         uint32_t gcy, uint32_t gcz, float xr, float yr, float zr,
+                                         T hi, T &ax, T &ay, T &az, T &ap, uint32_t &npp,
+                                         double gscale, double gbox)
 {
-    const T scale = (T)A.scale, as = (T)A.as, rcut2 = (T)A.rcut2;
-    for (int b = 0; b < total; b += 32) {
-        const int t = b + lane;
-        if (t < total) {
-            int lo = 0, hi_ = nleaf - 1;
-            while (lo < hi_) {
-                const int mid = (lo + hi_ + 1) >> 1;
-                if (S.pref[mid] <= t) lo = mid;
-                else hi_ = mid - 1;
-            }
-            const int j = S.first[lo] + (t - S.pref[lo]);
-            S.x[lane] = __ldg(A.pos + j);
-            S.y[lane] = __ldg(A.pos + A.n + j);
-            S.z[lane] = __ldg(A.pos + 2 * A.n + j);
-            S.m[lane] = __ldg(A.mass + j);
-            S.h[lane] = A.h_cls[A.cls ? __ldg(A.cls + j) : 0];
-            S.smask[lane] = S.mask[lo];
-            S.j[lane] = j;
+    const float fscale = (float)gscale, fbox = (float)gbox;
+    const T scale = (T)gscale, as = (T)A.as, rcut2 = (T)A.rcut2;
+    // 1. per-lane leaf masks and compaction
+    if (TREEPM) {
+        for (int e = 0; e < nleaf; e++) {
+            const G4Node nd = load_node(A.node + S.node[e]);
+            const float half = 0.5f * ldexpf(fbox, -(int)(nd.meta & 31u));
+            const float ex = fmaxf(fabsf((float)(int32_t)(nd.cx - gcx) * fscale - xr) - half, 0.f);
+            const float ey = fmaxf(fabsf((float)(int32_t)(nd.cy - gcy) * fscale - yr) - half, 0.f);
+            const float ez = fmaxf(fabsf((float)(int32_t)(nd.cz - gcz) * fscale - zr) - half, 0.f);
+            const bool reach = ex * ex + ey * ey + ez * ez <= 1.0001f * (float)A.rcut2 + 1e-30f;
+            const unsigned m = __ballot_sync(0xffffffffu, reach) & S.mask[e];
+            __syncwarp();
+            if (lane == 0) S.mask[e] = m;
+            __syncwarp();
+        }
+    }
+    int nk = 0, total = 0;
+    for (int b = 0; b < nleaf; b += 32) {
+        const int e = b + lane;
+        const bool ok = e < nleaf;
+        int f = 0, c = 0;
+        unsigned m = 0;
+        if (ok) {
+            f = S.first[e];
+            c = S.count[e];
+            m = S.mask[e];
+        }
+        const bool keep = ok && m != 0u;
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        const int cc = keep ? c : 0;
+        int pre = cc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += y;
         }
         __syncwarp();
-        const int nb = min(32, total - b);
-        for (int u = 0; u < nb; u++) {
-            const unsigned mk = S.smask[u];
-            const int j = S.j[u];
-            if (((mk >> lane) & 1u) && j != i) {
-                const T dx = (T)(int32_t)(S.x[u] - xi) * scale;
-                const T dy = (T)(int32_t)(S.y[u] - yi) * scale;
-                const T dz = (T)(int32_t)(S.z[u] - zi) * scale;
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                if (!(TREEPM && A.pp_cut && r2 >= rcut2)) {
-                    T g0, g1;
-                    pair_kernel<T, TREEPM>(r2, fmax(hi, (T)S.h[u]), as, g0, g1);
-                    const T mj = (T)S.m[u];
-                    const T mg1 = mj * g1;
-                    ax += mg1 * dx;
-                    ay += mg1 * dy;
-                    az += mg1 * dz;
-                    ap += mj * g0;
-                    npp++;
+        if (keep) {
+            const int pos = nk + __popc(km & ((1u << lane) - 1u));
+            S.first[pos] = f;
+            S.count[pos] = c;
+            S.mask[pos] = m;
+            S.pref[pos] = total + pre - cc;
+        }
+        __syncwarp();
+        nk += __popc(km);
+        total += __shfl_sync(0xffffffffu, pre, 31);
+    }
+    const float rc2t = TREEPM ? 1.0001f * (float)A.rcut2 + 1e-30f : 3.0e38f;
+    for (int b = 0; b < total; b += STAGE) {
+        const int nb = min(STAGE, total - b);
+        // stage up to 128 sources (4 per lane)
+#pragma unroll
+        for (int q = 0; q < STAGE / 32; q++) {
+            const int u = q * 32 + lane, t = b + u;
+            if (u < nb) {
+                int lo = 0, hi_ = nk - 1;
+                while (lo < hi_) {
+                    const int mid = (lo + hi_ + 1) >> 1;
+                    if (S.pref[mid] <= t) lo = mid;
+                    else hi_ = mid - 1;
                 }
+                const int j = S.first[lo] + (t - S.pref[lo]);
+                const uint32_t px = __ldg(A.pos + j), py = __ldg(A.pos + A.n + j),
+                               pz = __ldg(A.pos + 2 * A.n + j);
+                const float mj = __ldg(A.mass + j);
+                const float hj = A.h_cls[A.cls ? __ldg(A.cls + j) : 0];
+                S.rel[u] = make_float4((float)(int32_t)(px - gcx) * fscale,
+                                       (float)(int32_t)(py - gcy) * fscale,
+                                       (float)(int32_t)(pz - gcz) * fscale, mj);
+                S.ipos[u] = make_uint4(px, py, pz, __float_as_uint(hj));
+                S.mj[u] = make_int2((int)S.mask[lo], j);
             }
+        }
+        __syncwarp();
+        // candidate bits of this lane (64-bit: one per staged source)
+        unsigned long long cand = 0ull;
+#pragma unroll 4
+        for (int v = 0; v < nb; v++) {
+            const int2 mj = S.mj[v];
+            const float4 r = S.rel[v];
+            const float dx = r.x - xr, dy = r.y - yr, dz = r.z - zr;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            const bool c = (((unsigned)mj.x >> lane) & 1u) && mj.y != i && d2 <= rc2t;
+            cand |= (c ? 1ull : 0ull) << v;
+        }
+        // exact evaluation of the lane's own candidates
+        while (cand) {
+            const int u = __ffsll((long long)cand) - 1;
+            cand &= cand - 1ull;
+            const uint4 ip = S.ipos[u];
+            const T dx = (T)(int32_t)(ip.x - xi) * scale;
+            const T dy = (T)(int32_t)(ip.y - yi) * scale;
+            const T dz = (T)(int32_t)(ip.z - zi) * scale;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (TREEPM && A.pp_cut && r2 >= rcut2) continue;
+            T g0, g1;
+            pair_kernel<T, TREEPM>(r2, fmax(hi, (T)__uint_as_float(ip.w)), as, g0, g1);
+            const T mj = (T)S.rel[u].w;
+            const T mg1 = mj * g1;
+            ax += mg1 * dx;
+            ay += mg1 * dy;
+            az += mg1 * dz;
+            ap += mj * g0;
+            npp++;
         }
         __syncwarp();
     }
@@ -181,18 +263,36 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     if (*A.flags & G4_FLAG_CAPACITY) return;   // incomplete tree: outputs left untouched
-    const int nn = A.lvl[G4_NLEVELS];
-    const float fscale = (float)A.scale, fbox = (float)A.box;
-    const int ngroups = (A.n_sinks + 31) >> 5;
+    const int nn_all = A.lvl[G4_NLEVELS];
+    const int ngroups = A.n_sys ? A.sys_goff[A.n_sys] : (A.n_sinks + 31) >> 5;
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(A.work, 1);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
-        const int s = g * 32 + lane;
-        const bool valid = s < A.n_sinks;
+        if (A.group_order) g = A.group_order[g];
+        // the group's sinks, node range and box (a forest walks only its own system's tree)
+        int s0 = g * 32, s_end = A.n_sinks, k = 0, nn = nn_all;
+        double gbox = A.box;
+        if (A.n_sys) {
+            int lo = 0, hi_ = A.n_sys - 1;
+            while (lo < hi_) {
+                const int mid = (lo + hi_ + 1) >> 1;
+                if (A.sys_goff[mid] <= g) lo = mid;
+                else hi_ = mid - 1;
+            }
+            s0 = A.sys_first[lo] + (g - A.sys_goff[lo]) * 32;
+            s_end = A.sys_first[lo + 1];
+            k = A.b_dfs[lo];
+            nn = A.node[k].next;
+            gbox = A.sys_box[lo];
+        }
+        const double gscale = gbox * (1.0 / 4294967296.0);
+        const float fscale = (float)gscale, fbox = (float)gbox;
+        const int s = s0 + lane;
+        const bool valid = s < s_end;
         const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-        const int i = valid ? (A.active ? A.active[s] : s) : (A.active ? A.active[g * 32] : g * 32);
+        const int i = valid ? (A.active ? A.active[s] : s) : (A.active ? A.active[s0] : s0);
         const uint32_t xi = A.pos[i], yi = A.pos[A.n + i], zi = A.pos[2 * A.n + i];
         const T hi = (T)A.h_cls[A.cls ? A.cls[i] : 0];
         const T crit = GEOM ? T(0) : (T)A.alpha * (T)(A.aold ? A.aold[i] : 0.f);
@@ -206,9 +306,13 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
         const uint32_t gcx = x0 + (uint32_t)(int)(((long long)lox + hix) >> 1);
         const uint32_t gcy = y0 + (uint32_t)(int)(((long long)loy + hiy) >> 1);
         const uint32_t gcz = z0 + (uint32_t)(int)(((long long)loz + hiz) >> 1);
+        const float xr = (float)(int32_t)(xi - gcx) * fscale, yr = (float)(int32_t)(yi - gcy) * fscale,
+                    zr = (float)(int32_t)(zi - gcz) * fscale;
         const float ghx = (0.5f * (float)((long long)hix - lox) + 2.f) * fscale;
         const float ghy = (0.5f * (float)((long long)hiy - loy) + 2.f) * fscale;
         const float ghz = (0.5f * (float)((long long)hiz - loz) + 2.f) * fscale;
+        S.sink[lane] = make_float4(xr, yr, zr, valid ? (GEOM ? 1.f : (float)crit) : -1.f);
+        __syncwarp();
         float critmax = (float)crit;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) critmax = fmaxf(critmax, __shfl_xor_sync(0xffffffffu, critmax, o));
@@ -218,9 +322,14 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
         T bx = T(0), by = T(0), bz = T(0), bp = T(0);     // particle-node sums
         uint32_t npp = 0, npn = 0;
         int resume = valid ? 0 : 0x7fffffff;
-        int nleaf = 0, total = 0;
-        int k = 0;
-        while (k < nn) {
+        int nleaf = 0;
+        for (;;) {
+            // a window adds at most 32 leaves: flush before the list could overflow, and at the end
+            if (nleaf > LEAF_BUF - 32 || (k >= nn && nleaf > 0)) {
+                pp_flush<T, TREEPM>(A, S, nleaf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, hi, ax, ay, az, ap, npp, gscale, gbox);
+                nleaf = 0;
+            }
+            if (k >= nn) break;
             const int j = k + lane;
             const bool vj = j < nn;
             G4Node nd;
@@ -256,6 +365,26 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                     maybe = !none;
                 }
             }
+            if (__any_sync(0xffffffffu, maybe)) {
+                // necessary condition for any sink to use the multipole: its own opening
+                // criterion (exclusion, softening and inside-node tests can only open it)
+                bool any = false;
+                if (maybe) {
+                    const float side = ldexpf(fbox, -(int)(nd.meta & 31u));
+                    const float cx = (float)(int32_t)(nd.cx - gcx) * fscale + nd.sx;
+                    const float cy = (float)(int32_t)(nd.cy - gcy) * fscale + nd.sy;
+                    const float cz = (float)(int32_t)(nd.cz - gcz) * fscale + nd.sz;
+                    const float lhs = 0.999f * (GEOM ? side * side : (float)A.G * nd.mass * ipow<P>(side));
+                    for (int u = 0; u < 32 && !any; u++) {
+                        const float4 sk = S.sink[u];
+                        const float dx = cx - sk.x, dy = cy - sk.y, dz = cz - sk.z;
+                        const float r2 = (dx * dx + dy * dy + dz * dz) * 1.001f;
+                        if (GEOM) any = lhs < sk.w * (float)A.theta2 * r2;
+                        else any = lhs < sk.w * ipow<P + 2>(sqrtf(r2));
+                    }
+                }
+                maybe = any;
+            }
             // depth-first coverage inside the window by skipped subtrees
             int e = (vj && gskip) ? nd.next : 0;
             int pm = e;
@@ -274,22 +403,14 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
             if (maybem == 0 && all_active) {
                 const int nnew = __popc(leafm);
                 if (nnew > 0) {
-                    if (nleaf + nnew > LEAF_BUF) {
-                        pp_flush<T, TREEPM>(A, S, nleaf, total, lane, i, xi, yi, zi, hi, ax, ay, az, ap, npp);
-                        nleaf = 0;
-                        total = 0;
-                    }
                     const bool me = (leafm >> lane) & 1u;
-                    const int cnt = me ? nd.count : 0;
-                    const int pre = warp_excl_scan(cnt, lane);
                     if (me) {
                         const int pos = nleaf + __popc(leafm & lt);
                         S.first[pos] = nd.first;
                         S.count[pos] = nd.count;
                         S.mask[pos] = vmask;
-                        S.pref[pos] = total + pre;
+                        S.node[pos] = j;
                     }
-                    total += __shfl_sync(0xffffffffu, pre + cnt, 31);
                     nleaf += nnew;
                     __syncwarp();
                 }
@@ -307,26 +428,20 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                     if ((leafm >> src) & 1u) {
                         const unsigned m = __ballot_sync(0xffffffffu, resume <= jj);
                         if (m) {
-                            if (nleaf + 1 > LEAF_BUF) {
-                                pp_flush<T, TREEPM>(A, S, nleaf, total, lane, i, xi, yi, zi, hi, ax, ay, az, ap, npp);
-                                nleaf = 0;
-                                total = 0;
-                            }
                             if (lane == 0) {
                                 S.first[nleaf] = n2.first;
                                 S.count[nleaf] = n2.count;
                                 S.mask[nleaf] = m;
-                                S.pref[nleaf] = total;
+                                S.node[nleaf] = jj;
                             }
                             __syncwarp();
                             nleaf++;
-                            total += n2.count;
                         }
                     } else {
                         int act = ACT_NONE;
                         if (resume <= jj) {
-                            act = exact_decision<P, T, TREEPM, GEOM>(A, n2, jj, xi, yi, zi, hi, crit);
-                            if (act != ACT_OPEN) resume = max(n2.next, jj + 1);
+                            act = exact_decision<P, T, TREEPM, GEOM>(A, n2, jj, xi, yi, zi, hi, crit, gscale, gbox);
+                            if (act == ACT_ACCEPT) resume = max(n2.next, jj + 1);   // a cutoff skip is hereditary: nothing below can be used, so it acts as open
                         }
                         if (__any_sync(0xffffffffu, act == ACT_ACCEPT) && act == ACT_ACCEPT) {
                             T Qs[g4_nq(P) > 0 ? g4_nq(P) : 1];
@@ -342,9 +457,9 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
 #pragma unroll
                                 for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)__ldg(qq + c);
                             }
-                            const T rx = (T)(int32_t)(n2.cx - xi) * (T)A.scale + mx;
-                            const T ry = (T)(int32_t)(n2.cy - yi) * (T)A.scale + my;
-                            const T rz = (T)(int32_t)(n2.cz - zi) * (T)A.scale + mz;
+                            const T rx = (T)(int32_t)(n2.cx - xi) * (T)gscale + mx;
+                            const T ry = (T)(int32_t)(n2.cy - yi) * (T)gscale + my;
+                            const T rz = (T)(int32_t)(n2.cz - zi) * (T)gscale + mz;
                             pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, (T)A.as, bx, by, bz, bp);
                             npn++;
                         }
@@ -355,8 +470,6 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
             }
             k = knext;
         }
-        if (nleaf > 0)
-            pp_flush<T, TREEPM>(A, S, nleaf, total, lane, i, xi, yi, zi, hi, ax, ay, az, ap, npp);
         if (valid) {
             const T G = (T)A.G;
             A.acc[i] = (float)(-G * (ax + bx));
@@ -443,9 +556,9 @@ __global__ void k_zero_int(int *p) { *p = 0; }
 template <int P, typename T, bool TREEPM, bool GEOM>
 void launch_walk(const WalkArgs &A, cudaStream_t st)
 {
-    // residency: 8 warps per block; enough blocks to fill every SM several times
-    int nb = g4_num_sms() * 6;
-    k_walk<P, T, TREEPM, GEOM><<<nb, 256, 0, st>>>(A);
+    // persistent: enough 4-warp blocks to fill every SM; groups come from the work counter
+    int nb = g4_num_sms() * 8;
+    k_walk<P, T, TREEPM, GEOM><<<nb, WALK_THREADS, 0, st>>>(A);
 }
 
 template <int P, typename T>
@@ -539,6 +652,15 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     A.counts = counts;
     A.work = t->d_flags + 1;
     A.flags = t->d_flags;
+    A.b_dfs = t->b_dfs;
+    A.sys_first = t->sys_first;
+    A.sys_goff = t->sys_goff;
+    A.sys_box = t->sys_box;
+    A.n_sys = t->n_sys;
+    A.group_order = (t->group_order && !active && !t->n_sys && t->group_order_n == (ns + 31) / 32)
+                        ? t->group_order : nullptr;
+    if (t->n_sys && active)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_tree: active subsets are not supported for forests");
     A.scale = P->box_size / 4294967296.0;
     A.G = P->G;
     A.alpha = P->alpha;

@@ -68,6 +68,9 @@ def _declare(L):
         "g4_keys_sort_workspace": ([i64, C.POINTER(C.c_size_t)], i32),
         "g4_keys_sort": ([vp, i64, vp, vp, vp, C.c_size_t, vp], i32),
         "g4_keys_sort_noalloc": ([vp, i64, vp, vp, vp], i32),
+        "g4_keys_sort_batched_workspace": ([i64, C.POINTER(C.c_size_t)], i32),
+        "g4_keys_sort_batched": ([vp, i64, vp, vp, vp, vp, C.c_size_t, vp], i32),
+        "g4_tree_build_forest": ([vp, vp, vp, i64, vp, vp, C.c_int32, P, vp], i32),
         "g4_gather": ([vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "g4_scatter": ([vp, i64, vp, vp, vp, vp, vp], i32),
         "g4_tree_create": ([i64, i64, C.POINTER(vp)], i32),
@@ -81,6 +84,16 @@ def _declare(L):
         "g4_fmm_workspace": ([vp, P, C.POINTER(C.c_size_t)], i32),
         "g4_gravity_fmm": ([vp, vp, vp, vp, P, vp, vp, vp, vp, vp, C.c_size_t, vp], i32),
         "g4_direct": ([vp, vp, vp, i64, vp, i64, P, vp, vp, vp], i32),
+        "g4_mlp_param_count": ([], C.c_int32),
+        "g4_cost_features": ([vp, vp, vp, P, vp, vp, vp], i32),
+        "g4_cost_labels": ([vp, i64, C.c_float, vp, vp], i32),
+        "g4_mlp_forward": ([vp, vp, i64, vp, vp], i32),
+        "g4_mlp_train_workspace": ([i64, C.POINTER(C.c_size_t)], i32),
+        "g4_mlp_train_step": ([vp, vp, vp, C.c_int32, vp, vp, i64, C.c_float, vp, vp, vp,
+                               C.c_size_t, vp], i32),
+        "g4_schedule_workspace": ([i64, C.POINTER(C.c_size_t)], i32),
+        "g4_schedule_lpt": ([vp, i64, vp, vp, C.c_size_t, vp], i32),
+        "g4_tree_set_group_order": ([vp, vp, i64], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -172,6 +185,25 @@ def g4_keys_sort(pos_int: torch.Tensor, keys=None, perm=None, workspace=None, st
     return keys, perm
 
 
+def g4_keys_sort_batched(pos_int: torch.Tensor, sys_id: torch.Tensor, keys=None, perm=None,
+                         workspace=None, stream=None):
+    """Sort by (system, key).  sys_id: (n,) int16 tensor holding uint16 system ids."""
+    n = pos_int.shape[1]
+    dev = pos_int.device
+    keys = keys if keys is not None else torch.empty(n, dtype=torch.int64, device=dev)
+    perm = perm if perm is not None else torch.empty(n, dtype=torch.int32, device=dev)
+    if workspace is None:
+        b = C.c_size_t()
+        _check(lib().g4_keys_sort_batched_workspace(n, C.byref(b)), "g4_keys_sort_batched_workspace")
+        workspace = torch.empty(int(b.value) + 256, dtype=torch.uint8, device=dev)
+    wp = workspace.data_ptr()
+    off = (-wp) % 256
+    _check(lib().g4_keys_sort_batched(_ptr(pos_int), n, _ptr(sys_id), _ptr(keys), _ptr(perm),
+                                      C.c_void_p(wp + off), workspace.numel() - off, _stream(stream)),
+           "g4_keys_sort_batched")
+    return keys, perm
+
+
 def g4_gather(perm, pos, mass, cls=None, aold=None, out=None, stream=None):
     n = perm.shape[0]
     if out is None:
@@ -220,6 +252,15 @@ class Tree:
         _check(lib().g4_tree_build(self.h, _ptr(keys_sorted), _ptr(pos_sorted),
                                    int(pos_sorted.shape[1]), C.byref(p), _stream(stream)),
                "g4_tree_build")
+
+    def build_forest(self, keys_sorted, pos_sorted, sys_first, sys_box, p: G4Params, stream=None):
+        """sys_first: (n_sys+1,) int32 CUDA, sys_box: (n_sys,) float64 CUDA; both must outlive
+        the handle's later calls (the library keeps the pointers)."""
+        self._forest_refs = (sys_first, sys_box)
+        _check(lib().g4_tree_build_forest(self.h, _ptr(keys_sorted), _ptr(pos_sorted),
+                                          int(pos_sorted.shape[1]), _ptr(sys_first), _ptr(sys_box),
+                                          int(sys_box.shape[0]), C.byref(p), _stream(stream)),
+               "g4_tree_build_forest")
 
     def status(self, stream=None):
         nn = C.c_int64()
@@ -349,3 +390,162 @@ class TreeGravity:
     def forces(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None):
         self.prepare(pos_int, mass, cls, aold, p, stream)
         return self.walk(p, use_aold=aold is not None, stream=stream)
+
+
+class ForestGravity:
+    """Many independent systems solved together: one batched sort, one forest build, one
+    moments pass and one persistent walk launch for all systems (no per-system launches).
+
+    sizes: particle count per system; particles are passed system-major (system 0 first).
+    """
+
+    def __init__(self, sizes, p: G4Params, node_capacity: int = 0):
+        dev = torch.device("cuda")
+        sizes = [int(k) for k in sizes]
+        if min(sizes) < 1:
+            raise G4Error("every system needs at least one particle")
+        self.n = n = sum(sizes)
+        self.p = p
+        first = [0]
+        for k in sizes:
+            first.append(first[-1] + k)
+        self.sys_first = torch.tensor(first, dtype=torch.int32, device=dev)
+        self.sys_id = torch.repeat_interleave(torch.arange(len(sizes), dtype=torch.int32),
+                                              torch.tensor(sizes)).to(torch.int16).to(dev)
+        if node_capacity == 0:
+            node_capacity = 4096 + len(sizes) + int(n * max(1.5, 3.5 / max(1, int(p.leaf_max))))
+        self.tree = Tree(n, node_capacity)
+        b = C.c_size_t()
+        _check(lib().g4_keys_sort_batched_workspace(n, C.byref(b)), "g4_keys_sort_batched_workspace")
+        self.ws = torch.empty(int(b.value) + 256, dtype=torch.uint8, device=dev)
+        self.keys = torch.empty(n, dtype=torch.int64, device=dev)
+        self.perm = torch.empty(n, dtype=torch.int32, device=dev)
+        self.pos_s = torch.empty((3, n), dtype=torch.int32, device=dev)
+        self.mass_s = torch.empty(n, dtype=torch.float32, device=dev)
+        self.aold_s = torch.empty(n, dtype=torch.float32, device=dev)
+        self.acc_s = torch.zeros((3, n), dtype=torch.float32, device=dev)
+        self.pot_s = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.counts = torch.zeros((2, n), dtype=torch.int32, device=dev)
+        self.acc = torch.zeros((3, n), dtype=torch.float32, device=dev)
+        self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
+
+    def forces(self, pos_int, mass, sys_box, aold=None, p: G4Params | None = None, stream=None):
+        """pos_int (3,n) int32 (each system in its own integer frame), mass (n,) float32,
+        sys_box (n_sys,) float64 CUDA (kept alive by this object until the next call)."""
+        p = p or self.p
+        self.sys_box = sys_box
+        g4_keys_sort_batched(pos_int, self.sys_id, self.keys, self.perm, self.ws, stream)
+        g4_gather(self.perm, pos_int, mass, None, aold,
+                  out=(self.pos_s, self.mass_s, None, self.aold_s if aold is not None else None),
+                  stream=stream)
+        self.tree.build_forest(self.keys, self.pos_s, self.sys_first, sys_box, p, stream)
+        self.tree.multipoles(self.pos_s, self.mass_s, None, self.aold_s if aold is not None else None,
+                             p, stream)
+        self.tree.gravity_tree(self.pos_s, self.mass_s, None, self.aold_s if aold is not None else None,
+                               p, acc=self.acc_s, pot=self.pot_s, counts=self.counts, stream=stream)
+        g4_scatter(self.perm, self.acc_s, self.pot_s, out=(self.acc, self.pot), stream=stream)
+        return self.acc, self.pot
+
+
+# ---- learned cost model ---------------------------------------------------------------------------
+
+class CostModel:
+    """6 -> 32 -> 32 -> 1 MLP (BF16 weights/activations, FP32 sums) predicting log(1 + cost)
+    of each sink's walk from tree features; trained on the GPU by g4_mlp_train_step."""
+
+    def __init__(self, seed: int = 0):
+        dev = torch.device("cuda")
+        self.np = int(lib().g4_mlp_param_count())
+        g = torch.Generator().manual_seed(seed)
+        p = torch.empty(self.np)
+        # He-style initialisation, biases zero (layout W1,b1,W2,b2,W3,b3)
+        o = 0
+        for shape in ((32, 6), (32,), (32, 32), (32,), (32,), (1,)):
+            k = 1
+            for d in shape:
+                k *= d
+            if len(shape) == 2:
+                p[o:o + k] = torch.randn(k, generator=g) * (2.0 / shape[1]) ** 0.5
+            else:
+                p[o:o + k] = 0.0
+            o += k
+        p[self.np - 33:self.np - 1] = torch.randn(32, generator=g) * (1.0 / 32) ** 0.5
+        self.params = p.to(dev)
+        self.m = torch.zeros(self.np, device=dev)
+        self.v = torch.zeros(self.np, device=dev)
+        self.step = 0
+        self.loss = torch.zeros(1, device=dev)
+
+    def train(self, features, labels, steps: int = 200, lr: float = 3e-3, stream=None):
+        n = labels.shape[0]
+        b = C.c_size_t()
+        _check(lib().g4_mlp_train_workspace(n, C.byref(b)), "g4_mlp_train_workspace")
+        ws = torch.empty(int(b.value) // 4 + 64, dtype=torch.float32, device=labels.device)
+        losses = []
+        for _ in range(steps):
+            self.step += 1
+            _check(lib().g4_mlp_train_step(_ptr(self.params), _ptr(self.m), _ptr(self.v), self.step,
+                                           _ptr(features), _ptr(labels), n, float(lr), _ptr(self.loss),
+                                           None, _ptr(ws), ws.numel() * 4, _stream(stream)),
+                   "g4_mlp_train_step")
+            losses.append(self.loss.clone())
+        return torch.cat(losses)
+
+    def gradient(self, features, labels, stream=None):
+        n = labels.shape[0]
+        b = C.c_size_t()
+        _check(lib().g4_mlp_train_workspace(n, C.byref(b)), "g4_mlp_train_workspace")
+        ws = torch.empty(int(b.value) // 4 + 64, dtype=torch.float32, device=labels.device)
+        grad = torch.empty(self.np, device=labels.device)
+        m = torch.zeros_like(self.m)
+        v = torch.zeros_like(self.v)
+        _check(lib().g4_mlp_train_step(_ptr(self.params), _ptr(m), _ptr(v), 1, _ptr(features),
+                                       _ptr(labels), n, 0.0, _ptr(self.loss), _ptr(grad), _ptr(ws),
+                                       ws.numel() * 4, _stream(stream)), "g4_mlp_train_step")
+        return grad, self.loss.clone()
+
+    def predict(self, features, out=None, stream=None):
+        n = features.shape[0]
+        out = out if out is not None else torch.empty(n, device=features.device)
+        _check(lib().g4_mlp_forward(_ptr(self.params), _ptr(features), n, _ptr(out), _stream(stream)),
+               "g4_mlp_forward")
+        return out
+
+
+def cost_features(tree: Tree, p: G4Params, n: int, aold_sorted=None, bins_sorted=None, out=None,
+                  scratch=None, stream=None):
+    """(n, 6) float32 features of the tree's PH-sorted particles (g4_cost_features)."""
+    dev = torch.device("cuda")
+    out = out if out is not None else torch.empty((n, 6), dtype=torch.float32, device=dev)
+    scratch = scratch if scratch is not None else torch.empty(n, dtype=torch.int32, device=dev)
+    _check(lib().g4_cost_features(tree.h, _ptr(aold_sorted), _ptr(bins_sorted), C.byref(p), _ptr(out),
+                                  _ptr(scratch), _stream(stream)), "g4_cost_features")
+    return out
+
+
+def cost_labels(counts, c_pn: float = 5.0, out=None, stream=None):
+    n = counts.shape[1]
+    out = out if out is not None else torch.empty(n, device=counts.device)
+    _check(lib().g4_cost_labels(_ptr(counts), n, float(c_pn), _ptr(out), _stream(stream)), "g4_cost_labels")
+    return out
+
+
+def schedule_lpt(pred_sorted, group_order=None, stream=None):
+    n = pred_sorted.shape[0]
+    ng = (n + 31) // 32
+    group_order = group_order if group_order is not None else torch.empty(ng, dtype=torch.int32,
+                                                                         device=pred_sorted.device)
+    b = C.c_size_t()
+    _check(lib().g4_schedule_workspace(n, C.byref(b)), "g4_schedule_workspace")
+    ws = torch.empty(int(b.value) + 256, dtype=torch.uint8, device=pred_sorted.device)
+    wp = ws.data_ptr()
+    off = (-wp) % 256
+    _check(lib().g4_schedule_lpt(_ptr(pred_sorted), n, _ptr(group_order), C.c_void_p(wp + off),
+                                 ws.numel() - off, _stream(stream)), "g4_schedule_lpt")
+    return group_order
+
+
+def set_group_order(tree: Tree, group_order=None):
+    ng = 0 if group_order is None else int(group_order.shape[0])
+    tree._order_ref = group_order
+    _check(lib().g4_tree_set_group_order(tree.h, _ptr(group_order), ng), "g4_tree_set_group_order")

@@ -251,3 +251,46 @@ def test_small_and_degenerate_sets(n):
     else:
         assert np.allclose(ag, ao, rtol=1e-5, atol=1e-6 * np.abs(ao).max())
         assert np.allclose(pg, po, rtol=1e-5)
+
+
+# ---- batched independent systems (forest): one sort, one build, one walk launch ---------------
+
+def test_forest_many_plummer_spheres_parity():
+    systems = synth.multi_plummer(24, 1005, n_min=256, n_max=4096)
+    sizes = [ps.n for ps in systems]
+    qs, boxes, aolds, refs = [], [], [], []
+    for ps in systems:
+        q, frame = oracle.int_coords_isolated(ps.pos)
+        OP = oracle.OracleParams(box=frame[3], periodic=False, eps=ps.eps_table, alpha=0.0025)
+        ad, _ = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP)
+        aold = np.linalg.norm(ad, axis=1).astype(np.float32)
+        run = oracle.prepare(q, ps.mass, None, aold.astype(np.float64), OP, 8)
+        ao, po, co = oracle.tree_forces(run, np.arange(ps.n))
+        qs.append(q)
+        boxes.append(frame[3])
+        aolds.append(aold)
+        refs.append((ao, po, co))
+    P = g4.params(periodic=0, eps=[0.01], alpha=0.0025)
+    fg = g4.ForestGravity(sizes, P)
+    pos = u32_dev(torch, np.concatenate(qs, axis=1))
+    mass = to_dev(torch, np.concatenate([ps.mass for ps in systems]), torch.float32)
+    aold = to_dev(torch, np.concatenate(aolds), torch.float32)
+    box = torch.tensor(boxes, dtype=torch.float64, device="cuda")
+    acc, pot = fg.forces(pos, mass, box, aold)
+    torch.cuda.synchronize()
+    fg.tree.status()
+    ag = acc.cpu().numpy().T.astype(np.float64)
+    ao = np.concatenate([r[0] for r in refs])
+    e = relerr(ag, ao)
+    assert np.percentile(e, 99) < PARITY_P99, np.percentile(e, [50, 99, 100])
+    # forest topology: every system's tree equals its own oracle tree
+    nd = {k: v.cpu().numpy() for k, v in fg.tree.nodes().items()}
+    off = 0
+    for ps, q in zip(systems, qs):
+        ks, perm = oracle.sort(oracle.keys(q))
+        ot = oracle.Tree(ks, np.ascontiguousarray(q[:, perm]), 8).export()
+        m = len(ot["level"])
+        assert np.array_equal(nd["count"][off:off + m], ot["count"])
+        assert np.array_equal(nd["next"][off:off + m] - off, ot["next"])
+        off += m
+    assert off == len(nd["level"])
