@@ -43,7 +43,7 @@ FLOPS_PN = {1: 40, 2: 110, 3: 170, 4: 300, 5: 480}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA x max clock
 
 
-LEAF_MAX = 8
+LEAF_MAX = 32          # tuned on GB300 (profiles/autotune_leaf_256cubed.md)
 
 
 def workload_params(n_side=N_SIDE, L=L_BOX, leaf_max=None):
@@ -123,13 +123,13 @@ def oracle_sample_run(n_side=64):
     q = oracle.int_coords_periodic(ps.pos, L)
     OB = oracle.OracleParams(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
                              r_cut_factor=4.5, criterion=1, theta=0.5, order=3)
-    run = oracle.prepare(q, ps.mass, None, None, OB, 8)
+    run = oracle.prepare(q, ps.mass, None, None, OB, LEAF_MAX)
     ab, _, _ = oracle.tree_forces(run, np.arange(ps.n))
     aold = np.linalg.norm(ab, axis=1)
 
     def step():
         t0 = time.perf_counter()
-        r = oracle.prepare(q, ps.mass, None, aold, OP, 8)
+        r = oracle.prepare(q, ps.mass, None, aold, OP, LEAF_MAX)
         oracle.tree_forces(r, np.arange(ps.n))
         return time.perf_counter() - t0
 
@@ -161,12 +161,12 @@ def run_reference(args, rank, world):
     return 0
 
 
-def config_block(world, n_side=N_SIDE):
+def config_block(world, n_side=N_SIDE, leaf_max=None):
     L = L_BOX * n_side / N_SIDE
     return {"workload": f"periodic Zel'dovich box, {n_side}^3 particles, L={L:g}, rms displacement 2 "
                         f"spacings, TreePM short range r_s=1.25L/{2 * n_side}, R_cut=4.5, eps=L/{30 * n_side}, "
-                        "tree p=3, alpha=0.0025, leaf 8",
-            "n_particles": n_side ** 3, "order_p": 3, "alpha": 0.0025, "leaf_max": 8,
+                        f"tree p=3, alpha=0.0025, leaf {leaf_max or LEAF_MAX}",
+            "n_particles": n_side ** 3, "order_p": 3, "alpha": 0.0025, "leaf_max": leaf_max or LEAF_MAX,
             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
             "l2": "inputs (335 MB) larger than L2 (129 MB); no flush"}
 
@@ -289,6 +289,21 @@ def run_gpu(args, rank, world):
                     "sample": int(len(sinks)), "p50": float(np.percentile(e, 50)),
                     "p99": float(np.percentile(e, 99)), "max": float(np.max(e))}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        sample_ref = None
+        if accuracy is not None:
+            sample_ref = (sinks, ad)
+        for name, fn in (("cost_model", lambda: extra_cost_model(tg, P, n)),
+                         ("fmm", lambda: extra_fmm(pos_int, mass, aold, wp, n, sample_ref)),
+                         ("batched_systems", lambda: extra_forest(wp["leaf_max"])),
+                         ("hierarchical_bins", lambda: extra_bins(wp["leaf_max"]))):
+            try:
+                extras[name] = fn()
+            except Exception as ex:           # report, keep the headline line
+                extras[name] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
+            torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         nb, cstep = oracle_sample_run()
@@ -302,7 +317,7 @@ def run_gpu(args, rank, world):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic", "config": config_block(world, n_side), "clocks": clk,
+                "data": "synthetic", "config": config_block(world, n_side, args.leaf_max), "clocks": clk,
                 "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": int(n * (12 + 4 + 4)),
                         "d2h_bytes_per_step": int(n * (12 + 4))},
@@ -315,11 +330,164 @@ def run_gpu(args, rank, world):
                              "interactions_per_step": {"pp": int(counts[0]), "pn": int(counts[1])}},
                 "tree": {"nodes": nn, "max_level": ml},
                 "interactions_per_s": float((counts[0] + counts[1]) / (walk_ms * 1e-3)),
-                "accuracy": accuracy, "cpu_baseline": cpu}
+                "accuracy": accuracy, "cpu_baseline": cpu, **extras}
         print(json.dumps(line), flush=True)
     if dist:
         tdist.barrier()
     return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# further rows of the path, measured after the headline (each guarded: a failure is reported,
+# never fatal to the headline line)
+# ---------------------------------------------------------------------------------------------
+def _time(fn, reps, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_fmm(pos_int, mass, aold, wp, n, sample_ref):
+    """Symmetric FMM (p = 4, relative criterion) on the headline box."""
+    import torch
+    from paper_2010_03567_gb300 import g4
+    P4 = g4.params(**{**wp, "order_p": 4})
+    tg = g4.TreeGravity(n, P4)
+    tg.prepare(pos_int, mass, None, aold, P4)
+    ws = torch.empty(tg.tree.fmm_workspace(P4) + 256, dtype=torch.uint8, device="cuda")
+    out = {}
+
+    def step():
+        tg.prepare(pos_int, mass, None, aold, P4)
+        out["r"] = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, P4, workspace=ws)
+        g4.g4_scatter(tg.perm, out["r"][0], out["r"][1], out=(tg.acc, tg.pot))
+
+    ms = _time(step, 3)
+    tg.tree.status()
+    acc_s, _, cnt, mom = out["r"]
+    m = mass.double()
+    amag = torch.linalg.vector_norm(acc_s.double(), dim=0)
+    ms_s = tg.mass_s.double()
+    res = {"ms_per_step": ms, "forces_per_s": n / (ms * 1e-3), "order_p": 4,
+           "momentum_rel": float(torch.linalg.vector_norm(mom).item() / (ms_s * amag).sum().item()),
+           "pp_per_step": int(cnt[0].to(torch.int64).sum().item())}
+    if sample_ref is not None:
+        sinks, ad = sample_ref
+        ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
+        e = np.linalg.norm(ag - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        res["accuracy_vs_direct"] = {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99))}
+    del ws
+    return res
+
+
+def extra_forest(leaf_max):
+    """256 independent Plummer spheres (N log-uniform in [1024, 65536]) in one call sequence."""
+    import torch
+    from paper_2010_03567_gb300 import g4, synth
+    systems = synth.multi_plummer(256, 1005)
+    sizes = [ps.n for ps in systems]
+    n = sum(sizes)
+    qs, boxes = [], []
+    for ps in systems:
+        q, fr = g4.g4_int_coords(torch.from_numpy(ps.pos).cuda(), False)
+        qs.append(q)
+        boxes.append(fr[3:4])
+    pos = torch.cat(qs, dim=1).contiguous()
+    box = torch.cat(boxes).contiguous()
+    mass = torch.from_numpy(np.concatenate([ps.mass for ps in systems]).astype(np.float32)).cuda()
+    PB = g4.params(periodic=0, eps=[0.01], criterion=1, theta=0.5, leaf_max=leaf_max)
+    P = g4.params(periodic=0, eps=[0.01], alpha=0.0025, leaf_max=leaf_max)
+    fg = g4.ForestGravity(sizes, P)
+    acc0, _ = fg.forces(pos, mass, box, None, PB)
+    aold = torch.linalg.vector_norm(acc0, dim=0).contiguous()
+    l0 = g4.launch_count()
+    ms = _time(lambda: fg.forces(pos, mass, box, aold, P), 3)
+    launches = (g4.launch_count() - l0) / 4
+    fg.tree.status()
+    cnt = fg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+    return {"systems": len(sizes), "particles": n, "ms_per_step": ms, "forces_per_s": n / (ms * 1e-3),
+            "launches_per_step": launches, "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1])}
+
+
+def extra_bins(leaf_max):
+    """Zoom box with two softening classes and six nested active subsets (1..100%), one force
+    call per subset with its own tree, eager and replayed as one CUDA graph."""
+    import torch
+    from paper_2010_03567_gb300 import g4, synth
+    ps = synth.zoom(176, 100.0, 1004)
+    n = ps.n
+    rs = 1.25 * 100.0 / (2 * 176)
+    pos = torch.from_numpy(ps.pos).cuda()
+    q, _ = g4.g4_int_coords(pos, True, 100.0)
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    cls = torch.from_numpy(ps.eps_class).cuda()
+    base = dict(box_size=100.0, periodic=1, r_s=rs, r_cut_factor=4.5, eps=list(ps.eps_table),
+                leaf_max=leaf_max)
+    tg = g4.TreeGravity(n, g4.params(**base, criterion=1, theta=0.5), with_cls=True)
+    acc0, _ = tg.forces(q, mass, cls, None)
+    aold = torch.linalg.vector_norm(acc0, dim=0).contiguous()
+    order = torch.argsort(aold, descending=True).cpu().numpy()
+    fracs = [0.01, 0.03, 0.10, 0.30, 0.60, 1.00]
+    lists = [np.sort(order[:max(32, int(round(f * n)))]) for f in fracs]
+    del tg
+    P = g4.params(**base, alpha=0.0025)
+    bf = g4.BinnedForces(n, lists, P, with_cls=True)
+    forces = sum(len(a) for a in lists)
+    eager = _time(lambda: bf.run(q, mass, cls, aold), 3)
+    ref = [a.clone() for a in bf.acc]
+    bf.capture(q, mass, cls, aold)
+    graph = _time(bf.replay, 3)
+    same = all(torch.equal(a, b) for a, b in zip(ref, bf.acc))
+    return {"particles": n, "active_fractions": fracs, "forces_per_step": forces,
+            "eager_ms": eager, "graph_ms": graph, "forces_per_s_eager": forces / (eager * 1e-3),
+            "forces_per_s_graph": forces / (graph * 1e-3), "graph_equals_eager": bool(same)}
+
+
+def extra_cost_model(tg, P, n):
+    """Train the cost model on the counts of the last walk, schedule the walk's groups
+    heaviest first, and time the walk against the plain PH order."""
+    import torch
+    from paper_2010_03567_gb300 import g4
+    feats = g4.cost_features(tg.tree, P, n, tg.aold_s)
+    labels = g4.cost_labels(tg.counts)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    sub = torch.randperm(n, device="cuda", generator=g)[: min(n, 1 << 18)]
+    cm = g4.CostModel(seed=1)
+    t_train = _time(lambda: None, 1, warm=0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = cm.train(feats[sub].contiguous(), labels[sub].contiguous(), steps=400, lr=3e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    t_train = e0.elapsed_time(e1)
+    pred = cm.predict(feats)
+    order = g4.schedule_lpt(pred)
+    walk = lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, acc=tg.acc_s,
+                                        pot=tg.pot_s, counts=tg.counts)
+    g4.set_group_order(tg.tree, None)
+    ph_ms = _time(walk, 5)
+    ref = tg.acc_s.clone()
+    g4.set_group_order(tg.tree, order)
+    lpt_ms = _time(walk, 5)
+    same = bool(torch.equal(ref, tg.acc_s))
+    g4.set_group_order(tg.tree, None)
+    p_np, l_np = pred.cpu().numpy(), labels.cpu().numpy()
+    rk = lambda a: np.argsort(np.argsort(a))
+    return {"train_ms": t_train, "train_samples": int(sub.shape[0]), "steps": 400,
+            "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "rank_corr": float(np.corrcoef(rk(p_np), rk(l_np))[0, 1]),
+            "mean_abs_err_log_cost": float(np.mean(np.abs(p_np - l_np))),
+            "walk_ms_ph_order": ph_ms, "walk_ms_lpt_order": lpt_ms,
+            "forces_identical": same}
 
 
 def main():
@@ -330,6 +498,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FMM, batched-systems, time-bin and cost-model measurements")
     ap.add_argument("--leaf-max", type=int, default=None,
                     help="leaf threshold of the tree (default: the tuned value)")
     ap.add_argument("--n-side", type=int, default=N_SIDE,

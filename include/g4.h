@@ -160,6 +160,20 @@ g4_status g4_gather(const int32_t *perm, int64_t n, const uint32_t *pos_in,
 g4_status g4_scatter(const int32_t *perm, int64_t n, const float *acc_sorted,
                      const float *pot_sorted, float *acc_out, float *pot_out, void *stream);
 
+/* Active subsets (hierarchical time bins, where each force call builds its tree over the
+ * active particles only): out[k] = in[idx[k]] for k < n_sub, where the input arrays hold
+ * n_all particles (pos_in 3 x n_all SoA) and the outputs n_sub (pos_out 3 x n_sub SoA).
+ * cls/aold may be NULL (both in and out). */
+g4_status g4_gather_subset(const int32_t *idx, int64_t n_sub, int64_t n_all, const uint32_t *pos_in,
+                           const float *mass_in, const uint8_t *cls_in, const float *aold_in,
+                           uint32_t *pos_out, float *mass_out, uint8_t *cls_out, float *aold_out,
+                           void *stream);
+
+/* The inverse: acc_out[idx[k]] = acc_sub[k] (3 x n_sub into 3 x n_all SoA), pot likewise
+ * (both NULL or both set). */
+g4_status g4_scatter_subset(const int32_t *idx, int64_t n_sub, int64_t n_all, const float *acc_sub,
+                            const float *pot_sub, float *acc_out, float *pot_out, void *stream);
+
 /* ---- a4: oct-tree (Sec. 2.2.1) ---------------------------------------------------------- */
 
 /* Allocates a tree handle for up to n_max particles and node_capacity nodes (0 = a default

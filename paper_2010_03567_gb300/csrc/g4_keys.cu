@@ -316,6 +316,39 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
 // -------------------------------------------------------------------------------------------
 // gather / scatter of particle arrays
 // -------------------------------------------------------------------------------------------
+// gather / scatter of a subset between arrays of different SoA strides
+__global__ void k_gather_subset(const int32_t *__restrict__ idx, int64_t n_out, int64_t n_in,
+                                const uint32_t *__restrict__ pin, const float *__restrict__ min,
+                                const uint8_t *__restrict__ cin, const float *__restrict__ ain,
+                                uint32_t *__restrict__ pout, float *__restrict__ mout,
+                                uint8_t *__restrict__ cout, float *__restrict__ aout)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_out;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = idx[k];
+        pout[k] = pin[j];
+        pout[n_out + k] = pin[n_in + j];
+        pout[2 * n_out + k] = pin[2 * n_in + j];
+        mout[k] = min[j];
+        if (cin) cout[k] = cin[j];
+        if (ain) aout[k] = ain[j];
+    }
+}
+
+__global__ void k_scatter_subset(const int32_t *__restrict__ idx, int64_t n_sub, int64_t n_out,
+                                 const float *__restrict__ ain, const float *__restrict__ pin,
+                                 float *__restrict__ aout, float *__restrict__ pout)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_sub;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = idx[k];
+        aout[j] = ain[k];
+        aout[n_out + j] = ain[n_sub + k];
+        aout[2 * n_out + j] = ain[2 * n_sub + k];
+        if (pin) pout[j] = pin[k];
+    }
+}
+
 __global__ void k_gather(const int32_t *__restrict__ perm, int64_t n,
                          const uint32_t *__restrict__ pin, const float *__restrict__ min,
                          const uint8_t *__restrict__ cin, const float *__restrict__ ain,
@@ -562,6 +595,37 @@ extern "C" g4_status g4_gather(const int32_t *perm, int64_t n, const uint32_t *p
     k_gather<<<g4_blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
         perm, n, pos_in, mass_in, cls_in, aold_in, pos_out, mass_out, cls_out, aold_out);
     return g4_launch_check("gather", 1);
+}
+
+extern "C" g4_status g4_gather_subset(const int32_t *idx, int64_t n_sub, int64_t n_all,
+                                      const uint32_t *pos_in, const float *mass_in,
+                                      const uint8_t *cls_in, const float *aold_in,
+                                      uint32_t *pos_out, float *mass_out, uint8_t *cls_out,
+                                      float *aold_out, void *stream)
+{
+    if (n_sub < 0 || n_all < 0 || n_sub > n_all)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_gather_subset: sizes");
+    if (n_sub == 0) return G4_OK;
+    if (!idx || !pos_in || !mass_in || !pos_out || !mass_out || (!cls_in) != (!cls_out) ||
+        (!aold_in) != (!aold_out))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_gather_subset: bad pointers");
+    k_gather_subset<<<g4_blocks_for(n_sub, 256), 256, 0, (cudaStream_t)stream>>>(
+        idx, n_sub, n_all, pos_in, mass_in, cls_in, aold_in, pos_out, mass_out, cls_out, aold_out);
+    return g4_launch_check("gather subset", 1);
+}
+
+extern "C" g4_status g4_scatter_subset(const int32_t *idx, int64_t n_sub, int64_t n_all,
+                                       const float *acc_sub, const float *pot_sub, float *acc_out,
+                                       float *pot_out, void *stream)
+{
+    if (n_sub < 0 || n_all < 0 || n_sub > n_all)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_scatter_subset: sizes");
+    if (n_sub == 0) return G4_OK;
+    if (!idx || !acc_sub || !acc_out || (!pot_sub) != (!pot_out))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_scatter_subset: bad pointers");
+    k_scatter_subset<<<g4_blocks_for(n_sub, 256), 256, 0, (cudaStream_t)stream>>>(
+        idx, n_sub, n_all, acc_sub, pot_sub, acc_out, pot_out);
+    return g4_launch_check("scatter subset", 1);
 }
 
 extern "C" g4_status g4_scatter(const int32_t *perm, int64_t n, const float *acc_sorted,

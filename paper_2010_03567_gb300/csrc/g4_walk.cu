@@ -10,6 +10,8 @@
 // multipole (particle-node term), or -- for a leaf -- particle-particle terms with the
 // leaf's particles.  Groups are handed out by a device work counter, so warps that finish
 // early pull more groups (persistent kernel).
+#include <cuda_fp16.h>
+
 #include "g4_internal.cuh"
 #include "g4_kernels.cuh"
 
@@ -58,15 +60,16 @@ template <int P, typename T> __device__ __forceinline__ T ipow(T x)
 constexpr int WALK_THREADS = 128;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int LEAF_BUF = 64;
-constexpr int STAGE = 64;       // sources staged per pass of the particle-particle phase
+constexpr int STAGE = 128;      // sources staged per pass of the particle-particle phase
 
 // per-warp shared state: the pending leaf list of the group and the staged sources
 struct WalkSmem {
     int first[LEAF_BUF], count[LEAF_BUF], pref[LEAF_BUF], node[LEAF_BUF];
     unsigned mask[LEAF_BUF];
-    float4 rel[STAGE];          // source position relative to the group centre (float), mass
     uint4 ipos[STAGE];          // source integer position, softening length h (bits)
-    int2 mj[STAGE];             // lane mask of the source's leaf, particle index
+    float2 mj[STAGE];           // source mass, particle index (bits)
+    unsigned smask[STAGE];      // lane mask of the source's leaf
+    __half hx[STAGE], hy[STAGE], hz[STAGE];   // position / r_cut relative to the group centre
     float4 sink[32];            // sinks relative to the group centre, opening threshold
 };
 
@@ -120,39 +123,25 @@ __device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &n
 }
 
 // Particle-particle phase for the pending leaves of a group.
-//  1. TreePM: each leaf's lane mask is narrowed to the lanes whose cutoff sphere reaches the
-//     leaf's cube (the per-lane skip of a single-particle walk), empty leaves are dropped.
-//  2. Sources are staged 128 at a time; every lane tests them against its sink with positions
-//     relative to the group centre (cheap, slightly enlarged cutoff) and keeps a bit per
-//     candidate; then each lane evaluates its own candidates with exact integer separations,
-//     the exact cutoff and the full kernel.  Lanes only spend the expensive kernel on their
-//     own pairs, so the warp is not held back by pairs of other lanes.
-// The sum order of every sink is the order of its sources in the list (depth-first), so the
-// result does not depend on which other sinks share the group.
+// Sources are staged 128 at a time.  TreePM: every lane first tests all staged sources against
+// its own sink in packed FP16x2 (two sources per instruction; positions relative to the group
+// centre in units of r_cut, 5% margin on r^2, so no pair inside r_cut is missed) and keeps a
+// candidate bit per source; then each lane evaluates only its own candidates with exact
+// integer separations, the exact cutoff and the full kernel.  Leaf masks (lanes that used an
+// ancestor's multipole must not see the leaf) are applied per source when a staged leaf does
+// not reach the whole group.  The sum order of every sink is the order of its sources in the
+// list (depth-first), independent of which other sinks share the group.
 template <typename T, bool TREEPM>
 __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nleaf, int lane, int i,
                                          uint32_t xi, uint32_t yi, uint32_t zi, uint32_t gcx,
                                          uint32_t gcy, uint32_t gcz, float xr, float yr, float zr,
-                                         T hi, T &ax, T &ay, T &az, T &ap, uint32_t &npp,
-                                         double gscale, double gbox)
+                                         unsigned vmask, T hi, T &ax, T &ay, T &az, T &ap,
+                                         uint32_t &npp, double gscale, double gbox)
 {
-    const float fscale = (float)gscale, fbox = (float)gbox;
+    const float fscale = (float)gscale;
     const T scale = (T)gscale, as = (T)A.as, rcut2 = (T)A.rcut2;
-    // 1. per-lane leaf masks and compaction
-    if (TREEPM) {
-        for (int e = 0; e < nleaf; e++) {
-            const G4Node nd = load_node(A.node + S.node[e]);
-            const float half = 0.5f * ldexpf(fbox, -(int)(nd.meta & 31u));
-            const float ex = fmaxf(fabsf((float)(int32_t)(nd.cx - gcx) * fscale - xr) - half, 0.f);
-            const float ey = fmaxf(fabsf((float)(int32_t)(nd.cy - gcy) * fscale - yr) - half, 0.f);
-            const float ez = fmaxf(fabsf((float)(int32_t)(nd.cz - gcz) * fscale - zr) - half, 0.f);
-            const bool reach = ex * ex + ey * ey + ez * ez <= 1.0001f * (float)A.rcut2 + 1e-30f;
-            const unsigned m = __ballot_sync(0xffffffffu, reach) & S.mask[e];
-            __syncwarp();
-            if (lane == 0) S.mask[e] = m;
-            __syncwarp();
-        }
-    }
+    (void)gbox;
+    // drop leaves nobody reaches; prefix sums of the particle counts
     int nk = 0, total = 0;
     for (int b = 0; b < nleaf; b += 32) {
         const int e = b + lane;
@@ -185,10 +174,13 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
         nk += __popc(km);
         total += __shfl_sync(0xffffffffu, pre, 31);
     }
-    const float rc2t = TREEPM ? 1.0001f * (float)A.rcut2 + 1e-30f : 3.0e38f;
+    const float inv_rc = TREEPM ? rsqrtf((float)A.rcut2) : 0.f;
+    const __half2 sx2 = __float2half2_rn(xr * inv_rc), sy2 = __float2half2_rn(yr * inv_rc),
+                  sz2 = __float2half2_rn(zr * inv_rc);
+    const __half2 lim = __float2half2_rn(1.05f);
     for (int b = 0; b < total; b += STAGE) {
         const int nb = min(STAGE, total - b);
-        // stage up to 128 sources (4 per lane)
+        bool partial = false;
 #pragma unroll
         for (int q = 0; q < STAGE / 32; q++) {
             const int u = q * 32 + lane, t = b + u;
@@ -202,32 +194,61 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
                 const int j = S.first[lo] + (t - S.pref[lo]);
                 const uint32_t px = __ldg(A.pos + j), py = __ldg(A.pos + A.n + j),
                                pz = __ldg(A.pos + 2 * A.n + j);
-                const float mj = __ldg(A.mass + j);
                 const float hj = A.h_cls[A.cls ? __ldg(A.cls + j) : 0];
-                S.rel[u] = make_float4((float)(int32_t)(px - gcx) * fscale,
-                                       (float)(int32_t)(py - gcy) * fscale,
-                                       (float)(int32_t)(pz - gcz) * fscale, mj);
+                const unsigned mk = S.mask[lo];
                 S.ipos[u] = make_uint4(px, py, pz, __float_as_uint(hj));
-                S.mj[u] = make_int2((int)S.mask[lo], j);
+                S.mj[u] = make_float2(__ldg(A.mass + j), __int_as_float(j));
+                S.smask[u] = mk;
+                S.hx[u] = __float2half_rn((float)(int32_t)(px - gcx) * fscale * inv_rc);
+                S.hy[u] = __float2half_rn((float)(int32_t)(py - gcy) * fscale * inv_rc);
+                S.hz[u] = __float2half_rn((float)(int32_t)(pz - gcz) * fscale * inv_rc);
+                partial |= (mk != vmask);
+            } else {
+                S.hx[u] = S.hy[u] = S.hz[u] = __float2half_rn(100.f);
             }
         }
+        partial = __any_sync(0xffffffffu, partial);
         __syncwarp();
-        // candidate bits of this lane (64-bit: one per staged source)
-        unsigned long long cand = 0ull;
+        unsigned long long c0 = 0ull, c1 = 0ull;
+        if (TREEPM) {
+            const __half2 *X = reinterpret_cast<const __half2 *>(S.hx);
+            const __half2 *Y = reinterpret_cast<const __half2 *>(S.hy);
+            const __half2 *Z = reinterpret_cast<const __half2 *>(S.hz);
+            const int np = (nb + 1) >> 1;
 #pragma unroll 4
-        for (int v = 0; v < nb; v++) {
-            const int2 mj = S.mj[v];
-            const float4 r = S.rel[v];
-            const float dx = r.x - xr, dy = r.y - yr, dz = r.z - zr;
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            const bool c = (((unsigned)mj.x >> lane) & 1u) && mj.y != i && d2 <= rc2t;
-            cand |= (c ? 1ull : 0ull) << v;
+            for (int pr = 0; pr < np; pr++) {
+                const __half2 dx = __hsub2(X[pr], sx2), dy = __hsub2(Y[pr], sy2),
+                              dz = __hsub2(Z[pr], sz2);
+                const __half2 d2 = __hfma2(dz, dz, __hfma2(dy, dy, __hmul2(dx, dx)));
+                const unsigned m = __hle2_mask(d2, lim);
+                const unsigned long long bits2 = (m & 1u) | ((m >> 15) & 2u);
+                if (pr < 32) c0 |= bits2 << (2 * pr);
+                else c1 |= bits2 << (2 * (pr - 32));
+            }
+        } else {
+            c0 = nb >= 64 ? ~0ull : ((1ull << nb) - 1ull);
+            c1 = nb >= 128 ? ~0ull : (nb > 64 ? ((1ull << (nb - 64)) - 1ull) : 0ull);
+        }
+        if (partial) {
+            for (int u = 0; u < nb; u++)
+                if (!((S.smask[u] >> lane) & 1u)) {
+                    if (u < 64) c0 &= ~(1ull << u);
+                    else c1 &= ~(1ull << (u - 64));
+                }
         }
         // exact evaluation of the lane's own candidates
-        while (cand) {
-            const int u = __ffsll((long long)cand) - 1;
-            cand &= cand - 1ull;
+        while (c0 | c1) {
+            int u;
+            if (c0) {
+                u = __ffsll((long long)c0) - 1;
+                c0 &= c0 - 1ull;
+            } else {
+                u = 64 + __ffsll((long long)c1) - 1;
+                c1 &= c1 - 1ull;
+            }
             const uint4 ip = S.ipos[u];
+            const float2 mj = S.mj[u];
+            if (__float_as_int(mj.y) == i) continue;
             const T dx = (T)(int32_t)(ip.x - xi) * scale;
             const T dy = (T)(int32_t)(ip.y - yi) * scale;
             const T dz = (T)(int32_t)(ip.z - zi) * scale;
@@ -235,12 +256,12 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
             if (TREEPM && A.pp_cut && r2 >= rcut2) continue;
             T g0, g1;
             pair_kernel<T, TREEPM>(r2, fmax(hi, (T)__uint_as_float(ip.w)), as, g0, g1);
-            const T mj = (T)S.rel[u].w;
-            const T mg1 = mj * g1;
+            const T m_ = (T)mj.x;
+            const T mg1 = m_ * g1;
             ax += mg1 * dx;
             ay += mg1 * dy;
             az += mg1 * dz;
-            ap += mj * g0;
+            ap += m_ * g0;
             npp++;
         }
         __syncwarp();
@@ -326,7 +347,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
         for (;;) {
             // a window adds at most 32 leaves: flush before the list could overflow, and at the end
             if (nleaf > LEAF_BUF - 32 || (k >= nn && nleaf > 0)) {
-                pp_flush<T, TREEPM>(A, S, nleaf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, hi, ax, ay, az, ap, npp, gscale, gbox);
+                pp_flush<T, TREEPM>(A, S, nleaf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, vmask, hi, ax, ay, az, ap, npp, gscale, gbox);
                 nleaf = 0;
             }
             if (k >= nn) break;

@@ -73,6 +73,8 @@ def _declare(L):
         "g4_tree_build_forest": ([vp, vp, vp, i64, vp, vp, C.c_int32, P, vp], i32),
         "g4_gather": ([vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "g4_scatter": ([vp, i64, vp, vp, vp, vp, vp], i32),
+        "g4_gather_subset": ([vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
+        "g4_scatter_subset": ([vp, i64, i64, vp, vp, vp, vp, vp], i32),
         "g4_tree_create": ([i64, i64, C.POINTER(vp)], i32),
         "g4_tree_free": ([vp], None),
         "g4_tree_build": ([vp, vp, vp, i64, P, vp], i32),
@@ -549,3 +551,59 @@ def set_group_order(tree: Tree, group_order=None):
     ng = 0 if group_order is None else int(group_order.shape[0])
     tree._order_ref = group_order
     _check(lib().g4_tree_set_group_order(tree.h, _ptr(group_order), ng), "g4_tree_set_group_order")
+
+
+# ---- hierarchical time bins: one force call per bin over its active subset -------------------------
+
+class BinnedForces:
+    """Force calls over nested active subsets (the hierarchical time integration of the paper
+    builds each force call's tree over the active particles only).  Every bin has its own
+    preallocated pipeline, so the whole sequence allocates nothing and can be captured in one
+    CUDA graph (``capture``) and replayed."""
+
+    def __init__(self, n_all: int, active_lists, p: G4Params, with_cls: bool = False):
+        dev = torch.device("cuda")
+        self.n_all = n_all
+        self.p = p
+        self.idx = [torch.as_tensor(a, dtype=torch.int32).to(dev) for a in active_lists]
+        self.bins = []
+        for ix in self.idx:
+            k = int(ix.shape[0])
+            tg = TreeGravity(k, p, with_cls=with_cls)
+            sub = (torch.empty((3, k), dtype=torch.int32, device=dev),
+                   torch.empty(k, dtype=torch.float32, device=dev),
+                   torch.empty(k, dtype=torch.uint8, device=dev) if with_cls else None,
+                   torch.empty(k, dtype=torch.float32, device=dev))
+            self.bins.append((tg, sub))
+        self.acc = [torch.zeros((3, n_all), dtype=torch.float32, device=dev) for _ in self.idx]
+        self.pot = [torch.zeros(n_all, dtype=torch.float32, device=dev) for _ in self.idx]
+        self.graph = None
+
+    def run(self, pos_int, mass, cls, aold, stream=None):
+        for b, (ix, (tg, sub)) in enumerate(zip(self.idx, self.bins)):
+            k = int(ix.shape[0])
+            _check(lib().g4_gather_subset(_ptr(ix), k, self.n_all, _ptr(pos_int), _ptr(mass), _ptr(cls),
+                                          _ptr(aold), _ptr(sub[0]), _ptr(sub[1]), _ptr(sub[2]),
+                                          _ptr(sub[3]), _stream(stream)), "g4_gather_subset")
+            acc, pot = tg.forces(sub[0], sub[1], sub[2], sub[3], self.p, stream)
+            _check(lib().g4_scatter_subset(_ptr(ix), k, self.n_all, _ptr(acc), _ptr(pot), _ptr(self.acc[b]),
+                                           _ptr(self.pot[b]), _stream(stream)), "g4_scatter_subset")
+        return self.acc, self.pot
+
+    def capture(self, pos_int, mass, cls, aold):
+        """Capture the whole bin sequence in one CUDA graph (inputs are bound by address)."""
+        self.run(pos_int, mass, cls, aold)          # first call outside capture (lazy init)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.run(pos_int, mass, cls, aold)
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        return self.acc, self.pot

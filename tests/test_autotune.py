@@ -1,0 +1,34 @@
+"""Host logic of the leaf-size autotuner (selection and cache), with a fake timer (CPU)."""
+from paper_2010_03567_gb300 import autotune
+
+
+class FakeParams:
+    box_size = 100.0
+    periodic = 1
+    r_s = 0.5
+    r_cut_factor = 4.5
+    order_p = 3
+    alpha = 0.0025
+    criterion = 0
+
+
+def test_pick_and_cache(tmp_path):
+    path = str(tmp_path / "cache.json")
+    calls = []
+
+    def timer(leaf):
+        calls.append(leaf)
+        return {8: 5.0, 16: 3.0, 24: 2.5, 32: 2.5, 48: 2.7, 64: 4.0}[leaf]
+
+    best, times = autotune.tune(timer, "GB300", 1 << 20, FakeParams(), path=path)
+    assert best == 32            # tie between 24 and 32 goes to the larger leaf
+    assert sorted(calls) == [8, 16, 24, 32, 48, 64]
+    calls.clear()
+    best2, times2 = autotune.tune(timer, "GB300", 1 << 20, FakeParams(), path=path)
+    assert best2 == 32 and calls == [] and times2 == times
+    # another workload class is tuned separately
+    p = FakeParams()
+    p.alpha = 0.01
+    autotune.tune(timer, "GB300", 1 << 20, p, path=path)
+    assert len(calls) == 6
+    assert autotune.signature(1 << 20, p) != autotune.signature(1 << 20, FakeParams())
