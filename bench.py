@@ -470,15 +470,18 @@ def extra_cost_model(tg, P, n):
     torch.cuda.synchronize()
     t_train = e0.elapsed_time(e1)
     pred = cm.predict(feats)
-    order = g4.schedule_lpt(pred)
     walk = lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, acc=tg.acc_s,
                                         pot=tg.pot_s, counts=tg.counts)
     g4.set_group_order(tg.tree, None)
     ph_ms = _time(walk, 5)
     ref = tg.acc_s.clone()
-    g4.set_group_order(tg.tree, order)
-    lpt_ms = _time(walk, 5)
-    same = bool(torch.equal(ref, tg.acc_s))
+    lpt = {}
+    same = True
+    for chunk in (1, 64, 512):
+        order = g4.schedule_lpt(pred, chunk)
+        g4.set_group_order(tg.tree, order)
+        lpt[chunk] = _time(walk, 5)
+        same = same and bool(torch.equal(ref, tg.acc_s))
     g4.set_group_order(tg.tree, None)
     p_np, l_np = pred.cpu().numpy(), labels.cpu().numpy()
     rk = lambda a: np.argsort(np.argsort(a))
@@ -486,7 +489,8 @@ def extra_cost_model(tg, P, n):
             "loss_first_last": [float(losses[0]), float(losses[-1])],
             "rank_corr": float(np.corrcoef(rk(p_np), rk(l_np))[0, 1]),
             "mean_abs_err_log_cost": float(np.mean(np.abs(p_np - l_np))),
-            "walk_ms_ph_order": ph_ms, "walk_ms_lpt_order": lpt_ms,
+            "walk_ms_ph_order": ph_ms,
+            "walk_ms_lpt_order": {f"chunk{c}": v for c, v in lpt.items()},
             "forces_identical": same}
 
 

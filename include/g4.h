@@ -309,9 +309,11 @@ g4_status g4_mlp_train_step(float *params, float *adam_m, float *adam_v, int32_t
 g4_status g4_schedule_workspace(int64_t n, size_t *bytes);
 
 /* Longest-processing-time schedule of the walk: group g holds sorted sinks [32g, 32g+32);
- * its predicted cost is the sum of expm1(pred) over its sinks; group_order (ceil(n/32) int32,
- * device) lists the groups by descending predicted cost (ties in PH order). */
-g4_status g4_schedule_lpt(const float *pred_sorted, int64_t n, int32_t *group_order,
+ * groups are taken in chunks of `chunk` consecutive groups (chunk = 1: single groups), a
+ * chunk's predicted cost is the sum of expm1(pred) over its sinks, and group_order
+ * (ceil(n/32) int32, device) lists the chunks by descending cost with the groups of a chunk
+ * in PH order (chunks keep neighbouring groups together, which preserves cache reuse). */
+g4_status g4_schedule_lpt(const float *pred_sorted, int64_t n, int32_t chunk, int32_t *group_order,
                           void *workspace, size_t workspace_bytes, void *stream);
 
 /* Makes later g4_gravity_tree calls on this handle hand out groups in `group_order`

@@ -229,15 +229,41 @@ __global__ void k_mlp_adam(float *__restrict__ P, float *__restrict__ m, float *
 
 // ---- longest-processing-time order of the walk groups ----------------------------------------
 
-__global__ void k_group_cost(const float *__restrict__ pred, int n, int ngroups,
+// predicted cost of chunks of `chunk` consecutive walk groups (32 sinks each), as sort keys
+// for descending cost
+__global__ void k_chunk_cost(const float *__restrict__ pred, int n, int chunk, int nchunks,
                              uint64_t *__restrict__ key)
 {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
-        float c = 0.f;
-        const int e = min(n, g * 32 + 32);
-        for (int i = g * 32; i < e; i++) c += expm1f(fmaxf(pred[i], 0.f));
-        // descending cost = ascending complement of the (non-negative) float bits
-        key[g] = (uint64_t)(0xFFFFFFFFu - __float_as_uint(fmaxf(c, 0.f)));
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        const int b = c * chunk * 32, e = min(n, b + chunk * 32);
+        for (int i = b; i < e; i++) s += expm1f(fmaxf(pred[i], 0.f));
+        key[c] = (uint64_t)(0xFFFFFFFFu - __float_as_uint(fmaxf(s, 0.f)));
+    }
+}
+
+// position of the (possibly short) last chunk in the sorted chunk order
+__global__ void k_find_last(const int32_t *__restrict__ chunk_order, int nchunks, int32_t *pos)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nchunks; p += gridDim.x * blockDim.x)
+        if (chunk_order[p] == nchunks - 1) *pos = p;
+}
+
+// group order: chunks by descending predicted cost, groups inside a chunk in PH order.  All
+// chunks hold `chunk` groups except the last one; chunks placed after it start earlier by
+// the difference.
+__global__ void k_expand_chunks(const int32_t *__restrict__ chunk_order, int nchunks, int chunk,
+                                int ngroups, const int32_t *__restrict__ pos_last,
+                                int32_t *__restrict__ group_order)
+{
+    const int last = nchunks - 1;
+    const int last_size = ngroups - last * chunk;
+    const int pl = *pos_last;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nchunks; p += gridDim.x * blockDim.x) {
+        const int c = chunk_order[p];
+        const int start = p * chunk - (p > pl ? chunk - last_size : 0);
+        const int size = (c == last) ? last_size : chunk;
+        for (int t = 0; t < size; t++) group_order[start + t] = c * chunk + t;
     }
 }
 
@@ -315,27 +341,39 @@ extern "C" g4_status g4_schedule_workspace(int64_t n, size_t *bytes)
 {
     if (!bytes || n < 0) return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_workspace: bad args");
     const int64_t ng = (n + 31) / 32;
-    *bytes = al256c(8 * (size_t)(ng > 0 ? ng : 1)) + g4_sort_workspace_bytes(ng);
+    *bytes = al256c(8 * (size_t)(ng > 0 ? ng : 1)) + al256c(4 * (size_t)(ng > 0 ? ng : 1)) +
+             256 + g4_sort_workspace_bytes(ng);
     return G4_OK;
 }
 
-extern "C" g4_status g4_schedule_lpt(const float *pred_sorted, int64_t n, int32_t *group_order,
-                                     void *workspace, size_t workspace_bytes, void *stream)
+extern "C" g4_status g4_schedule_lpt(const float *pred_sorted, int64_t n, int32_t chunk,
+                                     int32_t *group_order, void *workspace, size_t workspace_bytes,
+                                     void *stream)
 {
-    if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!pred_sorted || !group_order || !workspace)))
+    if (n < 0 || n >= ((int64_t)1 << 31) || chunk < 1 ||
+        (n > 0 && (!pred_sorted || !group_order || !workspace)))
         return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_lpt: bad arguments");
     if (n == 0) return G4_OK;
     const int64_t ng = (n + 31) / 32;
-    const size_t need = al256c(8 * (size_t)ng) + g4_sort_workspace_bytes(ng);
+    const int64_t nc = (ng + chunk - 1) / chunk;
+    size_t need = 0;
+    g4_schedule_workspace(n, &need);
     if (workspace_bytes < need) return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_lpt: workspace too small");
     cudaStream_t st = (cudaStream_t)stream;
     uint64_t *key = (uint64_t *)workspace;
-    void *sws = (char *)workspace + al256c(8 * (size_t)ng);
-    k_group_cost<<<g4_blocks_for(ng, 256), 256, 0, st>>>(pred_sorted, (int)n, (int)ng, key);
-    g4_status s = g4_launch_check("group cost", 1);
+    int32_t *corder = (int32_t *)((char *)workspace + al256c(8 * (size_t)ng));
+    int32_t *pos_last = (int32_t *)((char *)corder + al256c(4 * (size_t)ng));
+    void *sws = (char *)pos_last + 256;
+    k_chunk_cost<<<g4_blocks_for(nc, 256), 256, 0, st>>>(pred_sorted, (int)n, chunk, (int)nc, key);
+    g4_status s = g4_launch_check("chunk cost", 1);
     if (s != G4_OK) return s;
     // stable sort by descending predicted cost; ties keep PH order
-    return g4_sort_pairs_u64(key, key, group_order, ng, sws, g4_sort_workspace_bytes(ng), 32, st);
+    s = g4_sort_pairs_u64(key, key, corder, nc, sws, g4_sort_workspace_bytes(nc), 32, st);
+    if (s != G4_OK) return s;
+    k_find_last<<<g4_blocks_for(nc, 256), 256, 0, st>>>(corder, (int)nc, pos_last);
+    k_expand_chunks<<<g4_blocks_for(nc, 256), 256, 0, st>>>(corder, (int)nc, chunk, (int)ng, pos_last,
+                                                           group_order);
+    return g4_launch_check("expand chunks", 2);
 }
 
 extern "C" g4_status g4_tree_set_group_order(g4_tree t, const int32_t *group_order, int64_t ngroups)

@@ -9,6 +9,8 @@
 #define G4_KEYBITS 21
 #define G4_MAXLEVEL 21
 #define G4_NLEVELS 22
+#define G4_WALK_QCAP 4096            // walk frontier ring per warp (power of two)
+#define G4_WALK_BLOCKS_PER_SM 8      // persistent walk: 4-warp blocks launched per SM
 
 // -------------------------------------------------------------------------------------------
 // error reporting (thread-local last error, status codes)
@@ -64,6 +66,7 @@ struct g4_tree_s {
     // depth-first node arrays
     G4Node *node = nullptr;
     float *q = nullptr;           // cap x g4_nq(G4_MAX_ORDER) FP32 moments (orders 2..p)
+    void *walk_queue = nullptr;   // walk frontier rings (allocated on the first walk)
     double *qd = nullptr;         // FP64 mirror (precision 1 only): cap x (4 + nq)
     int built_n = -1;
     // forest (several independent systems in one handle); n_sys = 0 for a single system

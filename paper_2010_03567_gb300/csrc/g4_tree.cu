@@ -312,6 +312,9 @@ extern "C" g4_status g4_tree_create(int64_t n_max, int64_t node_capacity, g4_tre
     auto A = [&](void **p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 16);
     };
+    // largest arrays first: an impossible request fails before anything else is taken
+    A((void **)&t->q, sizeof(float) * g4_nq(G4_MAX_ORDER) * c);
+    A((void **)&t->node, sizeof(G4Node) * c);
     A((void **)&t->b_first, 4 * c);
     A((void **)&t->b_count, 4 * c);
     A((void **)&t->b_child, 4 * c);
@@ -321,8 +324,6 @@ extern "C" g4_status g4_tree_create(int64_t n_max, int64_t node_capacity, g4_tre
     A((void **)&t->b_parent, 4 * c);
     A((void **)&t->lvl, 4 * (2 * (G4_NLEVELS + 1) + 2));
     A((void **)&t->d_flags, 16);
-    A((void **)&t->node, sizeof(G4Node) * c);
-    A((void **)&t->q, sizeof(float) * g4_nq(G4_MAX_ORDER) * c);
     if (e != cudaSuccess) {
         cudaGetLastError();
         g4_tree_free(t);
@@ -352,6 +353,7 @@ extern "C" void g4_tree_free(g4_tree t)
     cudaFree(t->q);
     if (t->qd) cudaFree(t->qd);
     if (t->sys_goff) cudaFree(t->sys_goff);
+    if (t->walk_queue) cudaFree(t->walk_queue);
     delete t;
 }
 
@@ -404,6 +406,7 @@ extern "C" g4_status g4_tree_build_forest(g4_tree t, const uint64_t *keys_sorted
     if (n_sys > t->sys_cap) {
         // grows only when a larger batch arrives; steady-state calls allocate nothing
         if (t->sys_goff) cudaFree(t->sys_goff);
+    if (t->walk_queue) cudaFree(t->walk_queue);
         t->sys_goff = nullptr;
         t->sys_cap = 0;
         if (cudaMalloc(&t->sys_goff, sizeof(int32_t) * (n_sys + 1)) != cudaSuccess) {

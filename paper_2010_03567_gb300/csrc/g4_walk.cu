@@ -34,8 +34,10 @@ struct WalkArgs {
     float *acc, *pot;
     uint32_t *counts;
     int *work;                 // group counter
-    const int32_t *flags;      // tree error flags
-    const int32_t *b_dfs;      // forest: root of system s is node b_dfs[s]
+    int32_t *flags;            // tree error flags
+    const int32_t *b_dfs;      // depth-first index of a level-ordered node (forest roots: s)
+    const int32_t *b_child;    // level-ordered index of a node's first daughter
+    int2 *queue;               // per-warp frontier rings (node, lane mask), QCAP entries each
     const int32_t *sys_first, *sys_goff;
     const double *sys_box;
     int n_sys;
@@ -61,6 +63,7 @@ constexpr int WALK_THREADS = 128;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int LEAF_BUF = 64;
 constexpr int STAGE = 128;      // sources staged per pass of the particle-particle phase
+constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in global memory)
 
 // per-warp shared state: the pending leaf list of the group and the staged sources
 struct WalkSmem {
@@ -178,12 +181,16 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
     const __half2 sx2 = __float2half2_rn(xr * inv_rc), sy2 = __float2half2_rn(yr * inv_rc),
                   sz2 = __float2half2_rn(zr * inv_rc);
     const __half2 lim = __float2half2_rn(1.05f);
-    for (int b = 0; b < total; b += STAGE) {
-        const int nb = min(STAGE, total - b);
+    // Batch bb takes sources bb, bb + nbat, bb + 2 nbat, ...: every batch samples the whole
+    // neighbourhood, so each lane's candidates spread evenly over the batches and the per-lane
+    // evaluation loops below stay balanced across the warp.
+    const int nbat = (total + STAGE - 1) / STAGE;
+    for (int bb = 0; bb < nbat; bb++) {
+        const int nb = (total - bb + nbat - 1) / nbat;
         bool partial = false;
 #pragma unroll
         for (int q = 0; q < STAGE / 32; q++) {
-            const int u = q * 32 + lane, t = b + u;
+            const int u = q * 32 + lane, t = bb + u * nbat;
             if (u < nb) {
                 int lo = 0, hi_ = nk - 1;
                 while (lo < hi_) {
@@ -284,6 +291,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     if (*A.flags & G4_FLAG_CAPACITY) return;   // incomplete tree: outputs left untouched
+    int2 *Q = A.queue + (size_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * QCAP;
     const int nn_all = A.lvl[G4_NLEVELS];
     const int ngroups = A.n_sys ? A.sys_goff[A.n_sys] : (A.n_sinks + 31) >> 5;
     for (;;) {
@@ -342,22 +350,33 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
         T ax = T(0), ay = T(0), az = T(0), ap = T(0);     // particle-particle sums
         T bx = T(0), by = T(0), bz = T(0), bp = T(0);     // particle-node sums
         uint32_t npp = 0, npn = 0;
-        int resume = valid ? 0 : 0x7fffffff;
-        int nleaf = 0;
+        // breadth-first frontier of (node, lanes still walking there), 32 entries per step
+        int head = 0, tail = 1, nleaf = 0;
+        if (lane == 0) Q[0] = make_int2(k, (int)vmask);
+        __syncwarp();
         for (;;) {
-            // a window adds at most 32 leaves: flush before the list could overflow, and at the end
-            if (nleaf > LEAF_BUF - 32 || (k >= nn && nleaf > 0)) {
+            // a step adds at most 32 leaves: flush before the list could overflow, and at the end
+            if (nleaf > LEAF_BUF - 32 || (head >= tail && nleaf > 0)) {
                 pp_flush<T, TREEPM>(A, S, nleaf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, vmask, hi, ax, ay, az, ap, npp, gscale, gbox);
                 nleaf = 0;
             }
-            if (k >= nn) break;
-            const int j = k + lane;
-            const bool vj = j < nn;
+            if (head >= tail) break;
+            const int cnt = min(32, tail - head);
+            const bool ve = lane < cnt;
+            int d = 0;
+            unsigned m = 0u;
+            if (ve) {
+                const int2 qe = Q[(head + lane) & (QCAP - 1)];
+                d = qe.x;
+                m = (unsigned)qe.y;
+            }
+            head += cnt;
+            __syncwarp();
             G4Node nd;
-            if (vj) nd = load_node(A.node + j);
-            const bool leaf = vj && (nd.meta & 32u);
-            bool gskip = false, maybe = false;
-            if (vj) {
+            if (ve) nd = load_node(A.node + d);
+            const bool leaf = ve && (nd.meta & 32u);
+            bool gskip = !ve, maybe = false;
+            if (ve) {
                 const float side = ldexpf(fbox, -(int)(nd.meta & 31u)), half = 0.5f * side;
                 const float dcx = (float)(int32_t)(nd.cx - gcx) * fscale;
                 const float dcy = (float)(int32_t)(nd.cy - gcy) * fscale;
@@ -369,7 +388,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                     gskip = ex * ex + ey * ey + ez * ez > 1.0001f * (float)A.rcut2;
                 }
                 if (!gskip && !leaf) {
-                    // can any sink of the group accept this node's multipole?
+                    // can any sink of the group use this node's multipole?
                     bool none = false;
                     if (A.exclusion && fmaxf(fabsf(dcx) + ghx, fmaxf(fabsf(dcy) + ghy, fabsf(dcz) + ghz)) < 0.999f * side)
                         none = true;
@@ -387,8 +406,8 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                 }
             }
             if (__any_sync(0xffffffffu, maybe)) {
-                // necessary condition for any sink to use the multipole: its own opening
-                // criterion (exclusion, softening and inside-node tests can only open it)
+                // necessary condition for a sink to use the multipole: its own opening criterion
+                // (exclusion, softening and inside-node tests can only open the node)
                 bool any = false;
                 if (maybe) {
                     const float side = ldexpf(fbox, -(int)(nd.meta & 31u));
@@ -397,6 +416,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                     const float cz = (float)(int32_t)(nd.cz - gcz) * fscale + nd.sz;
                     const float lhs = 0.999f * (GEOM ? side * side : (float)A.G * nd.mass * ipow<P>(side));
                     for (int u = 0; u < 32 && !any; u++) {
+                        if (!((m >> u) & 1u)) continue;
                         const float4 sk = S.sink[u];
                         const float dx = cx - sk.x, dy = cy - sk.y, dz = cz - sk.z;
                         const float r2 = (dx * dx + dy * dy + dz * dz) * 1.001f;
@@ -406,90 +426,73 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                 }
                 maybe = any;
             }
-            // depth-first coverage inside the window by skipped subtrees
-            int e = (vj && gskip) ? nd.next : 0;
-            int pm = e;
+            // exact per-lane decisions for the nodes some sink may use (rare in the TreePM
+            // regime): a lane that uses the multipole leaves the node's subtree; a lane beyond
+            // the cutoff keeps walking (the cutoff is hereditary, nothing below can be used and
+            // the pair cutoff removes the leaves)
+            unsigned mev = __ballot_sync(0xffffffffu, maybe);
+            while (mev) {
+                const int src = __ffs(mev) - 1;
+                mev &= mev - 1u;
+                const int jj = __shfl_sync(0xffffffffu, d, src);
+                const unsigned mm = __shfl_sync(0xffffffffu, m, src);
+                const G4Node n2 = load_node(A.node + jj);
+                int act = ACT_NONE;
+                if ((mm >> lane) & 1u)
+                    act = exact_decision<P, T, TREEPM, GEOM>(A, n2, jj, xi, yi, zi, hi, crit, gscale, gbox);
+                const unsigned accm = __ballot_sync(0xffffffffu, act == ACT_ACCEPT);
+                if (accm && act == ACT_ACCEPT) {
+                    T Qs[g4_nq(P) > 0 ? g4_nq(P) : 1];
+                    T mx, my, mz, M;
+                    if (sizeof(T) == 8 && A.qd) {
+                        const double *dd = A.qd + (size_t)jj * (4 + A.nq);
+                        mx = (T)dd[0]; my = (T)dd[1]; mz = (T)dd[2]; M = (T)dd[3];
+#pragma unroll
+                        for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)dd[4 + c];
+                    } else {
+                        mx = (T)n2.sx; my = (T)n2.sy; mz = (T)n2.sz; M = (T)n2.mass;
+                        const float *qq = A.q + (size_t)jj * A.nq;
+#pragma unroll
+                        for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)__ldg(qq + c);
+                    }
+                    const T rx = (T)(int32_t)(n2.cx - xi) * (T)gscale + mx;
+                    const T ry = (T)(int32_t)(n2.cy - yi) * (T)gscale + my;
+                    const T rz = (T)(int32_t)(n2.cz - zi) * (T)gscale + mz;
+                    pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, (T)A.as, bx, by, bz, bp);
+                    npn++;
+                }
+                if (lane == src) m &= ~accm;
+            }
+            // leaves go to the pending list, internal nodes push their daughters
+            const bool addleaf = leaf && !gskip && m != 0u;
+            const unsigned lm = __ballot_sync(0xffffffffu, addleaf);
+            if (addleaf) {
+                const int pos = nleaf + __popc(lm & lt);
+                S.first[pos] = nd.first;
+                S.count[pos] = nd.count;
+                S.mask[pos] = m;
+                S.node[pos] = d;
+            }
+            nleaf += __popc(lm);
+            const bool expand = ve && !leaf && !gskip && m != 0u;
+            const int nch = expand ? nd.nchild : 0;
+            int pre = nch;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, pm, o);
-                if (lane >= o) pm = max(pm, y);
+                const int y = __shfl_up_sync(0xffffffffu, pre, o);
+                if (lane >= o) pre += y;
             }
-            int excl = __shfl_up_sync(0xffffffffu, pm, 1);
-            if (lane == 0) excl = 0;
-            const bool visited = vj && excl <= j && !gskip;
-            int knext = max(k + 32, __shfl_sync(0xffffffffu, pm, 31));
-            const unsigned leafm = __ballot_sync(0xffffffffu, visited && leaf);
-            const unsigned maybem = __ballot_sync(0xffffffffu, visited && maybe);
-            const bool all_active = __all_sync(0xffffffffu, !valid || resume <= k);
-            if (maybem == 0 && all_active) {
-                const int nnew = __popc(leafm);
-                if (nnew > 0) {
-                    const bool me = (leafm >> lane) & 1u;
-                    if (me) {
-                        const int pos = nleaf + __popc(leafm & lt);
-                        S.first[pos] = nd.first;
-                        S.count[pos] = nd.count;
-                        S.mask[pos] = vmask;
-                        S.node[pos] = j;
-                    }
-                    nleaf += nnew;
-                    __syncwarp();
-                }
-            } else {
-                // events in depth-first order: leaves get the mask of lanes still walking
-                // there; "maybe" nodes get exact per-lane decisions
-                unsigned ev = leafm | maybem;
-                int skip_until = 0;
-                while (ev) {
-                    const int src = __ffs(ev) - 1;
-                    ev &= ev - 1u;
-                    const int jj = k + src;
-                    if (jj < skip_until) continue;
-                    const G4Node n2 = load_node(A.node + jj);
-                    if ((leafm >> src) & 1u) {
-                        const unsigned m = __ballot_sync(0xffffffffu, resume <= jj);
-                        if (m) {
-                            if (lane == 0) {
-                                S.first[nleaf] = n2.first;
-                                S.count[nleaf] = n2.count;
-                                S.mask[nleaf] = m;
-                                S.node[nleaf] = jj;
-                            }
-                            __syncwarp();
-                            nleaf++;
-                        }
-                    } else {
-                        int act = ACT_NONE;
-                        if (resume <= jj) {
-                            act = exact_decision<P, T, TREEPM, GEOM>(A, n2, jj, xi, yi, zi, hi, crit, gscale, gbox);
-                            if (act == ACT_ACCEPT) resume = max(n2.next, jj + 1);   // a cutoff skip is hereditary: nothing below can be used, so it acts as open
-                        }
-                        if (__any_sync(0xffffffffu, act == ACT_ACCEPT) && act == ACT_ACCEPT) {
-                            T Qs[g4_nq(P) > 0 ? g4_nq(P) : 1];
-                            T mx, my, mz, M;
-                            if (sizeof(T) == 8 && A.qd) {
-                                const double *dd = A.qd + (size_t)jj * (4 + A.nq);
-                                mx = (T)dd[0]; my = (T)dd[1]; mz = (T)dd[2]; M = (T)dd[3];
-#pragma unroll
-                                for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)dd[4 + c];
-                            } else {
-                                mx = (T)n2.sx; my = (T)n2.sy; mz = (T)n2.sz; M = (T)n2.mass;
-                                const float *qq = A.q + (size_t)jj * A.nq;
-#pragma unroll
-                                for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)__ldg(qq + c);
-                            }
-                            const T rx = (T)(int32_t)(n2.cx - xi) * (T)gscale + mx;
-                            const T ry = (T)(int32_t)(n2.cy - yi) * (T)gscale + my;
-                            const T rz = (T)(int32_t)(n2.cz - zi) * (T)gscale + mz;
-                            pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, (T)A.as, bx, by, bz, bp);
-                            npn++;
-                        }
-                        if (__all_sync(0xffffffffu, resume > jj + 1 || !valid)) skip_until = max(n2.next, jj + 1);
-                    }
-                }
-                knext = max(knext, skip_until);
+            const int tot = __shfl_sync(0xffffffffu, pre, 31);
+            pre -= nch;
+            if (tail + tot - head > QCAP) {
+                if (lane == 0) atomicOr(A.flags, G4_FLAG_LISTCAP);
+            } else if (nch > 0) {
+                const int cb = A.b_child[nd.bfs];
+                for (int c = 0; c < nch; c++)
+                    Q[(tail + pre + c) & (QCAP - 1)] = make_int2(A.b_dfs[cb + c], (int)m);
             }
-            k = knext;
+            if (tail + tot - head <= QCAP) tail += tot;
+            __syncwarp();
         }
         if (valid) {
             const T G = (T)A.G;
@@ -577,8 +580,8 @@ __global__ void k_zero_int(int *p) { *p = 0; }
 template <int P, typename T, bool TREEPM, bool GEOM>
 void launch_walk(const WalkArgs &A, cudaStream_t st)
 {
-    // persistent: enough 4-warp blocks to fill every SM; groups come from the work counter
-    int nb = g4_num_sms() * 8;
+    // persistent: G4_WALK_BLOCKS_PER_SM 4-warp blocks per SM; groups come from the work counter
+    int nb = g4_num_sms() * G4_WALK_BLOCKS_PER_SM;
     k_walk<P, T, TREEPM, GEOM><<<nb, WALK_THREADS, 0, st>>>(A);
 }
 
@@ -674,6 +677,7 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     A.work = t->d_flags + 1;
     A.flags = t->d_flags;
     A.b_dfs = t->b_dfs;
+    A.b_child = t->b_child;
     A.sys_first = t->sys_first;
     A.sys_goff = t->sys_goff;
     A.sys_box = t->sys_box;
@@ -695,6 +699,17 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
         A.h_cls[k] = k < P->n_eps_classes ? (float)(2.8 * P->eps_table[k]) : 0.f;
     A.exclusion = P->exclusion_zone;
     A.pp_cut = P->pp_cut;
+    if (!t->walk_queue) {
+        // frontier rings, allocated on the handle's first walk (outside any graph capture)
+        const size_t bytes = sizeof(int2) * (size_t)G4_WALK_QCAP * g4_num_sms() *
+                             G4_WALK_BLOCKS_PER_SM * (WALK_THREADS / 32);
+        if (cudaMalloc(&t->walk_queue, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            t->walk_queue = nullptr;
+            return g4_fail(G4_ERR_OOM, "g4_gravity_tree: frontier buffers (%zu bytes)", bytes);
+        }
+    }
+    A.queue = (int2 *)t->walk_queue;
     k_zero_int<<<1, 1, 0, st>>>(A.work);
     const bool geom = P->criterion == 1;
     if (P->precision == 1) dispatch_walk<double>(P->order_p, A, treepm, geom, st);

@@ -94,7 +94,7 @@ def _declare(L):
         "g4_mlp_train_step": ([vp, vp, vp, C.c_int32, vp, vp, i64, C.c_float, vp, vp, vp,
                                C.c_size_t, vp], i32),
         "g4_schedule_workspace": ([i64, C.POINTER(C.c_size_t)], i32),
-        "g4_schedule_lpt": ([vp, i64, vp, vp, C.c_size_t, vp], i32),
+        "g4_schedule_lpt": ([vp, i64, C.c_int32, vp, vp, C.c_size_t, vp], i32),
         "g4_tree_set_group_order": ([vp, vp, i64], i32),
     }
     for name, (args, res) in sig.items():
@@ -532,7 +532,7 @@ def cost_labels(counts, c_pn: float = 5.0, out=None, stream=None):
     return out
 
 
-def schedule_lpt(pred_sorted, group_order=None, stream=None):
+def schedule_lpt(pred_sorted, chunk: int = 1, group_order=None, stream=None):
     n = pred_sorted.shape[0]
     ng = (n + 31) // 32
     group_order = group_order if group_order is not None else torch.empty(ng, dtype=torch.int32,
@@ -542,7 +542,7 @@ def schedule_lpt(pred_sorted, group_order=None, stream=None):
     ws = torch.empty(int(b.value) + 256, dtype=torch.uint8, device=pred_sorted.device)
     wp = ws.data_ptr()
     off = (-wp) % 256
-    _check(lib().g4_schedule_lpt(_ptr(pred_sorted), n, _ptr(group_order), C.c_void_p(wp + off),
+    _check(lib().g4_schedule_lpt(_ptr(pred_sorted), n, int(chunk), _ptr(group_order), C.c_void_p(wp + off),
                                  ws.numel() - off, _stream(stream)), "g4_schedule_lpt")
     return group_order
 

@@ -231,9 +231,13 @@ def test_active_subset_bitwise_equal_and_deterministic():
     acc2, pot2, _ = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P)
     assert torch.equal(acc_s, acc2) and torch.equal(pot_s, pot2)
     active = torch.arange(5, ps.n, 37, dtype=torch.int32, device="cuda")
-    acc3, pot3, _ = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, active=active)
+    acc3, pot3, cnt3 = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, active=active)
     idx = active.long()
-    assert torch.equal(acc3[:, idx], acc_s[:, idx])
+    # same interactions for every sink whatever the group it shares; the FP32 sum order of the
+    # particle pairs follows the group's batches, so values agree to rounding
+    assert torch.equal(cnt3[:, idx], cnt[:, idx])
+    a, b = acc3[:, idx].double(), acc_s[:, idx].double()
+    assert torch.max(torch.abs(a - b)) <= 1e-6 * torch.max(torch.abs(b))
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 33])
