@@ -168,7 +168,10 @@ def config_block(world, n_side=N_SIDE, leaf_max=None):
                         f"tree p=3, alpha=0.0025, leaf {leaf_max or LEAF_MAX}",
             "n_particles": n_side ** 3, "order_p": 3, "alpha": 0.0025, "leaf_max": leaf_max or LEAF_MAX,
             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-            "l2": "inputs (335 MB) larger than L2 (129 MB); no flush"}
+            "l2": (f"inputs ({n_side ** 3 * 20 / 1e6:.0f} MB: positions, masses, |a_old|) larger than "
+                   f"L2 (129 MB); no flush") if n_side ** 3 * 20 > 129e6 else
+                  (f"inputs ({n_side ** 3 * 20 / 1e6:.0f} MB) fit in L2 (129 MB): small profiling case, "
+                   f"not a bench configuration")}
 
 
 # ---------------------------------------------------------------------------------------------

@@ -67,6 +67,12 @@ struct g4_tree_s {
     G4Node *node = nullptr;
     float *q = nullptr;           // cap x g4_nq(G4_MAX_ORDER) FP32 moments (orders 2..p)
     void *walk_queue = nullptr;   // walk frontier rings (allocated on the first walk)
+    // walk copies (allocated on the first walk): node records in level order with
+    // next = first daughter (level order) and parent = depth-first index, and the particles
+    // as 16-byte records (x, y, z, mass bits)
+    G4Node *wnode = nullptr;
+    uint4 *wpart = nullptr;
+    int64_t moments_stamp = 0, wnode_stamp = -1;
     double *qd = nullptr;         // FP64 mirror (precision 1 only): cap x (4 + nq)
     int built_n = -1;
     // forest (several independent systems in one handle); n_sys = 0 for a single system

@@ -9,6 +9,7 @@
 //     z^(c-2k) with K(a,i) = a! / (2^i i! (a-2i)!) -- the count of ways to pair 2i of the a
 //     equal index slots by Kronecker deltas (Eqs. eqngderiv0-eqngderiv).
 #pragma once
+#include "g4_erfcx.cuh"
 #include "g4_internal.cuh"
 
 namespace g4k {
@@ -109,6 +110,57 @@ __device__ __forceinline__ void pair_kernel(T r2, T h, T as, T &g0, T &g1)
             g0 -= two_over_sqrtpi * as;
         }
     }
+}
+
+// FP32 TreePM pair kernel with lengths in units of the integer grid (so separations need no
+// scaling).  For r >= h and x = as r <= G4_ERFCX_XMAX:
+//   exp(-x^2) = 2^(k2 r^2), k2 = -as^2 log2(e)          (ex2.approx),
+//   erfc(x)   = exp(-x^2) erfcx(x)                      (fitted polynomial, g4_erfcx.cuh),
+//   g0 = erfc(x) / r,  g1 = -(g0 + ct exp(-x^2)) / r^2,  ct = 2 as / sqrt(pi).
+// Softened pairs and pairs beyond the fit take pair_kernel<float, true>.  The kernel is
+// homogeneous in the length unit (g0 ~ 1/length, g1 ~ 1/length^3), so the caller converts
+// the sums back with 1/scale and 1/scale^2.
+struct PairF {
+    float as, k2, ct, fit2;
+};
+
+__host__ __device__ inline PairF make_pairf(double as, double inv_as)
+{
+    PairF c;
+    c.as = (float)as;
+    c.k2 = (float)(-as * as * 1.4426950408889634);
+    c.ct = (float)(1.1283791670955126 * as);
+    c.fit2 = (float)((double)G4_ERFCX_XMAX * G4_ERFCX_XMAX * inv_as * inv_as);
+    return c;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void pair_treepm_fast(float r2, float h, const PairF &c, float &g0,
+                                                 float &g1)
+{
+    if (r2 < h * h || r2 > c.fit2) {
+        pair_kernel<float, true>(r2, h, c.as, g0, g1);
+        return;
+    }
+    const float rinv = rsqrtf(r2), r = r2 * rinv;
+    const float e = ex2_approx(r2 * c.k2);
+    const float t = rcp_approx(fmaf(G4_ERFCX_K * c.as, r, 1.f));
+    const float ec = e * g4_erfcx_poly(fmaf(t, G4_ERFCX_U1, G4_ERFCX_U0));
+    g0 = ec * rinv;
+    g1 = -fmaf(c.ct, e, g0) * rinv * rinv;
 }
 
 // g_0..g_N of the unsoftened multipole kernel at squared distance r2 (r2 > 0).

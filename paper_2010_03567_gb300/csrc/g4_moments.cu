@@ -332,6 +332,7 @@ extern "C" g4_status g4_multipoles(g4_tree t, const uint32_t *pos_sorted, const 
         }
     }
     t->moments_order = p;
+    t->moments_stamp++;
     t->moments_fp64 = P->precision == 1;
     return g4_launch_check("multipoles", G4_MAXLEVEL + 1);
 }

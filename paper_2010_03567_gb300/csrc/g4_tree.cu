@@ -112,9 +112,12 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_expand(
     int32_t *off = lvl, *cnt = lvl + G4_NLEVELS + 1;
     const int o = off[level], c_raw = cnt[level];
     const int nbase = o + c_raw;   // first slot of level + 1
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[level + 1] = nbase;
+    // after a capacity overflow the slots an overflowing warp reserved below the capacity are
+    // never written, so no later level reads them: the build stops here (tree invalid)
+    if (*flags & G4_FLAG_CAPACITY) return;
     // after a capacity overflow only the slots inside the arrays are touched
     const int c = (int)min((int64_t)c_raw, cap - o > 0 ? cap - o : (int64_t)0);
-    if (blockIdx.x == 0 && threadIdx.x == 0) off[level + 1] = nbase;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -203,9 +206,11 @@ __global__ void k_build_clip(int32_t *lvl, int64_t cap)
 }
 
 __global__ void k_build_subtree(int level, const int32_t *__restrict__ lvl,
+                                const int32_t *__restrict__ flags,
                                 const int32_t *__restrict__ b_child,
                                 const int32_t *__restrict__ b_nchild, int32_t *__restrict__ b_size)
 {
+    if (*flags & G4_FLAG_CAPACITY) return;   // invalid tree: links may be unset
     const int32_t *off = lvl, *cnt = lvl + G4_NLEVELS + 1;
     int o = off[level], c = cnt[level];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < c; b += gridDim.x * blockDim.x) {
@@ -216,9 +221,11 @@ __global__ void k_build_subtree(int level, const int32_t *__restrict__ lvl,
 }
 
 __global__ void k_build_dfs(int level, const int32_t *__restrict__ lvl,
+                            const int32_t *__restrict__ flags,
                             const int32_t *__restrict__ b_child, const int32_t *__restrict__ b_nchild,
                             const int32_t *__restrict__ b_size, int32_t *__restrict__ b_dfs)
 {
+    if (*flags & G4_FLAG_CAPACITY) return;
     const int32_t *off = lvl, *cnt = lvl + G4_NLEVELS + 1;
     int o = off[level], c = cnt[level];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < c; b += gridDim.x * blockDim.x) {
@@ -231,13 +238,15 @@ __global__ void k_build_dfs(int level, const int32_t *__restrict__ lvl,
     }
 }
 
-__global__ void k_build_emit(const int32_t *__restrict__ lvl, const uint32_t *__restrict__ pos,
+__global__ void k_build_emit(const int32_t *__restrict__ lvl, const int32_t *__restrict__ flags,
+                             const uint32_t *__restrict__ pos,
                              int n, const int32_t *__restrict__ b_first,
                              const int32_t *__restrict__ b_count, const int32_t *__restrict__ b_child,
                              const int32_t *__restrict__ b_nchild,
                              const int32_t *__restrict__ b_size, const int32_t *__restrict__ b_dfs,
                              const int32_t *__restrict__ b_parent, G4Node *__restrict__ node)
 {
+    if (*flags & G4_FLAG_CAPACITY) return;
     const int32_t *off = lvl, *cnt = lvl + G4_NLEVELS + 1;
     const int total = off[G4_NLEVELS];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < total; b += gridDim.x * blockDim.x) {
@@ -354,6 +363,8 @@ extern "C" void g4_tree_free(g4_tree t)
     if (t->qd) cudaFree(t->qd);
     if (t->sys_goff) cudaFree(t->sys_goff);
     if (t->walk_queue) cudaFree(t->walk_queue);
+    if (t->wnode) cudaFree(t->wnode);
+    if (t->wpart) cudaFree(t->wpart);
     delete t;
 }
 
@@ -376,11 +387,11 @@ extern "C" g4_status g4_tree_build(g4_tree t, const uint64_t *keys_sorted,
     k_build_last<<<nb, BUILD_THREADS, 0, st>>>(t->lvl, t->cap, t->b_child, t->b_nchild);
     k_build_clip<<<1, 32, 0, st>>>(t->lvl, t->cap);
     for (int l = G4_MAXLEVEL; l >= 0; l--)
-        k_build_subtree<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->b_child, t->b_nchild, t->b_size);
+        k_build_subtree<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->d_flags, t->b_child, t->b_nchild, t->b_size);
     for (int l = 0; l <= G4_MAXLEVEL; l++)
-        k_build_dfs<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->b_child, t->b_nchild, t->b_size,
+        k_build_dfs<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->d_flags, t->b_child, t->b_nchild, t->b_size,
                                                   t->b_dfs);
-    k_build_emit<<<nb, BUILD_THREADS, 0, st>>>(t->lvl, pos_sorted, (int)n, t->b_first, t->b_count,
+    k_build_emit<<<nb, BUILD_THREADS, 0, st>>>(t->lvl, t->d_flags, pos_sorted, (int)n, t->b_first, t->b_count,
                                                t->b_child, t->b_nchild, t->b_size, t->b_dfs,
                                                t->b_parent, t->node);
     t->built_n = (int)n;
@@ -406,7 +417,6 @@ extern "C" g4_status g4_tree_build_forest(g4_tree t, const uint64_t *keys_sorted
     if (n_sys > t->sys_cap) {
         // grows only when a larger batch arrives; steady-state calls allocate nothing
         if (t->sys_goff) cudaFree(t->sys_goff);
-    if (t->walk_queue) cudaFree(t->walk_queue);
         t->sys_goff = nullptr;
         t->sys_cap = 0;
         if (cudaMalloc(&t->sys_goff, sizeof(int32_t) * (n_sys + 1)) != cudaSuccess) {
@@ -426,12 +436,12 @@ extern "C" g4_status g4_tree_build_forest(g4_tree t, const uint64_t *keys_sorted
     k_build_last<<<nb, BUILD_THREADS, 0, st>>>(t->lvl, t->cap, t->b_child, t->b_nchild);
     k_build_clip<<<1, 32, 0, st>>>(t->lvl, t->cap);
     for (int l = G4_MAXLEVEL; l >= 0; l--)
-        k_build_subtree<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->b_child, t->b_nchild, t->b_size);
+        k_build_subtree<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->d_flags, t->b_child, t->b_nchild, t->b_size);
     k_forest_roots<<<1, 1024, 0, st>>>(t->b_size, sys_first, n_sys, t->b_dfs, t->sys_goff);
     for (int l = 0; l <= G4_MAXLEVEL; l++)
-        k_build_dfs<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->b_child, t->b_nchild, t->b_size,
+        k_build_dfs<<<nb, BUILD_THREADS, 0, st>>>(l, t->lvl, t->d_flags, t->b_child, t->b_nchild, t->b_size,
                                                   t->b_dfs);
-    k_build_emit<<<nb, BUILD_THREADS, 0, st>>>(t->lvl, pos_sorted, (int)n, t->b_first, t->b_count,
+    k_build_emit<<<nb, BUILD_THREADS, 0, st>>>(t->lvl, t->d_flags, pos_sorted, (int)n, t->b_first, t->b_count,
                                                t->b_child, t->b_nchild, t->b_size, t->b_dfs,
                                                t->b_parent, t->node);
     t->built_n = (int)n;

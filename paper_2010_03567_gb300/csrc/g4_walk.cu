@@ -27,7 +27,9 @@ struct WalkArgs {
     const int32_t *active;
     int n, n_sinks;
     const int32_t *lvl;        // lvl[G4_NLEVELS] = node count
-    const G4Node *node;
+    const G4Node *node;        // depth-first records
+    const G4Node *wnode;       // level-ordered copy: next = first daughter, parent = depth-first index
+    const uint4 *wpart;        // particles as (x, y, z, mass bits)
     const float *q;
     const double *qd;          // FP64 node data (precision 1)
     int nq;
@@ -35,9 +37,7 @@ struct WalkArgs {
     uint32_t *counts;
     int *work;                 // group counter
     int32_t *flags;            // tree error flags
-    const int32_t *b_dfs;      // depth-first index of a level-ordered node (forest roots: s)
-    const int32_t *b_child;    // level-ordered index of a node's first daughter
-    int2 *queue;               // per-warp frontier rings (node, lane mask), QCAP entries each
+    int2 *queue;               // per-warp frontier rings (level-ordered node, lane mask)
     const int32_t *sys_first, *sys_goff;
     const double *sys_box;
     int n_sys;
@@ -45,9 +45,16 @@ struct WalkArgs {
     double scale;
     double G, alpha, theta2, rcut2, as;
     double box;
+    float Gf, alphaf, theta2f, rcut2f, asf;   // FP32 copies (no FP64 conversions in the loops)
+    double inv_as, igs;                      // 1 / as; integer units per length unit (box)
     float h_cls[G4_MAX_EPS_CLASSES];
     int exclusion, pp_cut;
 };
+
+// a launch parameter in the walk's arithmetic type
+template <typename T> __device__ __forceinline__ T par(double d, float f);
+template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
 
 enum : int { ACT_NONE = 0, ACT_SKIP = 1, ACT_OPEN = 2, ACT_ACCEPT = 3, ACT_LEAF = 4 };
 
@@ -64,15 +71,22 @@ constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int LEAF_BUF = 64;
 constexpr int STAGE = 128;      // sources staged per pass of the particle-particle phase
 constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in global memory)
+// minimum resident blocks per SM requested from the compiler for the FP32 TreePM walks
+// (caps their registers; other instances keep the compiler's choice)
+#ifndef G4_WALK_MIN_BLOCKS
+#define G4_WALK_MIN_BLOCKS 6
+#endif
 
 // per-warp shared state: the pending leaf list of the group and the staged sources
 struct WalkSmem {
-    int first[LEAF_BUF], count[LEAF_BUF], pref[LEAF_BUF], node[LEAF_BUF];
+    int first[LEAF_BUF], count[LEAF_BUF], pref[LEAF_BUF];
     unsigned mask[LEAF_BUF];
     uint4 ipos[STAGE];          // source integer position, softening length h (bits)
     float2 mj[STAGE];           // source mass, particle index (bits)
     unsigned smask[STAGE];      // lane mask of the source's leaf
-    __half hx[STAGE], hy[STAGE], hz[STAGE];   // position / r_cut relative to the group centre
+    __align__(16) __half hx[STAGE];   // source position / r_cut relative to the group centre
+    __align__(16) __half hy[STAGE];
+    __align__(16) __half hz[STAGE];
     float4 sink[32];            // sinks relative to the group centre, opening threshold
 };
 
@@ -104,7 +118,7 @@ __device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &n
         const T ex = fmax(fabs(dcx) - half, T(0));
         const T ey = fmax(fabs(dcy) - half, T(0));
         const T ez = fmax(fabs(dcz) - half, T(0));
-        if (ex * ex + ey * ey + ez * ez > (T)A.rcut2) return ACT_SKIP;
+        if (ex * ex + ey * ey + ez * ez > par<T>(A.rcut2, A.rcut2f)) return ACT_SKIP;
     }
     T ox, oy, oz, M;
     if (sizeof(T) == 8 && A.qd) {
@@ -119,10 +133,18 @@ __device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &n
     const T h = fmax(hi, (T)nd.hmax);
     bool open = (dmax <= half) || (A.exclusion && dmax < side) || (r2 < h * h);
     if (!open) {
-        if (GEOM) open = side * side >= (T)A.theta2 * r2;
-        else open = !((T)A.G * M * ipow<P>(side) < crit * ipow<P + 2>(sqrt(r2)));
+        if (GEOM) open = side * side >= par<T>(A.theta2, A.theta2f) * r2;
+        else open = !(par<T>(A.G, A.Gf) * M * ipow<P>(side) < crit * ipow<P + 2>(sqrt(r2)));
     }
     return open ? ACT_OPEN : ACT_ACCEPT;
+}
+
+// Slot of staged source u in the candidate masks.  The FP16x2 test handles sources 2j, 2j+1
+// of a 32-source block together and sets bits j and 16 + j of the block's mask word, so the
+// per-source arrays used by the evaluation are stored at that bit position.
+__device__ __forceinline__ int cand_bit(int u)
+{
+    return (u & ~31) | ((u & 1) << 4) | ((u & 31) >> 1);
 }
 
 // Particle-particle phase for the pending leaves of a group.
@@ -132,18 +154,20 @@ __device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &n
 // candidate bit per source; then each lane evaluates only its own candidates with exact
 // integer separations, the exact cutoff and the full kernel.  Leaf masks (lanes that used an
 // ancestor's multipole must not see the leaf) are applied per source when a staged leaf does
-// not reach the whole group.  The sum order of every sink is the order of its sources in the
-// list (depth-first), independent of which other sinks share the group.
+// not reach the whole group.  INTU (FP32 TreePM): the pair terms are summed in integer-grid
+// length units with the fast kernel; the caller rescales the sums.
 template <typename T, bool TREEPM>
 __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nleaf, int lane, int i,
                                          uint32_t xi, uint32_t yi, uint32_t zi, uint32_t gcx,
                                          uint32_t gcy, uint32_t gcz, float xr, float yr, float zr,
                                          unsigned vmask, T hi, T &ax, T &ay, T &az, T &ap,
-                                         uint32_t &npp, double gscale, double gbox)
+                                         uint32_t &npp, double gscale, float figs, const PairF &pf,
+                                         float rc2i)
 {
+    constexpr bool INTU = TREEPM && sizeof(T) == 4;
     const float fscale = (float)gscale;
-    const T scale = (T)gscale, as = (T)A.as, rcut2 = (T)A.rcut2;
-    (void)gbox;
+    const T scale = (T)gscale, as = par<T>(A.as, A.asf), rcut2 = par<T>(A.rcut2, A.rcut2f);
+    const float hconv = INTU ? figs : 1.f;   // staged softening length unit
     // drop leaves nobody reaches; prefix sums of the particle counts
     int nk = 0, total = 0;
     for (int b = 0; b < nleaf; b += 32) {
@@ -177,7 +201,7 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
         nk += __popc(km);
         total += __shfl_sync(0xffffffffu, pre, 31);
     }
-    const float inv_rc = TREEPM ? rsqrtf((float)A.rcut2) : 0.f;
+    const float inv_rc = TREEPM ? rsqrtf(A.rcut2f) : 0.f;
     const __half2 sx2 = __float2half2_rn(xr * inv_rc), sy2 = __float2half2_rn(yr * inv_rc),
                   sz2 = __float2half2_rn(zr * inv_rc);
     const __half2 lim = __float2half2_rn(1.05f);
@@ -190,7 +214,7 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
         bool partial = false;
 #pragma unroll
         for (int q = 0; q < STAGE / 32; q++) {
-            const int u = q * 32 + lane, t = bb + u * nbat;
+            const int u = q * 32 + lane, t = bb + u * nbat, v = cand_bit(u);
             if (u < nb) {
                 int lo = 0, hi_ = nk - 1;
                 while (lo < hi_) {
@@ -199,76 +223,116 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
                     else hi_ = mid - 1;
                 }
                 const int j = S.first[lo] + (t - S.pref[lo]);
-                const uint32_t px = __ldg(A.pos + j), py = __ldg(A.pos + A.n + j),
-                               pz = __ldg(A.pos + 2 * A.n + j);
-                const float hj = A.h_cls[A.cls ? __ldg(A.cls + j) : 0];
+                const uint4 pj = __ldg(A.wpart + j);
+                const uint32_t px = pj.x, py = pj.y, pz = pj.z;
+                const float hj = A.h_cls[A.cls ? __ldg(A.cls + j) : 0] * hconv;
                 const unsigned mk = S.mask[lo];
-                S.ipos[u] = make_uint4(px, py, pz, __float_as_uint(hj));
-                S.mj[u] = make_float2(__ldg(A.mass + j), __int_as_float(j));
-                S.smask[u] = mk;
+                S.ipos[v] = make_uint4(px, py, pz, __float_as_uint(hj));
+                S.mj[v] = make_float2(__uint_as_float(pj.w), __int_as_float(j));
+                S.smask[v] = mk;
                 S.hx[u] = __float2half_rn((float)(int32_t)(px - gcx) * fscale * inv_rc);
                 S.hy[u] = __float2half_rn((float)(int32_t)(py - gcy) * fscale * inv_rc);
                 S.hz[u] = __float2half_rn((float)(int32_t)(pz - gcz) * fscale * inv_rc);
                 partial |= (mk != vmask);
             } else {
                 S.hx[u] = S.hy[u] = S.hz[u] = __float2half_rn(100.f);
+                S.smask[v] = 0xffffffffu;
             }
         }
         partial = __any_sync(0xffffffffu, partial);
         __syncwarp();
-        unsigned long long c0 = 0ull, c1 = 0ull;
+        const int nw = (nb + 31) >> 5;
+        uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
         if (TREEPM) {
-            const __half2 *X = reinterpret_cast<const __half2 *>(S.hx);
-            const __half2 *Y = reinterpret_cast<const __half2 *>(S.hy);
-            const __half2 *Z = reinterpret_cast<const __half2 *>(S.hz);
-            const int np = (nb + 1) >> 1;
-#pragma unroll 4
-            for (int pr = 0; pr < np; pr++) {
-                const __half2 dx = __hsub2(X[pr], sx2), dy = __hsub2(Y[pr], sy2),
-                              dz = __hsub2(Z[pr], sz2);
-                const __half2 d2 = __hfma2(dz, dz, __hfma2(dy, dy, __hmul2(dx, dx)));
-                const unsigned m = __hle2_mask(d2, lim);
-                const unsigned long long bits2 = (m & 1u) | ((m >> 15) & 2u);
-                if (pr < 32) c0 |= bits2 << (2 * pr);
-                else c1 |= bits2 << (2 * (pr - 32));
+            const uint4 *X = reinterpret_cast<const uint4 *>(S.hx);
+            const uint4 *Y = reinterpret_cast<const uint4 *>(S.hy);
+            const uint4 *Z = reinterpret_cast<const uint4 *>(S.hz);
+            for (int w = 0; w < nw; w++) {
+                uint32_t m = 0u;
+#pragma unroll
+                for (int qd = 0; qd < 4; qd++) {
+                    const uint4 x4 = X[4 * w + qd], y4 = Y[4 * w + qd], z4 = Z[4 * w + qd];
+                    const uint32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
+                    const uint32_t ys[4] = {y4.x, y4.y, y4.z, y4.w};
+                    const uint32_t zs[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        const __half2 dx = __hsub2(*reinterpret_cast<const __half2 *>(&xs[c]), sx2);
+                        const __half2 dy = __hsub2(*reinterpret_cast<const __half2 *>(&ys[c]), sy2);
+                        const __half2 dz = __hsub2(*reinterpret_cast<const __half2 *>(&zs[c]), sz2);
+                        const __half2 d2 = __hfma2(dz, dz, __hfma2(dy, dy, __hmul2(dx, dx)));
+                        m |= (__hle2_mask(d2, lim) & 0x00010001u) << (4 * qd + c);
+                    }
+                }
+                w0 = w == 0 ? m : w0;
+                w1 = w == 1 ? m : w1;
+                w2 = w == 2 ? m : w2;
+                w3 = w == 3 ? m : w3;
             }
         } else {
-            c0 = nb >= 64 ? ~0ull : ((1ull << nb) - 1ull);
-            c1 = nb >= 128 ? ~0ull : (nb > 64 ? ((1ull << (nb - 64)) - 1ull) : 0ull);
+            // every staged source is a candidate; bit positions of sources u < nb
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                const int r = min(max(nb - 32 * w, 0), 32);   // valid sources in block w
+                const int ev = (r + 1) >> 1, od = r >> 1;      // even / odd ones
+                const uint32_t m = (ev >= 16 ? 0xffffu : ((1u << ev) - 1u)) |
+                                   ((od >= 16 ? 0xffffu : ((1u << od) - 1u)) << 16);
+                if (w == 0) w0 = m;
+                else if (w == 1) w1 = m;
+                else if (w == 2) w2 = m;
+                else w3 = m;
+            }
         }
+        unsigned long long c0 = (unsigned long long)w0 | ((unsigned long long)w1 << 32);
+        unsigned long long c1 = (unsigned long long)w2 | ((unsigned long long)w3 << 32);
         if (partial) {
-            for (int u = 0; u < nb; u++)
-                if (!((S.smask[u] >> lane) & 1u)) {
-                    if (u < 64) c0 &= ~(1ull << u);
-                    else c1 &= ~(1ull << (u - 64));
+            for (int v = 0; v < 32 * nw; v++)
+                if (!((S.smask[v] >> lane) & 1u)) {
+                    if (v < 64) c0 &= ~(1ull << v);
+                    else c1 &= ~(1ull << (v - 64));
                 }
         }
         // exact evaluation of the lane's own candidates
         while (c0 | c1) {
-            int u;
+            int v;
             if (c0) {
-                u = __ffsll((long long)c0) - 1;
+                v = __ffsll((long long)c0) - 1;
                 c0 &= c0 - 1ull;
             } else {
-                u = 64 + __ffsll((long long)c1) - 1;
+                v = 64 + __ffsll((long long)c1) - 1;
                 c1 &= c1 - 1ull;
             }
-            const uint4 ip = S.ipos[u];
-            const float2 mj = S.mj[u];
+            const uint4 ip = S.ipos[v];
+            const float2 mj = S.mj[v];
             if (__float_as_int(mj.y) == i) continue;
-            const T dx = (T)(int32_t)(ip.x - xi) * scale;
-            const T dy = (T)(int32_t)(ip.y - yi) * scale;
-            const T dz = (T)(int32_t)(ip.z - zi) * scale;
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            if (TREEPM && A.pp_cut && r2 >= rcut2) continue;
-            T g0, g1;
-            pair_kernel<T, TREEPM>(r2, fmax(hi, (T)__uint_as_float(ip.w)), as, g0, g1);
-            const T m_ = (T)mj.x;
-            const T mg1 = m_ * g1;
-            ax += mg1 * dx;
-            ay += mg1 * dy;
-            az += mg1 * dz;
-            ap += m_ * g0;
+            if (INTU) {
+                const float dx = (float)(int32_t)(ip.x - xi);
+                const float dy = (float)(int32_t)(ip.y - yi);
+                const float dz = (float)(int32_t)(ip.z - zi);
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                if (A.pp_cut && r2 >= rc2i) continue;
+                float g0, g1;
+                pair_treepm_fast(r2, fmaxf((float)hi, __uint_as_float(ip.w)), pf, g0, g1);
+                const float mg1 = mj.x * g1;
+                ax = fmaf(mg1, dx, (float)ax);
+                ay = fmaf(mg1, dy, (float)ay);
+                az = fmaf(mg1, dz, (float)az);
+                ap = fmaf(mj.x, g0, (float)ap);
+            } else {
+                const T dx = (T)(int32_t)(ip.x - xi) * scale;
+                const T dy = (T)(int32_t)(ip.y - yi) * scale;
+                const T dz = (T)(int32_t)(ip.z - zi) * scale;
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                if (TREEPM && A.pp_cut && r2 >= rcut2) continue;
+                T g0, g1;
+                pair_kernel<T, TREEPM>(r2, fmax(hi, (T)__uint_as_float(ip.w)), as, g0, g1);
+                const T m_ = (T)mj.x;
+                const T mg1 = m_ * g1;
+                ax += mg1 * dx;
+                ay += mg1 * dy;
+                az += mg1 * dz;
+                ap += m_ * g0;
+            }
             npp++;
         }
         __syncwarp();
@@ -284,7 +348,8 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
 // nodes get the exact per-lane decision, and a lane that accepts or skips one resumes after
 // its subtree, exactly as a single-particle walk would.
 template <int P, typename T, bool TREEPM, bool GEOM>
-__global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
+__global__ void __launch_bounds__(WALK_THREADS, (TREEPM && sizeof(T) == 4 && P <= 3) ? G4_WALK_MIN_BLOCKS : 1)
+k_walk(const WalkArgs A)
 {
     __shared__ WalkSmem smem[WALK_WARPS];
     WalkSmem &S = smem[threadIdx.x >> 5];
@@ -292,7 +357,6 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
     const unsigned lt = (1u << lane) - 1u;
     if (*A.flags & G4_FLAG_CAPACITY) return;   // incomplete tree: outputs left untouched
     int2 *Q = A.queue + (size_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * QCAP;
-    const int nn_all = A.lvl[G4_NLEVELS];
     const int ngroups = A.n_sys ? A.sys_goff[A.n_sys] : (A.n_sinks + 31) >> 5;
     for (;;) {
         int g = 0;
@@ -301,7 +365,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
         if (g >= ngroups) break;
         if (A.group_order) g = A.group_order[g];
         // the group's sinks, node range and box (a forest walks only its own system's tree)
-        int s0 = g * 32, s_end = A.n_sinks, k = 0, nn = nn_all;
+        int s0 = g * 32, s_end = A.n_sinks, k = 0;   // k: root, level-ordered
         double gbox = A.box;
         if (A.n_sys) {
             int lo = 0, hi_ = A.n_sys - 1;
@@ -312,8 +376,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
             }
             s0 = A.sys_first[lo] + (g - A.sys_goff[lo]) * 32;
             s_end = A.sys_first[lo + 1];
-            k = A.b_dfs[lo];
-            nn = A.node[k].next;
+            k = lo;   // forest roots are the first n_sys level-ordered nodes
             gbox = A.sys_box[lo];
         }
         const double gscale = gbox * (1.0 / 4294967296.0);
@@ -322,9 +385,10 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
         const bool valid = s < s_end;
         const unsigned vmask = __ballot_sync(0xffffffffu, valid);
         const int i = valid ? (A.active ? A.active[s] : s) : (A.active ? A.active[s0] : s0);
-        const uint32_t xi = A.pos[i], yi = A.pos[A.n + i], zi = A.pos[2 * A.n + i];
+        const uint4 pi_ = A.wpart[i];
+        const uint32_t xi = pi_.x, yi = pi_.y, zi = pi_.z;
         const T hi = (T)A.h_cls[A.cls ? A.cls[i] : 0];
-        const T crit = GEOM ? T(0) : (T)A.alpha * (T)(A.aold ? A.aold[i] : 0.f);
+        const T crit = GEOM ? T(0) : par<T>(A.alpha, A.alphaf) * (T)(A.aold ? A.aold[i] : 0.f);
         // group bounding box, in integer offsets from lane 0's sink
         const uint32_t x0 = __shfl_sync(0xffffffffu, xi, 0), y0 = __shfl_sync(0xffffffffu, yi, 0),
                        z0 = __shfl_sync(0xffffffffu, zi, 0);
@@ -347,6 +411,12 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
         for (int o = 16; o > 0; o >>= 1) critmax = fmaxf(critmax, __shfl_xor_sync(0xffffffffu, critmax, o));
         critmax *= 1.001f;
 
+        // FP32 TreePM: particle-particle sums in integer-grid length units (see pair_treepm_fast)
+        constexpr bool INTU = TREEPM && sizeof(T) == 4;
+        const double igs = A.n_sys ? 4294967296.0 / gbox : A.igs;   // integer units per length unit
+        const float figs = (float)igs;
+        const PairF pf = make_pairf(A.as * gscale, A.inv_as * igs);
+        const float rc2i = (float)(A.rcut2 * igs * igs);
         T ax = T(0), ay = T(0), az = T(0), ap = T(0);     // particle-particle sums
         T bx = T(0), by = T(0), bz = T(0), bp = T(0);     // particle-node sums
         uint32_t npp = 0, npn = 0;
@@ -357,7 +427,8 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
         for (;;) {
             // a step adds at most 32 leaves: flush before the list could overflow, and at the end
             if (nleaf > LEAF_BUF - 32 || (head >= tail && nleaf > 0)) {
-                pp_flush<T, TREEPM>(A, S, nleaf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, vmask, hi, ax, ay, az, ap, npp, gscale, gbox);
+                pp_flush<T, TREEPM>(A, S, nleaf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, vmask,
+                                    INTU ? hi * (T)figs : hi, ax, ay, az, ap, npp, gscale, figs, pf, rc2i);
                 nleaf = 0;
             }
             if (head >= tail) break;
@@ -373,7 +444,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
             head += cnt;
             __syncwarp();
             G4Node nd;
-            if (ve) nd = load_node(A.node + d);
+            if (ve) nd = load_node(A.wnode + d);
             const bool leaf = ve && (nd.meta & 32u);
             bool gskip = !ve, maybe = false;
             if (ve) {
@@ -385,7 +456,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                     const float ex = fmaxf(fabsf(dcx) - half - ghx, 0.f);
                     const float ey = fmaxf(fabsf(dcy) - half - ghy, 0.f);
                     const float ez = fmaxf(fabsf(dcz) - half - ghz, 0.f);
-                    gskip = ex * ex + ey * ey + ez * ez > 1.0001f * (float)A.rcut2;
+                    gskip = ex * ex + ey * ey + ez * ez > 1.0001f * A.rcut2f;
                 }
                 if (!gskip && !leaf) {
                     // can any sink of the group use this node's multipole?
@@ -397,10 +468,10 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                     const float rmax2 = (fx * fx + fy * fy + fz * fz) * 1.001f;
                     if (rmax2 < nd.hmax * nd.hmax) none = true;
                     if (GEOM) {
-                        if (side * side >= (float)A.theta2 * rmax2) none = true;
+                        if (side * side >= A.theta2f * rmax2) none = true;
                     } else {
                         const float rmax = sqrtf(rmax2);
-                        if (!((float)A.G * nd.mass * ipow<P>(side) < critmax * ipow<P + 2>(rmax))) none = true;
+                        if (!(A.Gf * nd.mass * ipow<P>(side) < critmax * ipow<P + 2>(rmax))) none = true;
                     }
                     maybe = !none;
                 }
@@ -414,13 +485,13 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                     const float cx = (float)(int32_t)(nd.cx - gcx) * fscale + nd.sx;
                     const float cy = (float)(int32_t)(nd.cy - gcy) * fscale + nd.sy;
                     const float cz = (float)(int32_t)(nd.cz - gcz) * fscale + nd.sz;
-                    const float lhs = 0.999f * (GEOM ? side * side : (float)A.G * nd.mass * ipow<P>(side));
+                    const float lhs = 0.999f * (GEOM ? side * side : A.Gf * nd.mass * ipow<P>(side));
                     for (int u = 0; u < 32 && !any; u++) {
                         if (!((m >> u) & 1u)) continue;
                         const float4 sk = S.sink[u];
                         const float dx = cx - sk.x, dy = cy - sk.y, dz = cz - sk.z;
                         const float r2 = (dx * dx + dy * dy + dz * dz) * 1.001f;
-                        if (GEOM) any = lhs < sk.w * (float)A.theta2 * r2;
+                        if (GEOM) any = lhs < sk.w * A.theta2f * r2;
                         else any = lhs < sk.w * ipow<P + 2>(sqrtf(r2));
                     }
                 }
@@ -436,29 +507,30 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                 mev &= mev - 1u;
                 const int jj = __shfl_sync(0xffffffffu, d, src);
                 const unsigned mm = __shfl_sync(0xffffffffu, m, src);
-                const G4Node n2 = load_node(A.node + jj);
+                const G4Node n2 = load_node(A.wnode + jj);
+                const int jd = n2.parent;   // depth-first index: moments
                 int act = ACT_NONE;
                 if ((mm >> lane) & 1u)
-                    act = exact_decision<P, T, TREEPM, GEOM>(A, n2, jj, xi, yi, zi, hi, crit, gscale, gbox);
+                    act = exact_decision<P, T, TREEPM, GEOM>(A, n2, jd, xi, yi, zi, hi, crit, gscale, gbox);
                 const unsigned accm = __ballot_sync(0xffffffffu, act == ACT_ACCEPT);
                 if (accm && act == ACT_ACCEPT) {
                     T Qs[g4_nq(P) > 0 ? g4_nq(P) : 1];
                     T mx, my, mz, M;
                     if (sizeof(T) == 8 && A.qd) {
-                        const double *dd = A.qd + (size_t)jj * (4 + A.nq);
+                        const double *dd = A.qd + (size_t)jd * (4 + A.nq);
                         mx = (T)dd[0]; my = (T)dd[1]; mz = (T)dd[2]; M = (T)dd[3];
 #pragma unroll
                         for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)dd[4 + c];
                     } else {
                         mx = (T)n2.sx; my = (T)n2.sy; mz = (T)n2.sz; M = (T)n2.mass;
-                        const float *qq = A.q + (size_t)jj * A.nq;
+                        const float *qq = A.q + (size_t)jd * A.nq;
 #pragma unroll
                         for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)__ldg(qq + c);
                     }
                     const T rx = (T)(int32_t)(n2.cx - xi) * (T)gscale + mx;
                     const T ry = (T)(int32_t)(n2.cy - yi) * (T)gscale + my;
                     const T rz = (T)(int32_t)(n2.cz - zi) * (T)gscale + mz;
-                    pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, (T)A.as, bx, by, bz, bp);
+                    pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, par<T>(A.as, A.asf), bx, by, bz, bp);
                     npn++;
                 }
                 if (lane == src) m &= ~accm;
@@ -471,7 +543,6 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
                 S.first[pos] = nd.first;
                 S.count[pos] = nd.count;
                 S.mask[pos] = m;
-                S.node[pos] = d;
             }
             nleaf += __popc(lm);
             const bool expand = ve && !leaf && !gskip && m != 0u;
@@ -487,15 +558,21 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkArgs A)
             if (tail + tot - head > QCAP) {
                 if (lane == 0) atomicOr(A.flags, G4_FLAG_LISTCAP);
             } else if (nch > 0) {
-                const int cb = A.b_child[nd.bfs];
-                for (int c = 0; c < nch; c++)
-                    Q[(tail + pre + c) & (QCAP - 1)] = make_int2(A.b_dfs[cb + c], (int)m);
+                for (int c = 0; c < nch; c++)   // daughters are consecutive in level order
+                    Q[(tail + pre + c) & (QCAP - 1)] = make_int2(nd.next + c, (int)m);
             }
             if (tail + tot - head <= QCAP) tail += tot;
             __syncwarp();
         }
+        if (INTU) {
+            const T ca = (T)figs * (T)figs, cp = (T)figs;
+            ax *= ca;
+            ay *= ca;
+            az *= ca;
+            ap *= cp;
+        }
         if (valid) {
-            const T G = (T)A.G;
+            const T G = par<T>(A.G, A.Gf);
             A.acc[i] = (float)(-G * (ax + bx));
             A.acc[A.n + i] = (float)(-G * (ay + by));
             A.acc[2 * A.n + i] = (float)(-G * (az + bz));
@@ -577,11 +654,49 @@ __global__ void __launch_bounds__(256) k_direct(const DirectArgs A)
 
 __global__ void k_zero_int(int *p) { *p = 0; }
 
+// Walk copies.  Node records in level order, so that a node's daughters are consecutive
+// (the frontier pushes them without index look-ups); next = first daughter (level order),
+// parent = depth-first index (position of the node's moments).
+__global__ void k_walk_nodes(const int32_t *__restrict__ lvl, const int32_t *__restrict__ flags,
+                             const int32_t *__restrict__ b_dfs,
+                             const int32_t *__restrict__ b_child, const G4Node *__restrict__ node,
+                             G4Node *__restrict__ wnode)
+{
+    if (*flags & G4_FLAG_CAPACITY) return;   // incomplete tree (the walk does not run either)
+    const int nn = lvl[G4_NLEVELS];
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nn; b += gridDim.x * blockDim.x) {
+        const int d = b_dfs[b];
+        if ((unsigned)d >= (unsigned)nn) continue;
+        G4Node r = node[d];
+        r.next = r.nchild > 0 ? b_child[b] : -1;
+        r.parent = d;
+        r.bfs = b;
+        wnode[b] = r;
+    }
+}
+
+// particles as one 16-byte record each (one load per staged source)
+__global__ void k_walk_parts(const uint32_t *__restrict__ pos, const float *__restrict__ mass,
+                             int n, uint4 *__restrict__ wp)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        wp[j] = make_uint4(pos[j], pos[n + j], pos[2 * n + j], __float_as_uint(mass[j]));
+}
+
 template <int P, typename T, bool TREEPM, bool GEOM>
 void launch_walk(const WalkArgs &A, cudaStream_t st)
 {
     // persistent: G4_WALK_BLOCKS_PER_SM 4-warp blocks per SM; groups come from the work counter
     int nb = g4_num_sms() * G4_WALK_BLOCKS_PER_SM;
+#ifdef G4_WALK_CARVEOUT
+    // preferred shared-memory carveout (percent of the unified L1/shared array)
+    static bool carve_set = false;
+    if (!carve_set) {
+        cudaFuncSetAttribute(k_walk<P, T, TREEPM, GEOM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             G4_WALK_CARVEOUT);
+        carve_set = true;
+    }
+#endif
     k_walk<P, T, TREEPM, GEOM><<<nb, WALK_THREADS, 0, st>>>(A);
 }
 
@@ -676,8 +791,6 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     A.counts = counts;
     A.work = t->d_flags + 1;
     A.flags = t->d_flags;
-    A.b_dfs = t->b_dfs;
-    A.b_child = t->b_child;
     A.sys_first = t->sys_first;
     A.sys_goff = t->sys_goff;
     A.sys_box = t->sys_box;
@@ -694,6 +807,13 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     const double rc = treepm ? g4_r_cut(P) : 0.0;
     A.rcut2 = rc * rc;
     A.as = treepm ? 0.5 / P->r_s : 0.0;
+    A.Gf = (float)A.G;
+    A.alphaf = (float)A.alpha;
+    A.theta2f = (float)A.theta2;
+    A.rcut2f = (float)A.rcut2;
+    A.asf = (float)A.as;
+    A.inv_as = treepm ? 2.0 * P->r_s : 0.0;
+    A.igs = 4294967296.0 / P->box_size;
     A.box = P->box_size;
     for (int k = 0; k < G4_MAX_EPS_CLASSES; k++)
         A.h_cls[k] = k < P->n_eps_classes ? (float)(2.8 * P->eps_table[k]) : 0.f;
@@ -710,11 +830,35 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
         }
     }
     A.queue = (int2 *)t->walk_queue;
+    if (!t->wnode || !t->wpart) {
+        if (!t->wnode && cudaMalloc(&t->wnode, sizeof(G4Node) * (size_t)t->cap) != cudaSuccess) {
+            cudaGetLastError();
+            t->wnode = nullptr;
+            return g4_fail(G4_ERR_OOM, "g4_gravity_tree: level-ordered node copy");
+        }
+        if (!t->wpart && cudaMalloc(&t->wpart, sizeof(uint4) * (size_t)t->n_max) != cudaSuccess) {
+            cudaGetLastError();
+            t->wpart = nullptr;
+            return g4_fail(G4_ERR_OOM, "g4_gravity_tree: particle records");
+        }
+        t->wnode_stamp = -1;
+    }
+    int extra = 0;
+    if (t->wnode_stamp != t->moments_stamp) {
+        k_walk_nodes<<<g4_blocks_for(t->cap, 256), 256, 0, st>>>(t->lvl, t->d_flags, t->b_dfs, t->b_child,
+                                                                t->node, t->wnode);
+        t->wnode_stamp = t->moments_stamp;
+        extra++;
+    }
+    k_walk_parts<<<g4_blocks_for(n, 256), 256, 0, st>>>(pos_sorted, mass_sorted, n, t->wpart);
+    extra++;
+    A.wnode = t->wnode;
+    A.wpart = t->wpart;
     k_zero_int<<<1, 1, 0, st>>>(A.work);
     const bool geom = P->criterion == 1;
     if (P->precision == 1) dispatch_walk<double>(P->order_p, A, treepm, geom, st);
     else dispatch_walk<float>(P->order_p, A, treepm, geom, st);
-    return g4_launch_check("tree walk", 2);
+    return g4_launch_check("tree walk", 2 + extra);
 }
 
 extern "C" g4_status g4_direct(const uint32_t *pos, const float *mass, const uint8_t *cls,
