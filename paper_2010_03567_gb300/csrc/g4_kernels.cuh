@@ -141,6 +141,13 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
@@ -155,7 +162,7 @@ __device__ __forceinline__ void pair_treepm_fast(float r2, float h, const PairF 
         pair_kernel<float, true>(r2, h, c.as, g0, g1);
         return;
     }
-    const float rinv = rsqrtf(r2), r = r2 * rinv;
+    const float rinv = rsqrt_approx(r2), r = r2 * rinv;   // r2 > 0 here, never subnormal
     const float e = ex2_approx(r2 * c.k2);
     const float t = rcp_approx(fmaf(G4_ERFCX_K * c.as, r, 1.f));
     const float ec = e * g4_erfcx_poly(fmaf(t, G4_ERFCX_U1, G4_ERFCX_U0));

@@ -68,13 +68,13 @@ template <int P, typename T> __device__ __forceinline__ T ipow(T x)
 
 constexpr int WALK_THREADS = 128;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
-constexpr int LEAF_BUF = 64;
+constexpr int LEAF_BUF = 128;   // pending leaves: a whole group's leaves usually fit (one flush)
 constexpr int STAGE = 128;      // sources staged per pass of the particle-particle phase
 constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in global memory)
 // minimum resident blocks per SM requested from the compiler for the FP32 TreePM walks
 // (caps their registers; other instances keep the compiler's choice)
 #ifndef G4_WALK_MIN_BLOCKS
-#define G4_WALK_MIN_BLOCKS 6
+#define G4_WALK_MIN_BLOCKS 5
 #endif
 
 // per-warp shared state: the pending leaf list of the group and the staged sources
@@ -209,26 +209,49 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
     // neighbourhood, so each lane's candidates spread evenly over the batches and the per-lane
     // evaluation loops below stay balanced across the warp.
     const int nbat = (total + STAGE - 1) / STAGE;
+    // slot q of this lane stages source t = bb + (32 q + lane) nbat of the list in batch bb;
+    // its leaf lq: a fixed-step binary search for bb = 0, then it only moves forward
+    int lq[STAGE / 32], tq[STAGE / 32];
+#pragma unroll
+    for (int q = 0; q < STAGE / 32; q++) {
+        lq[q] = 0;
+        tq[q] = (q * 32 + lane) * nbat;
+    }
+#pragma unroll
+    for (int step = LEAF_BUF / 2; step >= 1; step >>= 1)
+#pragma unroll
+        for (int q = 0; q < STAGE / 32; q++) {
+            const int c = lq[q] + step;
+            if (c < nk && S.pref[c] <= tq[q]) lq[q] = c;
+        }
     for (int bb = 0; bb < nbat; bb++) {
         const int nb = (total - bb + nbat - 1) / nbat;
         bool partial = false;
+        if (bb > 0) {
+#pragma unroll
+            for (int q = 0; q < STAGE / 32; q++) {
+                tq[q]++;
+                while (lq[q] + 1 < nk && S.pref[lq[q] + 1] <= tq[q]) lq[q]++;
+            }
+        }
+        uint4 pq[STAGE / 32];
+        int jq[STAGE / 32];
 #pragma unroll
         for (int q = 0; q < STAGE / 32; q++) {
-            const int u = q * 32 + lane, t = bb + u * nbat, v = cand_bit(u);
+            const int u = q * 32 + lane;
+            jq[q] = S.first[lq[q]] + (tq[q] - S.pref[lq[q]]);
+            if (u < nb) pq[q] = __ldg(A.wpart + jq[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < STAGE / 32; q++) {
+            const int u = q * 32 + lane, v = cand_bit(u);
             if (u < nb) {
-                int lo = 0, hi_ = nk - 1;
-                while (lo < hi_) {
-                    const int mid = (lo + hi_ + 1) >> 1;
-                    if (S.pref[mid] <= t) lo = mid;
-                    else hi_ = mid - 1;
-                }
-                const int j = S.first[lo] + (t - S.pref[lo]);
-                const uint4 pj = __ldg(A.wpart + j);
-                const uint32_t px = pj.x, py = pj.y, pz = pj.z;
+                const int j = jq[q];
+                const uint32_t px = pq[q].x, py = pq[q].y, pz = pq[q].z;
                 const float hj = A.h_cls[A.cls ? __ldg(A.cls + j) : 0] * hconv;
-                const unsigned mk = S.mask[lo];
+                const unsigned mk = S.mask[lq[q]];
                 S.ipos[v] = make_uint4(px, py, pz, __float_as_uint(hj));
-                S.mj[v] = make_float2(__uint_as_float(pj.w), __int_as_float(j));
+                S.mj[v] = make_float2(__uint_as_float(pq[q].w), __int_as_float(j));
                 S.smask[v] = mk;
                 S.hx[u] = __float2half_rn((float)(int32_t)(px - gcx) * fscale * inv_rc);
                 S.hy[u] = __float2half_rn((float)(int32_t)(py - gcy) * fscale * inv_rc);
@@ -304,21 +327,26 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
             }
             const uint4 ip = S.ipos[v];
             const float2 mj = S.mj[v];
-            if (__float_as_int(mj.y) == i) continue;
             if (INTU) {
+                // branch-free: the sink itself and pairs beyond the cutoff get mass 0 at a
+                // harmless separation, so the lanes of the warp stay in step
                 const float dx = (float)(int32_t)(ip.x - xi);
                 const float dy = (float)(int32_t)(ip.y - yi);
                 const float dz = (float)(int32_t)(ip.z - zi);
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if (A.pp_cut && r2 >= rc2i) continue;
+                const bool use = __float_as_int(mj.y) != i && !(A.pp_cut && r2 >= rc2i);
                 float g0, g1;
-                pair_treepm_fast(r2, fmaxf((float)hi, __uint_as_float(ip.w)), pf, g0, g1);
-                const float mg1 = mj.x * g1;
+                pair_treepm_fast(use ? r2 : rc2i, fmaxf((float)hi, __uint_as_float(ip.w)), pf, g0, g1);
+                const float m_ = use ? mj.x : 0.f;
+                const float mg1 = m_ * g1;
                 ax = fmaf(mg1, dx, (float)ax);
                 ay = fmaf(mg1, dy, (float)ay);
                 az = fmaf(mg1, dz, (float)az);
-                ap = fmaf(mj.x, g0, (float)ap);
+                ap = fmaf(m_, g0, (float)ap);
+                npp += use;
+                continue;
             } else {
+                if (__float_as_int(mj.y) == i) continue;
                 const T dx = (T)(int32_t)(ip.x - xi) * scale;
                 const T dy = (T)(int32_t)(ip.y - yi) * scale;
                 const T dz = (T)(int32_t)(ip.z - zi) * scale;
