@@ -306,25 +306,39 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
                 else w3 = m;
             }
         }
-        unsigned long long c0 = (unsigned long long)w0 | ((unsigned long long)w1 << 32);
-        unsigned long long c1 = (unsigned long long)w2 | ((unsigned long long)w3 << 32);
         if (partial) {
             for (int v = 0; v < 32 * nw; v++)
                 if (!((S.smask[v] >> lane) & 1u)) {
-                    if (v < 64) c0 &= ~(1ull << v);
-                    else c1 &= ~(1ull << (v - 64));
+                    const uint32_t clr = ~(1u << (v & 31));
+                    if (v < 32) w0 &= clr;
+                    else if (v < 64) w1 &= clr;
+                    else if (v < 96) w2 &= clr;
+                    else w3 &= clr;
                 }
         }
+        // the lane's nonempty candidate words packed to the front (cw first), with their slot
+        // offsets in the bytes of `bases`; popping a candidate is then a bit scan and a clear
+        uint32_t cw = 0u, n1 = 0u, n2 = 0u, n3 = 0u, bases = 0u;
+#pragma unroll
+        for (int w = 3; w >= 0; w--) {
+            const uint32_t x = w == 0 ? w0 : (w == 1 ? w1 : (w == 2 ? w2 : w3));
+            const bool e = x != 0u;
+            n3 = e ? n2 : n3;
+            n2 = e ? n1 : n2;
+            n1 = e ? cw : n1;
+            cw = e ? x : cw;
+            bases = e ? (bases << 8) | (uint32_t)(32 * w) : bases;
+        }
         // exact evaluation of the lane's own candidates
-        while (c0 | c1) {
-            int v;
-            if (c0) {
-                v = __ffsll((long long)c0) - 1;
-                c0 &= c0 - 1ull;
-            } else {
-                v = 64 + __ffsll((long long)c1) - 1;
-                c1 &= c1 - 1ull;
-            }
+        while (cw) {
+            const int v = (int)(bases & 0xffu) + __clz(__brev(cw));
+            cw &= cw - 1u;
+            const bool e = cw == 0u;
+            cw = e ? n1 : cw;
+            n1 = e ? n2 : n1;
+            n2 = e ? n3 : n2;
+            n3 = e ? 0u : n3;
+            bases = e ? bases >> 8 : bases;
             const uint4 ip = S.ipos[v];
             const float2 mj = S.mj[v];
             if (INTU) {
