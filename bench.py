@@ -161,6 +161,22 @@ def run_reference(args, rank, world):
     return 0
 
 
+def max_over_ranks(x, device, dist):
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if not dist:
+        return float(x)
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_per_rank, ms):
+    """Whole-job forces per second: every rank solves its own n_per_rank-particle box."""
+    return world * n_per_rank / (ms * 1e-3)
+
+
 def config_block(world, n_side=N_SIDE, leaf_max=None):
     L = L_BOX * n_side / N_SIDE
     return {"workload": f"periodic Zel'dovich box, {n_side}^3 particles, L={L:g}, rms displacement 2 "
@@ -235,10 +251,7 @@ def run_gpu(args, rank, world):
     launches = g4.launch_count() - l0
     ms = t0.elapsed_time(t1) / args.steps
     walk_ms = sum(a.elapsed_time(b) for a, b in ev_walk) / len(ev_walk)
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, "cuda", dist)
     clk = clocks.stop()
     counts = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
     flops = counts[0] * FLOPS_PP + counts[1] * FLOPS_PN[3]
@@ -272,10 +285,7 @@ def run_gpu(args, rank, world):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, "cuda", dist)
 
     # ---- accuracy on a sample against the FP64 direct sum (pairs with r < r_cut)
     accuracy = None
@@ -316,12 +326,12 @@ def run_gpu(args, rank, world):
                          f"({nb} forces, {tcpu:.1f} s)"}
 
     if rank == 0:
-        value = world * n / (ms * 1e-3)
+        value = job_throughput(world, n, ms)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": config_block(world, n_side, args.leaf_max), "clocks": clk,
-                "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT,
+                "e2e": {"value": job_throughput(world, n, e2e_ms), "unit": UNIT,
                         "h2d_bytes_per_step": int(n * (12 + 4 + 4)),
                         "d2h_bytes_per_step": int(n * (12 + 4))},
                 "gpu_launches": int(launches),
