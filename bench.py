@@ -43,6 +43,23 @@ FLOPS_PN = {1: 40, 2: 110, 3: 170, 4: 300, 5: 480}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA x max clock
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU type (MEASURED_PEAKS.json), else 6800 GB/s."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# algorithmic bytes per particle / per node of the HBM-bound stages (keys: 12 B read + 8 B
+# written; sort: 8 passes of (8 + 4) B read and written; gather: perm + 20 B in, 20 B out;
+# build: keys and positions read plus ~64 B per node; multipoles: particles read once, node
+# records and p = 3 moments (64 + 64 B) written; scatter: perm + 16 B in, 16 B out)
+STAGE_BYTES = {"keys_sort": (20 + 8 * 2 * 12, 0), "gather": (44, 0), "build": (24, 64),
+               "multipoles": (16, 128), "scatter": (36, 0)}
+
+
 LEAF_MAX = 32          # tuned on GB300 (profiles/autotune_leaf_256cubed.md)
 
 
@@ -110,30 +127,79 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------
 # oracle timing (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------------------------
-def oracle_sample_run(n_side=64):
-    """The FP64 oracle's full pipeline on a 64^3 box with the same spacing, split, softening
-    and clustering recipe as the headline workload (a bounded sample of it)."""
+def oracle_workload_sample(n_side=N_SIDE, k_sinks=262144):
+    """The FP64 oracle on the headline box itself: keys, sort, build and multipoles over all
+    N particles, then the relative-criterion walk for a seeded subset of k_sinks sinks.  The
+    step time is extrapolated to all N sinks: t_prepare + t_walk * N / k_sinks."""
     import oracle
     from paper_2010_03567_gb300 import synth
     L = L_BOX * n_side / N_SIDE
     ps = synth.zeldovich(n_side, L, RMS, SEED)
     wp = workload_params(n_side, L)
-    OP = oracle.OracleParams(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
-                             r_cut_factor=4.5, alpha=wp["alpha"], order=3)
+    kw = dict(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"], r_cut_factor=4.5, order=3)
+    OP = oracle.OracleParams(**kw, alpha=wp["alpha"])
+    OB = oracle.OracleParams(**kw, criterion=1, theta=0.5)
     q = oracle.int_coords_periodic(ps.pos, L)
-    OB = oracle.OracleParams(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
-                             r_cut_factor=4.5, criterion=1, theta=0.5, order=3)
+    sinks = synth.subset(ps.n, k_sinks, 2002)
     run = oracle.prepare(q, ps.mass, None, None, OB, LEAF_MAX)
-    ab, _, _ = oracle.tree_forces(run, np.arange(ps.n))
-    aold = np.linalg.norm(ab, axis=1)
+    ab, _, _ = oracle.tree_forces(run, sinks)
+    aold = np.zeros(ps.n)
+    aold[sinks] = np.linalg.norm(ab, axis=1)
 
     def step():
         t0 = time.perf_counter()
         r = oracle.prepare(q, ps.mass, None, aold, OP, LEAF_MAX)
-        oracle.tree_forces(r, np.arange(ps.n))
-        return time.perf_counter() - t0
+        t1 = time.perf_counter()
+        oracle.tree_forces(r, sinks)
+        t2 = time.perf_counter()
+        return (t1 - t0) + (t2 - t1) * ps.n / len(sinks), t2 - t0
 
-    return ps.n, step
+    sample = (f"FP64 oracle on the {n_side}^3 headline box: keys, sort, build and multipoles of all "
+              f"{ps.n} particles plus the relative-criterion walk of a {len(sinks)}-sink subset; "
+              f"step time extrapolated as t_prepare + t_walk * N / {len(sinks)}")
+    return ps.n, step, sample
+
+
+def stage_breakdown(tg, pos_int, mass, aold, P, n, n_nodes, reps=3):
+    """CUDA-event time of each pipeline stage (same calls as a timed step) and the achieved
+    algorithmic HBM bandwidth of the memory-bound ones."""
+    import torch
+    from paper_2010_03567_gb300 import g4
+    stages = [
+        ("keys_sort", lambda: g4.g4_keys_sort(pos_int, tg.keys, tg.perm, tg.ws)),
+        ("gather", lambda: g4.g4_gather(tg.perm, pos_int, mass, None, aold,
+                                        out=(tg.pos_s, tg.mass_s, None, tg.aold_s))),
+        ("build", lambda: tg.tree.build(tg.keys, tg.pos_s, P)),
+        ("multipoles", lambda: tg.tree.multipoles(tg.pos_s, tg.mass_s, None, tg.aold_s, P)),
+        ("walk", lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, acc=tg.acc_s,
+                                              pot=tg.pot_s, counts=tg.counts)),
+        ("scatter", lambda: g4.g4_scatter(tg.perm, tg.acc_s, tg.pot_s, out=(tg.acc, tg.pot))),
+    ]
+    s = torch.cuda.current_stream()
+    tot = {k: 0.0 for k, _ in stages}
+    for r in range(reps + 1):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
+        ev[0].record(s)
+        for i, (_, fn) in enumerate(stages):
+            fn()
+            ev[i + 1].record(s)
+        torch.cuda.synchronize()
+        if r > 0:
+            for i, (k, _) in enumerate(stages):
+                tot[k] += ev[i].elapsed_time(ev[i + 1]) / reps
+    peak, src = hbm_peak_gbs()
+    out = {}
+    for k, _ in stages:
+        d = {"ms": tot[k]}
+        if k in STAGE_BYTES:
+            bpp, bpn = STAGE_BYTES[k]
+            b = bpp * n + bpn * n_nodes
+            d.update({"bytes": int(b), "GB/s": b / (tot[k] * 1e-3) / 1e9,
+                      "frac_hbm": b / (tot[k] * 1e-3) / 1e9 / peak})
+        out[k] = d
+    out["hbm_peak_GB/s"] = peak
+    out["hbm_peak_source"] = src
+    return out
 
 
 def cpu_cores():
@@ -143,13 +209,12 @@ def cpu_cores():
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    n, step = oracle_sample_run()
-    for _ in range(max(0, min(args.warmup, 1))):
+    n, step, sample = oracle_workload_sample()
+    for _ in range(args.warmup):
         step()
     ts = [step() for _ in range(args.steps)]
-    t = sum(ts)
+    t = sum(x[0] for x in ts)
     val = n * args.steps / t
-    sample = f"FP64 oracle, full pipeline on a 64^3 (L=125) box of the same recipe, {n} forces per step"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -302,6 +367,8 @@ def run_gpu(args, rank, world):
                     "sample": int(len(sinks)), "p50": float(np.percentile(e, 50)),
                     "p99": float(np.percentile(e, 99)), "max": float(np.max(e))}
 
+    stages = stage_breakdown(tg, pos_int, mass, aold, P, n, nn) if rank == 0 else None
+
     extras = {}
     if rank == 0 and not args.no_extras:
         sample_ref = None
@@ -309,8 +376,12 @@ def run_gpu(args, rank, world):
             sample_ref = (sinks, ad)
         for name, fn in (("cost_model", lambda: extra_cost_model(tg, P, n)),
                          ("fmm", lambda: extra_fmm(pos_int, mass, aold, wp, n, sample_ref)),
+                         ("fp64_walk", lambda: extra_fp64(tg, P, n, sample_ref)),
                          ("batched_systems", lambda: extra_forest(wp["leaf_max"])),
-                         ("hierarchical_bins", lambda: extra_bins(wp["leaf_max"]))):
+                         ("hierarchical_bins", lambda: extra_bins(wp["leaf_max"])),
+                         ("plummer_16k", lambda: extra_plummer(wp["leaf_max"])),
+                         ("box_128cubed", lambda: extra_box128(wp["leaf_max"])),
+                         ("cost_model_512cubed", lambda: extra_c5(wp["leaf_max"]))):
             try:
                 extras[name] = fn()
             except Exception as ex:           # report, keep the headline line
@@ -319,11 +390,10 @@ def run_gpu(args, rank, world):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        nb, cstep = oracle_sample_run()
-        tcpu = cstep()
-        cpu = {"value": nb / tcpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": "FP64 oracle, full pipeline on a 64^3 (L=125) box of the same recipe "
-                         f"({nb} forces, {tcpu:.1f} s)"}
+        nb, cstep, csample = oracle_workload_sample(n_side)
+        text, treal = cstep()
+        cpu = {"value": nb / text, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": csample + f" ({treal:.1f} s of CPU time measured)"}
 
     if rank == 0:
         value = job_throughput(world, n, ms)
@@ -343,7 +413,7 @@ def run_gpu(args, rank, world):
                              "interactions_per_step": {"pp": int(counts[0]), "pn": int(counts[1])}},
                 "tree": {"nodes": nn, "max_level": ml},
                 "interactions_per_s": float((counts[0] + counts[1]) / (walk_ms * 1e-3)),
-                "accuracy": accuracy, "cpu_baseline": cpu, **extras}
+                "accuracy": accuracy, "stages": stages, "cpu_baseline": cpu, **extras}
         print(json.dumps(line), flush=True)
     if dist:
         tdist.barrier()
@@ -505,6 +575,116 @@ def extra_cost_model(tg, P, n):
             "walk_ms_ph_order": ph_ms,
             "walk_ms_lpt_order": {f"chunk{c}": v for c, v in lpt.items()},
             "forces_identical": same}
+
+
+def _errors(a, ref):
+    e = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    return {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99)), "max": float(e.max())}
+
+
+def extra_fp64(tg, P, n, sample_ref):
+    """The same walk in FP64 (FP64 multipoles and interactions) on the headline box: the FP32
+    walk's error against it, and both against the FP64 direct sum on the sample."""
+    import torch
+    from paper_2010_03567_gb300 import g4
+    P64 = g4.G4Params.from_buffer_copy(P)
+    P64.precision = 1
+    a32 = tg.acc_s.clone()
+    tg.tree.multipoles(tg.pos_s, tg.mass_s, None, tg.aold_s, P64)
+    acc64 = torch.zeros_like(tg.acc_s)
+    ms = _time(lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P64, acc=acc64,
+                                            pot=None, counts=None), 1)
+    tg.tree.multipoles(tg.pos_s, tg.mass_s, None, tg.aold_s, P)    # restore the FP32 state
+    res = {"walk_ms_fp64": ms, "fp32_vs_fp64_gpu": _errors(a32.double().cpu().numpy().T,
+                                                           acc64.double().cpu().numpy().T)}
+    if sample_ref is not None:
+        sinks, ad = sample_ref
+        inv = torch.empty_like(tg.perm)
+        inv[tg.perm.long()] = torch.arange(n, dtype=torch.int32, device="cuda")
+        rows = inv[torch.from_numpy(sinks).cuda().long()].long()
+        res["fp64_gpu_vs_direct"] = _errors(acc64[:, rows].double().cpu().numpy().T, ad)
+    return res
+
+
+def extra_plummer(leaf_max):
+    """Isolated Plummer sphere, N = 16384, p = 3, alpha = 0.0025 with |a_old| from the GPU
+    direct sum; accuracy against the oracle's FP64 direct sum."""
+    import torch
+    import oracle
+    from paper_2010_03567_gb300 import g4, synth
+    ps = synth.plummer_16k()
+    q, fr = g4.g4_int_coords(torch.from_numpy(ps.pos).cuda(), False)
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    box = float(fr[3].item())
+    PD = g4.params(box_size=box, periodic=0, eps=[0.01], leaf_max=leaf_max)
+    ad_gpu, _ = g4.g4_direct(q, mass, None, PD)
+    aold = torch.linalg.vector_norm(ad_gpu, dim=0).contiguous()
+    P = g4.params(box_size=box, periodic=0, eps=[0.01], alpha=0.0025, leaf_max=leaf_max)
+    tg = g4.TreeGravity(ps.n, P)
+    ms = _time(lambda: tg.forces(q, mass, None, aold, P), 10)
+    acc = tg.acc.double().cpu().numpy().T
+    OP = oracle.OracleParams(box=box, periodic=False, eps=np.array([0.01]))
+    ad, _ = oracle.direct(q.cpu().numpy().view(np.uint32), ps.mass, None, np.arange(ps.n), OP)
+    cnt = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+    return {"particles": ps.n, "ms_per_step": ms, "forces_per_s": ps.n / (ms * 1e-3),
+            "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
+            "accuracy_vs_direct": _errors(acc, ad)}
+
+
+def extra_box128(leaf_max):
+    """The 128^3 periodic box (L = 100, rms displacement 0.5 spacings), p = 3, alpha = 0.0025;
+    accuracy on a 65536-particle subset against the oracle's FP64 direct sum (r < r_cut)."""
+    import torch
+    import oracle
+    from paper_2010_03567_gb300 import g4, synth
+    L, ns = 100.0, 128
+    ps = synth.zeldovich(ns, L, 0.5, 1002)
+    wp = dict(box_size=L, periodic=1, r_s=1.25 * L / 256, r_cut_factor=4.5, eps=[L / ns / 30],
+              leaf_max=leaf_max)
+    q, _ = g4.g4_int_coords(torch.from_numpy(ps.pos).cuda(), True, L)
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    tg = g4.TreeGravity(ps.n, g4.params(**wp, criterion=1, theta=0.5))
+    a0, _ = tg.forces(q, mass)
+    aold = torch.linalg.vector_norm(a0, dim=0).contiguous()
+    P = g4.params(**wp, alpha=0.0025)
+    ms = _time(lambda: tg.forces(q, mass, None, aold, P), 10)
+    sinks = synth.subset(ps.n, 65536, 2002)
+    OP = oracle.OracleParams(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
+                             r_cut_factor=4.5)
+    ad, _ = oracle.direct(q.cpu().numpy().view(np.uint32), ps.mass, None, sinks, OP, r_max=OP.r_cut)
+    acc = tg.acc.double().cpu().numpy().T[sinks]
+    cnt = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+    return {"particles": ps.n, "ms_per_step": ms, "forces_per_s": ps.n / (ms * 1e-3),
+            "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
+            "accuracy_vs_direct": {**_errors(acc, ad), "sample": len(sinks)}}
+
+
+def extra_c5(leaf_max):
+    """512^3 box (L = 1000, rms 0.5 spacings, r_s = 1.25 L/1024): the cost model trained on the
+    counts logged by the first walk orders the groups of the next walks (heaviest first);
+    forces/s against the plain PH order, prediction error against the measured counts."""
+    import torch
+    from paper_2010_03567_gb300 import g4, synth
+    ns, L = 512, 1000.0
+    pos = synth.zeldovich_gpu(ns, L, 0.5, 1006)
+    q, _ = g4.g4_int_coords(pos, True, L)
+    del pos
+    torch.cuda.empty_cache()
+    n = ns ** 3
+    mass = torch.ones(n, dtype=torch.float32, device="cuda")
+    wp = dict(box_size=L, periodic=1, r_s=1.25 * L / 1024, r_cut_factor=4.5, eps=[L / ns / 30],
+              leaf_max=leaf_max)
+    tg = g4.TreeGravity(n, g4.params(**wp, criterion=1, theta=0.5))
+    a0, _ = tg.forces(q, mass)
+    aold = torch.linalg.vector_norm(a0, dim=0).contiguous()
+    del a0
+    P = g4.params(**wp, alpha=0.0025)
+    plain = _time(lambda: tg.forces(q, mass, None, aold, P), 2)
+    res = extra_cost_model(tg, P, n)
+    res.update({"particles": n, "ms_per_step_ph_order": plain,
+                "forces_per_s_ph_order": n / (plain * 1e-3)})
+    del tg
+    return res
 
 
 def main():

@@ -220,6 +220,49 @@ def plummer_16k() -> ParticleSet:
     return plummer(16384, 1001)
 
 
+def zeldovich_gpu(n_side: int, L: float, rms_in_spacing: float, seed: int):
+    """The ``zeldovich`` recipe drawn on the GPU with torch (seeded torch generator, cuFFT), for
+    sizes whose host FFTs would take minutes (512^3).  Same lattice, spectrum, Nyquist planes
+    and rms rescaling as ``zeldovich``; the numbers differ from the numpy generator's (another
+    random stream).  Returns a (N, 3) float64 CUDA tensor of positions in [0, L).  Masses are 1
+    and eps_0 = Delta / 30, as in ``zeldovich``.
+    """
+    import torch
+    n = n_side
+    dev = torch.device("cuda")
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    dk = torch.fft.rfftn(torch.randn((n, n, n), generator=gen, dtype=torch.float64, device=dev))
+    kf = 2.0 * math.pi / L
+    k1 = torch.fft.fftfreq(n, d=1.0 / n, dtype=torch.float64, device=dev)
+    kz1 = torch.fft.rfftfreq(n, d=1.0 / n, dtype=torch.float64, device=dev)
+    kx, ky, kz = k1[:, None, None], k1[None, :, None], kz1[None, None, :]
+    k2 = (kx * kx + ky * ky + kz * kz) * kf * kf
+    k2[0, 0, 0] = 1.0
+    nyq = n // 2
+    mask = (kx.abs() == nyq) | (ky.abs() == nyq) | (kz == nyq)
+    amp = torch.where(mask, torch.zeros((), dtype=torch.float64, device=dev), k2.rsqrt())
+    amp[0, 0, 0] = 0.0
+    dk = dk * amp / k2
+    del amp, mask
+    delta = L / n
+    idx = (torch.arange(n, dtype=torch.float64, device=dev) + 0.5) * delta
+    pos = torch.empty((n ** 3, 3), dtype=torch.float64, device=dev)
+    ss = 0.0
+    for ax, kk in enumerate((kx, ky, kz)):
+        psi = torch.fft.irfftn(dk * (1j * kk * kf), s=(n, n, n))
+        ss += float((psi * psi).sum().item())
+        pos[:, ax] = psi.reshape(-1)
+        del psi
+    rms = math.sqrt(ss / n ** 3)
+    scale = (rms_in_spacing * delta / rms) if rms > 0 else 0.0
+    lat = (idx[:, None, None].expand(n, n, n), idx[None, :, None].expand(n, n, n),
+           idx[None, None, :].expand(n, n, n))
+    for ax in range(3):
+        pos[:, ax] = torch.remainder(lat[ax].reshape(-1) + scale * pos[:, ax], L)
+    pos[pos >= L] -= L
+    return pos
+
+
 def zeldovich_box(n_side: int, L: float, rms_in_spacing: float, seed: int) -> ParticleSet:
     return zeldovich(n_side, L, rms_in_spacing, seed)
 
