@@ -240,13 +240,22 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_sort_rowscan(uint32_t *__restr
     if (threadIdx.x == 0) totals[blockIdx.x] = tot;
 }
 
+// Scatter of one tile: stable ranks per warp (match_any), then the tile is reordered by digit
+// in shared memory, so that consecutive threads write consecutive addresses of each digit's
+// output run (coalesced stores).  Dynamic shared memory: keys, values of the tile.
+constexpr size_t SCATTER_SMEM = (size_t)SORT_TILE * (sizeof(uint64_t) + sizeof(int32_t));
+
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
     const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     int32_t *__restrict__ vout, int n, int shift, const uint32_t *__restrict__ cnt,
     const uint32_t *__restrict__ totals, int ntiles)
 {
+    extern __shared__ __align__(16) unsigned char sort_smem[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(sort_smem);
+    int32_t *sv = reinterpret_cast<int32_t *>(sort_smem + (size_t)SORT_TILE * sizeof(uint64_t));
     __shared__ uint32_t wc[SORT_WARPS][256];
-    __shared__ uint32_t base[256];
+    __shared__ uint32_t gbase[256];    // output position of the tile's first key of each digit
+    __shared__ uint32_t lstart[256];   // first slot of each digit in the reordered tile
     __shared__ uint32_t ws[SORT_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     // digit bases: exclusive scan of the 256 digit totals (one digit per thread)
@@ -262,7 +271,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
         __syncthreads();
         uint32_t before = 0;
         for (int j = 0; j < w; j++) before += ws[j];
-        base[tid] = before + x - v + cnt[(size_t)tid * ntiles + blockIdx.x];
+        gbase[tid] = before + x - v + cnt[(size_t)tid * ntiles + blockIdx.x];
     }
 #pragma unroll
     for (int j = 0; j < SORT_WARPS; j++) wc[j][tid] = 0;
@@ -271,7 +280,8 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
     uint64_t key[SORT_ITEMS];
     int32_t val[SORT_ITEMS];
     uint32_t rank[SORT_ITEMS];
-    const int wbase = blockIdx.x * SORT_TILE + w * (SORT_TILE / SORT_WARPS);
+    const int tile0 = blockIdx.x * SORT_TILE;
+    const int wbase = tile0 + w * (SORT_TILE / SORT_WARPS);
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++) {
         int i = wbase + it * 32 + lane;
@@ -291,14 +301,27 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
         __syncwarp();
     }
     __syncthreads();
+    // per digit: offsets of the warps' runs, and the digit's first slot in the tile
+    uint32_t dcount = 0;
     {
-        uint32_t run = 0;
 #pragma unroll
         for (int j = 0; j < SORT_WARPS; j++) {
             uint32_t t = wc[j][tid];
-            wc[j][tid] = run;
-            run += t;
+            wc[j][tid] = dcount;
+            dcount += t;
         }
+        uint32_t x = dcount;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        __syncthreads();
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int j = 0; j < w; j++) before += ws[j];
+        lstart[tid] = before + x - dcount;
     }
     __syncthreads();
 #pragma unroll
@@ -306,10 +329,19 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
         int i = wbase + it * 32 + lane;
         if (i < n) {
             uint32_t d = (uint32_t)(key[it] >> shift) & 255u;
-            uint32_t p = base[d] + wc[w][d] + rank[it];
-            kout[p] = key[it];
-            vout[p] = val[it];
+            uint32_t p = lstart[d] + wc[w][d] + rank[it];
+            sk[p] = key[it];
+            sv[p] = val[it];
         }
+    }
+    __syncthreads();
+    const int tn = min(SORT_TILE, n - tile0);
+    for (int k = tid; k < tn; k += SORT_THREADS) {
+        const uint64_t kk = sk[k];
+        const uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        const uint32_t p = gbase[d] + (uint32_t)k - lstart[d];
+        kout[p] = kk;
+        vout[p] = sv[k];
     }
 }
 
@@ -439,6 +471,15 @@ g4_status g4_sort_pairs_u64(const uint64_t *keys_in, uint64_t *keys_out, int32_t
     uint32_t *cnt = (uint32_t *)p;
     p += align256(sizeof(uint32_t) * 256 * (size_t)ntiles);
     uint32_t *tot = (uint32_t *)p;
+    static int smem_set_dev = -1;   // opt in to the tile's dynamic shared memory once per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (smem_set_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SCATTER_SMEM);
+        if (e != cudaSuccess) return g4_cuda_check(e, "radix sort: shared memory opt-in");
+        smem_set_dev = dev;
+    }
     int passes = (key_bits + 7) / 8;
     if (passes & 1) passes++;   // even pass count: the result lands in keys_out
     // pass 0 reads keys_in with implicit values; ping-pong between keys_out/kalt and v0/v1 so
@@ -453,8 +494,8 @@ g4_status g4_sort_pairs_u64(const uint64_t *keys_in, uint64_t *keys_out, int32_t
         int shift = 8 * pass;
         k_sort_hist<<<ntiles, SORT_THREADS, 0, st>>>(ksrc, (int)n, shift, cnt, ntiles);
         k_sort_rowscan<<<256, SCAN_THREADS, 0, st>>>(cnt, ntiles, tot);
-        k_sort_scatter<<<ntiles, SORT_THREADS, 0, st>>>(ksrc, vsrc, kdst, vdst, (int)n, shift, cnt,
-                                                        tot, ntiles);
+        k_sort_scatter<<<ntiles, SORT_THREADS, SCATTER_SMEM, st>>>(ksrc, vsrc, kdst, vdst, (int)n,
+                                                                   shift, cnt, tot, ntiles);
         ksrc = kdst;
         vsrc = vdst;
     }
