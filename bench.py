@@ -577,6 +577,22 @@ def extra_cost_model(tg, P, n):
             "forces_identical": same}
 
 
+def _graph_time(fn, reps):
+    """Capture one call of fn (a whole allocation-free pipeline step) in a CUDA graph and time
+    its replays: what the step costs without host launch overhead."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()                                   # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return _time(g.replay, reps, warm=2)
+
+
 def _errors(a, ref):
     e = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
     return {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99)), "max": float(e.max())}
@@ -622,11 +638,13 @@ def extra_plummer(leaf_max):
     P = g4.params(box_size=box, periodic=0, eps=[0.01], alpha=0.0025, leaf_max=leaf_max)
     tg = g4.TreeGravity(ps.n, P)
     ms = _time(lambda: tg.forces(q, mass, None, aold, P), 10)
+    ms_graph = _graph_time(lambda: tg.forces(q, mass, None, aold, P), 10)
     acc = tg.acc.double().cpu().numpy().T
     OP = oracle.OracleParams(box=box, periodic=False, eps=np.array([0.01]))
     ad, _ = oracle.direct(q.cpu().numpy().view(np.uint32), ps.mass, None, np.arange(ps.n), OP)
     cnt = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
     return {"particles": ps.n, "ms_per_step": ms, "forces_per_s": ps.n / (ms * 1e-3),
+            "ms_per_step_graph": ms_graph, "forces_per_s_graph": ps.n / (ms_graph * 1e-3),
             "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
             "accuracy_vs_direct": _errors(acc, ad)}
 
@@ -648,6 +666,7 @@ def extra_box128(leaf_max):
     aold = torch.linalg.vector_norm(a0, dim=0).contiguous()
     P = g4.params(**wp, alpha=0.0025)
     ms = _time(lambda: tg.forces(q, mass, None, aold, P), 10)
+    ms_graph = _graph_time(lambda: tg.forces(q, mass, None, aold, P), 10)
     sinks = synth.subset(ps.n, 65536, 2002)
     OP = oracle.OracleParams(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
                              r_cut_factor=4.5)
@@ -655,6 +674,7 @@ def extra_box128(leaf_max):
     acc = tg.acc.double().cpu().numpy().T[sinks]
     cnt = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
     return {"particles": ps.n, "ms_per_step": ms, "forces_per_s": ps.n / (ms * 1e-3),
+            "ms_per_step_graph": ms_graph, "forces_per_s_graph": ps.n / (ms_graph * 1e-3),
             "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
             "accuracy_vs_direct": {**_errors(acc, ad), "sample": len(sinks)}}
 

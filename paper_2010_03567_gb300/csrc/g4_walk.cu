@@ -68,7 +68,7 @@ template <int P, typename T> __device__ __forceinline__ T ipow(T x)
 
 constexpr int WALK_THREADS = 128;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
-constexpr int LEAF_BUF = 128;   // pending leaves: a whole group's leaves usually fit (one flush)
+constexpr int LEAF_BUF = 256;   // pending leaves: a whole group's leaves usually fit (one flush)
 constexpr int STAGE = 128;      // sources staged per pass of the particle-particle phase
 constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in global memory)
 // minimum resident blocks per SM requested from the compiler for the FP32 TreePM walks
