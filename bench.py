@@ -593,6 +593,36 @@ def _graph_time(fn, reps):
     return _time(g.replay, reps, warm=2)
 
 
+def partition_gain(tg, P, n, step, reps=10, train_steps=400):
+    """The cost model trained on the counts of the last walk partitions the walk into work items
+    (g4_schedule_items); the same step is timed with plain 32-sink groups, with items from the
+    model's predictions, and with items from the measured counts (the paper's q_i of the last
+    step).  Every sink's interaction counts must be unchanged."""
+    import torch
+    from paper_2010_03567_gb300 import g4
+    ref_counts = tg.counts.clone()
+    labels = g4.cost_labels(tg.counts)
+    feats = g4.cost_features(tg.tree, P, n, tg.aold_s)
+    cm = g4.CostModel(seed=1)
+    cm.train(feats, labels, steps=train_steps, lr=3e-3)
+    pred = cm.predict(feats)
+    walk = lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, acc=tg.acc_s,
+                                        pot=tg.pot_s, counts=tg.counts)
+    out = {"plain": {"walk_ms": _time(walk, reps), "step_ms_graph": _graph_time(step, reps)}}
+    same = True
+    for name, src in (("model", pred), ("measured_counts", labels)):
+        items, ni = g4.schedule_items(src)
+        g4.set_work_items(tg.tree, items, ni, n)
+        out[name] = {"walk_ms": _time(walk, reps), "step_ms_graph": _graph_time(step, reps),
+                     "items": int(ni.item())}
+        same = same and bool(torch.equal(tg.counts, ref_counts))
+        g4.set_work_items(tg.tree, None)
+    out["groups"] = (n + 31) // 32
+    out["interaction_counts_identical"] = same
+    out["speedup_step_model"] = out["plain"]["step_ms_graph"] / out["model"]["step_ms_graph"]
+    return out
+
+
 def _errors(a, ref):
     e = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
     return {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99)), "max": float(e.max())}
@@ -643,10 +673,12 @@ def extra_plummer(leaf_max):
     OP = oracle.OracleParams(box=box, periodic=False, eps=np.array([0.01]))
     ad, _ = oracle.direct(q.cpu().numpy().view(np.uint32), ps.mass, None, np.arange(ps.n), OP)
     cnt = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+    part = partition_gain(tg, P, ps.n, lambda: tg.forces(q, mass, None, aold, P))
     return {"particles": ps.n, "ms_per_step": ms, "forces_per_s": ps.n / (ms * 1e-3),
             "ms_per_step_graph": ms_graph, "forces_per_s_graph": ps.n / (ms_graph * 1e-3),
             "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
-            "accuracy_vs_direct": _errors(acc, ad)}
+            "accuracy_vs_direct": _errors(acc, ad), "cost_partition": part,
+            "forces_per_s_graph_model_items": ps.n / (part["model"]["step_ms_graph"] * 1e-3)}
 
 
 def extra_box128(leaf_max):

@@ -321,6 +321,39 @@ g4_status g4_schedule_lpt(const float *pred_sorted, int64_t n, int32_t chunk, in
  * Used only for whole-set walks of a single system whose group count matches. */
 g4_status g4_tree_set_group_order(g4_tree tree, const int32_t *group_order, int64_t ngroups);
 
+/* Bytes of device workspace for g4_schedule_items with n sinks. */
+g4_status g4_schedule_items_workspace(int64_t n, size_t *bytes);
+
+/* Partition of the walk by predicted cost (Sec. 6.1 balances the work with q_i, the
+ * interactions of a particle's last force computation; here the prediction of the cost model
+ * or the measured counts).  Group g (sorted sinks [32g, 32g+32)) has predicted cost
+ * c_g = sum of expm1(max(pred, 0)) over its sinks.  A group with c_g > total / target (total =
+ * sum of all c_g, fixed-order reduction) is split into K in {2, 4, 8} parts, K the smallest
+ * power of two with c_g / K <= total / target: part k walks the tree for the same 32 sinks and
+ * evaluates every K-th source of the group's source list (list positions k, k + K, ...), part 0
+ * also the multipoles; the last part to finish adds the parts' sums in part order
+ * (deterministic) and writes the outputs.  At most max_split groups are split (the first ones
+ * in sink order); a large workload has c_g << total/target and is not split.  Items are ordered
+ * by descending predicted part cost (stable).
+ *   pred:    n floats (device): log(1 + cost) per sorted sink (cost model or measured labels).
+ *   target:  desired number of equal-cost items (e.g. four per resident warp).
+ *   items:   4 x 8 ceil(n/32) int32 (device): (first sink, count, part | parts << 8, split
+ *            slot or -1); n_items: 1 int32 (device) = the number of valid items (the rest zero).
+ * Every sink's interaction set is unchanged; sums round differently (other summation order). */
+g4_status g4_schedule_items(const float *pred_sorted, int64_t n, int32_t target, int32_t max_split,
+                            int32_t *items, int32_t *n_items, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
+/* Makes later FP32 g4_gravity_tree calls on this handle take their work from `items` (device,
+ * kept by pointer, as written by g4_schedule_items with the same max_split; n_items read on the
+ * device) instead of fixed 32-sink groups.  capacity = number of items in the array.  Allocates
+ * the partial-sum buffers of max_split split groups (6 KB each) when they grow, so call it
+ * outside graph capture.  NULL restores the plain groups.  Used only for whole-set walks of a
+ * single system (no active list, no forest) with n_sinks sinks; a malformed item sets the
+ * list-capacity flag reported by g4_tree_status. */
+g4_status g4_tree_set_work_items(g4_tree tree, const int32_t *items, const int32_t *n_items,
+                                 int64_t capacity, int64_t n_sinks, int32_t max_split);
+
 /* ---- helper: direct summation on the GPU --------------------------------------------------- */
 
 /* O(n * n_sinks) direct sum with the same pair kernel (nearest image when periodic, pair

@@ -267,6 +267,119 @@ __global__ void k_expand_chunks(const int32_t *__restrict__ chunk_order, int nch
     }
 }
 
+// ---- cost-partitioned work items of the walk ---------------------------------------------------
+// A 32-sink group whose predicted cost exceeds the target item cost is split into K parts
+// (K in {2, 4, 8}); part k of K walks the same tree for the same 32 sinks but evaluates only
+// every K-th source of the group's source list (and, for k = 0, the multipoles).  Lanes stay
+// full; the parts' sums are combined in part order by whichever part finishes last.
+
+constexpr int ITEM_SPLIT_MAX = 8;
+
+// predicted cost of each 32-sink group (sequential sum: deterministic)
+__global__ void k_group_cost(const float *__restrict__ pred, int n, int ngroups,
+                             float *__restrict__ gcost)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+        float c = 0.f;
+        const int b = 32 * g, e = min(n, b + 32);
+        for (int i = b; i < e; i++) c += expm1f(fmaxf(pred[i], 0.f));
+        gcost[g] = c;
+    }
+}
+
+// total predicted cost, one block, fixed summation order
+__global__ void __launch_bounds__(1024) k_cost_total(const float *__restrict__ gcost, int ngroups,
+                                                     double *__restrict__ total)
+{
+    __shared__ double part[1024];
+    double s = 0.0;
+    for (int g = threadIdx.x; g < ngroups; g += 1024) s += (double)gcost[g];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = part[0];
+}
+
+// wanted number of parts of each group
+__global__ void k_group_parts(const float *__restrict__ gcost, int ngroups,
+                              const double *__restrict__ total, float target,
+                              int32_t *__restrict__ kparts)
+{
+    const float T = (float)(*total / (double)target);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+        const float c = gcost[g];
+        int K = 1;
+        while (K < ITEM_SPLIT_MAX && c > (float)K * T) K <<= 1;
+        kparts[g] = K;
+    }
+}
+
+// split slot of each group: exclusive count of split groups before it (one block, fixed
+// order); groups beyond the capacity stay whole
+__global__ void __launch_bounds__(1024) k_split_ids(int32_t *__restrict__ kparts, int ngroups,
+                                                    int max_split, int32_t *__restrict__ sid)
+{
+    __shared__ int32_t cnt[1024];
+    const int per = (ngroups + 1023) / 1024, b = threadIdx.x * per, e = min(ngroups, b + per);
+    int c = 0;
+    for (int g = b; g < e; g++) c += kparts[g] > 1;
+    cnt[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int t = 0; t < 1024; t++) {
+            const int v = cnt[t];
+            cnt[t] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    int run = cnt[threadIdx.x];
+    for (int g = b; g < e; g++) {
+        if (kparts[g] > 1) {
+            if (run < max_split) sid[g] = run;
+            else {
+                sid[g] = -1;
+                kparts[g] = 1;
+            }
+            run++;
+        } else {
+            sid[g] = -1;
+        }
+    }
+}
+
+// sort keys of the item slots 8g .. 8g+7: descending part cost for the K parts, all-ones
+// (last) for the unused slots
+__global__ void k_item_slots(const float *__restrict__ gcost, const int32_t *__restrict__ kparts,
+                             int ngroups, uint64_t *__restrict__ key, int32_t *__restrict__ nitems)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+        const int K = kparts[g];
+        const uint32_t ck = 0xFFFFFFFEu - __float_as_uint(fmaxf(gcost[g] / (float)K, 0.f));
+        for (int j = 0; j < ITEM_SPLIT_MAX; j++)
+            key[(size_t)ITEM_SPLIT_MAX * g + j] = j < K ? (uint64_t)ck : 0xFFFFFFFFull;
+        atomicAdd(nitems, K);
+    }
+}
+
+// items in sorted slot order: (first sink, count, part | parts << 8, split slot), unused
+// slots all zero
+__global__ void k_items_out(const int32_t *__restrict__ slot_order, int nslots,
+                            const int32_t *__restrict__ kparts, const int32_t *__restrict__ sid,
+                            int n, int4 *__restrict__ items)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nslots; k += gridDim.x * blockDim.x) {
+        const int slot = slot_order[k], g = slot / ITEM_SPLIT_MAX, j = slot % ITEM_SPLIT_MAX;
+        const int K = kparts[g];
+        items[k] = j < K ? make_int4(32 * g, min(32, n - 32 * g), j | (K << 8), sid[g])
+                         : make_int4(0, 0, 0, 0);
+    }
+}
+
 }  // namespace
 
 static inline size_t al256c(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -374,6 +487,94 @@ extern "C" g4_status g4_schedule_lpt(const float *pred_sorted, int64_t n, int32_
     k_expand_chunks<<<g4_blocks_for(nc, 256), 256, 0, st>>>(corder, (int)nc, chunk, (int)ng, pos_last,
                                                            group_order);
     return g4_launch_check("expand chunks", 2);
+}
+
+extern "C" g4_status g4_schedule_items_workspace(int64_t n, size_t *bytes)
+{
+    if (!bytes || n < 0) return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_items_workspace: bad args");
+    const size_t ng = (size_t)((n + 31) / 32 > 0 ? (n + 31) / 32 : 1);
+    const size_t ns = ITEM_SPLIT_MAX * ng;
+    *bytes = al256c(4 * ng) + al256c(8) + 2 * al256c(4 * ng) + al256c(8 * ns) + al256c(4 * ns) +
+             g4_sort_workspace_bytes((int64_t)ns);
+    return G4_OK;
+}
+
+extern "C" g4_status g4_schedule_items(const float *pred_sorted, int64_t n, int32_t target,
+                                       int32_t max_split, int32_t *items, int32_t *n_items,
+                                       void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (n < 0 || n >= ((int64_t)1 << 28) || target < 1 || max_split < 0 || !items || !n_items ||
+        !workspace || (n > 0 && !pred_sorted))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_items: bad arguments");
+    size_t need = 0;
+    g4_schedule_items_workspace(n, &need);
+    if (workspace_bytes < need) return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_items: workspace too small");
+    if (((uintptr_t)workspace & 255) != 0)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_schedule_items: workspace not 256-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(n_items, 0, sizeof(int32_t), st) != cudaSuccess)
+        return g4_cuda_check(cudaGetLastError(), "g4_schedule_items: clear count");
+    if (n == 0) return G4_OK;
+    const int64_t ng = (n + 31) / 32, ns = ITEM_SPLIT_MAX * ng;
+    char *p = (char *)workspace;
+    float *gcost = (float *)p;
+    p += al256c(4 * (size_t)ng);
+    double *total = (double *)p;
+    p += al256c(8);
+    int32_t *kparts = (int32_t *)p;
+    p += al256c(4 * (size_t)ng);
+    int32_t *sid = (int32_t *)p;
+    p += al256c(4 * (size_t)ng);
+    uint64_t *key = (uint64_t *)p;
+    p += al256c(8 * (size_t)ns);
+    int32_t *slot_order = (int32_t *)p;
+    p += al256c(4 * (size_t)ns);
+    void *sws = p;
+    k_group_cost<<<g4_blocks_for(ng, 256), 256, 0, st>>>(pred_sorted, (int)n, (int)ng, gcost);
+    k_cost_total<<<1, 1024, 0, st>>>(gcost, (int)ng, total);
+    k_group_parts<<<g4_blocks_for(ng, 256), 256, 0, st>>>(gcost, (int)ng, total, (float)target, kparts);
+    k_split_ids<<<1, 1024, 0, st>>>(kparts, (int)ng, max_split, sid);
+    k_item_slots<<<g4_blocks_for(ng, 256), 256, 0, st>>>(gcost, kparts, (int)ng, key, n_items);
+    g4_status s = g4_launch_check("item slots", 5);
+    if (s != G4_OK) return s;
+    s = g4_sort_pairs_u64(key, key, slot_order, ns, sws, g4_sort_workspace_bytes(ns), 32, st);
+    if (s != G4_OK) return s;
+    k_items_out<<<g4_blocks_for(ns, 256), 256, 0, st>>>(slot_order, (int)ns, kparts, sid, (int)n,
+                                                       (int4 *)items);
+    return g4_launch_check("items", 1);
+}
+
+extern "C" g4_status g4_tree_set_work_items(g4_tree t, const int32_t *items, const int32_t *n_items,
+                                            int64_t capacity, int64_t n_sinks, int32_t max_split)
+{
+    if (!t || capacity < 0 || n_sinks < 0 || max_split < 0 || (items && !n_items))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_tree_set_work_items: bad args");
+    if (items && max_split > t->part_cap) {
+        // partial sums of split groups: 8 parts x 32 lanes x (4 floats + 2 counts), plus one
+        // arrival counter per split group (zero between walks)
+        if (t->part_buf) cudaFree(t->part_buf);
+        if (t->part_cnt) cudaFree(t->part_cnt);
+        t->part_buf = nullptr;
+        t->part_cnt = nullptr;
+        t->part_cap = 0;
+        const size_t bb = (size_t)max_split * ITEM_SPLIT_MAX * 32 * 6 * sizeof(float);
+        if (cudaMalloc(&t->part_buf, bb) != cudaSuccess ||
+            cudaMalloc(&t->part_cnt, sizeof(int32_t) * (size_t)max_split) != cudaSuccess) {
+            cudaGetLastError();
+            if (t->part_buf) cudaFree(t->part_buf);
+            t->part_buf = nullptr;
+            t->part_cnt = nullptr;
+            return g4_fail(G4_ERR_OOM, "g4_tree_set_work_items: partial-sum buffers (%zu bytes)", bb);
+        }
+        if (cudaMemset(t->part_cnt, 0, sizeof(int32_t) * (size_t)max_split) != cudaSuccess)
+            return g4_cuda_check(cudaGetLastError(), "g4_tree_set_work_items: clear counters");
+        t->part_cap = max_split;
+    }
+    t->items = items;
+    t->n_items = items ? n_items : nullptr;
+    t->items_cap = items ? capacity : 0;
+    t->items_n_sinks = items ? n_sinks : -1;
+    return G4_OK;
 }
 
 extern "C" g4_status g4_tree_set_group_order(g4_tree t, const int32_t *group_order, int64_t ngroups)

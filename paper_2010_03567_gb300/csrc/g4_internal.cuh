@@ -84,6 +84,13 @@ struct g4_tree_s {
     // optional walk schedule: order in which the 32-sink groups are handed out
     const int32_t *group_order = nullptr;
     int64_t group_order_n = 0;
+    // optional cost-partitioned work items: (first sink, count) pairs, count on the device
+    const int32_t *items = nullptr;
+    const int32_t *n_items = nullptr;
+    int64_t items_cap = 0, items_n_sinks = -1;
+    float *part_buf = nullptr;    // partial sums of split groups (see g4_tree_set_work_items)
+    int32_t *part_cnt = nullptr;
+    int part_cap = 0;
     int moments_order = -1;
     int moments_fp64 = 0;
     // host copies filled by g4_tree_status

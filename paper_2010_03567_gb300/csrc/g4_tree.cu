@@ -365,6 +365,8 @@ extern "C" void g4_tree_free(g4_tree t)
     if (t->walk_queue) cudaFree(t->walk_queue);
     if (t->wnode) cudaFree(t->wnode);
     if (t->wpart) cudaFree(t->wpart);
+    if (t->part_buf) cudaFree(t->part_buf);
+    if (t->part_cnt) cudaFree(t->part_cnt);
     delete t;
 }
 

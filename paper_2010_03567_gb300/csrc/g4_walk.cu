@@ -42,6 +42,11 @@ struct WalkArgs {
     const double *sys_box;
     int n_sys;
     const int32_t *group_order;   // optional schedule (longest predicted cost first)
+    const int4 *items;            // optional work items (first sink, count, part | parts << 8,
+    const int32_t *n_items;       //   split slot); their number on the device
+    float *part_buf;              // partial sums of split groups: [slot][part][lane][6]
+    int32_t *part_cnt;            // arrivals per split slot (zero between walks)
+    int part_cap;                 // split slots available
     double scale;
     double G, alpha, theta2, rcut2, as;
     double box;
@@ -71,7 +76,7 @@ constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int LEAF_BUF = 256;   // pending leaves: a whole group's leaves usually fit (one flush)
 constexpr int STAGE = 128;      // sources staged per pass of the particle-particle phase
 constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in global memory)
-// minimum resident blocks per SM requested from the compiler for the FP32 TreePM walks
+// minimum resident blocks per SM requested from the compiler for the FP32 walks of order <= 3
 // (caps their registers; other instances keep the compiler's choice)
 #ifndef G4_WALK_MIN_BLOCKS
 #define G4_WALK_MIN_BLOCKS 5
@@ -162,7 +167,7 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
                                          uint32_t gcy, uint32_t gcz, float xr, float yr, float zr,
                                          unsigned vmask, T hi, T &ax, T &ay, T &az, T &ap,
                                          uint32_t &npp, double gscale, float figs, const PairF &pf,
-                                         float rc2i)
+                                         float rc2i, int kp, int Kp)
 {
     constexpr bool INTU = TREEPM && sizeof(T) == 4;
     const float fscale = (float)gscale;
@@ -208,14 +213,18 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
     // Batch bb takes sources bb, bb + nbat, bb + 2 nbat, ...: every batch samples the whole
     // neighbourhood, so each lane's candidates spread evenly over the batches and the per-lane
     // evaluation loops below stay balanced across the warp.
-    const int nbat = (total + STAGE - 1) / STAGE;
-    // slot q of this lane stages source t = bb + (32 q + lane) nbat of the list in batch bb;
-    // its leaf lq: a fixed-step binary search for bb = 0, then it only moves forward
+    // part kp of Kp takes list positions kp, kp + Kp, kp + 2 Kp, ... (a split group's parts
+    // share the list; Kp = 1: the whole list)
+    const int tv = total > kp ? (total - kp + Kp - 1) / Kp : 0;
+    const int nbat = (tv + STAGE - 1) / STAGE;
+    // slot q of this lane stages virtual position bb + (32 q + lane) nbat in batch bb, list
+    // position t = kp + Kp * (that); its leaf lq: a fixed-step binary search for bb = 0, then
+    // it only moves forward
     int lq[STAGE / 32], tq[STAGE / 32];
 #pragma unroll
     for (int q = 0; q < STAGE / 32; q++) {
         lq[q] = 0;
-        tq[q] = (q * 32 + lane) * nbat;
+        tq[q] = kp + Kp * ((q * 32 + lane) * nbat);
     }
 #pragma unroll
     for (int step = LEAF_BUF / 2; step >= 1; step >>= 1)
@@ -225,12 +234,12 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
             if (c < nk && S.pref[c] <= tq[q]) lq[q] = c;
         }
     for (int bb = 0; bb < nbat; bb++) {
-        const int nb = (total - bb + nbat - 1) / nbat;
+        const int nb = (tv - bb + nbat - 1) / nbat;
         bool partial = false;
         if (bb > 0) {
 #pragma unroll
             for (int q = 0; q < STAGE / 32; q++) {
-                tq[q]++;
+                tq[q] += Kp;
                 while (lq[q] + 1 < nk && S.pref[lq[q] + 1] <= tq[q]) lq[q]++;
             }
         }
@@ -390,7 +399,7 @@ __device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nle
 // nodes get the exact per-lane decision, and a lane that accepts or skips one resumes after
 // its subtree, exactly as a single-particle walk would.
 template <int P, typename T, bool TREEPM, bool GEOM>
-__global__ void __launch_bounds__(WALK_THREADS, (TREEPM && sizeof(T) == 4 && P <= 3) ? G4_WALK_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(WALK_THREADS, (sizeof(T) == 4 && P <= 3) ? G4_WALK_MIN_BLOCKS : 1)
 k_walk(const WalkArgs A)
 {
     __shared__ WalkSmem smem[WALK_WARPS];
@@ -399,7 +408,7 @@ k_walk(const WalkArgs A)
     const unsigned lt = (1u << lane) - 1u;
     if (*A.flags & G4_FLAG_CAPACITY) return;   // incomplete tree: outputs left untouched
     int2 *Q = A.queue + (size_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * QCAP;
-    const int ngroups = A.n_sys ? A.sys_goff[A.n_sys] : (A.n_sinks + 31) >> 5;
+    const int ngroups = A.items ? *A.n_items : (A.n_sys ? A.sys_goff[A.n_sys] : (A.n_sinks + 31) >> 5);
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(A.work, 1);
@@ -408,6 +417,20 @@ k_walk(const WalkArgs A)
         if (A.group_order) g = A.group_order[g];
         // the group's sinks, node range and box (a forest walks only its own system's tree)
         int s0 = g * 32, s_end = A.n_sinks, k = 0;   // k: root, level-ordered
+        int kp = 0, Kp = 1, pslot = -1;               // part of a split group
+        if (A.items) {
+            const int4 it = A.items[g];
+            s0 = it.x;
+            s_end = min(A.n_sinks, s0 + it.y);
+            kp = it.z & 255;
+            Kp = it.z >> 8;
+            pslot = it.w;
+            if (s0 < 0 || s0 >= s_end || Kp < 1 || kp >= Kp ||
+                (Kp > 1 && (pslot < 0 || pslot >= A.part_cap))) {
+                if (lane == 0) atomicOr(A.flags, G4_FLAG_LISTCAP);   // malformed item: reported
+                continue;
+            }
+        }
         double gbox = A.box;
         if (A.n_sys) {
             int lo = 0, hi_ = A.n_sys - 1;
@@ -470,7 +493,8 @@ k_walk(const WalkArgs A)
             // a step adds at most 32 leaves: flush before the list could overflow, and at the end
             if (nleaf > LEAF_BUF - 32 || (head >= tail && nleaf > 0)) {
                 pp_flush<T, TREEPM>(A, S, nleaf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, vmask,
-                                    INTU ? hi * (T)figs : hi, ax, ay, az, ap, npp, gscale, figs, pf, rc2i);
+                                    INTU ? hi * (T)figs : hi, ax, ay, az, ap, npp, gscale, figs, pf, rc2i,
+                                    kp, Kp);
                 nleaf = 0;
             }
             if (head >= tail) break;
@@ -555,7 +579,7 @@ k_walk(const WalkArgs A)
                 if ((mm >> lane) & 1u)
                     act = exact_decision<P, T, TREEPM, GEOM>(A, n2, jd, xi, yi, zi, hi, crit, gscale, gbox);
                 const unsigned accm = __ballot_sync(0xffffffffu, act == ACT_ACCEPT);
-                if (accm && act == ACT_ACCEPT) {
+                if (accm && act == ACT_ACCEPT && kp == 0) {   // multipoles: part 0 of a split group
                     T Qs[g4_nq(P) > 0 ? g4_nq(P) : 1];
                     T mx, my, mz, M;
                     if (sizeof(T) == 8 && A.qd) {
@@ -613,15 +637,58 @@ k_walk(const WalkArgs A)
             az *= ca;
             ap *= cp;
         }
-        if (valid) {
-            const T G = par<T>(A.G, A.Gf);
-            A.acc[i] = (float)(-G * (ax + bx));
-            A.acc[A.n + i] = (float)(-G * (ay + by));
-            A.acc[2 * A.n + i] = (float)(-G * (az + bz));
-            if (A.pot) A.pot[i] = (float)(-G * (ap + bp));
-            if (A.counts) {
-                A.counts[i] = npp;
-                A.counts[A.n + i] = npn;
+        if (Kp == 1) {
+            if (valid) {
+                const T G = par<T>(A.G, A.Gf);
+                A.acc[i] = (float)(-G * (ax + bx));
+                A.acc[A.n + i] = (float)(-G * (ay + by));
+                A.acc[2 * A.n + i] = (float)(-G * (az + bz));
+                if (A.pot) A.pot[i] = (float)(-G * (ap + bp));
+                if (A.counts) {
+                    A.counts[i] = npp;
+                    A.counts[A.n + i] = npn;
+                }
+            }
+        } else {
+            // split group: store this part's sums; the last part to arrive adds the parts in
+            // part order (deterministic) and writes the outputs
+            float *pb = A.part_buf + (((size_t)pslot * 8 + kp) * 32 + lane) * 6;
+            pb[0] = (float)(ax + bx);
+            pb[1] = (float)(ay + by);
+            pb[2] = (float)(az + bz);
+            pb[3] = (float)(ap + bp);
+            pb[4] = __uint_as_float(npp);
+            pb[5] = __uint_as_float(npn);
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(A.part_cnt + pslot, 1) == Kp - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                float sx = 0.f, sy = 0.f, sz = 0.f, sp = 0.f;
+                uint32_t cp = 0, cn = 0;
+                for (int q = 0; q < Kp; q++) {
+                    const float *qb = A.part_buf + (((size_t)pslot * 8 + q) * 32 + lane) * 6;
+                    sx += __ldcg(qb);
+                    sy += __ldcg(qb + 1);
+                    sz += __ldcg(qb + 2);
+                    sp += __ldcg(qb + 3);
+                    cp += __float_as_uint(__ldcg(qb + 4));
+                    cn += __float_as_uint(__ldcg(qb + 5));
+                }
+                if (valid) {
+                    const float G = A.Gf;
+                    A.acc[i] = -G * sx;
+                    A.acc[A.n + i] = -G * sy;
+                    A.acc[2 * A.n + i] = -G * sz;
+                    if (A.pot) A.pot[i] = -G * sp;
+                    if (A.counts) {
+                        A.counts[i] = cp;
+                        A.counts[A.n + i] = cn;
+                    }
+                }
+                if (lane == 0) A.part_cnt[pslot] = 0;   // ready for the next walk
             }
         }
     }
@@ -839,6 +906,14 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     A.n_sys = t->n_sys;
     A.group_order = (t->group_order && !active && !t->n_sys && t->group_order_n == (ns + 31) / 32)
                         ? t->group_order : nullptr;
+    const bool use_items = t->items && !active && !t->n_sys && t->items_n_sinks == ns &&
+                           P->precision == 0;
+    A.items = use_items ? (const int4 *)t->items : nullptr;
+    A.n_items = use_items ? t->n_items : nullptr;
+    A.part_buf = t->part_buf;
+    A.part_cnt = t->part_cnt;
+    A.part_cap = t->part_cap;
+    if (use_items) A.group_order = nullptr;
     if (t->n_sys && active)
         return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_tree: active subsets are not supported for forests");
     A.scale = P->box_size / 4294967296.0;

@@ -96,6 +96,9 @@ def _declare(L):
         "g4_schedule_workspace": ([i64, C.POINTER(C.c_size_t)], i32),
         "g4_schedule_lpt": ([vp, i64, C.c_int32, vp, vp, C.c_size_t, vp], i32),
         "g4_tree_set_group_order": ([vp, vp, i64], i32),
+        "g4_schedule_items_workspace": ([i64, C.POINTER(C.c_size_t)], i32),
+        "g4_schedule_items": ([vp, i64, C.c_int32, C.c_int32, vp, vp, vp, C.c_size_t, vp], i32),
+        "g4_tree_set_work_items": ([vp, vp, vp, i64, i64, C.c_int32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -545,6 +548,47 @@ def schedule_lpt(pred_sorted, chunk: int = 1, group_order=None, stream=None):
     _check(lib().g4_schedule_lpt(_ptr(pred_sorted), n, int(chunk), _ptr(group_order), C.c_void_p(wp + off),
                                  ws.numel() - off, _stream(stream)), "g4_schedule_lpt")
     return group_order
+
+
+ITEM_SPLIT_MAX = 8
+
+
+def resident_warps() -> int:
+    """Warps the persistent walk keeps resident on the current GPU (5 four-warp blocks per SM)."""
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 5 * 4
+
+
+MAX_SPLIT = 16384     # split groups per handle (6 KB of partial sums each)
+
+
+def schedule_items(pred_sorted, target: int = 0, max_split: int = MAX_SPLIT, stream=None):
+    """Cost-partitioned work items of the walk (g4_schedule_items): returns (items, n_items),
+    items a (capacity, 4) int32 tensor of (first sink, count, part | parts << 8, split slot),
+    n_items a 1-element device tensor.  target = 0: four items per resident warp."""
+    n = pred_sorted.shape[0]
+    dev = pred_sorted.device
+    cap = ITEM_SPLIT_MAX * ((n + 31) // 32)
+    items = torch.zeros((max(cap, 1), 4), dtype=torch.int32, device=dev)
+    n_items = torch.zeros(1, dtype=torch.int32, device=dev)
+    b = C.c_size_t()
+    _check(lib().g4_schedule_items_workspace(n, C.byref(b)), "g4_schedule_items_workspace")
+    ws = torch.empty(int(b.value) + 256, dtype=torch.uint8, device=dev)
+    wp = ws.data_ptr()
+    off = (-wp) % 256
+    tgt = int(target) if target else 4 * resident_warps()
+    _check(lib().g4_schedule_items(_ptr(pred_sorted), n, tgt, int(max_split), _ptr(items), _ptr(n_items),
+                                   C.c_void_p(wp + off), ws.numel() - off, _stream(stream)),
+           "g4_schedule_items")
+    return items, n_items
+
+
+def set_work_items(tree: Tree, items=None, n_items=None, n_sinks: int = 0, max_split: int = MAX_SPLIT):
+    """Make later walks on this handle take their work from `items` (None: plain groups)."""
+    tree._items_ref = (items, n_items)
+    cap = 0 if items is None else int(items.shape[0])
+    _check(lib().g4_tree_set_work_items(tree.h, _ptr(items), _ptr(n_items), cap,
+                                        int(n_sinks) if items is not None else 0, int(max_split)),
+           "g4_tree_set_work_items")
 
 
 def set_group_order(tree: Tree, group_order=None):

@@ -94,3 +94,116 @@ def test_lpt_schedule_is_a_permutation_and_keeps_forces():
     acc1, pot1, _ = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P)
     assert torch.equal(acc0, acc1) and torch.equal(pot0, pot1)
     g4.set_group_order(tg.tree, None)
+
+
+# ---- cost-partitioned work items (g4_schedule_items) ------------------------------------------
+
+def _host_parts(pred, target):
+    """Plain restatement of the partition rule, FP64: parts per 32-sink group."""
+    n = pred.shape[0]
+    ng = (n + 31) // 32
+    c = np.array([np.expm1(np.maximum(pred[32 * g:32 * g + 32], 0)).sum() for g in range(ng)])
+    T = c.sum() / target
+    K = np.ones(ng, dtype=np.int64)
+    while True:
+        grow = (K < 8) & (c > K * T)
+        if not grow.any():
+            break
+        K[grow] *= 2
+    return c, K, T
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,target,max_split", [(16384 + 7, 3000, 16384), (4096, 64, 16384),
+                                                (300000, 500, 20)])
+def test_items_partition_and_order(n, target, max_split):
+    from paper_2010_03567_gb300 import g4
+    rng = np.random.default_rng(11)
+    # heavy-tailed costs: a few expensive groups among many cheap ones
+    pred = np.log1p(rng.pareto(1.5, size=n) * 50.0).astype(np.float32)
+    items, ni = g4.schedule_items(torch.from_numpy(pred).cuda(), target, max_split)
+    k = int(ni.item())
+    it = items.cpu().numpy()
+    assert (it[k:] == 0).all()
+    first, cnt, kk, slot = it[:k, 0], it[:k, 1], it[:k, 2], it[:k, 3]
+    part, parts = kk & 255, kk >> 8
+    ng = (n + 31) // 32
+    # every group appears with parts 0..K-1 exactly once, covering its 32 (or fewer) sinks
+    g = first // 32
+    assert (first % 32 == 0).all() and (cnt == np.minimum(32, n - first)).all()
+    seen = {}
+    for gi, pi, Ki, si in zip(g, part, parts, slot):
+        seen.setdefault(gi, []).append((pi, Ki, si))
+    assert sorted(seen) == list(range(ng))
+    slots = [v[0][2] for v in seen.values() if v[0][1] > 1]
+    assert len(set(slots)) == len(slots) and all(0 <= x < max_split for x in slots)
+    for gi, v in seen.items():
+        Ks = {x[1] for x in v}
+        assert len(Ks) == 1 and sorted(x[0] for x in v) == list(range(v[0][1]))
+        assert len({x[2] for x in v}) == 1
+        assert (v[0][1] == 1) == (v[0][2] == -1)
+    c, K, T = _host_parts(pred.astype(np.float64), target)
+    Kg = np.array([seen[x][0][1] for x in range(ng)])
+    sid = np.array([seen[x][0][2] for x in range(ng)])
+    # split slots are handed out in sink order: 0, 1, 2, ...
+    split = np.flatnonzero(Kg > 1)
+    assert (sid[split] == np.arange(split.shape[0])).all() and split.shape[0] <= max_split
+    near = np.isclose(c / K, T, rtol=1e-3) | np.isclose(c / np.maximum(K // 2, 1), T, rtol=1e-3)
+    if (K > 1).sum() <= max_split:
+        # no capacity limit reached: away from the thresholds the part counts are the host's
+        assert (Kg[~near] == K[~near]).all()
+    else:
+        assert split.shape[0] == max_split
+        assert np.all((K[split] > 1) | near[split])
+    # descending predicted part cost (stable)
+    ic = c[g] / parts
+    assert (np.diff(ic) <= 1e-5 * ic[:-1] + 1e-12).all()
+
+
+@pytest.mark.gpu
+def test_items_walk_same_interactions_and_gain():
+    """The Plummer sphere (16384 particles, 512 groups for ~3000 resident warps): source-split
+    parts chosen from the trained cost model keep every sink's interactions, change forces
+    only by rounding, are deterministic, and shorten the estimated makespan
+    max(total / warps, largest item) of the walk."""
+    from paper_2010_03567_gb300 import g4
+    ps = synth.plummer_16k()
+    q, fr = g4.g4_int_coords(torch.from_numpy(ps.pos).cuda(), False)
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    box = float(fr[3].item())
+    P = g4.params(box_size=box, periodic=0, eps=[0.01], alpha=0.0025, leaf_max=32)
+    PB = g4.params(box_size=box, periodic=0, eps=[0.01], criterion=1, theta=0.5, leaf_max=32)
+    tg = g4.TreeGravity(ps.n, P)
+    a0, _ = tg.forces(q, mass, None, None, PB)
+    aold = torch.linalg.vector_norm(a0, dim=0).contiguous()
+    tg.forces(q, mass, None, aold, P)
+    acc_ref, counts_ref = tg.acc.clone(), tg.counts.clone()
+    labels = g4.cost_labels(tg.counts)
+    feats = g4.cost_features(tg.tree, P, ps.n, tg.aold_s)
+    cm = g4.CostModel(seed=1)
+    cm.train(feats, labels, steps=400, lr=3e-3)
+    pred = cm.predict(feats)
+    items, ni = g4.schedule_items(pred)
+    g4.set_work_items(tg.tree, items, ni, ps.n)
+    tg.forces(q, mass, None, aold, P)
+    acc1 = tg.acc.clone()
+    tg.forces(q, mass, None, aold, P)
+    assert torch.equal(tg.acc, acc1)                        # deterministic combine
+    assert tg.tree.status()[0] >= 0                         # no flag raised
+    g4.set_work_items(tg.tree, None)
+    assert torch.equal(tg.counts, counts_ref)
+    # same interactions, other FP32 summation order: rounding-level differences (largest where
+    # the net force nearly cancels, e.g. at the centre of the sphere)
+    e = (torch.linalg.vector_norm(acc1 - acc_ref, dim=0) / torch.linalg.vector_norm(acc_ref, dim=0))
+    assert float(torch.quantile(e, 0.99)) < 5e-6 and float(e.max()) < 1e-4
+    # makespan estimate with the measured per-sink costs
+    cost = np.expm1(labels.cpu().numpy().astype(np.float64))
+    W = g4.resident_warps()
+    grp = np.add.reduceat(cost, np.arange(0, ps.n, 32))
+    k = int(ni.item())
+    it = items.cpu().numpy()[:k]
+    icost = np.array([cost[a:a + c].sum() / (kk >> 8) for a, c, kk, _ in it])
+    plain = max(cost.sum() / W, grp.max())
+    split = max(cost.sum() / W, icost.max())
+    assert k > grp.shape[0]
+    assert plain / split > 1.5, (plain, split)
