@@ -530,9 +530,31 @@ def extra_bins(leaf_max):
     bf.capture(q, mass, cls, aold)
     graph = _time(bf.replay, 3)
     same = all(torch.equal(a, b) for a, b in zip(ref, bf.acc))
+    per_bin = [_time(lambda b=b: bf.run_bin(b, q, mass, cls, aold), 3) for b in range(len(lists))]
+    ref_counts = [tgb.counts.clone() for tgb, _ in bf.bins]
+    # the cost model trained on the counts of the full-set call partitions every bin's walk
+    tga = bf.bins[-1][0]
+    feats = g4.cost_features(tga.tree, P, n, tga.aold_s)
+    labels = g4.cost_labels(tga.counts)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    sub = torch.randperm(n, device="cuda", generator=gen)[: 1 << 18]
+    cm = g4.CostModel(seed=1)
+    cm.train(feats[sub].contiguous(), labels[sub].contiguous(), steps=400, lr=3e-3)
+    bf.set_cost_model(cm)
+    eager_m = _time(lambda: bf.run(q, mass, cls, aold), 3)
+    per_bin_m = [_time(lambda b=b: bf.run_bin(b, q, mass, cls, aold), 3) for b in range(len(lists))]
+    counts_same = all(torch.equal(tgb.counts, c) for (tgb, _), c in zip(bf.bins, ref_counts))
+    bf.capture(q, mass, cls, aold)
+    graph_m = _time(bf.replay, 3)
+    bf.set_cost_model(None)
     return {"particles": n, "active_fractions": fracs, "forces_per_step": forces,
             "eager_ms": eager, "graph_ms": graph, "forces_per_s_eager": forces / (eager * 1e-3),
-            "forces_per_s_graph": forces / (graph * 1e-3), "graph_equals_eager": bool(same)}
+            "forces_per_s_graph": forces / (graph * 1e-3), "graph_equals_eager": bool(same),
+            "per_bin_ms": per_bin,
+            "cost_partition": {"eager_ms": eager_m, "graph_ms": graph_m, "per_bin_ms": per_bin_m,
+                               "forces_per_s_graph": forces / (graph_m * 1e-3),
+                               "speedup_graph": graph / graph_m,
+                               "interaction_counts_identical": bool(counts_same)}}
 
 
 def extra_cost_model(tg, P, n):

@@ -623,16 +623,34 @@ class BinnedForces:
         self.pot = [torch.zeros(n_all, dtype=torch.float32, device=dev) for _ in self.idx]
         self.graph = None
 
+    def run_bin(self, b, pos_int, mass, cls, aold, stream=None):
+        """One force call: gather bin b's active subset, its own tree and walk, scatter."""
+        ix, (tg, sub) = self.idx[b], self.bins[b]
+        k = int(ix.shape[0])
+        _check(lib().g4_gather_subset(_ptr(ix), k, self.n_all, _ptr(pos_int), _ptr(mass), _ptr(cls),
+                                      _ptr(aold), _ptr(sub[0]), _ptr(sub[1]), _ptr(sub[2]),
+                                      _ptr(sub[3]), _stream(stream)), "g4_gather_subset")
+        acc, pot = tg.forces(sub[0], sub[1], sub[2], sub[3], self.p, stream)
+        _check(lib().g4_scatter_subset(_ptr(ix), k, self.n_all, _ptr(acc), _ptr(pot), _ptr(self.acc[b]),
+                                       _ptr(self.pot[b]), _stream(stream)), "g4_scatter_subset")
+
     def run(self, pos_int, mass, cls, aold, stream=None):
-        for b, (ix, (tg, sub)) in enumerate(zip(self.idx, self.bins)):
-            k = int(ix.shape[0])
-            _check(lib().g4_gather_subset(_ptr(ix), k, self.n_all, _ptr(pos_int), _ptr(mass), _ptr(cls),
-                                          _ptr(aold), _ptr(sub[0]), _ptr(sub[1]), _ptr(sub[2]),
-                                          _ptr(sub[3]), _stream(stream)), "g4_gather_subset")
-            acc, pot = tg.forces(sub[0], sub[1], sub[2], sub[3], self.p, stream)
-            _check(lib().g4_scatter_subset(_ptr(ix), k, self.n_all, _ptr(acc), _ptr(pot), _ptr(self.acc[b]),
-                                           _ptr(self.pot[b]), _stream(stream)), "g4_scatter_subset")
+        for b in range(len(self.idx)):
+            self.run_bin(b, pos_int, mass, cls, aold, stream)
         return self.acc, self.pot
+
+    def set_cost_model(self, model, stream=None):
+        """Partition every bin's walk by the model's predicted costs (g4_schedule_items), from
+        the features of the bin's current tree; None restores the plain groups."""
+        for ix, (tg, sub) in zip(self.idx, self.bins):
+            k = int(ix.shape[0])
+            if model is None:
+                set_work_items(tg.tree, None)
+                continue
+            feats = cost_features(tg.tree, self.p, k, tg.aold_s, stream=stream)
+            items, ni = schedule_items(model.predict(feats, stream=stream), stream=stream)
+            set_work_items(tg.tree, items, ni, k)
+        self.graph = None
 
     def capture(self, pos_int, mass, cls, aold):
         """Capture the whole bin sequence in one CUDA graph (inputs are bound by address)."""
