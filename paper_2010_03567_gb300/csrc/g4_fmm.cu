@@ -22,6 +22,7 @@
 // and the potential near A's centre of mass is Phi(s_A + a) = sum_k T_k a^k / k!.
 #include "g4_internal.cuh"
 #include "g4_kernels.cuh"
+#include "g4_pp.cuh"
 
 namespace {
 
@@ -57,6 +58,10 @@ struct FmmArgs {
     double scale, G, alpha, theta2, rcut2, as, box;
     float h_cls[G4_MAX_EPS_CLASSES];
     int exclusion, pp_cut, keep_qp;
+    // particle-particle phase (shared with the tree walk)
+    const uint4 *wpart;        // particles as (x, y, z, mass bits)
+    float rcut2f, asf, figs, rc2i;
+    PairF pf;
 };
 
 template <int P> struct FT { static constexpr int NT = g4_nmono(P); };
@@ -177,73 +182,80 @@ __device__ __forceinline__ int warp_excl_i(int v, int lane)
 }
 
 // P2P: particles of leaf A (owned by this warp) from the particles of the buffered leaves.
-// Lanes form (sink, source-slot) pairs so that small leaves keep most lanes busy; the partial
-// sums of one sink are reduced over its source slots and added to the sink's outputs.
+// Leaf-leaf (P2P) interactions of sink leaf A with the buffered source leaves, 32 sinks at a
+// time (one per lane): the tree walk's particle-particle phase (staged sources, packed FP16x2
+// candidate tests, exact evaluation of each lane's candidates; in integer-grid units for
+// TreePM), the results added to the sinks' outputs.
 template <bool TREEPM>
-__device__ void p2p_flush(const FmmArgs &A, const G4Node &na, int da, const int *buf, int nbuf,
-                          int lane)
+__device__ void p2p_flush(const FmmArgs &A, PPSmem<FMM_P2PBUF> &S, const G4Node &na, const int *buf,
+                          int nbuf, int lane)
 {
-    const float scale = (float)A.scale, as = (float)A.as, rcut2 = (float)A.rcut2;
+    const double gscale = A.scale;
+    const float fscale = (float)gscale, figs = A.figs;
     const int nA = na.count;
     for (int ic = 0; ic < nA; ic += 32) {
         const int nac = min(32, nA - ic);
-        int pad = 1;
-        while (pad < nac) pad <<= 1;
-        const int J = 32 / pad;
-        const int il = lane & (pad - 1), js = lane / pad;
-        const bool iv = il < nac;
-        const int i = na.first + ic + (iv ? il : 0);
-        const uint32_t xi = A.pos[i], yi = A.pos[A.n + i], zi = A.pos[2 * A.n + i];
-        const float hi = A.h_cls[A.cls ? A.cls[i] : 0];
-        float sx = 0.f, sy = 0.f, sz = 0.f, sp = 0.f;
-        int npp = 0;
-        for (int k = 0; k < nbuf; k++) {
+        const bool valid = lane < nac;
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        const int i = na.first + ic + (valid ? lane : 0);
+        const uint4 pi_ = A.wpart[i];
+        const uint32_t xi = pi_.x, yi = pi_.y, zi = pi_.z;
+        // centre of the sinks' bounding box (integer offsets from lane 0's sink)
+        const uint32_t x0 = __shfl_sync(0xffffffffu, xi, 0), y0 = __shfl_sync(0xffffffffu, yi, 0),
+                       z0 = __shfl_sync(0xffffffffu, zi, 0);
+        const int ox = (int32_t)(xi - x0), oy = (int32_t)(yi - y0), oz = (int32_t)(zi - z0);
+        const int lox = __reduce_min_sync(0xffffffffu, ox), hix = __reduce_max_sync(0xffffffffu, ox);
+        const int loy = __reduce_min_sync(0xffffffffu, oy), hiy = __reduce_max_sync(0xffffffffu, oy);
+        const int loz = __reduce_min_sync(0xffffffffu, oz), hiz = __reduce_max_sync(0xffffffffu, oz);
+        const uint32_t gcx = x0 + (uint32_t)(int)(((long long)lox + hix) >> 1);
+        const uint32_t gcy = y0 + (uint32_t)(int)(((long long)loy + hiy) >> 1);
+        const uint32_t gcz = z0 + (uint32_t)(int)(((long long)loz + hiz) >> 1);
+        const float xr = (float)(int32_t)(xi - gcx) * fscale, yr = (float)(int32_t)(yi - gcy) * fscale,
+                    zr = (float)(int32_t)(zi - gcz) * fscale;
+        for (int k = lane; k < nbuf; k += 32) {
             const G4Node nb = load_node(A.node + buf[k]);
-            for (int j0 = 0; j0 < nb.count; j0 += J) {
-                const int jj = j0 + js;
-                if (!iv || jj >= nb.count) continue;
-                const int j = nb.first + jj;
-                if (j == i) continue;
-                const float dx = (float)(int32_t)(__ldg(A.pos + j) - xi) * scale;
-                const float dy = (float)(int32_t)(__ldg(A.pos + A.n + j) - yi) * scale;
-                const float dz = (float)(int32_t)(__ldg(A.pos + 2 * A.n + j) - zi) * scale;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (TREEPM && A.pp_cut && r2 >= rcut2) continue;
-                float g0, g1;
-                const float hj = A.h_cls[A.cls ? __ldg(A.cls + j) : 0];
-                pair_kernel<float, TREEPM>(r2, fmaxf(hi, hj), as, g0, g1);
-                const float mj = __ldg(A.mass + j);
-                sx += mj * g1 * dx;
-                sy += mj * g1 * dy;
-                sz += mj * g1 * dz;
-                sp += mj * g0;
-                npp++;
-            }
+            S.first[k] = nb.first;
+            S.count[k] = nb.count;
+            S.mask[k] = vmask;
         }
-        for (int o = pad; o < 32; o <<= 1) {
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            sz += __shfl_xor_sync(0xffffffffu, sz, o);
-            sp += __shfl_xor_sync(0xffffffffu, sp, o);
-            npp += __shfl_xor_sync(0xffffffffu, npp, o);
+        __syncwarp();
+        const float hi = A.h_cls[A.cls ? A.cls[i] : 0];
+        float ax = 0.f, ay = 0.f, az = 0.f, ap = 0.f;
+        uint32_t npp = 0;
+        pp_flush<float, TREEPM>(A, S, nbuf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, vmask,
+                                TREEPM ? hi * figs : hi, ax, ay, az, ap, npp, gscale, figs, A.pf,
+                                A.rc2i, 0, 1);
+        if (TREEPM) {
+            const float ca = figs * figs;
+            ax *= ca;
+            ay *= ca;
+            az *= ca;
+            ap *= figs;
         }
-        if (iv && js == 0) {
+        if (valid) {
             const float mG = -(float)A.G;
-            A.acc[i] += mG * sx;
-            A.acc[A.n + i] += mG * sy;
-            A.acc[2 * A.n + i] += mG * sz;
-            if (A.pot) A.pot[i] += mG * sp;
-            if (A.counts) A.counts[i] += (uint32_t)npp;
+            A.acc[i] += mG * ax;
+            A.acc[A.n + i] += mG * ay;
+            A.acc[2 * A.n + i] += mG * az;
+            if (A.pot) A.pot[i] += mG * ap;
+            if (A.counts) A.counts[i] += npp;
         }
+        __syncwarp();
     }
 }
 
+// minimum resident blocks per SM requested from the compiler for the dual walk
+#ifndef G4_FMM_MIN_BLOCKS
+#define G4_FMM_MIN_BLOCKS 1
+#endif
+
 template <int P, bool TREEPM, bool GEOM>
-__global__ void __launch_bounds__(FMM_THREADS) k_fmm_level(const FmmArgs A, int level)
+__global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(const FmmArgs A, int level)
 {
     constexpr int NT = FT<P>::NT;
     __shared__ int s_stack[FMM_WARPS][FMM_STACK];
     __shared__ int s_p2p[FMM_WARPS][FMM_P2PBUF];
+    __shared__ PPSmem<FMM_P2PBUF> s_pp[FMM_WARPS];
     if (*A.flags & G4_FLAG_CAPACITY) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int32_t *off = A.lvl, *cnt = A.lvl + G4_NLEVELS + 1;
@@ -385,14 +397,14 @@ __global__ void __launch_bounds__(FMM_THREADS) k_fmm_level(const FmmArgs A, int 
                 const int pcount = __popc(m);
                 if (nbuf + pcount > FMM_P2PBUF) {
                     __syncwarp();
-                    p2p_flush<TREEPM>(A, na, da, p2p, nbuf, lane);
+                    p2p_flush<TREEPM>(A, s_pp[wib], na, p2p, nbuf, lane);
                     nbuf = 0;
                 }
                 if (isp) p2p[nbuf + ppre] = db;
                 nbuf += pcount;
                 __syncwarp();
             }
-            if (nbuf > 0) p2p_flush<TREEPM>(A, na, da, p2p, nbuf, lane);
+            if (nbuf > 0) p2p_flush<TREEPM>(A, s_pp[wib], na, p2p, nbuf, lane);
         }
         // reduce the lane-private fields and store the node's own field
 #pragma unroll
@@ -665,7 +677,16 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     A.exclusion = P->exclusion_zone;
     A.pp_cut = P->pp_cut;
     A.keep_qp = P->keep_qp;
+    A.rcut2f = (float)A.rcut2;
+    A.asf = (float)A.as;
+    const double igs = 4294967296.0 / P->box_size;
+    A.figs = (float)igs;
+    A.rc2i = (float)(A.rcut2 * igs * igs);
+    A.pf = make_pairf(A.as * A.scale, treepm ? 2.0 * P->r_s * igs : 0.0);
     cudaStream_t st = (cudaStream_t)stream;
+    s = g4_particle_records(t, pos_sorted, mass_sorted, n, st);
+    if (s != G4_OK) return s;
+    A.wpart = t->wpart;
     k_fmm_reset<<<1, 32, 0, st>>>(A.dcount, momentum_out);
     const bool geom = P->criterion == 1;
     switch (P->order_p) {

@@ -138,3 +138,5 @@ g4_status g4_sort_pairs_u64(const uint64_t *keys_in, uint64_t *keys_out, int32_t
                             int64_t n, void *workspace, size_t ws_bytes, int key_bits,
                             cudaStream_t st);
 size_t g4_sort_workspace_bytes(int64_t n);
+g4_status g4_particle_records(struct g4_tree_s *t, const uint32_t *pos_sorted, const float *mass_sorted,
+                              int n, cudaStream_t st);

@@ -14,6 +14,7 @@
 
 #include "g4_internal.cuh"
 #include "g4_kernels.cuh"
+#include "g4_pp.cuh"
 
 namespace {
 
@@ -56,10 +57,6 @@ struct WalkArgs {
     int exclusion, pp_cut;
 };
 
-// a launch parameter in the walk's arithmetic type
-template <typename T> __device__ __forceinline__ T par(double d, float f);
-template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
-template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
 
 enum : int { ACT_NONE = 0, ACT_SKIP = 1, ACT_OPEN = 2, ACT_ACCEPT = 3, ACT_LEAF = 4 };
 
@@ -74,7 +71,6 @@ template <int P, typename T> __device__ __forceinline__ T ipow(T x)
 constexpr int WALK_THREADS = 128;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int LEAF_BUF = 256;   // pending leaves: a whole group's leaves usually fit (one flush)
-constexpr int STAGE = 128;      // sources staged per pass of the particle-particle phase
 constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in global memory)
 // minimum resident blocks per SM requested from the compiler for the FP32 walks of order <= 3
 // (caps their registers; other instances keep the compiler's choice)
@@ -82,16 +78,8 @@ constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in glob
 #define G4_WALK_MIN_BLOCKS 5
 #endif
 
-// per-warp shared state: the pending leaf list of the group and the staged sources
-struct WalkSmem {
-    int first[LEAF_BUF], count[LEAF_BUF], pref[LEAF_BUF];
-    unsigned mask[LEAF_BUF];
-    uint4 ipos[STAGE];          // source integer position, softening length h (bits)
-    float2 mj[STAGE];           // source mass, particle index (bits)
-    unsigned smask[STAGE];      // lane mask of the source's leaf
-    __align__(16) __half hx[STAGE];   // source position / r_cut relative to the group centre
-    __align__(16) __half hy[STAGE];
-    __align__(16) __half hz[STAGE];
+// per-warp shared state: the pending leaf list of the group, the staged sources, the sinks
+struct WalkSmem : PPSmem<LEAF_BUF> {
     float4 sink[32];            // sinks relative to the group centre, opening threshold
 };
 
@@ -142,252 +130,6 @@ __device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &n
         else open = !(par<T>(A.G, A.Gf) * M * ipow<P>(side) < crit * ipow<P + 2>(sqrt(r2)));
     }
     return open ? ACT_OPEN : ACT_ACCEPT;
-}
-
-// Slot of staged source u in the candidate masks.  The FP16x2 test handles sources 2j, 2j+1
-// of a 32-source block together and sets bits j and 16 + j of the block's mask word, so the
-// per-source arrays used by the evaluation are stored at that bit position.
-__device__ __forceinline__ int cand_bit(int u)
-{
-    return (u & ~31) | ((u & 1) << 4) | ((u & 31) >> 1);
-}
-
-// Particle-particle phase for the pending leaves of a group.
-// Sources are staged 128 at a time.  TreePM: every lane first tests all staged sources against
-// its own sink in packed FP16x2 (two sources per instruction; positions relative to the group
-// centre in units of r_cut, 5% margin on r^2, so no pair inside r_cut is missed) and keeps a
-// candidate bit per source; then each lane evaluates only its own candidates with exact
-// integer separations, the exact cutoff and the full kernel.  Leaf masks (lanes that used an
-// ancestor's multipole must not see the leaf) are applied per source when a staged leaf does
-// not reach the whole group.  INTU (FP32 TreePM): the pair terms are summed in integer-grid
-// length units with the fast kernel; the caller rescales the sums.
-template <typename T, bool TREEPM>
-__device__ __forceinline__ void pp_flush(const WalkArgs &A, WalkSmem &S, int nleaf, int lane, int i,
-                                         uint32_t xi, uint32_t yi, uint32_t zi, uint32_t gcx,
-                                         uint32_t gcy, uint32_t gcz, float xr, float yr, float zr,
-                                         unsigned vmask, T hi, T &ax, T &ay, T &az, T &ap,
-                                         uint32_t &npp, double gscale, float figs, const PairF &pf,
-                                         float rc2i, int kp, int Kp)
-{
-    constexpr bool INTU = TREEPM && sizeof(T) == 4;
-    const float fscale = (float)gscale;
-    const T scale = (T)gscale, as = par<T>(A.as, A.asf), rcut2 = par<T>(A.rcut2, A.rcut2f);
-    const float hconv = INTU ? figs : 1.f;   // staged softening length unit
-    // drop leaves nobody reaches; prefix sums of the particle counts
-    int nk = 0, total = 0;
-    for (int b = 0; b < nleaf; b += 32) {
-        const int e = b + lane;
-        const bool ok = e < nleaf;
-        int f = 0, c = 0;
-        unsigned m = 0;
-        if (ok) {
-            f = S.first[e];
-            c = S.count[e];
-            m = S.mask[e];
-        }
-        const bool keep = ok && m != 0u;
-        const unsigned km = __ballot_sync(0xffffffffu, keep);
-        const int cc = keep ? c : 0;
-        int pre = cc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, pre, o);
-            if (lane >= o) pre += y;
-        }
-        __syncwarp();
-        if (keep) {
-            const int pos = nk + __popc(km & ((1u << lane) - 1u));
-            S.first[pos] = f;
-            S.count[pos] = c;
-            S.mask[pos] = m;
-            S.pref[pos] = total + pre - cc;
-        }
-        __syncwarp();
-        nk += __popc(km);
-        total += __shfl_sync(0xffffffffu, pre, 31);
-    }
-    const float inv_rc = TREEPM ? rsqrtf(A.rcut2f) : 0.f;
-    const __half2 sx2 = __float2half2_rn(xr * inv_rc), sy2 = __float2half2_rn(yr * inv_rc),
-                  sz2 = __float2half2_rn(zr * inv_rc);
-    const __half2 lim = __float2half2_rn(1.05f);
-    // Batch bb takes sources bb, bb + nbat, bb + 2 nbat, ...: every batch samples the whole
-    // neighbourhood, so each lane's candidates spread evenly over the batches and the per-lane
-    // evaluation loops below stay balanced across the warp.
-    // part kp of Kp takes list positions kp, kp + Kp, kp + 2 Kp, ... (a split group's parts
-    // share the list; Kp = 1: the whole list)
-    const int tv = total > kp ? (total - kp + Kp - 1) / Kp : 0;
-    const int nbat = (tv + STAGE - 1) / STAGE;
-    // slot q of this lane stages virtual position bb + (32 q + lane) nbat in batch bb, list
-    // position t = kp + Kp * (that); its leaf lq: a fixed-step binary search for bb = 0, then
-    // it only moves forward
-    int lq[STAGE / 32], tq[STAGE / 32];
-#pragma unroll
-    for (int q = 0; q < STAGE / 32; q++) {
-        lq[q] = 0;
-        tq[q] = kp + Kp * ((q * 32 + lane) * nbat);
-    }
-#pragma unroll
-    for (int step = LEAF_BUF / 2; step >= 1; step >>= 1)
-#pragma unroll
-        for (int q = 0; q < STAGE / 32; q++) {
-            const int c = lq[q] + step;
-            if (c < nk && S.pref[c] <= tq[q]) lq[q] = c;
-        }
-    for (int bb = 0; bb < nbat; bb++) {
-        const int nb = (tv - bb + nbat - 1) / nbat;
-        bool partial = false;
-        if (bb > 0) {
-#pragma unroll
-            for (int q = 0; q < STAGE / 32; q++) {
-                tq[q] += Kp;
-                while (lq[q] + 1 < nk && S.pref[lq[q] + 1] <= tq[q]) lq[q]++;
-            }
-        }
-        uint4 pq[STAGE / 32];
-        int jq[STAGE / 32];
-#pragma unroll
-        for (int q = 0; q < STAGE / 32; q++) {
-            const int u = q * 32 + lane;
-            jq[q] = S.first[lq[q]] + (tq[q] - S.pref[lq[q]]);
-            if (u < nb) pq[q] = __ldg(A.wpart + jq[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < STAGE / 32; q++) {
-            const int u = q * 32 + lane, v = cand_bit(u);
-            if (u < nb) {
-                const int j = jq[q];
-                const uint32_t px = pq[q].x, py = pq[q].y, pz = pq[q].z;
-                const float hj = A.h_cls[A.cls ? __ldg(A.cls + j) : 0] * hconv;
-                const unsigned mk = S.mask[lq[q]];
-                S.ipos[v] = make_uint4(px, py, pz, __float_as_uint(hj));
-                S.mj[v] = make_float2(__uint_as_float(pq[q].w), __int_as_float(j));
-                S.smask[v] = mk;
-                S.hx[u] = __float2half_rn((float)(int32_t)(px - gcx) * fscale * inv_rc);
-                S.hy[u] = __float2half_rn((float)(int32_t)(py - gcy) * fscale * inv_rc);
-                S.hz[u] = __float2half_rn((float)(int32_t)(pz - gcz) * fscale * inv_rc);
-                partial |= (mk != vmask);
-            } else {
-                S.hx[u] = S.hy[u] = S.hz[u] = __float2half_rn(100.f);
-                S.smask[v] = 0xffffffffu;
-            }
-        }
-        partial = __any_sync(0xffffffffu, partial);
-        __syncwarp();
-        const int nw = (nb + 31) >> 5;
-        uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
-        if (TREEPM) {
-            const uint4 *X = reinterpret_cast<const uint4 *>(S.hx);
-            const uint4 *Y = reinterpret_cast<const uint4 *>(S.hy);
-            const uint4 *Z = reinterpret_cast<const uint4 *>(S.hz);
-            for (int w = 0; w < nw; w++) {
-                uint32_t m = 0u;
-#pragma unroll
-                for (int qd = 0; qd < 4; qd++) {
-                    const uint4 x4 = X[4 * w + qd], y4 = Y[4 * w + qd], z4 = Z[4 * w + qd];
-                    const uint32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
-                    const uint32_t ys[4] = {y4.x, y4.y, y4.z, y4.w};
-                    const uint32_t zs[4] = {z4.x, z4.y, z4.z, z4.w};
-#pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        const __half2 dx = __hsub2(*reinterpret_cast<const __half2 *>(&xs[c]), sx2);
-                        const __half2 dy = __hsub2(*reinterpret_cast<const __half2 *>(&ys[c]), sy2);
-                        const __half2 dz = __hsub2(*reinterpret_cast<const __half2 *>(&zs[c]), sz2);
-                        const __half2 d2 = __hfma2(dz, dz, __hfma2(dy, dy, __hmul2(dx, dx)));
-                        m |= (__hle2_mask(d2, lim) & 0x00010001u) << (4 * qd + c);
-                    }
-                }
-                w0 = w == 0 ? m : w0;
-                w1 = w == 1 ? m : w1;
-                w2 = w == 2 ? m : w2;
-                w3 = w == 3 ? m : w3;
-            }
-        } else {
-            // every staged source is a candidate; bit positions of sources u < nb
-#pragma unroll
-            for (int w = 0; w < 4; w++) {
-                const int r = min(max(nb - 32 * w, 0), 32);   // valid sources in block w
-                const int ev = (r + 1) >> 1, od = r >> 1;      // even / odd ones
-                const uint32_t m = (ev >= 16 ? 0xffffu : ((1u << ev) - 1u)) |
-                                   ((od >= 16 ? 0xffffu : ((1u << od) - 1u)) << 16);
-                if (w == 0) w0 = m;
-                else if (w == 1) w1 = m;
-                else if (w == 2) w2 = m;
-                else w3 = m;
-            }
-        }
-        if (partial) {
-            for (int v = 0; v < 32 * nw; v++)
-                if (!((S.smask[v] >> lane) & 1u)) {
-                    const uint32_t clr = ~(1u << (v & 31));
-                    if (v < 32) w0 &= clr;
-                    else if (v < 64) w1 &= clr;
-                    else if (v < 96) w2 &= clr;
-                    else w3 &= clr;
-                }
-        }
-        // the lane's nonempty candidate words packed to the front (cw first), with their slot
-        // offsets in the bytes of `bases`; popping a candidate is then a bit scan and a clear
-        uint32_t cw = 0u, n1 = 0u, n2 = 0u, n3 = 0u, bases = 0u;
-#pragma unroll
-        for (int w = 3; w >= 0; w--) {
-            const uint32_t x = w == 0 ? w0 : (w == 1 ? w1 : (w == 2 ? w2 : w3));
-            const bool e = x != 0u;
-            n3 = e ? n2 : n3;
-            n2 = e ? n1 : n2;
-            n1 = e ? cw : n1;
-            cw = e ? x : cw;
-            bases = e ? (bases << 8) | (uint32_t)(32 * w) : bases;
-        }
-        // exact evaluation of the lane's own candidates
-        while (cw) {
-            const int v = (int)(bases & 0xffu) + __clz(__brev(cw));
-            cw &= cw - 1u;
-            const bool e = cw == 0u;
-            cw = e ? n1 : cw;
-            n1 = e ? n2 : n1;
-            n2 = e ? n3 : n2;
-            n3 = e ? 0u : n3;
-            bases = e ? bases >> 8 : bases;
-            const uint4 ip = S.ipos[v];
-            const float2 mj = S.mj[v];
-            if (INTU) {
-                // branch-free: the sink itself and pairs beyond the cutoff get mass 0 at a
-                // harmless separation, so the lanes of the warp stay in step
-                const float dx = (float)(int32_t)(ip.x - xi);
-                const float dy = (float)(int32_t)(ip.y - yi);
-                const float dz = (float)(int32_t)(ip.z - zi);
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const bool use = __float_as_int(mj.y) != i && !(A.pp_cut && r2 >= rc2i);
-                float g0, g1;
-                pair_treepm_fast(use ? r2 : rc2i, fmaxf((float)hi, __uint_as_float(ip.w)), pf, g0, g1);
-                const float m_ = use ? mj.x : 0.f;
-                const float mg1 = m_ * g1;
-                ax = fmaf(mg1, dx, (float)ax);
-                ay = fmaf(mg1, dy, (float)ay);
-                az = fmaf(mg1, dz, (float)az);
-                ap = fmaf(m_, g0, (float)ap);
-                npp += use;
-                continue;
-            } else {
-                if (__float_as_int(mj.y) == i) continue;
-                const T dx = (T)(int32_t)(ip.x - xi) * scale;
-                const T dy = (T)(int32_t)(ip.y - yi) * scale;
-                const T dz = (T)(int32_t)(ip.z - zi) * scale;
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                if (TREEPM && A.pp_cut && r2 >= rcut2) continue;
-                T g0, g1;
-                pair_kernel<T, TREEPM>(r2, fmax(hi, (T)__uint_as_float(ip.w)), as, g0, g1);
-                const T m_ = (T)mj.x;
-                const T mg1 = m_ * g1;
-                ax += mg1 * dx;
-                ay += mg1 * dy;
-                az += mg1 * dz;
-                ap += m_ * g0;
-            }
-            npp++;
-        }
-        __syncwarp();
-    }
 }
 
 // The group walk.  Nodes are scanned in depth-first order in windows of 32 (one node per lane,
@@ -857,6 +599,22 @@ g4_status g4_check_params(const g4_params *P, const char *who)
     return G4_OK;
 }
 
+// 16-byte particle records (x, y, z, mass bits) of the sorted particles in the handle's
+// buffer, allocated on first use (outside graph capture), rewritten on every call
+g4_status g4_particle_records(g4_tree t, const uint32_t *pos_sorted, const float *mass_sorted,
+                              int n, cudaStream_t st)
+{
+    if (!t->wpart) {
+        if (cudaMalloc(&t->wpart, sizeof(uint4) * (size_t)(t->n_max > 0 ? t->n_max : 1)) != cudaSuccess) {
+            cudaGetLastError();
+            t->wpart = nullptr;
+            return g4_fail(G4_ERR_OOM, "particle records (%lld)", (long long)t->n_max);
+        }
+    }
+    if (n > 0) k_walk_parts<<<g4_blocks_for(n, 256), 256, 0, st>>>(pos_sorted, mass_sorted, n, t->wpart);
+    return g4_launch_check("particle records", n > 0 ? 1 : 0);
+}
+
 extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
                                      const float *mass_sorted, const uint8_t *cls_sorted,
                                      const float *aold_sorted, const int32_t *active,
@@ -947,16 +705,11 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
         }
     }
     A.queue = (int2 *)t->walk_queue;
-    if (!t->wnode || !t->wpart) {
-        if (!t->wnode && cudaMalloc(&t->wnode, sizeof(G4Node) * (size_t)t->cap) != cudaSuccess) {
+    if (!t->wnode) {
+        if (cudaMalloc(&t->wnode, sizeof(G4Node) * (size_t)t->cap) != cudaSuccess) {
             cudaGetLastError();
             t->wnode = nullptr;
             return g4_fail(G4_ERR_OOM, "g4_gravity_tree: level-ordered node copy");
-        }
-        if (!t->wpart && cudaMalloc(&t->wpart, sizeof(uint4) * (size_t)t->n_max) != cudaSuccess) {
-            cudaGetLastError();
-            t->wpart = nullptr;
-            return g4_fail(G4_ERR_OOM, "g4_gravity_tree: particle records");
         }
         t->wnode_stamp = -1;
     }
@@ -967,8 +720,8 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
         t->wnode_stamp = t->moments_stamp;
         extra++;
     }
-    k_walk_parts<<<g4_blocks_for(n, 256), 256, 0, st>>>(pos_sorted, mass_sorted, n, t->wpart);
-    extra++;
+    s = g4_particle_records(t, pos_sorted, mass_sorted, n, st);
+    if (s != G4_OK) return s;
     A.wnode = t->wnode;
     A.wpart = t->wpart;
     k_zero_int<<<1, 1, 0, st>>>(A.work);
