@@ -41,6 +41,11 @@ SEED = 1003
 FLOPS_PP = 35
 FLOPS_PN = {1: 40, 2: 110, 3: 170, 4: 300, 5: 480}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA x max clock
+# DRAM bytes (read + write) of one k_walk launch of the headline workload, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, single-pass capture of the timed walk; the
+# command is in profiles/ncu_walk_dram_256cubed.md).  Reported as roofline.traffic for the
+# default workload only; re-measured whenever the walk kernel changes.
+WALK_DRAM_BYTES_256 = 603.94e6 + 447.35e6
 
 
 def hbm_peak_gbs():
@@ -408,7 +413,9 @@ def run_gpu(args, rank, world):
                 "roofline": {"bound": "alu", "kernel": "k_walk (tree walk, p=3, TreePM)",
                              "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
-                             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                             "frac": achieved / FP32_PEAK_TFLOPS,
+                             "traffic": WALK_DRAM_BYTES_256 if n_side == N_SIDE else None,
+                             "traffic_per_sink_bytes": (WALK_DRAM_BYTES_256 / n) if n_side == N_SIDE else None,
                              "walk_ms": walk_ms,
                              "interactions_per_step": {"pp": int(counts[0]), "pn": int(counts[1])}},
                 "tree": {"nodes": nn, "max_level": ml},
