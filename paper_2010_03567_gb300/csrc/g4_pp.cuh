@@ -44,7 +44,10 @@ __device__ __forceinline__ int cand_bit(int u)
 // integer separations, the exact cutoff and the full kernel.  Leaf masks (lanes that used an
 // ancestor's multipole must not see the leaf) are applied per source when a staged leaf does
 // not reach the whole group.  INTU (FP32 TreePM): the pair terms are summed in integer-grid
-// length units with the fast kernel; the caller rescales the sums.
+// length units with the fast kernel; the caller rescales the sums.  Part kp of Kp (a group
+// split by the cost-model schedule) takes list positions kp, kp + Kp, ...; Kp = 1: all.
+// A lane's sums follow its staging order (deterministic for a given leaf list).
+// Args provides: wpart (16-byte particle records), cls, h_cls, pp_cut, rcut2/rcut2f, as/asf.
 template <typename T, bool TREEPM, int LB, class Args>
 __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf, int lane, int i,
                                          uint32_t xi, uint32_t yi, uint32_t zi, uint32_t gcx,

@@ -2,14 +2,17 @@
 // (Eq. eqnrelcriterion) and the TreePM short-range kernel (Sec. 2.3), plus a GPU direct sum.
 //
 // Work decomposition: a warp owns a group of 32 PH-consecutive sinks (one per lane) and walks
-// the depth-first node array once for the whole group.  Each lane keeps its own walk exact:
-// `resume` is the next node index the lane still has to look at; the warp visits node
-// min(resume) over its lanes, so every lane sees precisely the nodes a single-particle walk
-// would see, while node records are fetched once per warp (broadcast loads).  Per node and
-// lane the decision is one of: skip (TreePM cutoff), open (descend: resume = k + 1), use the
-// multipole (particle-node term), or -- for a leaf -- particle-particle terms with the
-// leaf's particles.  Groups are handed out by a device work counter, so warps that finish
-// early pull more groups (persistent kernel).
+// the tree breadth-first for the whole group.  The frontier holds (node, mask of the lanes
+// still walking there) entries in a per-warp ring; each step takes 32 entries, one per lane
+// (coalesced 64-byte records of the level-ordered node copy).  Group-level tests are
+// conservative (a cube beyond r_cut of the group's bounding box is skipped for all lanes); a
+// node some sink could use as a multipole gets the exact per-lane decision of the
+// single-particle walk (skip, open, or accept: particle-node term, the lane leaves the
+// subtree).  A lane's cutoff skip is hereditary and treated as "open" (the pair cutoff
+// removes the leaves below), so every lane's interaction set is exactly that of a
+// single-particle walk.  Leaves collect in a pending list; the particle-particle phase
+// (g4_pp.cuh) evaluates them.  Groups -- or, with a cost-model schedule, parts of groups --
+// come from a device work counter, so warps that finish early pull more (persistent kernel).
 #include <cuda_fp16.h>
 
 #include "g4_internal.cuh"
@@ -82,17 +85,6 @@ constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in glob
 struct WalkSmem : PPSmem<LEAF_BUF> {
     float4 sink[32];            // sinks relative to the group centre, opening threshold
 };
-
-__device__ __forceinline__ int warp_excl_scan(int v, int lane)
-{
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    return x - v;
-}
 
 // Per-lane decision for an internal node (the single-particle walk's rule): skip beyond the
 // TreePM cutoff, open when inside the node / its exclusion zone / the softening range or
