@@ -162,15 +162,21 @@ __global__ void k_keys(const uint32_t *__restrict__ pos, int64_t n, uint64_t *__
 }
 
 // -------------------------------------------------------------------------------------------
-// a3: stable LSD radix sort, 8-bit digits, tiles of 4096 keys.
+// a3: stable LSD radix sort, 8-bit digits, tiles of SORT_TILE keys (2048 by default).
 //   hist:    per-tile digit counts, digit-major  cnt[d * ntiles + t]
 //   rowscan: per-digit exclusive scan over tiles, digit totals
 //   scatter: warp-ordered stable ranks (match_any), global position = digit base + tile
 //            offset + warp offset + rank
 // -------------------------------------------------------------------------------------------
+#ifndef G4_SORT_ITEMS
+#define G4_SORT_ITEMS 8         // keys per thread in a tile
+#endif
+#ifndef G4_SORT_MIN_BLOCKS
+#define G4_SORT_MIN_BLOCKS 4    // resident scatter blocks per SM requested from the compiler
+#endif
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SORT_ITEMS = 16;
+constexpr int SORT_ITEMS = G4_SORT_ITEMS;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int SCAN_THREADS = 1024;
 
@@ -245,7 +251,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_sort_rowscan(uint32_t *__restr
 // output run (coalesced stores).  Dynamic shared memory: keys, values of the tile.
 constexpr size_t SCATTER_SMEM = (size_t)SORT_TILE * (sizeof(uint64_t) + sizeof(int32_t));
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
+__global__ void __launch_bounds__(SORT_THREADS, G4_SORT_MIN_BLOCKS) k_sort_scatter(
     const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     int32_t *__restrict__ vout, int n, int shift, const uint32_t *__restrict__ cnt,
     const uint32_t *__restrict__ totals, int ntiles)
