@@ -31,7 +31,7 @@ using namespace g4k;
 constexpr int FMM_THREADS = 128;
 constexpr int FMM_WARPS = FMM_THREADS / 32;
 constexpr int FMM_STACK = 1024;     // per-warp stack of opened sources for leaf sinks
-constexpr int FMM_P2PBUF = 64;      // per-warp buffer of P2P source leaves
+constexpr int FMM_P2PBUF = 128;     // per-warp buffer of P2P source leaves (one deferred chunk)
 
 enum : int { D_DROP = 0, D_ACCEPT = 1, D_P2P = 2, D_OPEN = 3, D_SELF = 4 };
 
@@ -62,6 +62,14 @@ struct FmmArgs {
     const uint4 *wpart;        // particles as (x, y, z, mass bits)
     float rcut2f, asf, figs, rc2i;
     PairF pf;
+    // deferred leaf-leaf work: chunks of source leaves per sink leaf, chained in the order the
+    // sink's warp found them; evaluated after the dual walk by k_fmm_p2p
+    int32_t *p2p_src;          // source leaf (depth-first index) lists
+    int4 *p2p_chunk;           // (offset, count, next chunk, -)
+    int32_t *p2p_head;         // per node: first chunk of a sink leaf, -1 if none
+    int32_t *p2p_sinks;        // sink leaves with P2P work
+    int32_t *p2p_fill;         // [0] list entries, [1] chunks, [2] sink leaves
+    int64_t p2p_cap, chunk_cap;
 };
 
 template <int P> struct FT { static constexpr int NT = g4_nmono(P); };
@@ -244,6 +252,58 @@ __device__ void p2p_flush(const FmmArgs &A, PPSmem<FMM_P2PBUF> &S, const G4Node 
     }
 }
 
+// Append the buffered source leaves of sink leaf da to the deferred P2P lists as one chunk,
+// chained after the sink's previous chunk (tail); the first chunk registers the sink.
+// Returns false when the lists are full: the caller then evaluates the chunk at once (same
+// interactions; which chunks overflow depends on the warps' timing, so only the rounding of
+// such sinks can differ from run to run).
+__device__ bool defer_p2p(const FmmArgs &A, int da, const int *buf, int nbuf, int lane, int &tail)
+{
+    int off = 0, cid = 0;
+    if (lane == 0) {
+        off = atomicAdd(A.p2p_fill, nbuf);
+        cid = atomicAdd(A.p2p_fill + 1, 1);
+    }
+    off = __shfl_sync(0xffffffffu, off, 0);
+    cid = __shfl_sync(0xffffffffu, cid, 0);
+    if ((int64_t)off + nbuf > A.p2p_cap || (int64_t)cid >= A.chunk_cap) return false;
+    for (int k = lane; k < nbuf; k += 32) A.p2p_src[off + k] = buf[k];
+    if (lane == 0) {
+        A.p2p_chunk[cid] = make_int4(off, nbuf, -1, 0);
+        if (tail < 0) {
+            A.p2p_head[da] = cid;
+            A.p2p_sinks[atomicAdd(A.p2p_fill + 2, 1)] = da;
+        } else {
+            A.p2p_chunk[tail].z = cid;
+        }
+    }
+    tail = cid;
+    __syncwarp();
+    return true;
+}
+
+// Deferred leaf-leaf interactions: one warp per sink leaf, its chunks in the order they were
+// found; the results are added to the sink particles' outputs (zeroed by the dual walk)
+template <bool TREEPM>
+__global__ void __launch_bounds__(FMM_THREADS, 5) k_fmm_p2p(const FmmArgs A)
+{
+    __shared__ PPSmem<FMM_P2PBUF> s_pp[FMM_WARPS];
+    if (*A.flags & G4_FLAG_CAPACITY) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nsink = A.p2p_fill[2];
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int w = gw; w < nsink; w += nw) {
+        const int da = A.p2p_sinks[w];
+        const G4Node na = load_node(A.node + da);
+        for (int c = A.p2p_head[da]; c >= 0;) {
+            const int4 ch = A.p2p_chunk[c];
+            p2p_flush<TREEPM>(A, s_pp[wib], na, A.p2p_src + ch.x, ch.y, lane);
+            c = ch.z;
+        }
+    }
+}
+
 // minimum resident blocks per SM requested from the compiler for the dual walk
 #ifndef G4_FMM_MIN_BLOCKS
 #define G4_FMM_MIN_BLOCKS 1
@@ -255,7 +315,7 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
     constexpr int NT = FT<P>::NT;
     __shared__ int s_stack[FMM_WARPS][FMM_STACK];
     __shared__ int s_p2p[FMM_WARPS][FMM_P2PBUF];
-    __shared__ PPSmem<FMM_P2PBUF> s_pp[FMM_WARPS];
+    __shared__ PPSmem<FMM_P2PBUF> s_pp[FMM_WARPS];   // overflow of the deferred lists only
     if (*A.flags & G4_FLAG_CAPACITY) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int32_t *off = A.lvl, *cnt = A.lvl + G4_NLEVELS + 1;
@@ -348,8 +408,9 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                 if (A.pot) A.pot[i] = 0.f;
                 if (A.counts) A.counts[i] = 0u;
             }
+            if (lane == 0) A.p2p_head[da] = -1;
             __syncwarp();
-            int sp = 0, cursor = 0, nbuf = 0;
+            int sp = 0, cursor = 0, nbuf = 0, tail = -1;
             for (;;) {
                 int db = -1;
                 int navail;
@@ -397,14 +458,16 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                 const int pcount = __popc(m);
                 if (nbuf + pcount > FMM_P2PBUF) {
                     __syncwarp();
-                    p2p_flush<TREEPM>(A, s_pp[wib], na, p2p, nbuf, lane);
+                    if (!defer_p2p(A, da, p2p, nbuf, lane, tail))
+                        p2p_flush<TREEPM>(A, s_pp[wib], na, p2p, nbuf, lane);
                     nbuf = 0;
                 }
                 if (isp) p2p[nbuf + ppre] = db;
                 nbuf += pcount;
                 __syncwarp();
             }
-            if (nbuf > 0) p2p_flush<TREEPM>(A, s_pp[wib], na, p2p, nbuf, lane);
+            if (nbuf > 0 && !defer_p2p(A, da, p2p, nbuf, lane, tail))
+                p2p_flush<TREEPM>(A, s_pp[wib], na, p2p, nbuf, lane);
         }
         // reduce the lane-private fields and store the node's own field
 #pragma unroll
@@ -548,6 +611,7 @@ void run_fmm(const FmmArgs &A, cudaStream_t st)
         }
         k_fmm_level<P, TREEPM, GEOM><<<nb, FMM_THREADS, 0, st>>>(A, l);
     }
+    k_fmm_p2p<TREEPM><<<g4_num_sms() * 5, FMM_THREADS, 0, st>>>(A);
     for (int l = 0; l <= G4_MAXLEVEL; l++) k_fmm_down<P><<<nb, 128, 0, st>>>(A, l);
 }
 
@@ -566,11 +630,14 @@ void dispatch_fmm(const FmmArgs &A, bool treepm, bool geom, cudaStream_t st)
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct FmmLayout {
-    size_t T_own, T_tot, Doff, Dlen, m2l_own, m2l_cum, dcount, D0, D1, total;
-    int64_t dcap;
+    size_t T_own, T_tot, Doff, Dlen, m2l_own, m2l_cum, dcount, p2p_src, p2p_chunk, p2p_head,
+        p2p_sinks, p2p_fill, D0, D1, total;
+    int64_t dcap, p2p_cap, chunk_cap;
 };
 
-FmmLayout fmm_layout(int64_t nodes, int nt, size_t ws_bytes)
+// deferred P2P lists: 16 source-leaf entries and 1.25 chunks per particle of the handle (plus
+// a floor for small sets); overflowing chunks are evaluated by the dual walk itself
+FmmLayout fmm_layout(int64_t nodes, int64_t n_max, int nt, size_t ws_bytes)
 {
     FmmLayout L;
     size_t o = 0;
@@ -582,6 +649,14 @@ FmmLayout fmm_layout(int64_t nodes, int nt, size_t ws_bytes)
     L.m2l_own = take(4 * nodes);
     L.m2l_cum = take(4 * nodes);
     L.dcount = take(16);
+    const int64_t nm = n_max > 0 ? n_max : 1;
+    L.p2p_cap = 16 * nm + ((int64_t)1 << 20);
+    L.chunk_cap = nm + nm / 4 + ((int64_t)1 << 14);
+    L.p2p_src = take(4 * (size_t)L.p2p_cap);
+    L.p2p_chunk = take(16 * (size_t)L.chunk_cap);
+    L.p2p_head = take(4 * nodes);
+    L.p2p_sinks = take(4 * nodes);
+    L.p2p_fill = take(16);
     size_t fixed = o;
     int64_t dcap = 0;
     if (ws_bytes == 0) dcap = (int64_t)1 << 20 > 48 * nodes ? (int64_t)1 << 20 : 48 * nodes;
@@ -605,7 +680,7 @@ extern "C" g4_status g4_fmm_workspace(g4_tree t, const g4_params *P, size_t *byt
     if (s != G4_OK) return s;
     if (!t || !bytes) return g4_fail(G4_ERR_INVALID_ARG, "g4_fmm_workspace: NULL argument");
     // sized for the handle's node capacity, so no host synchronisation is needed
-    *bytes = fmm_layout(t->cap, g4_nmono(P->order_p), 0).total;
+    *bytes = fmm_layout(t->cap, t->n_max, g4_nmono(P->order_p), 0).total;
     return G4_OK;
 }
 
@@ -633,7 +708,7 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     if (n == 0) return G4_OK;
     const int nt = g4_nmono(P->order_p);
     // node count bound: the handle's capacity (no host synchronisation here)
-    FmmLayout L = fmm_layout(t->cap, nt, workspace_bytes);
+    FmmLayout L = fmm_layout(t->cap, t->n_max, nt, workspace_bytes);
     if (L.dcap < 1024 || L.total > workspace_bytes)
         return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: workspace too small (%zu bytes)",
                        workspace_bytes);
@@ -658,6 +733,13 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     A.D0 = (int32_t *)(w + L.D0);
     A.D1 = (int32_t *)(w + L.D1);
     A.dcap = L.dcap;
+    A.p2p_src = (int32_t *)(w + L.p2p_src);
+    A.p2p_chunk = (int4 *)(w + L.p2p_chunk);
+    A.p2p_head = (int32_t *)(w + L.p2p_head);
+    A.p2p_sinks = (int32_t *)(w + L.p2p_sinks);
+    A.p2p_fill = (int32_t *)(w + L.p2p_fill);
+    A.p2p_cap = L.p2p_cap;
+    A.chunk_cap = L.chunk_cap;
     A.flags = t->d_flags;
     A.acc = acc;
     A.pot = pot;
@@ -688,6 +770,8 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     if (s != G4_OK) return s;
     A.wpart = t->wpart;
     k_fmm_reset<<<1, 32, 0, st>>>(A.dcount, momentum_out);
+    if (cudaMemsetAsync(A.p2p_fill, 0, 16, st) != cudaSuccess)
+        return g4_cuda_check(cudaGetLastError(), "g4_gravity_fmm: clear P2P counters");
     const bool geom = P->criterion == 1;
     switch (P->order_p) {
     case 2: dispatch_fmm<2>(A, treepm, geom, st); break;
@@ -696,5 +780,5 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     default: dispatch_fmm<5>(A, treepm, geom, st); break;
     }
     if (momentum_out) k_momentum<<<g4_num_sms() * 4, 256, 0, st>>>(mass_sorted, acc, n, momentum_out);
-    return g4_launch_check("fmm", 1 + 2 * (G4_MAXLEVEL + 1) + (momentum_out ? 1 : 0));
+    return g4_launch_check("fmm", 2 + 2 * (G4_MAXLEVEL + 1) + (momentum_out ? 1 : 0));
 }
