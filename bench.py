@@ -768,6 +768,34 @@ def extra_c5(leaf_max):
     return res
 
 
+def run_fmm_only(args):
+    """FMM calls on the bench workload (for launch lists and captures of the FMM kernels)."""
+    import torch
+    from paper_2010_03567_gb300 import g4, synth
+    n_side = args.n_side
+    L = L_BOX * n_side / N_SIDE
+    ps = synth.zeldovich(n_side, L, RMS, SEED)
+    wp = workload_params(n_side, L, args.leaf_max)
+    pos = torch.from_numpy(ps.pos).cuda()
+    q, _ = g4.g4_int_coords(pos, True, L)
+    del pos
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    tg = g4.TreeGravity(ps.n, g4.params(**{**wp, "criterion": 1, "theta": 0.5}))
+    a0, _ = tg.forces(q, mass)
+    aold = torch.linalg.vector_norm(a0, dim=0).contiguous()
+    del tg, a0
+    P4 = g4.params(**{**wp, "order_p": 4})
+    tg = g4.TreeGravity(ps.n, P4)
+    tg.prepare(q, mass, None, aold, P4)
+    ws = torch.empty(tg.tree.fmm_workspace(P4) + 256, dtype=torch.uint8, device="cuda")
+    call = lambda: tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, P4, workspace=ws)
+    ms = _time(call, max(1, args.steps), warm=1)
+    tg.tree.status()
+    print(json.dumps({"fmm_only": True, "n_particles": ps.n, "order_p": 4, "calls": args.steps,
+                      "ms_per_call": ms}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -780,6 +808,9 @@ def main():
                     help="skip the FMM, batched-systems, time-bin and cost-model measurements")
     ap.add_argument("--leaf-max", type=int, default=None,
                     help="leaf threshold of the tree (default: the tuned value)")
+    ap.add_argument("--fmm-only", action="store_true",
+                    help="profiling aid: bootstrap walk, then --steps FMM calls (p = 4) on the workload; "
+                         "prints their mean time, not the bench line")
     ap.add_argument("--n-side", type=int, default=N_SIDE,
                     help="particles per side (default 256: the headline workload; smaller sizes "
                          "keep the spacing, split and softening, for profiling)")
@@ -793,6 +824,8 @@ def main():
         tdist.init_process_group("nccl")
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.fmm_only:
+        return run_fmm_only(args)
     return run_gpu(args, rank, world)
 
 
