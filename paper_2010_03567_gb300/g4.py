@@ -397,6 +397,63 @@ class TreeGravity:
         return self.walk(p, use_aold=aold is not None, stream=stream)
 
 
+class HostPipeline:
+    """Forces for a stream of host input sets (pinned host tensors), double-buffered: the copy
+    of the next step's inputs to the device and the copy of the previous step's results back to
+    the host run on two copy streams while the current step computes.  Every step still moves its
+    whole input (positions, masses, |a_old|) and output (accelerations, potentials) across the
+    link; the results are those of TreeGravity.forces."""
+
+    def __init__(self, n: int, p: G4Params, node_capacity: int = 0):
+        dev = torch.device("cuda")
+        self.n, self.p = n, p
+        self.tg = TreeGravity(n, p, node_capacity)
+        self.h2d = torch.cuda.Stream()
+        self.d2h = torch.cuda.Stream()
+        self.inp = [(torch.empty((3, n), dtype=torch.int32, device=dev),
+                     torch.empty(n, dtype=torch.float32, device=dev),
+                     torch.empty(n, dtype=torch.float32, device=dev)) for _ in range(2)]
+        self.out = [(torch.empty((3, n), dtype=torch.float32, device=dev),
+                     torch.empty(n, dtype=torch.float32, device=dev)) for _ in range(2)]
+        ev = lambda: [torch.cuda.Event() for _ in range(2)]
+        self.in_ready, self.in_free, self.out_ready, self.out_free = ev(), ev(), ev(), ev()
+        self.k = 0
+
+    def submit(self, h_pos, h_mass, h_aold, h_acc, h_pot, p: G4Params | None = None):
+        """Enqueue one step: inputs from, results into pinned host tensors (h_acc (3, n),
+        h_pot (n,)).  Returns an event (on the result-copy stream) that completes when h_acc and h_pot
+        hold this step's results."""
+        p = p or self.p
+        b = self.k & 1
+        cs, ds, ms = self.h2d, self.d2h, torch.cuda.current_stream()
+        d_pos, d_mass, d_aold = self.inp[b]
+        d_acc, d_pot = self.out[b]
+        cs.wait_event(self.in_free[b])          # step k-2 has finished reading this input set
+        with torch.cuda.stream(cs):
+            d_pos.copy_(h_pos, non_blocking=True)
+            d_mass.copy_(h_mass, non_blocking=True)
+            d_aold.copy_(h_aold, non_blocking=True)
+            self.in_ready[b].record(cs)
+        ms.wait_event(self.in_ready[b])
+        ms.wait_event(self.out_free[b])         # step k-2's results have left this buffer
+        tg = self.tg
+        tg.prepare(d_pos, d_mass, None, d_aold, p)
+        self.in_free[b].record(ms)
+        tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, p, acc=tg.acc_s, pot=tg.pot_s,
+                             counts=tg.counts)
+        g4_scatter(tg.perm, tg.acc_s, tg.pot_s, out=(d_acc, d_pot))
+        self.out_ready[b].record(ms)
+        ds.wait_event(self.out_ready[b])
+        done = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(ds):
+            h_acc.copy_(d_acc, non_blocking=True)
+            h_pot.copy_(d_pot, non_blocking=True)
+            self.out_free[b].record(ds)
+            done.record(ds)
+        self.k += 1
+        return done
+
+
 class ForestGravity:
     """Many independent systems solved together: one batched sort, one forest build, one
     moments pass and one persistent walk launch for all systems (no per-system launches).

@@ -298,3 +298,26 @@ def test_forest_many_plummer_spheres_parity():
         assert np.array_equal(nd["next"][off:off + m] - off, ot["next"])
         off += m
     assert off == len(nd["level"])
+
+
+def test_host_pipeline_equals_device_forces():
+    """g4.HostPipeline (inputs from and results into pinned host memory, copies overlapped
+    with the computation of neighbouring steps) returns exactly TreeGravity.forces' results,
+    step by step, for changing inputs."""
+    ps, tp = _treepm_box(24)
+    q, box = int_coords(ps)
+    P = gpu_params(g4, ps, box, alpha=0.0025, leaf_max=16, **tp)
+    aold = torch.full((ps.n,), 5.0, dtype=torch.float32)
+    h_pos = torch.from_numpy(np.ascontiguousarray(q).view(np.int32)).pin_memory()
+    h_aold = aold.pin_memory()
+    masses = [torch.from_numpy((ps.mass * s).astype(np.float32)).pin_memory() for s in (1.0, 0.5, 2.0)]
+    h_acc = [torch.empty((3, ps.n), dtype=torch.float32).pin_memory() for _ in range(3)]
+    h_pot = [torch.empty(ps.n, dtype=torch.float32).pin_memory() for _ in range(3)]
+    pipe = g4.HostPipeline(ps.n, P)
+    for k in range(3):
+        pipe.submit(h_pos, masses[k], h_aold, h_acc[k], h_pot[k])
+    torch.cuda.synchronize()
+    tg = g4.TreeGravity(ps.n, P)
+    for k in range(3):
+        acc, pot = tg.forces(h_pos.cuda(), masses[k].cuda(), None, h_aold.cuda(), P)
+        assert torch.equal(acc.cpu(), h_acc[k]) and torch.equal(pot.cpu(), h_pot[k])
