@@ -244,7 +244,14 @@ g4_status g4_tree_moments(g4_tree tree, double *mass, double *com, double *mono,
  *          pairs use g = g_soft - erf(r / 2 r_s) / r (Eq. eqnpo4).
  * Outputs (sorted order, written only at sink indices): acc 3 x n SoA float, pot n float
  * (nullable), counts 2 x n uint32 (PP interactions, PN interactions; nullable).
- * Requires g4_tree_build and g4_multipoles on the same handle with the same order_p. */
+ * Work: 32-sink groups from a device counter (persistent kernel), optionally in the order set
+ * by g4_tree_set_group_order or as the parts set by g4_tree_set_work_items.  The handle keeps
+ * walk copies (allocated on its first walk, outside any graph capture): the node records in
+ * level order (rebuilt after each g4_multipoles) and 16-byte particle records (rewritten by
+ * every call), plus per-warp frontier rings (a frontier overflow sets the list-capacity flag).
+ * FP32 TreePM pairs use erfc(x) = exp(-x^2) erfcx(x) with a fitted erfcx (relative error
+ * below 5e-7).  Requires g4_tree_build and g4_multipoles on the same handle with the same
+ * order_p. */
 g4_status g4_gravity_tree(g4_tree tree, const uint32_t *pos_sorted, const float *mass_sorted,
                           const uint8_t *cls_sorted, const float *aold_sorted,
                           const int32_t *active, int64_t n_active, const g4_params *params,
@@ -252,7 +259,9 @@ g4_status g4_gravity_tree(g4_tree tree, const uint32_t *pos_sorted, const float 
 
 /* ---- a8: symmetric Cartesian FMM (Sec. 2.4, Sec. 2.5) ----------------------------------- */
 
-/* Bytes of device workspace g4_gravity_fmm needs for the tree's current size. */
+/* Bytes of device workspace g4_gravity_fmm needs, sized from the handle's node capacity and
+ * n_max (no host synchronisation): field tensors, pass-down lists and the deferred leaf-leaf
+ * lists (16 source-leaf entries per particle plus a floor). */
 g4_status g4_fmm_workspace(g4_tree tree, const g4_params *params, size_t *bytes);
 
 /* Forces for all n particles by the dual tree walk: node pairs either interact by the
@@ -261,8 +270,11 @@ g4_status g4_fmm_workspace(g4_tree tree, const g4_params *params, size_t *bytes)
  * replaced by all pairs of its daughters).  Criterion G M_max / r^2 (l_max/r)^(p-1) <
  * alpha min |a|_min (or (l_A + l_B)/r < theta), touching nodes never interact, pairs whose
  * nearest faces are beyond r_cut are dropped.  Fields are passed down (L2L) and evaluated
- * at the particles (L2P).  Outputs as for g4_gravity_tree (counts: PP, node-node);
- * momentum_out (3 doubles of device memory, nullable) receives sum m a in FP64. */
+ * at the particles (L2P).  Leaf-leaf interactions are recorded during the dual walk and
+ * evaluated afterwards by a separate kernel with the tree walk's particle-particle phase
+ * (when the workspace's lists are full, the dual walk evaluates them itself: same
+ * interactions, possibly other rounding order).  Outputs as for g4_gravity_tree (counts: PP,
+ * node-node); momentum_out (3 doubles of device memory, nullable) receives sum m a in FP64. */
 g4_status g4_gravity_fmm(g4_tree tree, const uint32_t *pos_sorted, const float *mass_sorted,
                          const uint8_t *cls_sorted, const g4_params *params, float *acc,
                          float *pot, uint32_t *counts, double *momentum_out, void *workspace,
