@@ -646,6 +646,11 @@ def partition_gain(tg, P, n, step, reps=10, train_steps=400):
     out["groups"] = (n + 31) // 32
     out["interaction_counts_identical"] = same
     out["speedup_step_model"] = out["plain"]["step_ms_graph"] / out["model"]["step_ms_graph"]
+    # the partition granularity picked by the autotuner (items per resident warp; 0 = none)
+    from paper_2010_03567_gb300 import autotune
+    best, times = autotune.tune_partition(autotune.gpu_partition_timer(tg, P, pred),
+                                          torch.cuda.get_device_name(), n, P, use_cache=False)
+    out["autotuned_partition"] = {"items_per_warp": best, "walk_ms": times}
     return out
 
 

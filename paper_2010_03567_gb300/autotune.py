@@ -1,4 +1,5 @@
-"""Autotuner for the tree walk's leaf threshold.
+"""Autotuners for the tree walk: the leaf threshold and the granularity of the cost-model
+work partition.
 
 The leaf threshold trades node visits against particle-pair candidates: small leaves mean a
 deep tree whose frontier every 32-sink group must scan, large leaves mean coarser leaf
@@ -90,6 +91,64 @@ def gpu_step_timer(pos_int, mass, aold, p, reps: int = 2):
         e1.record(s)
         torch.cuda.synchronize()
         tg.tree.close()
+        return e0.elapsed_time(e1) / reps
+
+    return run
+
+
+# ---- work partition ------------------------------------------------------------------------
+
+PARTITION_TARGETS = (0, 1, 2, 4, 8, 16)   # items per resident warp; 0 = plain 32-sink groups
+
+
+def pick_partition(times: dict) -> int:
+    """Fastest target; ties go to the coarser partition (fewer items)."""
+    return min(times, key=lambda k: (times[k], k))
+
+
+def tune_partition(time_walk, device_name: str, n: int, p, targets=PARTITION_TARGETS,
+                   path: str | None = None, use_cache: bool = True) -> tuple[int, dict]:
+    """time_walk(target) -> milliseconds of the walk with items at `target` items per resident
+    warp (0: no partition).  Returns (best, times); cached like the leaf threshold."""
+    key = f"{device_name}|{signature(n, p)}|partition"
+    if use_cache:
+        hit = load_cache(path).get(key)
+        if hit is not None:
+            return int(hit["target"]), {int(k): v for k, v in hit["times_ms"].items()}
+    times = {int(t): float(time_walk(int(t))) for t in targets}
+    best = pick_partition(times)
+    store(key, {"target": best, "times_ms": times}, path)
+    return best, times
+
+
+def gpu_partition_timer(tg, p, pred_sorted, reps: int = 3):
+    """A time_walk for `tune_partition` on a prepared TreeGravity: items from the per-sink
+    predicted (or measured) costs at the candidate granularity, walk timed with CUDA events.
+    Leaves the handle with plain groups."""
+    import torch
+
+    from . import g4
+
+    n = tg.n
+    walk = lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, p, acc=tg.acc_s,
+                                        pot=tg.pot_s, counts=tg.counts)
+
+    def run(target: int) -> float:
+        if target > 0:
+            items, ni = g4.schedule_items(pred_sorted, target * g4.resident_warps())
+            g4.set_work_items(tg.tree, items, ni, n)
+        else:
+            g4.set_work_items(tg.tree, None)
+        walk()
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            walk()
+        e1.record(s)
+        torch.cuda.synchronize()
+        g4.set_work_items(tg.tree, None)
         return e0.elapsed_time(e1) / reps
 
     return run

@@ -32,3 +32,24 @@ def test_pick_and_cache(tmp_path):
     autotune.tune(timer, "GB300", 1 << 20, p, path=path)
     assert len(calls) == 6
     assert autotune.signature(1 << 20, p) != autotune.signature(1 << 20, FakeParams())
+
+
+def test_partition_pick_and_cache(tmp_path):
+    path = str(tmp_path / "cache.json")
+    calls = []
+
+    def timer(target):
+        calls.append(target)
+        return {0: 4.0, 1: 2.0, 2: 1.3, 4: 1.2, 8: 1.2, 16: 1.5}[target]
+
+    best, times = autotune.tune_partition(timer, "GB300", 16384, FakeParams(), path=path)
+    assert best == 4             # tie between 4 and 8 goes to the coarser partition
+    assert sorted(calls) == [0, 1, 2, 4, 8, 16]
+    calls.clear()
+    assert autotune.tune_partition(timer, "GB300", 16384, FakeParams(), path=path)[0] == 4
+    assert calls == []
+    # the leaf threshold and the partition of the same workload are cached separately
+    autotune.tune(lambda leaf: float(leaf), "GB300", 16384, FakeParams(), path=path)
+    assert autotune.load_cache(path).keys() >= {
+        "GB300|" + autotune.signature(16384, FakeParams()),
+        "GB300|" + autotune.signature(16384, FakeParams()) + "|partition"}
