@@ -67,10 +67,15 @@ typedef struct g4_params {
     double G;              /* gravitational constant */
     int n_eps_classes;     /* number of softening classes (1..G4_MAX_EPS_CLASSES) */
     double eps_table[G4_MAX_EPS_CLASSES]; /* softening length eps_0 per class (Sec. 2.9) */
-    int group_size;        /* sinks per warp group of the walk (8, 16 or 32; 0 = 32) */
+    int group_size;        /* sinks per warp group of the tree walk: 8, 16 or 32 (0 = 32);
+                              smaller groups stage fewer sources per sink but leave lanes
+                              idle.  Forests, LPT orders and work items use 32. */
     int fp64_count;        /* nodes holding >= fp64_count particles accumulate moments in
                               FP64 (0 = 4096) */
     int keep_qp;           /* FMM: 1 keeps Q_p in the potential (Sec. 2.4 drops it) */
+    int fmm_p2p_per_particle; /* FMM: deferred leaf-leaf list entries per particle of the
+                              handle (0 = 16); beyond them the dual walk evaluates the
+                              leaf-leaf work itself */
 } g4_params;
 
 typedef struct g4_tree_s *g4_tree;
@@ -87,7 +92,8 @@ int64_t g4_launch_count(void);
 
 /* Fills *p with the defaults: periodic=0, r_s=0, R_cut=4.5, pp_cut=1, alpha=0.0025,
  * theta=0.5, criterion=0, p=3, leaf_max=8, exclusion=1, precision=0, G=1, one class with
- * eps=0.01, group_size=32, fp64_count=4096, keep_qp=0.  Host-only, never fails for p!=NULL. */
+ * eps=0.01, group_size=32, fp64_count=4096, keep_qp=0, fmm_p2p_per_particle=0.  Host-only,
+ * never fails for p!=NULL. */
 g4_status g4_params_default(g4_params *p);
 
 /* ---- a1: integer coordinates (Sec. 2.10, Sec. 2.11) ----------------------------------- */

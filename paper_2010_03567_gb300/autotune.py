@@ -1,5 +1,5 @@
-"""Autotuners for the tree walk: the leaf threshold and the granularity of the cost-model
-work partition.
+"""Autotuners for the tree walk: the leaf threshold, the sink-group size and the granularity
+of the cost-model work partition.
 
 The leaf threshold trades node visits against particle-pair candidates: small leaves mean a
 deep tree whose frontier every 32-sink group must scan, large leaves mean coarser leaf
@@ -152,3 +152,23 @@ def gpu_partition_timer(tg, p, pred_sorted, reps: int = 3):
         return e0.elapsed_time(e1) / reps
 
     return run
+
+
+# ---- sink-group size ---------------------------------------------------------------------------
+
+GROUP_SIZES = (8, 16, 32)
+
+
+def tune_group_size(time_walk, device_name: str, n: int, p, sizes=GROUP_SIZES,
+                    path: str | None = None, use_cache: bool = True) -> tuple[int, dict]:
+    """time_walk(group_size) -> milliseconds of the walk.  Fastest wins, ties to the larger
+    group.  Cached per GPU and workload like the leaf threshold."""
+    key = f"{device_name}|{signature(n, p)}|group"
+    if use_cache:
+        hit = load_cache(path).get(key)
+        if hit is not None:
+            return int(hit["group_size"]), {int(k): v for k, v in hit["times_ms"].items()}
+    times = {int(g): float(time_walk(int(g))) for g in sizes}
+    best = min(times, key=lambda k: (times[k], -k))
+    store(key, {"group_size": best, "times_ms": times}, path)
+    return best, times

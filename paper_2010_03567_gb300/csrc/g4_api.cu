@@ -81,5 +81,6 @@ extern "C" g4_status g4_params_default(g4_params *p)
     p->group_size = 32;
     p->fp64_count = 4096;
     p->keep_qp = 0;
+    p->fmm_p2p_per_particle = 0;
     return G4_OK;
 }

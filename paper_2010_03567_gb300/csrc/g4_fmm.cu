@@ -637,7 +637,7 @@ struct FmmLayout {
 
 // deferred P2P lists: 16 source-leaf entries and 1.25 chunks per particle of the handle (plus
 // a floor for small sets); overflowing chunks are evaluated by the dual walk itself
-FmmLayout fmm_layout(int64_t nodes, int64_t n_max, int nt, size_t ws_bytes)
+FmmLayout fmm_layout(int64_t nodes, int64_t n_max, int nt, size_t ws_bytes, int per_particle)
 {
     FmmLayout L;
     size_t o = 0;
@@ -650,8 +650,13 @@ FmmLayout fmm_layout(int64_t nodes, int64_t n_max, int nt, size_t ws_bytes)
     L.m2l_cum = take(4 * nodes);
     L.dcount = take(16);
     const int64_t nm = n_max > 0 ? n_max : 1;
-    L.p2p_cap = 16 * nm + ((int64_t)1 << 20);
-    L.chunk_cap = nm + nm / 4 + ((int64_t)1 << 14);
+    if (per_particle <= 0) {
+        L.p2p_cap = 16 * nm + ((int64_t)1 << 20);
+        L.chunk_cap = nm + nm / 4 + ((int64_t)1 << 14);
+    } else {   // explicit budget (small values exercise the in-walk evaluation)
+        L.p2p_cap = (int64_t)per_particle * nm;
+        L.chunk_cap = L.p2p_cap / 8 + 1;
+    }
     L.p2p_src = take(4 * (size_t)L.p2p_cap);
     L.p2p_chunk = take(16 * (size_t)L.chunk_cap);
     L.p2p_head = take(4 * nodes);
@@ -680,7 +685,7 @@ extern "C" g4_status g4_fmm_workspace(g4_tree t, const g4_params *P, size_t *byt
     if (s != G4_OK) return s;
     if (!t || !bytes) return g4_fail(G4_ERR_INVALID_ARG, "g4_fmm_workspace: NULL argument");
     // sized for the handle's node capacity, so no host synchronisation is needed
-    *bytes = fmm_layout(t->cap, t->n_max, g4_nmono(P->order_p), 0).total;
+    *bytes = fmm_layout(t->cap, t->n_max, g4_nmono(P->order_p), 0, P->fmm_p2p_per_particle).total;
     return G4_OK;
 }
 
@@ -708,7 +713,7 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     if (n == 0) return G4_OK;
     const int nt = g4_nmono(P->order_p);
     // node count bound: the handle's capacity (no host synchronisation here)
-    FmmLayout L = fmm_layout(t->cap, t->n_max, nt, workspace_bytes);
+    FmmLayout L = fmm_layout(t->cap, t->n_max, nt, workspace_bytes, P->fmm_p2p_per_particle);
     if (L.dcap < 1024 || L.total > workspace_bytes)
         return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: workspace too small (%zu bytes)",
                        workspace_bytes);

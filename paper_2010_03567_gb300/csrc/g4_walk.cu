@@ -48,6 +48,7 @@ struct WalkArgs {
     const int32_t *group_order;   // optional schedule (longest predicted cost first)
     const int4 *items;            // optional work items (first sink, count, part | parts << 8,
     const int32_t *n_items;       //   split slot); their number on the device
+    int gs;                       // sinks per group (8, 16 or 32)
     float *part_buf;              // partial sums of split groups: [slot][part][lane][6]
     int32_t *part_cnt;            // arrivals per split slot (zero between walks)
     int part_cap;                 // split slots available
@@ -142,7 +143,8 @@ k_walk(const WalkArgs A)
     const unsigned lt = (1u << lane) - 1u;
     if (*A.flags & G4_FLAG_CAPACITY) return;   // incomplete tree: outputs left untouched
     int2 *Q = A.queue + (size_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * QCAP;
-    const int ngroups = A.items ? *A.n_items : (A.n_sys ? A.sys_goff[A.n_sys] : (A.n_sinks + 31) >> 5);
+    const int ngroups = A.items ? *A.n_items
+                                : (A.n_sys ? A.sys_goff[A.n_sys] : (A.n_sinks + A.gs - 1) / A.gs);
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(A.work, 1);
@@ -150,7 +152,7 @@ k_walk(const WalkArgs A)
         if (g >= ngroups) break;
         if (A.group_order) g = A.group_order[g];
         // the group's sinks, node range and box (a forest walks only its own system's tree)
-        int s0 = g * 32, s_end = A.n_sinks, k = 0;   // k: root, level-ordered
+        int s0 = g * A.gs, s_end = min(A.n_sinks, s0 + A.gs), k = 0;   // k: root, level-ordered
         int kp = 0, Kp = 1, pslot = -1;               // part of a split group
         if (A.items) {
             const int4 it = A.items[g];
@@ -588,6 +590,8 @@ g4_status g4_check_params(const g4_params *P, const char *who)
         return g4_fail(G4_ERR_INVALID_ARG, "%s: criterion=%d", who, P->criterion);
     if (P->precision != 0 && P->precision != 1)
         return g4_fail(G4_ERR_INVALID_ARG, "%s: precision=%d", who, P->precision);
+    if (P->group_size != 0 && P->group_size != 8 && P->group_size != 16 && P->group_size != 32)
+        return g4_fail(G4_ERR_INVALID_ARG, "%s: group_size=%d (8, 16 or 32)", who, P->group_size);
     return G4_OK;
 }
 
@@ -654,10 +658,11 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     A.sys_goff = t->sys_goff;
     A.sys_box = t->sys_box;
     A.n_sys = t->n_sys;
-    A.group_order = (t->group_order && !active && !t->n_sys && t->group_order_n == (ns + 31) / 32)
-                        ? t->group_order : nullptr;
+    A.gs = (P->group_size == 0 || t->n_sys) ? 32 : P->group_size;
+    A.group_order = (t->group_order && !active && !t->n_sys && A.gs == 32 &&
+                     t->group_order_n == (ns + 31) / 32) ? t->group_order : nullptr;
     const bool use_items = t->items && !active && !t->n_sys && t->items_n_sinks == ns &&
-                           P->precision == 0;
+                           P->precision == 0 && A.gs == 32;
     A.items = use_items ? (const int4 *)t->items : nullptr;
     A.n_items = use_items ? t->n_items : nullptr;
     A.part_buf = t->part_buf;

@@ -33,7 +33,7 @@ class G4Params(C.Structure):
                 ("leaf_max", C.c_int), ("exclusion_zone", C.c_int), ("precision", C.c_int),
                 ("G", C.c_double), ("n_eps_classes", C.c_int),
                 ("eps_table", C.c_double * MAX_EPS), ("group_size", C.c_int),
-                ("fp64_count", C.c_int), ("keep_qp", C.c_int)]
+                ("fp64_count", C.c_int), ("keep_qp", C.c_int), ("fmm_p2p_per_particle", C.c_int)]
 
     def copy(self) -> "G4Params":
         p = G4Params()

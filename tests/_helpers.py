@@ -33,6 +33,7 @@ def oracle_params(ps, box, **kw):
     kw.pop("fp64_count", None)
     kw.pop("precision", None)
     kw.pop("group_size", None)
+    kw.pop("fmm_p2p_per_particle", None)
     if "order_p" in kw:
         kw["order"] = kw.pop("order_p")
     if "exclusion_zone" in kw:

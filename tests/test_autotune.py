@@ -53,3 +53,14 @@ def test_partition_pick_and_cache(tmp_path):
     assert autotune.load_cache(path).keys() >= {
         "GB300|" + autotune.signature(16384, FakeParams()),
         "GB300|" + autotune.signature(16384, FakeParams()) + "|partition"}
+
+
+def test_group_size_pick_and_cache(tmp_path):
+    path = str(tmp_path / "cache.json")
+    times = {8: 49.5, 16: 28.6, 32: 17.2}     # 256^3 walk, measured on a GB300
+    best, got = autotune.tune_group_size(lambda g: times[g], "GB300", 1 << 24, FakeParams(), path=path)
+    assert best == 32 and got == times
+    best, _ = autotune.tune_group_size(lambda g: 1.0, "GB300", 1 << 24, FakeParams(), path=path)
+    assert best == 32                            # cached
+    best, _ = autotune.tune_group_size(lambda g: 1.0, "GB300", 1 << 10, FakeParams(), path=path)
+    assert best == 32                            # tie goes to the larger group

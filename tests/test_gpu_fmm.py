@@ -97,3 +97,17 @@ def test_fmm_alpha0_is_direct_sum():
     assert np.all(cg[:, 1] == 0)
     ad2, pd = oracle.direct(q, ps.mass, None, np.arange(ps.n), oracle_params(ps, box))
     assert np.percentile(relerr(ag, ad2), 99) < 1e-5
+
+
+def test_fmm_inwalk_leaf_leaf_when_lists_are_full():
+    """With the deferred leaf-leaf lists almost empty (one entry per particle) the dual walk
+    evaluates the overflowing leaf-leaf work itself: same interactions, same forces to
+    rounding as the deferred pass."""
+    L = 24 * 1.953125
+    ps = synth.zeldovich(24, L, 2.0, 1003)
+    q, box = int_coords(ps)
+    kw = dict(criterion=1, theta=0.5, order_p=4, r_s=1.25 * L / 48, r_cut_factor=4.5, leaf_max=8)
+    a0, p0, c0, _ = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), None)
+    a1, p1, c1, _ = gpu_fmm(ps, q, gpu_params(g4, ps, box, fmm_p2p_per_particle=1, **kw), None)
+    assert np.array_equal(c0, c1)
+    assert np.percentile(relerr(a1, a0), 99) < 2e-5

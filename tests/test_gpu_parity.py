@@ -321,3 +321,18 @@ def test_host_pipeline_equals_device_forces():
     for k in range(3):
         acc, pot = tg.forces(h_pos.cuda(), masses[k].cuda(), None, h_aold.cuda(), P)
         assert torch.equal(acc.cpu(), h_acc[k]) and torch.equal(pot.cpu(), h_pot[k])
+
+
+@pytest.mark.parametrize("gs", [8, 16])
+def test_walk_group_sizes_same_interactions(gs):
+    """Smaller sink groups (group_size 8 or 16) walk the same per-sink interaction sets as
+    32-sink groups; the sums differ only by rounding order."""
+    ps, tp = _treepm_box(24)
+    q, box = int_coords(ps)
+    aold = np.full(ps.n, 5.0, np.float32)
+    P32 = gpu_params(g4, ps, box, alpha=0.0025, leaf_max=16, **tp)
+    Pgs = gpu_params(g4, ps, box, alpha=0.0025, leaf_max=16, group_size=gs, **tp)
+    a32, p32, c32, _ = gpu_forces(torch, g4, ps, q, P32, aold)
+    ags, pgs, cgs, _ = gpu_forces(torch, g4, ps, q, Pgs, aold)
+    assert np.array_equal(c32, cgs)
+    assert np.percentile(relerr(ags, a32), 99) < 2e-5
