@@ -113,6 +113,7 @@ struct MomArgs {
     int n;
     const int32_t *lvl;
     const int32_t *b_dfs;
+    const int32_t *b_child;   // first daughter's level-order slot per level-order slot
     G4Node *node;
     float *q;        // nq floats per node
     double *qd;      // precision 1: (4 + nq) doubles per node, or nullptr
@@ -233,6 +234,96 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd)
     }
 }
 
+// sum over lanes 0..7 (the others hold zero); the result is valid in lanes 0..7
+template <typename T>
+__device__ __forceinline__ T octet_sum(T v)
+{
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+// The internal-node combination of node_moments with one lane per daughter (at most eight):
+// each lane shifts its daughter's moments to the node's centre of mass and the eight
+// contributions are summed across lanes, so a large node costs one daughter's shift instead
+// of eight in a row (this matters in FP64, where one thread's chain of products is slow).
+// Only the order of the sums over daughters differs from node_moments.
+template <int P, typename T>
+__device__ void node_moments_warp(const MomArgs &A, int d, const G4Node &nd, int slot, int lane)
+{
+    constexpr int NM = g4_nmono(P);
+    const T scale = A.n_sys ? (T)(A.sys_box[g4_system_of(A.sys_first, A.n_sys, nd.first)] *
+                                  (1.0 / 4294967296.0))
+                            : (T)A.scale;
+    const bool has = lane < nd.nchild;
+    T mc = T(0), ex = T(0), ey = T(0), ez = T(0);
+    T qc[NM];
+#pragma unroll
+    for (int k = 0; k < NM; k++) qc[k] = T(0);
+    float hmax = 0.f, amin = 3.0e38f;
+    if (has) {
+        const int ch = A.b_dfs[A.b_child[slot] + lane];
+        const G4Node c = A.node[ch];
+        T ox = (T)c.sx, oy = (T)c.sy, oz = (T)c.sz;
+        mc = (T)c.mass;
+        if (A.all_fp64 && A.qd) {
+            const double *src = A.qd + (size_t)ch * (4 + A.nq);
+            mc = (T)src[3];
+            ox = (T)src[0];
+            oy = (T)src[1];
+            oz = (T)src[2];
+#pragma unroll
+            for (int k = 4; k < NM; k++) qc[k] = (T)src[4 + k - 4];
+        } else {
+#pragma unroll
+            for (int k = 4; k < NM; k++) qc[k] = (T)A.q[(size_t)ch * A.nq + k - 4];
+        }
+        qc[0] = mc;
+        // daughter's centre of mass relative to the node's geometric centre
+        ex = (T)(int32_t)(c.cx - nd.cx) * scale + ox;
+        ey = (T)(int32_t)(c.cy - nd.cy) * scale + oy;
+        ez = (T)(int32_t)(c.cz - nd.cz) * scale + oz;
+        hmax = c.hmax;
+        amin = c.amin;
+    }
+    const T M = octet_sum(mc);
+    const T inv = M > T(0) ? T(1) / M : T(0);
+    const T sx = octet_sum(mc * ex) * inv, sy = octet_sum(mc * ey) * inv,
+            sz = octet_sum(mc * ez) * inv;
+    T q[NM];
+#pragma unroll
+    for (int k = 0; k < NM; k++) q[k] = T(0);
+    if (has) shift_add<P, T>(q, qc, ex - sx, ey - sy, ez - sz);
+#pragma unroll
+    for (int k = 4; k < NM; k++) q[k] = octet_sum(q[k]);
+#pragma unroll
+    for (int s = 4; s >= 1; s >>= 1) {
+        hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, s));
+        amin = fminf(amin, __shfl_xor_sync(0xffffffffu, amin, s));
+    }
+    if (lane != 0) return;
+    G4Node &o = A.node[d];
+    o.sx = (float)sx;
+    o.sy = (float)sy;
+    o.sz = (float)sz;
+    o.mass = (float)M;
+    o.hmax = hmax;
+    o.amin = amin;
+    float *dst = A.q + (size_t)d * A.nq;
+#pragma unroll
+    for (int k = 4; k < NM; k++) dst[k - 4] = (float)q[k];
+    if (A.qd) {
+        double *dd = A.qd + (size_t)d * (4 + A.nq);
+        dd[0] = (double)sx;
+        dd[1] = (double)sy;
+        dd[2] = (double)sz;
+        dd[3] = (double)M;
+#pragma unroll
+        for (int k = 4; k < NM; k++) dd[4 + k - 4] = (double)q[k];
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) k_moments_level(const MomArgs A, int level)
 {
@@ -240,6 +331,26 @@ __global__ void __launch_bounds__(128) k_moments_level(const MomArgs A, int leve
     const int o = off[level], c = cnt[level];
     if (*A.flags & G4_FLAG_CAPACITY) return;   // the tree is incomplete: leave it untouched
     const int total = off[G4_NLEVELS];
+    if (c <= (int)((gridDim.x * blockDim.x) >> 5)) {
+        // few (large) nodes: a warp per node, a lane per daughter
+        const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+        if (b >= c) return;
+        const int d = A.b_dfs[o + b];
+        if ((unsigned)d >= (unsigned)total) return;
+        const G4Node nd = A.node[d];
+        const bool fp64 = A.all_fp64 || nd.count >= A.fp64_count;
+        if (nd.meta & 32u) {
+            if (lane == 0) {
+                if (fp64) node_moments<P, double>(A, d, nd);
+                else node_moments<P, float>(A, d, nd);
+            }
+        } else if (fp64) {
+            node_moments_warp<P, double>(A, d, nd, o + b, lane);
+        } else {
+            node_moments_warp<P, float>(A, d, nd, o + b, lane);
+        }
+        return;
+    }
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < c; b += gridDim.x * blockDim.x) {
         const int d = A.b_dfs[o + b];
         if ((unsigned)d >= (unsigned)total) continue;
@@ -297,6 +408,7 @@ extern "C" g4_status g4_multipoles(g4_tree t, const uint32_t *pos_sorted, const 
     A.n = t->built_n;
     A.lvl = t->lvl;
     A.b_dfs = t->b_dfs;
+    A.b_child = t->b_child;
     A.node = t->node;
     A.q = t->q;
     A.nq = g4_nq(p);

@@ -103,6 +103,96 @@ __device__ __forceinline__ int lower_bound_digit(const uint64_t *__restrict__ ke
     return lo;
 }
 
+// Splits the nodes [o, o + c) of one level with 8 * G lanes per node: lane group g (G lanes)
+// finds, for digit g >= 1, the first key of the node whose digit is >= g by a (G + 1)-ary
+// search over the whole node (the digits of a node's keys are non-decreasing), so the seven
+// boundaries are searched at once and each needs about log_{G+1}(n) dependent loads instead
+// of the seven chained binary searches of a thread per node. Group 0 stands for digit 0,
+// whose boundary is the node's first key. Children are numbered in digit order, as below.
+template <int G>
+__device__ __forceinline__ void expand_grouped(
+    const uint64_t *__restrict__ keys, int o, int c, int nbase, int level, int leaf_max,
+    int64_t cap, int shift, int32_t *__restrict__ cnt, int32_t *__restrict__ flags,
+    int32_t *__restrict__ b_first, int32_t *__restrict__ b_count, int32_t *__restrict__ b_child,
+    int32_t *__restrict__ b_nchild, int32_t *__restrict__ b_parent, int warp, int nwarps,
+    int lane)
+{
+    constexpr unsigned FULL = 0xffffffffu, GMASK = (1u << G) - 1u;
+    constexpr int L = 8 * G, NPW = 32 / L;
+    const int base = lane - lane % L, g = (lane - base) / G, j = lane % G, gb = lane - j;
+    for (int b0 = warp * NPW; b0 < c; b0 += nwarps * NPW) {   // uniform within the warp
+        const int b = b0 + (lane / L);
+        const bool ok = b < c;
+        const int node = o + b;
+        int f = 0, n = 0;
+        if (ok) {
+            f = b_first[node];
+            n = b_count[node];
+        }
+        const bool split = ok && n > leaf_max && level < G4_MAXLEVEL;
+        const bool act = split && g >= 1;
+        const uint32_t d = (uint32_t)g;
+        int lo = f, hi = f + n;   // the boundary lies in [lo, hi]
+        while (__any_sync(FULL, act && hi - lo > G)) {
+            const bool go = act && hi - lo > G;
+            int p = lo;
+            bool below = false;
+            if (go) {
+                // G strictly increasing probes inside (lo, hi)
+                p = lo + (int)((int64_t)(hi - lo) * (j + 1) / (G + 1));
+                below = ((uint32_t)(keys[p] >> shift) & 7u) < d;
+            }
+            const int cb = __popc((__ballot_sync(FULL, below) >> gb) & GMASK);
+            const int pl = __shfl_sync(FULL, p, gb + (cb > 0 ? cb - 1 : 0));
+            const int ph = __shfl_sync(FULL, p, gb + (cb < G ? cb : G - 1));
+            if (go) {
+                if (cb > 0) lo = pl + 1;
+                if (cb < G) hi = ph;
+            }
+        }
+        const int q = lo + j;
+        const bool below = act && q < hi && ((uint32_t)(keys[q] >> shift) & 7u) < d;
+        const int bound = lo + __popc((__ballot_sync(FULL, below) >> gb) & GMASK);
+        int nch = 0, before = 0, my_lo = f, my_hi = f;
+        int prev = __shfl_sync(FULL, bound, base);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int nxt = k < 7 ? __shfl_sync(FULL, bound, base + (k + 1) * G) : f + n;
+            const int ne = nxt > prev;
+            nch += ne;
+            if (k < g) before += ne;
+            if (k == g) {
+                my_lo = prev;
+                my_hi = nxt;
+            }
+            prev = nxt;
+        }
+        if (!split) nch = 0;
+        int slot = 0;
+        if (lane == base && nch > 0) slot = atomicAdd(&cnt[level + 1], nch);
+        slot = nbase + __shfl_sync(FULL, slot, base);
+        if (!ok) continue;
+        if (nch == 0 || (int64_t)slot + nch > cap) {
+            if (lane == base) {
+                if (nch > 0) atomicOr(flags, G4_FLAG_CAPACITY);
+                b_child[node] = -1;
+                b_nchild[node] = 0;
+            }
+            continue;
+        }
+        if (lane == base) {
+            b_child[node] = slot;
+            b_nchild[node] = nch;
+        }
+        if (j == 0 && my_hi > my_lo) {
+            const int k = slot + before;
+            b_first[k] = my_lo;
+            b_count[k] = my_hi - my_lo;
+            b_parent[k] = node;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(BUILD_THREADS) k_build_expand(
     const uint64_t *__restrict__ keys, int level, int leaf_max, int64_t cap,
     int32_t *__restrict__ lvl, int32_t *__restrict__ flags, int32_t *__restrict__ b_first,
@@ -122,6 +212,17 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_expand(
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int shift = 3 * (G4_KEYBITS - level - 1);
+    // few, large nodes: several lanes per node; many small nodes: a thread per node
+    if (c <= nwarps) {
+        expand_grouped<4>(keys, o, c, nbase, level, leaf_max, cap, shift, cnt, flags, b_first,
+                          b_count, b_child, b_nchild, b_parent, warp, nwarps, lane);
+        return;
+    }
+    if (c <= 16 * nwarps) {
+        expand_grouped<1>(keys, o, c, nbase, level, leaf_max, cap, shift, cnt, flags, b_first,
+                          b_count, b_child, b_nchild, b_parent, warp, nwarps, lane);
+        return;
+    }
     for (int wb = warp * 32; wb < c; wb += nwarps * 32) {
         int b = wb + lane;
         bool ok = b < c;
