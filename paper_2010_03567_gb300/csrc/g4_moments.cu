@@ -129,7 +129,7 @@ struct MomArgs {
 };
 
 template <int P, typename T>
-__device__ void node_moments(const MomArgs &A, int d, const G4Node &nd)
+__device__ void node_moments(const MomArgs &A, int d, const G4Node &nd, int slot)
 {
     constexpr int NM = g4_nmono(P);
     T q[NM];
@@ -143,6 +143,7 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd)
     const bool leaf = nd.meta & 32u;
     if (leaf) {
         const int f = nd.first, e = nd.first + nd.count;
+#pragma unroll 4
         for (int j = f; j < e; j++) {
             T m = (T)A.mass[j];
             M += m;
@@ -156,6 +157,7 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd)
         sx *= inv;
         sy *= inv;
         sz *= inv;
+#pragma unroll 4
         for (int j = f; j < e; j++) {
             T dx = (T)(int32_t)(A.pos[j] - nd.cx) * scale - sx;
             T dy = (T)(int32_t)(A.pos[A.n + j] - nd.cy) * scale - sy;
@@ -163,8 +165,15 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd)
             mono_add<P, T>(q, (T)A.mass[j], dx, dy, dz);
         }
     } else {
-        // daughters: d+1, then next[] until the end of this subtree
-        for (int ch = d + 1; ch < nd.next; ch = max(A.node[ch].next, ch + 1)) {
+        // daughters in key order, from the level-ordered child slots (independent loads)
+        const int c0 = A.b_child[slot], nch = min(nd.nchild, 8);
+        int chs[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) chs[k] = k < nch ? A.b_dfs[c0 + k] : 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (k >= nch) break;
+            const int ch = chs[k];
             const G4Node &c = A.node[ch];
             T mc = (T)c.mass, ox = (T)c.sx, oy = (T)c.sy, oz = (T)c.sz;
             if (A.all_fp64 && A.qd) {
@@ -185,7 +194,9 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd)
         sx *= inv;
         sy *= inv;
         sz *= inv;
-        for (int ch = d + 1; ch < nd.next; ch = max(A.node[ch].next, ch + 1)) {
+#pragma unroll 1
+        for (int k = 0; k < nch; k++) {
+            const int ch = chs[k];
             const G4Node &c = A.node[ch];
             T qc[NM];
             qc[0] = (T)c.mass;
@@ -341,8 +352,8 @@ __global__ void __launch_bounds__(128) k_moments_level(const MomArgs A, int leve
         const bool fp64 = A.all_fp64 || nd.count >= A.fp64_count;
         if (nd.meta & 32u) {
             if (lane == 0) {
-                if (fp64) node_moments<P, double>(A, d, nd);
-                else node_moments<P, float>(A, d, nd);
+                if (fp64) node_moments<P, double>(A, d, nd, o + b);
+                else node_moments<P, float>(A, d, nd, o + b);
             }
         } else if (fp64) {
             node_moments_warp<P, double>(A, d, nd, o + b, lane);
@@ -355,8 +366,8 @@ __global__ void __launch_bounds__(128) k_moments_level(const MomArgs A, int leve
         const int d = A.b_dfs[o + b];
         if ((unsigned)d >= (unsigned)total) continue;
         const G4Node nd = A.node[d];
-        if (A.all_fp64 || nd.count >= A.fp64_count) node_moments<P, double>(A, d, nd);
-        else node_moments<P, float>(A, d, nd);
+        if (A.all_fp64 || nd.count >= A.fp64_count) node_moments<P, double>(A, d, nd, o + b);
+        else node_moments<P, float>(A, d, nd, o + b);
     }
 }
 
