@@ -45,7 +45,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA 
 # (dram__bytes_read.sum + dram__bytes_write.sum, single-pass capture of the timed walk; the
 # command is in profiles/ncu_walk_dram_256cubed.md).  Reported as roofline.traffic for the
 # default workload only; re-measured whenever the walk kernel changes.
-WALK_DRAM_BYTES_256 = 603.78e6 + 446.40e6
+WALK_DRAM_BYTES_256 = 610.77e6 + 450.58e6
 
 
 def hbm_peak_gbs():

@@ -55,7 +55,10 @@ typedef struct g4_params {
     int periodic;          /* 1: nearest periodic image via two's complement (Sec. 2.10) */
     double r_s;            /* TreePM split scale (Sec. 2.3); <= 0: plain Newtonian kernel */
     double r_cut_factor;   /* R_cut; r_cut = max(R_cut * r_s, 2.8 eps_max) (Sec. 2.3) */
-    int pp_cut;            /* 1: particle pairs with r >= r_cut are dropped (TreePM only) */
+    int pp_cut;            /* 1: particle pairs with r >= r_cut are dropped (TreePM only).
+                              0: every pair of each leaf the walk reaches is kept; leaves
+                              are skipped per group of sinks (conservatively), so that set
+                              depends on the grouping: a diagnostic mode */
     double alpha;          /* relative opening parameter of Eq. (eqnrelcriterion) */
     double theta;          /* geometric opening angle theta_c (criterion 1, bootstrap) */
     int criterion;         /* 0: relative criterion (needs a_old), 1: geometric l/r < theta */

@@ -16,6 +16,8 @@ Workloads (stand-ins for the paper's test problems, none of whose data is used):
                    and 1/64 particle mass, the stand-in for the zoom runs of Sec. 3.5.
 * ``multi_plummer`` -- many independent Plummer spheres of log-uniform size.
 * ``lattice``   -- a perfect cubic lattice (zero net force by symmetry).
+* ``sparse_pairs`` -- isolated particle pairs just inside a cutoff, scattered sparsely (every
+                   group of consecutive particles spans many cutoff radii).
 """
 from __future__ import annotations
 
@@ -203,6 +205,26 @@ def lattice(n_side: int, L: float, eps_in_spacing: float = 1.0 / 30.0) -> Partic
     return ParticleSet(pos=pos, mass=np.ones(n), eps_class=np.zeros(n, np.uint8),
                        eps_table=np.array([eps_in_spacing * d]), box_size=float(L),
                        periodic=True)
+
+
+def sparse_pairs(n_pairs: int, L: float, sep: float, seed: int,
+                 eps: float | None = None) -> ParticleSet:
+    """Periodic box holding n_pairs particle pairs: pair centres uniform in the box, the two
+    members sep apart along a uniformly random direction.  With sep just below a cutoff radius
+    and few pairs per cutoff volume, most particles have exactly one neighbour inside the
+    cutoff, close to it, and groups of consecutive particles spread far apart (a sparse
+    active subset)."""
+    g = _rng(seed)
+    c = g.uniform(0.0, L, size=(n_pairs, 3))
+    u = g.normal(size=(n_pairs, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    pos = np.concatenate([c - 0.5 * sep * u, c + 0.5 * sep * u])
+    pos = np.mod(pos, L)
+    pos[pos >= L] = 0.0
+    n = pos.shape[0]
+    return ParticleSet(pos=pos, mass=np.ones(n), eps_class=np.zeros(n, np.uint8),
+                       eps_table=np.array([sep / 100.0 if eps is None else eps]),
+                       box_size=float(L), periodic=True)
 
 
 def subset(n: int, k: int, seed: int) -> np.ndarray:

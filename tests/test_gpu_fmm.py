@@ -111,3 +111,20 @@ def test_fmm_inwalk_leaf_leaf_when_lists_are_full():
     a1, p1, c1, _ = gpu_fmm(ps, q, gpu_params(g4, ps, box, fmm_p2p_per_particle=1, **kw), None)
     assert np.array_equal(c0, c1)
     assert np.percentile(relerr(a1, a0), 99) < 2e-5
+
+
+def test_fmm_sparse_leaves_keep_pairs_near_cutoff():
+    """Sparse pairs 0.99 r_cut apart: sink leaves span many r_cut, beyond the range where the
+    FP16 candidate test is exact; the leaf-leaf pass must still keep every pair."""
+    L = 1.0
+    rc = L / 1000
+    ps = synth.sparse_pairs(2048, L, 0.99 * rc, 7001)
+    q, box = int_coords(ps)
+    kw = dict(alpha=0.0, order_p=4, r_s=rc / 4.5, r_cut_factor=4.5)
+    aold = np.ones(ps.n, np.float32)   # alpha = 0: leaf-leaf pairs only
+    ag, pg, cg, _ = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), aold)
+    assert np.all(cg[:, 1] == 0)
+    OP = oracle_params(ps, box, **kw)
+    ad, _ = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP, r_max=OP.r_cut)
+    # a dropped partner would leave its particle with no force at all
+    assert np.percentile(relerr(ag, ad), 99) < 1e-5 and relerr(ag, ad).max() < 1e-3

@@ -240,6 +240,45 @@ def test_active_subset_bitwise_equal_and_deterministic():
     assert torch.max(torch.abs(a - b)) <= 1e-6 * torch.max(torch.abs(b))
 
 
+def _sparse_pairs():
+    """2,048 pairs 0.99 r_cut apart in a box of 1,000 r_cut: every 32-sink group spans ~120
+    r_cut, where FP16 positions relative to the group centre err by more than the candidate
+    test's margin (an unguarded test drops ~4% of these pairs)."""
+    L = 1.0
+    rc = L / 1000
+    ps = synth.sparse_pairs(2048, L, 0.99 * rc, 7001)
+    return ps, dict(r_s=rc / 4.5, r_cut_factor=4.5, alpha=0.0)
+
+
+def test_walk_sparse_groups_keep_pairs_near_cutoff():
+    ps, kw = _sparse_pairs()
+    q, box = int_coords(ps)
+    OP = oracle_params(ps, box, **kw)
+    aold = np.ones(ps.n, np.float32)   # alpha = 0: every node opened, a pure pair sum
+    ag, pg, cg, _ = gpu_forces(torch, g4, ps, q, gpu_params(g4, ps, box, **kw), aold)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, aold.astype(np.float64), OP, 8)
+    ao, po, co = oracle.tree_forces(run, np.arange(ps.n))
+    # every particle sees its partner, 1% inside r_cut: the pair sets are identical
+    assert np.array_equal(cg, co)
+    assert np.all(cg[:, 0] >= 1) and np.all(cg[:, 1] == 0)
+    assert np.percentile(relerr(ag, ao), 99) < PARITY_P99
+    ad, _ = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP, r_max=OP.r_cut)
+    assert np.percentile(relerr(ag, ad), 99) < PARITY_P99
+
+
+def test_walk_without_pair_cutoff_keeps_more_pairs():
+    """pp_cut = 0: particle pairs of every leaf the walk does not skip are kept, including
+    those beyond r_cut; with the cutoff they are dropped.  Same nodes either way."""
+    ps, tp = _treepm_box(16)
+    q, box = int_coords(ps)
+    kw = dict(criterion=1, theta=0.5, **tp)
+    a1, _, c1, _ = gpu_forces(torch, g4, ps, q, gpu_params(g4, ps, box, **kw), None)
+    a0, _, c0, _ = gpu_forces(torch, g4, ps, q, gpu_params(g4, ps, box, pp_cut=0, **kw), None)
+    assert np.all(c0[:, 0] >= c1[:, 0]) and c0[:, 0].sum() > c1[:, 0].sum()
+    assert np.array_equal(c0[:, 1], c1[:, 1])
+    assert np.all(np.isfinite(a0))
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 33])
 def test_small_and_degenerate_sets(n):
     ps = synth.plummer(max(n, 1), 77 + n)
