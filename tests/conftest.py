@@ -1,8 +1,6 @@
-"""Shared pytest configuration: the ``gpu`` marker and a few cached workloads."""
+"""Shared pytest configuration: the repository root on sys.path and the ``gpu`` marker."""
 import os
 import sys
-
-import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -11,4 +9,3 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the sm_103a library)")
-    config.addinivalue_line("markers", "slow: long-running CPU test")
