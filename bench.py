@@ -45,7 +45,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA 
 # (dram__bytes_read.sum + dram__bytes_write.sum, single-pass capture of the timed walk; the
 # command is in profiles/ncu_walk_dram_256cubed.md).  Reported as roofline.traffic for the
 # default workload only; re-measured whenever the walk kernel changes.
-WALK_DRAM_BYTES_256 = 610.77e6 + 450.58e6
+WALK_DRAM_BYTES_256 = None   # walk kernel changed since the last capture
 
 
 def hbm_peak_gbs():
@@ -411,8 +411,8 @@ def run_gpu(args, rank, world):
                              "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
                              "frac": achieved / FP32_PEAK_TFLOPS,
-                             "traffic": WALK_DRAM_BYTES_256 if n_side == N_SIDE else None,
-                             "traffic_per_sink_bytes": (WALK_DRAM_BYTES_256 / n) if n_side == N_SIDE else None,
+                             "traffic": WALK_DRAM_BYTES_256 if (n_side == N_SIDE and WALK_DRAM_BYTES_256) else None,
+                             "traffic_per_sink_bytes": (WALK_DRAM_BYTES_256 / n) if (n_side == N_SIDE and WALK_DRAM_BYTES_256) else None,
                              "walk_ms": walk_ms,
                              "interactions_per_step": {"pp": int(counts[0]), "pn": int(counts[1])}},
                 "tree": {"nodes": nn, "max_level": ml},

@@ -10,11 +10,14 @@
 namespace g4k {
 
 constexpr int PP_STAGE = 128;   // sources staged per pass
-// Largest |sink coordinate - group centre| (per axis, in units of r_cut) for which the FP16x2
-// candidate test cannot miss a pair inside r_cut: FP16 positions there err by at most
-// (2 R + 2) 2^-11 per axis, which moves r^2 near r_cut^2 by at most 2 sqrt(3) (2 R + 2) 2^-11
-// plus ~0.0016 of rounding in the sums; at R = 12 that is 0.048 < the 5% margin.
-constexpr float PP_FP16_RMAX = 12.f;
+// FP16x2 candidate test.  For a group whose sinks lie within R r_cut of the group centre (per
+// axis), FP16 positions relative to the centre in units of r_cut err by at most e = (2 R + 2)
+// 2^-11 per axis (sink, source, difference), so a pair inside r_cut has a computed r^2 of at
+// most 1 + 2 sqrt(3) e + 3 e^2, plus ~0.0016 of rounding in the FP16 sums.  The threshold is
+// that bound (with slack, rounded up), so no pair inside r_cut is missed: ~1.012 r_cut^2 for
+// compact groups, wider for spread ones.  Beyond PP_FP16_RMAX (where the threshold reaches 20)
+// every staged source is a candidate.
+constexpr float PP_FP16_RMAX = 2048.f;
 
 // pending source leaves and the staged sources of one warp
 template <int LB> struct PPSmem {
@@ -44,11 +47,11 @@ __device__ __forceinline__ int cand_bit(int u)
 // Particle-particle phase for the pending leaves of a group.
 // Sources are staged 128 at a time.  TreePM with the pair cutoff: every lane first tests all
 // staged sources against its own sink in packed FP16x2 (two sources per instruction;
-// positions relative to the group centre in units of r_cut, 5% margin on r^2, so no pair
-// inside r_cut is missed) and keeps a candidate bit per source; then each lane evaluates only
-// its own candidates with exact integer separations, the exact cutoff and the full kernel.
-// Without the pair cutoff, or for a group spread wider than PP_FP16_RMAX, every staged source
-// is a candidate.  Leaf masks (lanes that used an
+// positions relative to the group centre in units of r_cut, threshold from the group's FP16
+// error bound, so no pair inside r_cut is missed) and keeps a candidate bit per source; then
+// each lane evaluates only its own candidates with exact integer separations, the exact
+// cutoff and the full kernel.  Without the pair cutoff, or for a group spread wider than
+// PP_FP16_RMAX, every staged source is a candidate.  Leaf masks (lanes that used an
 // ancestor's multipole must not see the leaf) are applied per source when a staged leaf does
 // not reach the whole group.  INTU (FP32 TreePM): the pair terms are summed in integer-grid
 // length units with the fast kernel; the caller rescales the sums.  Part kp of Kp (a group
@@ -101,13 +104,15 @@ __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf
         total += __shfl_sync(0xffffffffu, pre, 31);
     }
     const float inv_rc = TREEPM ? rsqrtf(A.rcut2f) : 0.f;
-    const bool test16 =
-        TREEPM && A.pp_cut &&
-        !__any_sync(0xffffffffu,
-                    fmaxf(fabsf(xr), fmaxf(fabsf(yr), fabsf(zr))) * inv_rc > PP_FP16_RMAX);
+    // group radius R in units of r_cut (non-negative floats order like their bit patterns)
+    const float R = __uint_as_float(__reduce_max_sync(
+        0xffffffffu, __float_as_uint(fmaxf(fabsf(xr), fmaxf(fabsf(yr), fabsf(zr))) * inv_rc)));
+    const bool test16 = TREEPM && A.pp_cut && R <= PP_FP16_RMAX;
+    const float e16 = (2.f * R + 2.f) * (1.f / 2048.f);
+    const __half2 nlim = __half2half2(
+        __float2half_rd(-((1.f + 3.4642f * e16 + 3.f * e16 * e16) * 1.002f + 0.002f)));
     const __half2 sx2 = __float2half2_rn(xr * inv_rc), sy2 = __float2half2_rn(yr * inv_rc),
                   sz2 = __float2half2_rn(zr * inv_rc);
-    const __half2 nlim = __float2half2_rn(-1.05f);
     // Batch bb takes sources bb, bb + nbat, bb + 2 nbat, ...: every batch samples the whole
     // neighbourhood, so each lane's candidates spread evenly over the batches and the per-lane
     // evaluation loops below stay balanced across the warp.
@@ -190,7 +195,7 @@ __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf
                         const __half2 dx = __hsub2(*reinterpret_cast<const __half2 *>(&xs[c]), sx2);
                         const __half2 dy = __hsub2(*reinterpret_cast<const __half2 *>(&ys[c]), sy2);
                         const __half2 dz = __hsub2(*reinterpret_cast<const __half2 *>(&zs[c]), sz2);
-                        // r^2 - 1.05 r_cut^2: a set sign bit marks a candidate; the low / high
+                        // r^2 - threshold: a set sign bit marks a candidate; the low / high
                         // halves' sign bits (15, 31) move to bits k, 16 + k
                         const __half2 d2 = __hfma2(dz, dz, __hfma2(dy, dy, __hfma2(dx, dx, nlim)));
                         const int k = 4 * qd + c;   // a constant once unrolled

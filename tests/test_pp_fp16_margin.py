@@ -1,11 +1,11 @@
 """The particle-particle phase first tests every staged source against each sink in packed FP16
-(positions relative to the group centre in units of r_cut, threshold 1.05 r_cut^2) and then
-evaluates only the candidates exactly.  Dropping a pair inside r_cut (Sec. 2.3: pairs are
-summed up to r_cut) would change the interaction set, so the test may be used only where the
-FP16 rounding stays inside the 5% margin: sinks within PP_FP16_RMAX r_cut of the group centre
-(per axis).  Here the kernel's arithmetic (each FP16 operation rounded once from the exact
-value) is emulated in numpy for pairs just inside r_cut at the edge of that range; beyond it
-(a sparse group) pairs inside r_cut are lost, which is why wider groups skip the test."""
+(positions relative to the group centre in units of r_cut) and then evaluates only the
+candidates exactly.  Dropping a pair inside r_cut (Sec. 2.3: pairs are summed up to r_cut)
+would change the interaction set, so the test's threshold on r^2 / r_cut^2 follows the FP16
+error bound for the group's radius R (sinks within R r_cut of the centre, per axis):
+e = (2 R + 2) 2^-11 per axis, threshold (1 + 2 sqrt(3) e + 3 e^2) 1.002 + 0.002, rounded
+up.  Here the kernel's arithmetic (each FP16 operation rounded once from the exact value) is
+emulated in numpy for pairs just inside r_cut at the edge of that range."""
 import pathlib
 import re
 
@@ -21,17 +21,34 @@ def _rmax():
     return float(m.group(1))
 
 
+def test_threshold_formula_matches_the_kernel():
+    src = " ".join(HDR.read_text().split())
+    assert "const float e16 = (2.f * R + 2.f) * (1.f / 2048.f);" in src
+    assert "__float2half_rd(-((1.f + 3.4642f * e16 + 3.f * e16 * e16) * 1.002f + 0.002f))" in src
+
+
 def _h(x):
     return np.asarray(x, np.float64).astype(np.float16)
 
 
-def _candidates(sink, src):
+def _threshold(R):
+    """Negative FP16 threshold for radius R, rounded toward -inf as __float2half_rd does."""
+    e = np.float32((2.0 * R + 2.0) / 2048.0)
+    lim = np.float32((np.float32(1.0) + np.float32(3.4642) * e + np.float32(3.0) * e * e)
+                     * np.float32(1.002) + np.float32(0.002))
+    v = np.float16(-lim)
+    if float(v) > -float(lim):
+        v = np.nextafter(v, np.float16(-np.inf))
+    return v
+
+
+def _candidates(sink, src, nlim):
     """sink, src: (n, 3) float64 positions in r_cut units relative to the group centre.
-    Returns the FP16 candidate flags: sign of r^2 - 1.05 computed as the kernel does."""
+    Returns the FP16 candidate flags: sign of r^2 - threshold computed as the kernel does."""
     s16 = _h(sink.astype(np.float32))
     x16 = _h(src.astype(np.float32))
     d = _h(x16.astype(np.float64) - s16.astype(np.float64))          # HSUB2
-    acc = _h(-1.05)
+    acc = np.full(len(sink), nlim, np.float16)
     for c in range(3):                                                  # HFMA2 chain
         dc = d[:, c].astype(np.float64)
         acc = _h(dc * dc + acc.astype(np.float64))
@@ -50,30 +67,34 @@ def _pairs(rng, n, R, rmin=0.95):
     return sink, sink + r * u
 
 
-def test_fp16_test_keeps_every_pair_inside_rcut_within_rmax():
-    R = _rmax()
-    assert 1.0 <= R <= 16.0
+@pytest.mark.parametrize("R", [0.25, 1.0, 4.0, 12.0, 50.0, 300.0, "rmax"])
+def test_fp16_test_keeps_every_pair_inside_rcut(R):
+    R = _rmax() if R == "rmax" else R
     rng = np.random.Generator(np.random.PCG64(9101))
-    for _ in range(4):
-        sink, src = _pairs(rng, 200_000, R)
-        assert np.all(_candidates(sink, src))
+    nlim = _threshold(R)
+    for rmin in (0.95, 0.999):
+        sink, src = _pairs(rng, 200_000, R, rmin)
+        assert np.all(_candidates(sink, src, nlim)), R
 
 
-def test_fp16_test_alone_loses_pairs_in_wide_groups():
-    """Negative control: at 100 r_cut from the centre the same test misses pairs inside
-    r_cut, so the range check is needed (and this emulation can see a miss)."""
+def test_fixed_margin_loses_pairs_in_wide_groups():
+    """Negative control: a fixed 5% margin at 100 r_cut from the centre misses pairs inside
+    r_cut, so the threshold has to grow with R (and this emulation can see a miss)."""
     rng = np.random.Generator(np.random.PCG64(9102))
     sink, src = _pairs(rng, 200_000, 100.0, rmin=0.99)
-    assert not np.all(_candidates(sink, src))
+    assert not np.all(_candidates(sink, src, np.float16(-1.05)))
+    assert np.all(_candidates(sink, src, _threshold(100.0)))
 
 
 @pytest.mark.parametrize("r", [0.5, 0.9, 0.999])
-def test_fp16_test_near_the_centre(r):
-    """Close to the group centre the FP16 test is essentially exact: inside r_cut always a
-    candidate, beyond 1.1 r_cut never."""
+def test_fp16_test_compact_group(r):
+    """A compact group (R <= 1) keeps every pair inside r_cut and rejects everything beyond
+    1.03 r_cut: the threshold is about 1.012 r_cut^2 there."""
+    assert -float(_threshold(1.0)) < 1.02
     rng = np.random.Generator(np.random.PCG64(9103))
-    sink = rng.uniform(-0.5, 0.5, size=(10_000, 3))
+    sink = rng.uniform(-1.0, 1.0, size=(10_000, 3))
     u = rng.normal(size=(10_000, 3))
     u /= np.linalg.norm(u, axis=1, keepdims=True)
-    assert np.all(_candidates(sink, sink + r * u))
-    assert not np.any(_candidates(sink, sink + 1.1 * u))
+    nlim = _threshold(1.0)
+    assert np.all(_candidates(sink, sink + r * u, nlim))
+    assert not np.any(_candidates(sink, sink + 1.03 * u, nlim))
