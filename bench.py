@@ -466,7 +466,9 @@ def extra_fmm(pos_int, mass, aold, wp, n, sample_ref):
     ms_s = tg.mass_s.double()
     res = {"ms_per_step": ms, "forces_per_s": n / (ms * 1e-3), "order_p": 4,
            "momentum_rel": float(torch.linalg.vector_norm(mom).item() / (ms_s * amag).sum().item()),
-           "pp_per_step": int(cnt[0].to(torch.int64).sum().item())}
+           "pp_per_step": int(cnt[0].to(torch.int64).sum().item()),
+           # node-node (M2L) terms acting on each particle through its ancestors, summed
+           "nn_per_particle_sum": int(cnt[1].to(torch.int64).sum().item())}
     if sample_ref is not None:
         sinks, ad = sample_ref
         ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
