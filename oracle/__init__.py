@@ -110,7 +110,10 @@ def _declare(L):
     L.or_D_full.argtypes = [i32, vp, vp, vp]
     L.or_tree_walk.argtypes = [vp, vp, i64, vp, vp, vp, vp, i64, C.POINTER(_Params), vp, vp, vp]
     L.or_direct.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(_Params), d, vp, vp]
-    L.or_fmm.argtypes = [vp, vp, i64, vp, vp, C.POINTER(_Params), vp, vp, vp]
+    L.or_fmm.argtypes = [vp, vp, i64, vp, vp, vp, C.POINTER(_Params), vp, vp, vp, vp]
+    L.or_moments_points.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.or_two_node_tree.argtypes = [vp, i64, vp, vp, i64, i32, d, d, vp, vp]
+    L.or_two_node_fmm.argtypes = [vp, vp, i64, vp, vp, i64, i32, d, d, i32, vp, vp, vp, vp]
 
 
 # ---- a1 / a2 / a3 ------------------------------------------------------------------------
@@ -252,15 +255,54 @@ class Tree:
                            _p(sinks), ns, C.byref(cp), _p(acc), _p(pot), _p(cnt))
         return acc, pot, cnt
 
-    def fmm(self, params: OracleParams):
-        """Full FP64 FMM for all particles (sorted order): acc (n,3), pot (n,), counts."""
+    def fmm(self, params: OracleParams, per_particle: bool = False):
+        """Full FP64 FMM for all particles (sorted order): acc (n,3), pot (n,), counts
+        [node-node, particle-node, particle-particle] (each unordered pair once); with
+        ``per_particle`` also (n,2) [particle pairs, particle-node terms] of each particle."""
         acc = np.empty((self.n, 3))
         pot = np.empty(self.n)
-        cnt = np.empty(2, np.int64)
+        cnt = np.empty(3, np.int64)
+        pc = np.empty((self.n, 2), np.int64) if per_particle else None
         cp = params.c()
-        lib().or_fmm(self.h, _p(self.pos), self.n, _p(self.mass), _p(self.cls), C.byref(cp),
-                     _p(acc), _p(pot), _p(cnt))
-        return acc, pot, cnt
+        lib().or_fmm(self.h, _p(self.pos), self.n, _p(self.mass), _p(self.cls), _p(self.aold),
+                     C.byref(cp), _p(acc), _p(pot), _p(cnt), _p(pc))
+        return (acc, pot, cnt, pc) if per_particle else (acc, pot, cnt)
+
+
+def moments_points(x, m, order: int):
+    """Centre of mass and monomial moments (orders 0..order) of points x (n,3), masses m."""
+    x = np.ascontiguousarray(x, np.float64)
+    m = np.ascontiguousarray(m, np.float64)
+    com = np.empty(3)
+    mono = np.empty(nmono(order))
+    lib().or_moments_points(_p(x), _p(m), x.shape[0], int(order), _p(com), _p(mono))
+    return com, mono
+
+
+def two_node_tree(xa, xb, mb, order: int, r_s: float = 0.0, G: float = 1.0):
+    """One-sided expansion of group B (positions xb (nb,3), masses mb) at the points xa."""
+    xa = np.ascontiguousarray(xa, np.float64)
+    xb = np.ascontiguousarray(xb, np.float64)
+    mb = np.ascontiguousarray(mb, np.float64)
+    acc = np.empty((xa.shape[0], 3))
+    pot = np.empty(xa.shape[0])
+    lib().or_two_node_tree(_p(xa), xa.shape[0], _p(xb), _p(mb), xb.shape[0], int(order),
+                           float(r_s), float(G), _p(acc), _p(pot))
+    return acc, pot
+
+
+def two_node_fmm(xa, ma, xb, mb, order: int, r_s: float = 0.0, G: float = 1.0,
+                 keep_qp: bool = False):
+    """Mutual FMM expansion of groups A and B: (acc_a, pot_a, acc_b, pot_b)."""
+    xa = np.ascontiguousarray(xa, np.float64)
+    ma = np.ascontiguousarray(ma, np.float64)
+    xb = np.ascontiguousarray(xb, np.float64)
+    mb = np.ascontiguousarray(mb, np.float64)
+    aa, pa = np.empty((xa.shape[0], 3)), np.empty(xa.shape[0])
+    ab, pb = np.empty((xb.shape[0], 3)), np.empty(xb.shape[0])
+    lib().or_two_node_fmm(_p(xa), _p(ma), xa.shape[0], _p(xb), _p(mb), xb.shape[0], int(order),
+                          float(r_s), float(G), int(keep_qp), _p(aa), _p(pa), _p(ab), _p(pb))
+    return aa, pa, ab, pb
 
 
 def direct(pos_int: np.ndarray, mass, cls, sinks, params: OracleParams, r_max: float = 0.0):

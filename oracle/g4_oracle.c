@@ -736,76 +736,102 @@ typedef struct {
     int64_t np;
     const double *mass;
     const uint8_t *cls;
+    const double *aold;
     const or_params *P;
     double *T;      /* nn x ntens */
     int ntens;
     int toff[OR_MAXP + 2];
     double *acc, *pot;
-    int64_t n_m2l, n_p2p;
+    int64_t *pcnt;  /* per particle: particle-particle and particle-node interactions (or NULL) */
+    int64_t n_m2l, n_pn, n_p2p;
 } or_fmm_ctx;
+
+/* A cell of the dual walk: a tree node, or a single particle.  Sec. 2.4 lets the walk pair
+ * "nodes or particles"; a particle is a cell of side 0 centred on itself whose only moment is
+ * Q_0 = m (its dipole and higher moments about its own position vanish). */
+typedef struct {
+    int64_t k;   /* node index, or sorted particle index */
+    int part;    /* 1: particle */
+} or_cell;
 
 static int or_is_leaf(const or_tree *t, int64_t k) { return t->next[k] == k + 1; }
 
-static void or_node_dc(const or_fmm_ctx *C, int64_t A, int64_t B, double *dc)
+static double or_cell_side(const or_fmm_ctx *C, or_cell X)
 {
-    /* geometric-centre separation c_B - c_A (nearest image when periodic) */
+    return X.part ? 0.0 : ldexp(C->P->box, -C->t->level[X.k]);
+}
+
+static uint32_t or_cell_centre(const or_fmm_ctx *C, or_cell X, int ax)
+{
+    return X.part ? C->pos[ax * C->np + X.k] : C->t->center[3 * X.k + ax];
+}
+
+static double or_cell_com(const or_fmm_ctx *C, or_cell X, int ax)
+{
+    return X.part ? 0.0 : C->t->com[3 * X.k + ax];   /* s - geometric centre */
+}
+
+static double or_cell_mass(const or_fmm_ctx *C, or_cell X)
+{
+    return X.part ? C->mass[X.k] : C->t->mass[X.k];
+}
+
+static double or_cell_eps(const or_fmm_ctx *C, or_cell X)
+{
+    if (!X.part) return C->t->eps_max[X.k];
+    return C->P->eps[C->cls ? C->cls[X.k] : 0];
+}
+
+static double or_cell_amin(const or_fmm_ctx *C, or_cell X)
+{
+    if (!X.part) return C->t->amin[X.k];
+    return C->aold ? C->aold[X.k] : 0.0;
+}
+
+/* symmetric particle-particle interaction of sorted particles i != j (Eqs. eqnsoft, eqnpo4) */
+static void or_pp(or_fmm_ctx *C, int64_t i, int64_t j)
+{
+    const or_params *P = C->P;
+    double d[3];
     for (int ax = 0; ax < 3; ax++)
-        dc[ax] = or_sep(C->t->center[3 * B + ax], C->t->center[3 * A + ax], C->P);
-}
-
-/* symmetric particle-particle interactions between leaves A and B (A == B: pairs i < j) */
-static void or_p2p(or_fmm_ctx *C, int64_t A, int64_t B)
-{
-    const or_tree *t = C->t;
-    const or_params *P = C->P;
-    double rc2 = P->r_cut * P->r_cut;
-    int treepm = P->r_s > 0.0;
-    for (int64_t i = t->first[A]; i < t->first[A] + t->count[A]; i++) {
-        int64_t j0 = (A == B) ? i + 1 : t->first[B];
-        for (int64_t j = j0; j < t->first[B] + t->count[B]; j++) {
-            double d[3];
-            for (int ax = 0; ax < 3; ax++)
-                d[ax] = or_sep(C->pos[ax * C->np + j], C->pos[ax * C->np + i], P);
-            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (treepm && P->pp_cut && r2 >= rc2) continue;
-            double ei = P->eps[C->cls ? C->cls[i] : 0], ej = P->eps[C->cls ? C->cls[j] : 0];
-            double h = 2.8 * (ei > ej ? ei : ej), g0, g1;
-            or_pair_kernel(sqrt(r2), h, P->r_s, &g0, &g1);
-            C->pot[i] += -P->G * C->mass[j] * g0;
-            C->pot[j] += -P->G * C->mass[i] * g0;
-            for (int ax = 0; ax < 3; ax++) {
-                C->acc[3 * i + ax] += -P->G * C->mass[j] * g1 * d[ax];
-                C->acc[3 * j + ax] += P->G * C->mass[i] * g1 * d[ax];
-            }
-            C->n_p2p++;
-        }
+        d[ax] = or_sep(C->pos[ax * C->np + j], C->pos[ax * C->np + i], P);
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (P->r_s > 0.0 && P->pp_cut && r2 >= P->r_cut * P->r_cut) return;
+    double ei = P->eps[C->cls ? C->cls[i] : 0], ej = P->eps[C->cls ? C->cls[j] : 0];
+    double h = 2.8 * (ei > ej ? ei : ej), g0, g1;
+    or_pair_kernel(sqrt(r2), h, P->r_s, &g0, &g1);
+    C->pot[i] += -P->G * C->mass[j] * g0;
+    C->pot[j] += -P->G * C->mass[i] * g0;
+    for (int ax = 0; ax < 3; ax++) {
+        C->acc[3 * i + ax] += -P->G * C->mass[j] * g1 * d[ax];
+        C->acc[3 * j + ax] += P->G * C->mass[i] * g1 * d[ax];
     }
+    C->n_p2p++;
+    if (C->pcnt) { C->pcnt[2 * i]++; C->pcnt[2 * j]++; }
 }
 
-/* Node-node expansion, both directions, with r = s_B - s_A (Sec. 2.4):
- *   T^A_k += -G (-1)^k sum_{n=0}^{p-k} (1/n!) D_{n+k}(r) . Q^B_n
- *   T^B_k += -G        sum_{n=0}^{p-k} ((-1)^n/n!) D_{n+k}(r) . Q^A_n
- * Q_p is dropped unless keep_qp is set (it only shifts the potential by a constant).     */
-static void or_m2l(or_fmm_ctx *C, int64_t A, int64_t B, const double *rv)
+/* Field tensors of the mutual expansion of two cells with moments QA, QB (monomials of orders
+ * 0..p about their centres of mass) and r = s_B - s_A (Sec. 2.4):
+ *   fA_k = -G (-1)^k sum_{n=0}^{p-k} (1/n!) D_{n+k}(r) . Q^B_n      (field of B around s_A)
+ *   fB_k = -G        sum_{n=0}^{p-k} ((-1)^n/n!) D_{n+k}(r) . Q^A_n (field of A around s_B)
+ * Q_p is dropped unless keep_qp is set (it only shifts the potential by a constant).
+ * fA, fB: full tensors of orders 0..p at offsets toff[k]. */
+static void or_m2l_fields(const double *QA, const double *QB, const double *rv, int p,
+                          double r_s, double G, int keep_qp, const int *toff, double *fA,
+                          double *fB)
 {
-    const or_tree *t = C->t;
-    const or_params *P = C->P;
-    int p = P->order;
-    int64_t nm = or_nmono(t->order);
     double r = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
     double g[OR_MAXP + 2];
-    or_gn(r, P->r_s, p, g);
+    or_gn(r, r_s, p, g);
     static __thread double D[OR_MAXP + 1][729];
     for (int m = 0; m <= p; m++) or_D_full(m, rv, g, D[m]);
-    double *TA = C->T + (int64_t)C->ntens * A, *TB = C->T + (int64_t)C->ntens * B;
-    const double *QA = t->mono + nm * A, *QB = t->mono + nm * B;
     for (int k = 0; k <= p; k++) {
         int k3 = or_pow3(k);
         double sk = (k & 1) ? -1.0 : 1.0;
         for (int I = 0; I < k3; I++) {
             double fa = 0.0, fb = 0.0;
             for (int n = 0; n <= p - k; n++) {
-                if (n == p && !P->keep_qp) continue;
+                if (n == p && !keep_qp) continue;
                 double inv = 1.0 / or_factorial(n), sn = (n & 1) ? -1.0 : 1.0;
                 int n3 = or_pow3(n);
                 for (int J = 0; J < n3; J++) {
@@ -814,36 +840,130 @@ static void or_m2l(or_fmm_ctx *C, int64_t A, int64_t B, const double *rv)
                     fb += inv * sn * d * or_Q_full(QA, n, J);
                 }
             }
-            TA[C->toff[k] + I] += -P->G * sk * fa;
-            TB[C->toff[k] + I] += -P->G * fb;
+            fA[toff[k] + I] = -G * sk * fa;
+            fB[toff[k] + I] = -G * fb;
         }
     }
-    C->n_m2l++;
 }
 
-/* Dual tree walk (Sec. 2.4): a pair of nodes either interacts through a symmetric multipole
- * expansion, or both nodes are opened ("open both", so interacting nodes have equal sizes);
- * if one of them is a leaf only the other is opened; two leaves interact particle by
- * particle.  A node interacting with itself is replaced by all pairs of its daughters.
- * Readings: leaves are the finest cells (they are not opened into single particles);
- * pairs whose nearest faces are further apart than r_cut are dropped (Sec. 2.5); touching
- * nodes never interact when the exclusion zone is on; a pair with r < 2.8 max(eps_max) is
- * opened (multipoles unsoftened); the relative criterion is
- *   G M_max / r^2 (l_max / r)^(p-1) < alpha min(|a|_min,A, |a|_min,B)
- * and the geometric one (l_A + l_B) / r < theta_c (Eq. eqnNodeDec).                       */
-static void or_interact(or_fmm_ctx *C, int64_t A, int64_t B)
+/* Adds a field to a cell: a node keeps it for the downward pass; a particle evaluates it at
+ * its own position (a = 0): potential T_0, acceleration -T_1. */
+static void or_deposit(or_fmm_ctx *C, or_cell X, const double *f)
+{
+    if (X.part) {
+        C->pot[X.k] += f[C->toff[0]];
+        for (int ax = 0; ax < 3; ax++) C->acc[3 * X.k + ax] += -f[C->toff[1] + ax];
+        return;
+    }
+    double *T = C->T + (int64_t)C->ntens * X.k;
+    for (int c = 0; c < C->ntens; c++) T[c] += f[c];
+}
+
+/* Accepted interaction of two cells, both directions (node-node or particle-node). */
+static void or_m2l(or_fmm_ctx *C, or_cell A, or_cell B, const double *rv)
 {
     const or_tree *t = C->t;
     const or_params *P = C->P;
-    if (A == B) {
-        if (or_is_leaf(t, A)) { or_p2p(C, A, A); return; }
-        for (int64_t c1 = A + 1; c1 < t->next[A]; c1 = t->next[c1])
-            for (int64_t c2 = c1; c2 < t->next[A]; c2 = t->next[c2]) or_interact(C, c1, c2);
+    int64_t nm = or_nmono(t->order);
+    static __thread double QpA[OR_MAXP * 64], QpB[OR_MAXP * 64], fA[800], fB[800];
+    const double *QA, *QB;
+    if (A.part) {
+        for (int64_t c = 0; c < nm; c++) QpA[c] = 0.0;
+        QpA[0] = C->mass[A.k];
+        QA = QpA;
+    } else {
+        QA = t->mono + nm * A.k;
+    }
+    if (B.part) {
+        for (int64_t c = 0; c < nm; c++) QpB[c] = 0.0;
+        QpB[0] = C->mass[B.k];
+        QB = QpB;
+    } else {
+        QB = t->mono + nm * B.k;
+    }
+    or_m2l_fields(QA, QB, rv, P->order, P->r_s, P->G, P->keep_qp, C->toff, fA, fB);
+    or_deposit(C, A, fA);
+    or_deposit(C, B, fB);
+    if (A.part || B.part) {
+        C->n_pn++;
+        if (C->pcnt) C->pcnt[2 * (A.part ? A.k : B.k) + 1]++;
+    } else {
+        C->n_m2l++;
+    }
+}
+
+static void or_interact(or_fmm_ctx *C, or_cell A, or_cell B);
+
+/* all pairs of the daughters of X (a leaf's daughters are its particles), each pair once */
+static void or_self(or_fmm_ctx *C, or_cell X)
+{
+    const or_tree *t = C->t;
+    if (X.part) return;   /* a particle has no self-interaction */
+    int64_t k = X.k;
+    if (or_is_leaf(t, k)) {
+        for (int64_t i = t->first[k]; i < t->first[k] + t->count[k]; i++)
+            for (int64_t j = i + 1; j < t->first[k] + t->count[k]; j++) {
+                or_cell a = {i, 1}, b = {j, 1};
+                or_interact(C, a, b);
+            }
         return;
     }
-    double lA = ldexp(P->box, -t->level[A]), lB = ldexp(P->box, -t->level[B]);
+    for (int64_t c1 = k + 1; c1 < t->next[k]; c1 = t->next[c1])
+        for (int64_t c2 = c1; c2 < t->next[k]; c2 = t->next[c2]) {
+            or_cell a = {c1, 0}, b = {c2, 0};
+            if (c1 == c2) or_self(C, a);
+            else or_interact(C, a, b);
+        }
+}
+
+/* daughters of node X: child nodes, or the particles of a leaf */
+static int64_t or_daughters(const or_fmm_ctx *C, int64_t k, or_cell **out)
+{
+    const or_tree *t = C->t;
+    int64_t n = 0;
+    if (or_is_leaf(t, k)) {
+        *out = (or_cell *)malloc(sizeof(or_cell) * (size_t)(t->count[k] > 0 ? t->count[k] : 1));
+        for (int64_t i = t->first[k]; i < t->first[k] + t->count[k]; i++) {
+            (*out)[n].k = i;
+            (*out)[n].part = 1;
+            n++;
+        }
+        return n;
+    }
+    *out = (or_cell *)malloc(sizeof(or_cell) * 8);
+    for (int64_t c = k + 1; c < t->next[k]; c = t->next[c]) {
+        (*out)[n].k = c;
+        (*out)[n].part = 0;
+        n++;
+    }
+    return n;
+}
+
+/* Dual tree walk (Sec. 2.4) over cells A != B: a pair either interacts through the symmetric
+ * expansion (fields added to both cells), or is opened.  Readings:
+ *   - two particles always interact directly (pair kernel, softened);
+ *   - a failing pair opens both cells ("open both"); a particle cannot be opened, so a
+ *     particle paired with a node opens the node only; a leaf opens into its particles, which
+ *     then meet the other side's daughters as particle-node pairs (the cell-particle
+ *     interactions of the method's second phase);
+ *   - pairs whose nearest faces are further apart than r_cut are dropped (Sec. 2.5); for a
+ *     particle the "cube" is its position;
+ *   - with the exclusion zone on, a pair does not interact when the centre separation is
+ *     within max(l_A, l_B) along every axis: touching equal-sized nodes, or a particle inside
+ *     the exclusion cube of side 2l around a node (the tree's zone, Sec. 2.2.3); overlapping
+ *     cubes never interact;
+ *   - a pair with r < 2.8 max(eps) is opened (multipoles are unsoftened);
+ *   - relative criterion G M_max / r^2 (l_max / r)^(p-1) < alpha min(|a|_A, |a|_B), or the
+ *     geometric one (l_A + l_B) / r < theta_c (Eq. eqnNodeDec); a particle contributes its
+ *     own mass, side 0, softening and |a_old|.                                              */
+static void or_interact(or_fmm_ctx *C, or_cell A, or_cell B)
+{
+    const or_params *P = C->P;
+    if (A.part && B.part) { or_pp(C, A.k, B.k); return; }
+    double lA = or_cell_side(C, A), lB = or_cell_side(C, B);
     double dc[3];
-    or_node_dc(C, A, B, dc);
+    for (int ax = 0; ax < 3; ax++)
+        dc[ax] = or_sep(or_cell_centre(C, B, ax), or_cell_centre(C, A, ax), P);
     if (P->r_s > 0.0) {
         double e2 = 0.0;
         for (int ax = 0; ax < 3; ax++) {
@@ -853,37 +973,36 @@ static void or_interact(or_fmm_ctx *C, int64_t A, int64_t B)
         if (e2 > P->r_cut * P->r_cut) return;
     }
     double rv[3];
-    for (int ax = 0; ax < 3; ax++) rv[ax] = dc[ax] + t->com[3 * B + ax] - t->com[3 * A + ax];
+    for (int ax = 0; ax < 3; ax++) rv[ax] = dc[ax] + or_cell_com(C, B, ax) - or_cell_com(C, A, ax);
     double r2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
     int accept = 1;
     double dmax = fmax(fabs(dc[0]), fmax(fabs(dc[1]), fabs(dc[2])));
-    if (P->exclusion && dmax <= 0.5 * (lA + lB)) accept = 0;   /* touching */
-    if (dmax < 0.5 * (lA + lB)) accept = 0;                     /* overlapping cubes */
-    double em = fmax(t->eps_max[A], t->eps_max[B]);
+    if (P->exclusion && dmax <= fmax(lA, lB)) accept = 0;   /* touching / exclusion zone */
+    if (dmax < 0.5 * (lA + lB)) accept = 0;                  /* overlapping cubes */
+    double em = fmax(or_cell_eps(C, A), or_cell_eps(C, B));
     if (r2 < (2.8 * em) * (2.8 * em)) accept = 0;
     if (accept) {
         if (P->criterion == 1) {
             if ((lA + lB) * (lA + lB) >= P->theta * P->theta * r2) accept = 0;
         } else {
             double r = sqrt(r2);
-            double Mmax = fmax(t->mass[A], t->mass[B]), lmax = fmax(lA, lB);
-            double amin = fmin(t->amin[A], t->amin[B]);
+            double Mmax = fmax(or_cell_mass(C, A), or_cell_mass(C, B)), lmax = fmax(lA, lB);
+            double amin = fmin(or_cell_amin(C, A), or_cell_amin(C, B));
             double lhs = P->G * Mmax * or_ipow(lmax, P->order - 1);
             double rhs = P->alpha * amin * or_ipow(r, P->order + 1);
             if (!(lhs < rhs)) accept = 0;
         }
     }
     if (accept) { or_m2l(C, A, B, rv); return; }
-    int la = or_is_leaf(t, A), lb = or_is_leaf(t, B);
-    if (la && lb) { or_p2p(C, A, B); return; }
-    if (la) {
-        for (int64_t c = B + 1; c < t->next[B]; c = t->next[c]) or_interact(C, A, c);
-    } else if (lb) {
-        for (int64_t c = A + 1; c < t->next[A]; c = t->next[c]) or_interact(C, c, B);
-    } else {
-        for (int64_t ca = A + 1; ca < t->next[A]; ca = t->next[ca])
-            for (int64_t cb = B + 1; cb < t->next[B]; cb = t->next[cb]) or_interact(C, ca, cb);
-    }
+    or_cell *da = NULL, *db = NULL;
+    int64_t na = 1, nb = 1;
+    if (!A.part) na = or_daughters(C, A.k, &da);
+    if (!B.part) nb = or_daughters(C, B.k, &db);
+    for (int64_t u = 0; u < na; u++)
+        for (int64_t v = 0; v < nb; v++)
+            or_interact(C, da ? da[u] : A, db ? db[v] : B);
+    free(da);
+    free(db);
 }
 
 /* contraction of a full order-(k+j) tensor with v^(j) over its last j slots */
@@ -900,10 +1019,34 @@ static double or_contract_tail(const double *Tkj, int k, int j, int I, const dou
     return s;
 }
 
+/* Evaluation of a field T (full tensors of orders 0..p at toff) at offset a from its centre:
+ * Phi = sum_k (1/k!) T_k . a^(k),  grad Phi = sum_{k>=1} (1/(k-1)!) T_k . a^(k-1). */
+static void or_l2p(const double *T, const int *toff, int p, const double *a, double *phi,
+                   double *grad)
+{
+    double ph = 0.0;
+    for (int q = 0; q <= p; q++) {
+        int q3 = or_pow3(q);
+        double inv = 1.0 / or_factorial(q);
+        for (int I = 0; I < q3; I++) {
+            double ap = 1.0;
+            int w = I;
+            for (int u = 0; u < q; u++) { ap *= a[w % 3]; w /= 3; }
+            ph += inv * T[toff[q] + I] * ap;
+        }
+    }
+    *phi = ph;
+    for (int ax = 0; ax < 3; ax++) {
+        double s = 0.0;
+        for (int q = 1; q <= p; q++)
+            s += or_contract_tail(T + toff[q], 1, q - 1, ax, a) / or_factorial(q - 1);
+        grad[ax] = s;
+    }
+}
+
 /* Downward pass (Sec. 2.4, phase 3): the parent field is shifted to each daughter's centre
  * of mass, T^C_k += sum_j (1/j!) T^P_{k+j} . d^(j) with d = s_C - s_P, and at the leaves
- * evaluated at the particles: Phi = sum_k (1/k!) T_k . a^(k),
- * acc = -sum_{k>=1} (1/(k-1)!) T_k . a^(k-1) with a = x - s.                             */
+ * evaluated at the particles (or_l2p with a = x - s; acceleration = -grad Phi).           */
 static void or_down(or_fmm_ctx *C, int64_t k)
 {
     const or_tree *t = C->t;
@@ -913,28 +1056,13 @@ static void or_down(or_fmm_ctx *C, int64_t k)
     double *Tp = C->T + (int64_t)C->ntens * k;
     if (or_is_leaf(t, k)) {
         for (int64_t i = t->first[k]; i < t->first[k] + t->count[k]; i++) {
-            double a[3];
+            double a[3], phi, grad[3];
             for (int ax = 0; ax < 3; ax++)
                 a[ax] = or_isep(C->pos[ax * C->np + i], t->center[3 * k + ax], 0) * scale
                         - t->com[3 * k + ax];
-            double phi = 0.0;
-            for (int q = 0; q <= p; q++) {
-                int q3 = or_pow3(q);
-                double inv = 1.0 / or_factorial(q);
-                for (int I = 0; I < q3; I++) {
-                    double ap = 1.0;
-                    int w = I;
-                    for (int u = 0; u < q; u++) { ap *= a[w % 3]; w /= 3; }
-                    phi += inv * Tp[C->toff[q] + I] * ap;
-                }
-            }
+            or_l2p(Tp, C->toff, p, a, &phi, grad);
             C->pot[i] += phi;
-            for (int ax = 0; ax < 3; ax++) {
-                double s = 0.0;
-                for (int q = 1; q <= p; q++)
-                    s += or_contract_tail(Tp + C->toff[q], 1, q - 1, ax, a) / or_factorial(q - 1);
-                C->acc[3 * i + ax] += -s;
-            }
+            for (int ax = 0; ax < 3; ax++) C->acc[3 * i + ax] += -grad[ax];
         }
         return;
     }
@@ -957,26 +1085,115 @@ static void or_down(or_fmm_ctx *C, int64_t k)
     }
 }
 
+static int or_tensor_offsets(int p, int *toff)
+{
+    int off = 0;
+    for (int k = 0; k <= p; k++) { toff[k] = off; off += or_pow3(k); }
+    return off;
+}
+
 /* Full FMM force computation for all particles (sorted order).  acc: n x 3, pot: n.
- * counts[0] = number of node-node expansions (each pair once), counts[1] = particle pairs. */
+ * aold: |a_old| per sorted particle (relative criterion; NULL = 0).
+ * counts[0] = node-node expansions, counts[1] = particle-node expansions, counts[2] = particle
+ * pairs (each unordered pair once).  pcounts (n x 2, nullable): per particle, the particle
+ * pairs and the particle-node expansions it takes part in. */
 void or_fmm(const or_tree *t, const uint32_t *pos, int64_t np, const double *mass,
-            const uint8_t *cls, const or_params *P, double *acc, double *pot, int64_t *counts)
+            const uint8_t *cls, const double *aold, const or_params *P, double *acc,
+            double *pot, int64_t *counts, int64_t *pcounts)
 {
     or_fmm_ctx C;
     memset(&C, 0, sizeof(C));
-    C.t = t; C.pos = pos; C.np = np; C.mass = mass; C.cls = cls; C.P = P;
-    C.acc = acc; C.pot = pot;
-    int off = 0;
-    for (int k = 0; k <= P->order; k++) { C.toff[k] = off; off += or_pow3(k); }
-    C.ntens = off;
+    C.t = t; C.pos = pos; C.np = np; C.mass = mass; C.cls = cls; C.aold = aold; C.P = P;
+    C.acc = acc; C.pot = pot; C.pcnt = pcounts;
+    C.ntens = or_tensor_offsets(P->order, C.toff);
     C.T = (double *)calloc((size_t)C.ntens * (size_t)(t->nn ? t->nn : 1), sizeof(double));
     for (int64_t i = 0; i < 3 * np; i++) acc[i] = 0.0;
     for (int64_t i = 0; i < np; i++) pot[i] = 0.0;
+    if (pcounts)
+        for (int64_t i = 0; i < 2 * np; i++) pcounts[i] = 0;
     if (t->nn > 0) {
-        or_interact(&C, 0, 0);
+        or_cell root = {0, 0};
+        or_self(&C, root);   /* the root interacting with itself */
         or_down(&C, 0);
     }
     counts[0] = C.n_m2l;
-    counts[1] = C.n_p2p;
+    counts[1] = C.n_pn;
+    counts[2] = C.n_p2p;
     free(C.T);
+}
+
+/* ===================================================================================== */
+/* Two-node expansion test harness (Sec. 3.1): the particles of two groups A and B, given in */
+/* physical coordinates (n x 3), interact only through one expansion.                     */
+/* ===================================================================================== */
+
+/* Monomial moments of orders 0..p about the centre of mass, by definition (Sec. 2.2.2). */
+void or_moments_points(const double *x, const double *m, int64_t n, int p, double *com,
+                       double *mono)
+{
+    double M = 0.0, d[3] = {0, 0, 0};
+    for (int64_t j = 0; j < n; j++) {
+        M += m[j];
+        for (int ax = 0; ax < 3; ax++) d[ax] += m[j] * x[3 * j + ax];
+    }
+    for (int ax = 0; ax < 3; ax++) com[ax] = d[ax] / M;
+    int64_t nm = or_nmono(p);
+    for (int64_t c = 0; c < nm; c++) mono[c] = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+        double dx[3];
+        for (int ax = 0; ax < 3; ax++) dx[ax] = x[3 * j + ax] - com[ax];
+        for (int q = 0; q <= p; q++)
+            for (int a = q; a >= 0; a--)
+                for (int b = q - a; b >= 0; b--) {
+                    int c = q - a - b;
+                    mono[or_mono_index(a, b, c)] +=
+                        m[j] * or_ipow(dx[0], a) * or_ipow(dx[1], b) * or_ipow(dx[2], c);
+                }
+    }
+}
+
+/* One-sided tree: the particle-node term (or_pn) of group B at every particle of A. */
+void or_two_node_tree(const double *xa, int64_t na, const double *xb, const double *mb,
+                      int64_t nb, int p, double r_s, double G, double *acc, double *pot)
+{
+    double com[3], mono[64];
+    or_moments_points(xb, mb, nb, p, com, mono);
+    for (int64_t i = 0; i < na; i++) {
+        double rv[3];
+        for (int ax = 0; ax < 3; ax++) rv[ax] = com[ax] - xa[3 * i + ax];
+        acc[3 * i] = acc[3 * i + 1] = acc[3 * i + 2] = 0.0;
+        pot[i] = 0.0;
+        or_pn(mono, rv, p, r_s, G, acc + 3 * i, pot + i);
+    }
+}
+
+/* FMM: the mutual expansion of A and B (or_m2l_fields), each field evaluated at its own
+ * group's particles (or_l2p); outputs for A's particles then B's. */
+void or_two_node_fmm(const double *xa, const double *ma, int64_t na, const double *xb,
+                     const double *mb, int64_t nb, int p, double r_s, double G, int keep_qp,
+                     double *acc_a, double *pot_a, double *acc_b, double *pot_b)
+{
+    double sA[3], sB[3], QA[64], QB[64], rv[3];
+    int toff[OR_MAXP + 2];
+    int nt = or_tensor_offsets(p, toff);
+    double *fA = (double *)calloc((size_t)nt, sizeof(double));
+    double *fB = (double *)calloc((size_t)nt, sizeof(double));
+    or_moments_points(xa, ma, na, p, sA, QA);
+    or_moments_points(xb, mb, nb, p, sB, QB);
+    for (int ax = 0; ax < 3; ax++) rv[ax] = sB[ax] - sA[ax];
+    or_m2l_fields(QA, QB, rv, p, r_s, G, keep_qp, toff, fA, fB);
+    for (int64_t i = 0; i < na; i++) {
+        double a[3], grad[3];
+        for (int ax = 0; ax < 3; ax++) a[ax] = xa[3 * i + ax] - sA[ax];
+        or_l2p(fA, toff, p, a, pot_a + i, grad);
+        for (int ax = 0; ax < 3; ax++) acc_a[3 * i + ax] = -grad[ax];
+    }
+    for (int64_t i = 0; i < nb; i++) {
+        double a[3], grad[3];
+        for (int ax = 0; ax < 3; ax++) a[ax] = xb[3 * i + ax] - sB[ax];
+        or_l2p(fB, toff, p, a, pot_b + i, grad);
+        for (int ax = 0; ax < 3; ax++) acc_b[3 * i + ax] = -grad[ax];
+    }
+    free(fA);
+    free(fB);
 }
