@@ -455,7 +455,7 @@ def extra_fmm(pos_int, mass, aold, wp, n, sample_ref):
 
     def step():
         tg.prepare(pos_int, mass, None, aold, P4)
-        out["r"] = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, P4, workspace=ws)
+        out["r"] = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, tg.aold_s, P4, workspace=ws)
         g4.g4_scatter(tg.perm, out["r"][0], out["r"][1], out=(tg.acc, tg.pot))
 
     ms = _time(step, 3)
@@ -466,9 +466,11 @@ def extra_fmm(pos_int, mass, aold, wp, n, sample_ref):
     ms_s = tg.mass_s.double()
     res = {"ms_per_step": ms, "forces_per_s": n / (ms * 1e-3), "order_p": 4,
            "momentum_rel": float(torch.linalg.vector_norm(mom).item() / (ms_s * amag).sum().item()),
+           # ordered particle pairs (each pair counted at both particles), particle-node terms
            "pp_per_step": int(cnt[0].to(torch.int64).sum().item()),
-           # node-node (M2L) terms acting on each particle through its ancestors, summed
-           "nn_per_particle_sum": int(cnt[1].to(torch.int64).sum().item())}
+           "pn_per_step": int(cnt[1].to(torch.int64).sum().item()),
+           # node-node (M2L) fields acting on each particle through its ancestors, summed
+           "nn_per_particle_sum": int(cnt[2].to(torch.int64).sum().item())}
     if sample_ref is not None:
         sinks, ad = sample_ref
         ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
@@ -503,8 +505,74 @@ def extra_forest(leaf_max):
     launches = (g4.launch_count() - l0) / 4
     fg.tree.status()
     cnt = fg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
-    return {"systems": len(sizes), "particles": n, "ms_per_step": ms, "forces_per_s": n / (ms * 1e-3),
-            "launches_per_step": launches, "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1])}
+    res = {"systems": len(sizes), "particles": n, "ms_per_step": ms, "forces_per_s": n / (ms * 1e-3),
+           "launches_per_step": launches, "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1])}
+    # the same systems one at a time: every system its own sort, gather, tree build, moments,
+    # walk and scatter launches (one handle and one set of buffers sized for the largest
+    # system, reused in turn), eager and as one CUDA graph of all those launches
+    first = np.concatenate([[0], np.cumsum(sizes)])
+    nmax = max(sizes)
+    tree1 = g4.Tree(nmax, 4096 + int(nmax * max(1.5, 3.5 / leaf_max)))
+    keys1 = torch.empty(nmax, dtype=torch.int64, device="cuda")
+    perm1 = torch.empty(nmax, dtype=torch.int32, device="cuda")
+    ws1 = torch.empty(g4.g4_keys_sort_workspace(nmax) + 256, dtype=torch.uint8, device="cuda")
+    flat = {k: torch.empty(3 * nmax, dtype=dt, device="cuda")
+            for k, dt in (("pos", torch.int32), ("acc_s", torch.float32), ("acc", torch.float32))}
+    one = {k: torch.empty(nmax, dtype=torch.float32, device="cuda")
+           for k in ("mass", "aold", "pot_s", "pot")}
+    cnt1 = torch.empty(2 * nmax, dtype=torch.int32, device="cuda")
+    Ps = [g4.params(periodic=0, eps=[0.01], alpha=0.0025, leaf_max=leaf_max,
+                    box_size=float(box[k].item())) for k in range(len(sizes))]
+
+    def one_system(k):
+        a, b = int(first[k]), int(first[k + 1])
+        m = b - a
+        q_, P_ = pos[:, a:b].contiguous(), Ps[k]
+        ps_ = flat["pos"][:3 * m].view(3, m)
+        g4.g4_keys_sort(q_, keys1[:m], perm1[:m], ws1)
+        g4.g4_gather(perm1[:m], q_, mass[a:b], None, aold[a:b],
+                     out=(ps_, one["mass"][:m], None, one["aold"][:m]))
+        tree1.build(keys1[:m], ps_, P_)
+        tree1.multipoles(ps_, one["mass"][:m], None, one["aold"][:m], P_)
+        tree1.gravity_tree(ps_, one["mass"][:m], None, one["aold"][:m], P_,
+                           acc=flat["acc_s"][:3 * m].view(3, m), pot=one["pot_s"][:m],
+                           counts=cnt1[:2 * m].view(2, m))
+        g4.g4_scatter(perm1[:m], flat["acc_s"][:3 * m].view(3, m), one["pot_s"][:m],
+                      out=(flat["acc"][:3 * m].view(3, m), one["pot"][:m]))
+
+    for k in range(len(sizes)):   # first calls outside any capture (walk buffers)
+        one_system(k)
+    ms_sys = _time(lambda: [one_system(k) for k in range(len(sizes))], 3)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        for k in range(len(sizes)):
+            one_system(k)
+    ms_sys_graph = _time(g.replay, 3)
+    res["per_system_launches"] = {"ms_per_step": ms_sys, "ms_per_step_graphs": ms_sys_graph,
+                                  "forest_speedup": ms_sys / ms,
+                                  "forest_speedup_vs_graphs": ms_sys_graph / ms}
+    # accuracy: 512 sampled sinks of 16 systems against the oracle's FP64 direct sum over each
+    # whole system
+    import oracle
+    acc = fg.acc.double().cpu().numpy().T
+    pick = np.random.default_rng(3005).choice(len(sizes), 16, replace=False)
+    errs = []
+    for k in pick:
+        ps = systems[k]
+        qk = pos[:, int(first[k]):int(first[k + 1])].cpu().numpy().view(np.uint32)
+        sinks = np.sort(np.random.default_rng(int(k)).choice(ps.n, min(512, ps.n), replace=False))
+        OP = oracle.OracleParams(box=float(box[k].item()), periodic=False, eps=np.array([0.01]))
+        ad, _ = oracle.direct(qk, ps.mass, None, sinks, OP)
+        ak = acc[int(first[k]):int(first[k + 1])][sinks]
+        errs.append(np.linalg.norm(ak - ad, axis=1) / np.linalg.norm(ad, axis=1))
+    e = np.concatenate(errs)
+    res["accuracy_vs_direct"] = {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99)),
+                                 "max": float(e.max()), "sample": f"512 sinks of each of 16 systems"}
+    del g, tree1
+    return res
 
 
 def extra_bins(leaf_max):
@@ -533,6 +601,19 @@ def extra_bins(leaf_max):
     forces = sum(len(a) for a in lists)
     eager = _time(lambda: bf.run(q, mass, cls, aold), 3)
     ref = [a.clone() for a in bf.acc]
+    # accuracy of every bin's forces: 2048 sampled sinks per bin against the oracle's FP64
+    # direct sum over that bin's active set (r < r_cut, both softening classes)
+    import oracle
+    q_np = q.cpu().numpy().view(np.uint32)
+    OPb = oracle.OracleParams(box=100.0, periodic=True, eps=np.array(ps.eps_table), r_s=rs,
+                              r_cut_factor=4.5)
+    acc_bins = []
+    for b, ix in enumerate(lists):
+        sel = np.sort(np.random.default_rng(4004 + b).choice(len(ix), min(2048, len(ix)), replace=False))
+        ad, _ = oracle.direct(np.ascontiguousarray(q_np[:, ix]), ps.mass[ix], ps.eps_class[ix], sel,
+                              OPb, r_max=OPb.r_cut)
+        ag = ref[b].double().cpu().numpy().T[ix[sel]]
+        acc_bins.append({"fraction": fracs[b], **_errors(ag, ad), "sample": int(len(sel))})
     bf.capture(q, mass, cls, aold)
     graph = _time(bf.replay, 3)
     same = all(torch.equal(a, b) for a, b in zip(ref, bf.acc))
@@ -554,6 +635,7 @@ def extra_bins(leaf_max):
     graph_m = _time(bf.replay, 3)
     bf.set_cost_model(None)
     return {"particles": n, "active_fractions": fracs, "forces_per_step": forces,
+            "accuracy_vs_direct": acc_bins,
             "eager_ms": eager, "graph_ms": graph, "forces_per_s_eager": forces / (eager * 1e-3),
             "forces_per_s_graph": forces / (graph * 1e-3), "graph_equals_eager": bool(same),
             "per_bin_ms": per_bin,
@@ -765,9 +847,20 @@ def extra_c5(leaf_max):
     del a0
     P = g4.params(**wp, alpha=0.0025)
     plain = _time(lambda: tg.forces(q, mass, None, aold, P), 2)
+    # accuracy: 512 sampled sinks against the oracle's FP64 direct sum (r < r_cut) over all
+    # 134M particles
+    import oracle
+    sinks = synth.subset(n, 512, 2006)
+    OP = oracle.OracleParams(box=L, periodic=True, eps=np.array(wp["eps"]), r_s=wp["r_s"],
+                             r_cut_factor=4.5)
+    q_np = q.cpu().numpy().view(np.uint32)
+    ad, _ = oracle.direct(q_np, np.ones(n), None, sinks, OP, r_max=OP.r_cut)
+    del q_np
+    accuracy = {**_errors(tg.acc[:, torch.from_numpy(sinks).cuda().long()].double().cpu().numpy().T, ad),
+                "sample": len(sinks)}
     res = extra_cost_model(tg, P, n)
     res.update({"particles": n, "ms_per_step_ph_order": plain,
-                "forces_per_s_ph_order": n / (plain * 1e-3)})
+                "forces_per_s_ph_order": n / (plain * 1e-3), "accuracy_vs_direct": accuracy})
     del tg
     return res
 
@@ -792,7 +885,7 @@ def run_fmm_only(args):
     tg = g4.TreeGravity(ps.n, P4)
     tg.prepare(q, mass, None, aold, P4)
     ws = torch.empty(tg.tree.fmm_workspace(P4) + 256, dtype=torch.uint8, device="cuda")
-    call = lambda: tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, P4, workspace=ws)
+    call = lambda: tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, tg.aold_s, P4, workspace=ws)
     ms = _time(call, max(1, args.steps), warm=1)
     tg.tree.status()
     print(json.dumps({"fmm_only": True, "n_particles": ps.n, "order_p": 4, "calls": args.steps,

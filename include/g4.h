@@ -69,7 +69,7 @@ typedef struct g4_params {
     int precision;         /* 0: FP32 interactions, FP64 moments for big nodes; 1: all FP64 */
     double G;              /* gravitational constant */
     int n_eps_classes;     /* number of softening classes (1..G4_MAX_EPS_CLASSES) */
-    double eps_table[G4_MAX_EPS_CLASSES]; /* softening length eps_0 per class (Sec. 2.9) */
+    double eps_table[G4_MAX_EPS_CLASSES]; /* softening length eps_0 per class (Sec. 2.7) */
     int group_size;        /* sinks per warp group of the tree walk: 8, 16 or 32 (0 = 32);
                               smaller groups stage fewer sources per sink but leave lanes
                               idle.  Forests, LPT orders and work items use 32. */
@@ -108,8 +108,11 @@ g4_status g4_params_default(g4_params *p);
  *     cube: S = smallest power of two >= 2 * (largest extent), centred on the bounding-box
  *     midpoint c: x_int = floor((x - c) * 2^32 / S) + 2^31; frame = {c - S/2 (3), S}
  *     (box_size is ignored).
- * frame: 4 doubles of device memory receiving {origin_x, origin_y, origin_z, side}; the
- * isolated case needs `side` as params.box_size of the later calls.
+ * frame: 8 doubles of device memory (caller-owned); receives {origin_x, origin_y, origin_z,
+ * side} in its first four, the rest is the call's own scratch (the bounding-box reduction
+ * runs in this buffer, so the call allocates nothing, never synchronises, and calls with
+ * different frame buffers may overlap).  The isolated case needs `side` as params.box_size
+ * of the later calls.
  * Errors: G4_ERR_INVALID_ARG for NULL pointers, n < 0 or box_size <= 0 when periodic. */
 g4_status g4_int_coords(const double *pos, int64_t n, int periodic, double box_size,
                         uint32_t *pos_int, double *frame, void *stream);
@@ -269,25 +272,36 @@ g4_status g4_gravity_tree(g4_tree tree, const uint32_t *pos_sorted, const float 
 /* ---- a8: symmetric Cartesian FMM (Sec. 2.4, Sec. 2.5) ----------------------------------- */
 
 /* Bytes of device workspace g4_gravity_fmm needs, sized from the handle's node capacity and
- * n_max (no host synchronisation): field tensors, pass-down lists and the deferred leaf-leaf
- * lists (16 source-leaf entries per particle plus a floor). */
+ * n_max (no host synchronisation): field tensors, pass-down lists and the deferred
+ * particle-pair lists (16 entries per particle plus a floor). */
 g4_status g4_fmm_workspace(g4_tree tree, const g4_params *params, size_t *bytes);
 
-/* Forces for all n particles by the dual tree walk: node pairs either interact by the
- * symmetric expansion (field added to both nodes) or both are opened ("open both"; a leaf is
- * never opened, two leaves interact particle by particle; a node paired with itself is
- * replaced by all pairs of its daughters).  Criterion G M_max / r^2 (l_max/r)^(p-1) <
- * alpha min |a|_min (or (l_A + l_B)/r < theta), touching nodes never interact, pairs whose
- * nearest faces are beyond r_cut are dropped.  Fields are passed down (L2L) and evaluated
- * at the particles (L2P).  Leaf-leaf interactions are recorded during the dual walk and
+/* Forces for all n particles by the dual tree walk over pairs of cells, a cell being a node or
+ * a single particle (Sec. 2.4: "interacting pairs of nodes or particles"; a particle is a cell
+ * of side 0 with Q_0 = m).  A pair interacts by the symmetric expansion (fields added to both
+ * cells; at a particle the field is evaluated on the spot), or fails and is opened: both cells
+ * ("open both"), a leaf into its particles, a particle never; two particles interact directly
+ * (pair kernel).  A node paired with itself is replaced by all pairs of its daughters.
+ * Criterion G M_max / r^2 (l_max/r)^(p-1) < alpha min |a|_min (a particle contributes its own
+ * mass, side 0 and |a_old|), or (l_A + l_B)/r < theta; with the exclusion zone no pair
+ * interacts whose centre separation is within max(l_A, l_B) along every axis (touching nodes,
+ * a particle inside a node's exclusion cube); pairs closer than 2.8 max(eps) are opened;
+ * pairs whose nearest faces are beyond r_cut are dropped.  Node fields are passed down (L2L)
+ * and evaluated at the particles (L2P).  Particle pairs are recorded during the dual walk and
  * evaluated afterwards by a separate kernel with the tree walk's particle-particle phase
  * (when the workspace's lists are full, the dual walk evaluates them itself: same
- * interactions, possibly other rounding order).  Outputs as for g4_gravity_tree (counts: PP,
- * node-node); momentum_out (3 doubles of device memory, nullable) receives sum m a in FP64. */
+ * interactions, possibly other rounding order).
+ *   aold_sorted: |a_old| per sorted particle (required by the relative criterion; may be NULL
+ *          for the geometric one).  The nodes' |a|_min come from g4_multipoles.
+ *   counts: 3 x n uint32 (nullable): particle pairs of the particle, particle-node terms
+ *          evaluated at the particle, node-node fields reaching its leaf.
+ *   momentum_out: 3 doubles of device memory (nullable), receives sum m a in FP64.
+ * Outputs otherwise as for g4_gravity_tree. */
 g4_status g4_gravity_fmm(g4_tree tree, const uint32_t *pos_sorted, const float *mass_sorted,
-                         const uint8_t *cls_sorted, const g4_params *params, float *acc,
-                         float *pot, uint32_t *counts, double *momentum_out, void *workspace,
-                         size_t workspace_bytes, void *stream);
+                         const uint8_t *cls_sorted, const float *aold_sorted,
+                         const g4_params *params, float *acc, float *pot, uint32_t *counts,
+                         double *momentum_out, void *workspace, size_t workspace_bytes,
+                         void *stream);
 
 /* ---- learned cost model for scheduling the walk (no counterpart in the paper's method; its
  *      load-balancing cost q_i is the interaction count of the last force computation,

@@ -45,7 +45,7 @@ typedef struct {
     int exclusion;     /* 1: exclusion zone around node centres (Sec. 2.2.3) */
     double G;          /* gravitational constant */
     int n_eps;         /* number of softening classes */
-    const double *eps; /* softening length eps_0 per class (Sec. 2.9) */
+    const double *eps; /* softening length eps_0 per class (Sec. 2.7) */
     int keep_qp;       /* FMM: 1 keeps Q_p in the potential (Sec. 2.4 drops it by default) */
 } or_params;
 
@@ -551,7 +551,7 @@ static double or_sep(uint32_t a, uint32_t b, const or_params *P)
  *   - an internal node is opened if the particle lies inside the node's cube, or inside the
  *     exclusion cube of half-width l around the geometric centre (Sec. 2.2.3, reading of
  *     Fig. FigTREESketch), or if r < 2.8 max(eps_i, eps_max(node)) (multipoles are always
- *     unsoftened, reading of Sec. 2.9), or if the opening criterion fails:
+ *     unsoftened, reading of Sec. 2.7), or if the opening criterion fails:
  *       relative  G M / r^2 (l / r)^p < alpha |a_old|     (Eq. eqnrelcriterion)
  *       geometric l / r < theta_c;
  *     otherwise its multipole expansion is used.                                          */

@@ -273,7 +273,7 @@ __global__ void k_expand_chunks(const int32_t *__restrict__ chunk_order, int nch
 // every K-th source of the group's source list (and, for k = 0, the multipoles).  Lanes stay
 // full; the parts' sums are combined in part order by whichever part finishes last.
 
-constexpr int ITEM_SPLIT_MAX = 8;
+constexpr int ITEM_SPLIT_MAX = G4_ITEM_SPLIT_MAX;
 
 // predicted cost of each 32-sink group (sequential sum: deterministic)
 __global__ void k_group_cost(const float *__restrict__ pred, int n, int ngroups,

@@ -11,6 +11,7 @@
 #define G4_NLEVELS 22
 #define G4_WALK_QCAP 4096            // walk frontier ring per warp (power of two)
 #define G4_WALK_BLOCKS_PER_SM 8      // persistent walk: 4-warp blocks launched per SM
+#define G4_ITEM_SPLIT_MAX 8          // largest number of source parts of a split walk group
 
 // -------------------------------------------------------------------------------------------
 // error reporting (thread-local last error, status codes)

@@ -22,8 +22,29 @@ __global__ void k_int_coords_periodic(const double *__restrict__ pos, int64_t n,
     }
 }
 
-// bounding box, stage 1: per-block min/max of each axis
-__global__ void k_bbox_partial(const double *__restrict__ pos, int64_t n, double *__restrict__ part)
+// Bounding box of an isolated set, accumulated in the caller's frame buffer (no scratch):
+// doubles are mapped to unsigned integers that order like them (sign bit set: all bits
+// inverted; otherwise the sign bit set), so atomicMin / atomicMax give exact minima / maxima.
+__device__ __forceinline__ unsigned long long ord_of(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double of_ord(unsigned long long v)
+{
+    return __longlong_as_double((long long)((v >> 63) ? (v & 0x7fffffffffffffffull) : ~v));
+}
+
+// stage 0: frame[0..2] = ord(+inf) (minima), frame[3..5] = ord(-inf) (maxima)
+__global__ void k_bbox_init(double *__restrict__ frame)
+{
+    unsigned long long *f = reinterpret_cast<unsigned long long *>(frame);
+    if (threadIdx.x < 3) f[threadIdx.x] = ord_of(INFINITY);
+    else if (threadIdx.x < 6) f[threadIdx.x] = ord_of(-INFINITY);
+}
+
+// stage 1: per-block minima / maxima of each axis, folded into the frame with atomics
+__global__ void k_bbox_partial(const double *__restrict__ pos, int64_t n, double *__restrict__ frame)
 {
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -49,20 +70,22 @@ __global__ void k_bbox_partial(const double *__restrict__ pos, int64_t n, double
         double v = s[threadIdx.x][0];
         for (int j = 1; j < nw; j++)
             v = threadIdx.x < 3 ? fmin(v, s[threadIdx.x][j]) : fmax(v, s[threadIdx.x][j]);
-        part[blockIdx.x * 6 + threadIdx.x] = v;
+        unsigned long long *f = reinterpret_cast<unsigned long long *>(frame);
+        if (threadIdx.x < 3) atomicMin(f + threadIdx.x, ord_of(v));
+        else atomicMax(f + threadIdx.x, ord_of(v));
     }
 }
 
-// bounding box, stage 2: frame = {c - S/2, S}; S = smallest power of two >= 2 * extent
-__global__ void k_bbox_frame(const double *__restrict__ part, int nb, double *__restrict__ frame)
+// stage 2: frame = {c - S/2, S, c}; S = smallest power of two >= 2 * extent
+__global__ void k_bbox_frame(double *__restrict__ frame)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nb; b++)
-        for (int k = 0; k < 3; k++) {
-            lo[k] = fmin(lo[k], part[6 * b + k]);
-            hi[k] = fmax(hi[k], part[6 * b + 3 + k]);
-        }
+    const unsigned long long *f = reinterpret_cast<const unsigned long long *>(frame);
+    double lo[3], hi[3];
+    for (int k = 0; k < 3; k++) {
+        lo[k] = of_ord(f[k]);
+        hi[k] = of_ord(f[3 + k]);
+    }
     double ext = 0.0, c[3];
     for (int k = 0; k < 3; k++) {
         c[k] = __dmul_rn(0.5, __dadd_rn(lo[k], hi[k]));
@@ -72,14 +95,21 @@ __global__ void k_bbox_frame(const double *__restrict__ part, int nb, double *__
     double S = 1.0;
     if (ext > 0.0) {
         int e;
-        double f = frexp(2.0 * ext, &e);
-        S = (f == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+        double fr = frexp(2.0 * ext, &e);
+        S = (fr == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
     }
     for (int k = 0; k < 3; k++) frame[k] = __dsub_rn(c[k], 0.5 * S);
     frame[3] = S;
     frame[4] = c[0];
     frame[5] = c[1];
     frame[6] = c[2];
+    frame[7] = 0.0;
+}
+
+// periodic frame {0, 0, 0, L} (written on the device: no host copy, no synchronisation)
+__global__ void k_frame_periodic(double *__restrict__ frame, double L)
+{
+    if (threadIdx.x < 8) frame[threadIdx.x] = threadIdx.x == 3 ? L : 0.0;
 }
 
 __global__ void k_int_coords_isolated(const double *__restrict__ pos, int64_t n,
@@ -477,14 +507,18 @@ g4_status g4_sort_pairs_u64(const uint64_t *keys_in, uint64_t *keys_out, int32_t
     uint32_t *cnt = (uint32_t *)p;
     p += align256(sizeof(uint32_t) * 256 * (size_t)ntiles);
     uint32_t *tot = (uint32_t *)p;
-    static int smem_set_dev = -1;   // opt in to the tile's dynamic shared memory once per device
+    // opt in to the tile's dynamic shared memory once per device (flags per device, set
+    // atomically, so that threads and devices do not repeat the call -- in particular not
+    // during a later stream capture)
+    static int smem_set[64] = {0};
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (smem_set_dev != dev) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return g4_fail(G4_ERR_CUDA, "radix sort: no usable device");
+    if (!__atomic_load_n(&smem_set[dev], __ATOMIC_ACQUIRE)) {
         cudaError_t e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)SCATTER_SMEM);
         if (e != cudaSuccess) return g4_cuda_check(e, "radix sort: shared memory opt-in");
-        smem_set_dev = dev;
+        __atomic_store_n(&smem_set[dev], 1, __ATOMIC_RELEASE);
     }
     int passes = (key_bits + 7) / 8;
     if (passes & 1) passes++;   // even pass count: the result lands in keys_out
@@ -595,38 +629,17 @@ extern "C" g4_status g4_int_coords(const double *pos, int64_t n, int periodic, d
         return g4_fail(G4_ERR_INVALID_ARG, "g4_int_coords: box_size must be > 0");
     cudaStream_t st = (cudaStream_t)stream;
     if (periodic) {
-        double h[4] = {0.0, 0.0, 0.0, box_size};
-        g4_status s = g4_cuda_check(
-            cudaMemcpyAsync(frame, h, sizeof(h), cudaMemcpyHostToDevice, st), "frame copy");
-        if (s != G4_OK) return s;
-        // the host array must stay valid until the copy ran
-        s = g4_cuda_check(cudaStreamSynchronize(st), "frame copy");
-        if (s != G4_OK) return s;
+        k_frame_periodic<<<1, 32, 0, st>>>(frame, box_size);
         if (n > 0) k_int_coords_periodic<<<g4_blocks_for(n, 256), 256, 0, st>>>(pos, n, box_size, pos_int);
-        return g4_launch_check("int coords", n > 0 ? 1 : 0);
+        return g4_launch_check("int coords", n > 0 ? 2 : 1);
     }
     if (n == 0) return g4_fail(G4_ERR_INVALID_ARG, "g4_int_coords: isolated set needs n > 0");
-    // frame needs 7 doubles of scratch; use a small static device buffer per call sequence
-    static double *part = nullptr;
-    static int part_cap = 0;
-    int nb = g4_blocks_for(n, 256, 2);
-    if (part_cap < nb + 1) {
-        if (part) cudaFree(part);
-        if (cudaMalloc(&part, sizeof(double) * 6 * (nb + 1) + sizeof(double) * 8) != cudaSuccess) {
-            part = nullptr;
-            part_cap = 0;
-            return g4_fail(G4_ERR_OOM, "g4_int_coords: scratch allocation failed");
-        }
-        part_cap = nb + 1;
-    }
-    double *fr7 = part + 6 * part_cap;
-    k_bbox_partial<<<nb, 256, 0, st>>>(pos, n, part);
-    k_bbox_frame<<<1, 32, 0, st>>>(part, nb, fr7);
-    k_int_coords_isolated<<<g4_blocks_for(n, 256), 256, 0, st>>>(pos, n, fr7, pos_int);
-    g4_status s = g4_cuda_check(
-        cudaMemcpyAsync(frame, fr7, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st), "frame");
-    if (s != G4_OK) return s;
-    return g4_launch_check("int coords (isolated)", 3);
+    // the bounding box is reduced into the caller's frame buffer itself (8 doubles)
+    k_bbox_init<<<1, 32, 0, st>>>(frame);
+    k_bbox_partial<<<g4_blocks_for(n, 256, 2), 256, 0, st>>>(pos, n, frame);
+    k_bbox_frame<<<1, 32, 0, st>>>(frame);
+    k_int_coords_isolated<<<g4_blocks_for(n, 256), 256, 0, st>>>(pos, n, frame, pos_int);
+    return g4_launch_check("int coords (isolated)", 4);
 }
 
 extern "C" g4_status g4_gather(const int32_t *perm, int64_t n, const uint32_t *pos_in,

@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 
 #include "g4_kernels.cuh"
+#include "g4_pp_fp16.h"
 
 namespace g4k {
 
@@ -16,8 +17,8 @@ constexpr int PP_STAGE = 128;   // sources staged per pass
 // most 1 + 2 sqrt(3) e + 3 e^2, plus ~0.0016 of rounding in the FP16 sums.  The threshold is
 // that bound (with slack, rounded up), so no pair inside r_cut is missed: ~1.012 r_cut^2 for
 // compact groups, wider for spread ones.  Beyond PP_FP16_RMAX (where the threshold reaches 20)
-// every staged source is a candidate.
-constexpr float PP_FP16_RMAX = 2048.f;
+// every staged source is a candidate.  The constants are in g4_pp_fp16.h.
+constexpr float PP_FP16_RMAX = G4_PP_FP16_RMAX;
 
 // pending source leaves and the staged sources of one warp
 template <int LB> struct PPSmem {
@@ -35,6 +36,10 @@ template <int LB> struct PPSmem {
 template <typename T> __device__ __forceinline__ T par(double d, float f);
 template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
 template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
+
+// largest power of two <= n; a binary search over n + 1 pending leaves starts with that step,
+// so that every index up to n is reachable
+__host__ __device__ constexpr int pow2_floor(int n) { return n < 2 ? 1 : 2 * pow2_floor(n / 2); }
 
 // Slot of staged source u in the candidate masks.  The FP16x2 test handles sources 2j, 2j+1
 // of a 32-source block together and sets bits j and 16 + j of the block's mask word, so the
@@ -108,9 +113,10 @@ __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf
     const float R = __uint_as_float(__reduce_max_sync(
         0xffffffffu, __float_as_uint(fmaxf(fabsf(xr), fmaxf(fabsf(yr), fabsf(zr))) * inv_rc)));
     const bool test16 = TREEPM && A.pp_cut && R <= PP_FP16_RMAX;
-    const float e16 = (2.f * R + 2.f) * (1.f / 2048.f);
-    const __half2 nlim = __half2half2(
-        __float2half_rd(-((1.f + 3.4642f * e16 + 3.f * e16 * e16) * 1.002f + 0.002f)));
+    const float e16 = (G4_PP_FP16_EA * R + G4_PP_FP16_EB) * (1.f / G4_PP_FP16_ULP);
+    const __half2 nlim = __half2half2(__float2half_rd(
+        -((1.f + G4_PP_FP16_C1 * e16 + G4_PP_FP16_C2 * e16 * e16) * G4_PP_FP16_SLACK_MUL +
+          G4_PP_FP16_SLACK_ADD)));
     const __half2 sx2 = __float2half2_rn(xr * inv_rc), sy2 = __float2half2_rn(yr * inv_rc),
                   sz2 = __float2half2_rn(zr * inv_rc);
     // Batch bb takes sources bb, bb + nbat, bb + 2 nbat, ...: every batch samples the whole
@@ -130,7 +136,7 @@ __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf
         tq[q] = kp + Kp * ((q * 32 + lane) * nbat);
     }
 #pragma unroll
-    for (int step = LB / 2; step >= 1; step >>= 1)
+    for (int step = pow2_floor(LB - 1); step >= 1; step >>= 1)
 #pragma unroll
         for (int q = 0; q < PP_STAGE / 32; q++) {
             const int c = lq[q] + step;

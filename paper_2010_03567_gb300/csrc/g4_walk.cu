@@ -161,8 +161,8 @@ k_walk(const WalkArgs A)
             kp = it.z & 255;
             Kp = it.z >> 8;
             pslot = it.w;
-            if (s0 < 0 || s0 >= s_end || Kp < 1 || kp >= Kp ||
-                (Kp > 1 && (pslot < 0 || pslot >= A.part_cap))) {
+            if (s0 < 0 || s0 >= s_end || it.y > 32 || Kp < 1 || Kp > G4_ITEM_SPLIT_MAX ||
+                kp >= Kp || (Kp > 1 && (pslot < 0 || pslot >= A.part_cap))) {
                 if (lane == 0) atomicOr(A.flags, G4_FLAG_LISTCAP);   // malformed item: reported
                 continue;
             }
@@ -388,7 +388,7 @@ k_walk(const WalkArgs A)
         } else {
             // split group: store this part's sums; the last part to arrive adds the parts in
             // part order (deterministic) and writes the outputs
-            float *pb = A.part_buf + (((size_t)pslot * 8 + kp) * 32 + lane) * 6;
+            float *pb = A.part_buf + (((size_t)pslot * G4_ITEM_SPLIT_MAX + kp) * 32 + lane) * 6;
             pb[0] = (float)(ax + bx);
             pb[1] = (float)(ay + by);
             pb[2] = (float)(az + bz);
@@ -405,7 +405,7 @@ k_walk(const WalkArgs A)
                 float sx = 0.f, sy = 0.f, sz = 0.f, sp = 0.f;
                 uint32_t cp = 0, cn = 0;
                 for (int q = 0; q < Kp; q++) {
-                    const float *qb = A.part_buf + (((size_t)pslot * 8 + q) * 32 + lane) * 6;
+                    const float *qb = A.part_buf + (((size_t)pslot * G4_ITEM_SPLIT_MAX + q) * 32 + lane) * 6;
                     sx += __ldcg(qb);
                     sy += __ldcg(qb + 1);
                     sz += __ldcg(qb + 2);

@@ -84,7 +84,7 @@ def _declare(L):
         "g4_tree_moments": ([vp, vp, vp, vp, vp], i32),
         "g4_gravity_tree": ([vp, vp, vp, vp, vp, vp, i64, P, vp, vp, vp, vp], i32),
         "g4_fmm_workspace": ([vp, P, C.POINTER(C.c_size_t)], i32),
-        "g4_gravity_fmm": ([vp, vp, vp, vp, P, vp, vp, vp, vp, vp, C.c_size_t, vp], i32),
+        "g4_gravity_fmm": ([vp, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, C.c_size_t, vp], i32),
         "g4_direct": ([vp, vp, vp, i64, vp, i64, P, vp, vp, vp], i32),
         "g4_mlp_param_count": ([], C.c_int32),
         "g4_cost_features": ([vp, vp, vp, P, vp, vp, vp], i32),
@@ -160,10 +160,13 @@ def launch_count() -> int:
 
 def g4_int_coords(pos: torch.Tensor, periodic: bool, box_size: float = 0.0, out=None, frame=None,
                   stream=None):
-    """pos: (n,3) float64 CUDA -> (pos_int (3,n) int32 holding uint32 bits, frame (4,) f64)."""
+    """pos: (n,3) float64 CUDA -> (pos_int (3,n) int32 holding uint32 bits, frame (8,) f64
+    whose first four entries are {origin_x, origin_y, origin_z, side})."""
     n = pos.shape[0]
     out = out if out is not None else torch.empty((3, n), dtype=torch.int32, device=pos.device)
-    frame = frame if frame is not None else torch.empty(4, dtype=torch.float64, device=pos.device)
+    frame = frame if frame is not None else torch.empty(8, dtype=torch.float64, device=pos.device)
+    if frame.numel() < 8:
+        raise G4Error("frame needs 8 doubles")
     _check(lib().g4_int_coords(_ptr(pos), n, int(periodic), float(box_size), _ptr(out),
                                _ptr(frame), _stream(stream)), "g4_int_coords")
     return out, frame
@@ -315,20 +318,23 @@ class Tree:
         _check(lib().g4_fmm_workspace(self.h, C.byref(p), C.byref(b)), "g4_fmm_workspace")
         return int(b.value)
 
-    def gravity_fmm(self, pos_sorted, mass_sorted, cls_sorted, p: G4Params, workspace=None,
-                    acc=None, pot=None, counts=None, momentum=None, stream=None):
+    def gravity_fmm(self, pos_sorted, mass_sorted, cls_sorted, aold_sorted, p: G4Params,
+                    workspace=None, acc=None, pot=None, counts=None, momentum=None, stream=None):
+        """FMM forces (g4_gravity_fmm).  counts: (3, n) particle pairs, particle-node terms,
+        node-node fields of each particle."""
         n = pos_sorted.shape[1]
         dev = pos_sorted.device
         acc = acc if acc is not None else torch.zeros((3, n), dtype=torch.float32, device=dev)
         pot = pot if pot is not None else torch.zeros(n, dtype=torch.float32, device=dev)
-        counts = counts if counts is not None else torch.zeros((2, n), dtype=torch.int32, device=dev)
+        counts = counts if counts is not None else torch.zeros((3, n), dtype=torch.int32, device=dev)
         momentum = momentum if momentum is not None else torch.zeros(3, dtype=torch.float64, device=dev)
         if workspace is None:
             workspace = torch.empty(self.fmm_workspace(p) + 256, dtype=torch.uint8, device=dev)
         wp = workspace.data_ptr()
         off = (-wp) % 256
         _check(lib().g4_gravity_fmm(self.h, _ptr(pos_sorted), _ptr(mass_sorted), _ptr(cls_sorted),
-                                    C.byref(p), _ptr(acc), _ptr(pot), _ptr(counts), _ptr(momentum),
+                                    _ptr(aold_sorted), C.byref(p), _ptr(acc), _ptr(pot),
+                                    _ptr(counts), _ptr(momentum),
                                     C.c_void_p(wp + off), workspace.numel() - off, _stream(stream)),
                "g4_gravity_fmm")
         return acc, pot, counts, momentum

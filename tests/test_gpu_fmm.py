@@ -1,5 +1,6 @@
-"""GPU FMM (g4_gravity_fmm) against the FP64 oracle FMM: same dual-walk decisions, M2L both
-ways, L2L/L2P downward pass (Sec. 2.4); plus momentum conservation and the alpha = 0 limit."""
+"""GPU FMM (g4_gravity_fmm) against the FP64 oracle FMM: the same dual walk over pairs of nodes
+or particles (node-node, particle-node and particle-particle interactions), fields both ways,
+L2L/L2P downward pass (Sec. 2.4); plus momentum conservation and the alpha = 0 limit."""
 import numpy as np
 import pytest
 
@@ -16,10 +17,13 @@ pytestmark = pytest.mark.gpu
 
 
 def gpu_fmm(ps, q, P, aold):
+    """GPU FMM through the C ABI; caller order.  Counts (n, 3): particle pairs, particle-node
+    terms, node-node fields of each particle."""
     tg = g4.TreeGravity(ps.n, P)
     tg.prepare(u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32), None,
                None if aold is None else to_dev(torch, aold, torch.float32), P)
-    acc, pot, cnt, mom = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, P)
+    acc, pot, cnt, mom = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None,
+                                             None if aold is None else tg.aold_s, P)
     torch.cuda.synchronize()
     tg.tree.status()
     perm = tg.perm.cpu().numpy()
@@ -27,19 +31,30 @@ def gpu_fmm(ps, q, P, aold):
     a[perm] = acc.cpu().numpy().T
     p = np.empty(ps.n)
     p[perm] = pot.cpu().numpy()
-    c = np.empty((ps.n, 2), np.int64)
+    c = np.empty((ps.n, 3), np.int64)
     c[perm] = cnt.cpu().numpy().T
     return a, p, c, mom.cpu().numpy()
 
 
 def oracle_fmm(ps, q, OP, aold, leaf=8):
+    """Oracle FMM; caller order.  Returns acc, pot, totals [NN, PN, PP], per-particle counts
+    (n, 2): particle pairs, particle-node terms."""
     run = oracle.prepare(q, ps.mass, None, aold, OP, leaf)
-    acc_s, pot_s, cnt = run.tree.fmm(OP)
+    acc_s, pot_s, cnt, pc_s = run.tree.fmm(OP, per_particle=True)
     a = np.empty_like(acc_s)
     a[run.perm] = acc_s
     p = np.empty_like(pot_s)
     p[run.perm] = pot_s
-    return a, p, cnt
+    pc = np.empty_like(pc_s)
+    pc[run.perm] = pc_s
+    return a, p, cnt, pc
+
+
+def same_counts(cg, pc, frac=0.99):
+    """At least `frac` of the particles see exactly the oracle's particle pairs and
+    particle-node terms (FP32 decisions may fall on the other side of a threshold)."""
+    same = (cg[:, 0] == pc[:, 0]) & (cg[:, 1] == pc[:, 1])
+    return np.mean(same) >= frac
 
 
 def _plummer(n=16384):
@@ -53,7 +68,12 @@ def test_fmm_parity_plummer_p4():
     ps, q, box, aold, ad = _plummer()
     kw = dict(alpha=0.0025, order_p=4)
     ag, pg, cg, mom = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), aold)
-    ao, po, co = oracle_fmm(ps, q, oracle_params(ps, box, **kw), aold.astype(np.float64))
+    ao, po, co, pc = oracle_fmm(ps, q, oracle_params(ps, box, **kw), aold.astype(np.float64))
+    # the paper's three kinds of FMM interaction all occur (Sec. 3.2 counts them)
+    assert co[0] > 0 and co[1] > 0 and co[2] > 0
+    assert same_counts(cg, pc)
+    assert abs(cg[:, 1].sum() - co[1]) <= 0.01 * co[1]
+    assert abs(cg[:, 0].sum() - 2 * co[2]) <= 0.01 * 2 * co[2]
     e = relerr(ag, ao)
     assert np.percentile(e, 99) < 1e-5, np.percentile(e, [50, 99, 100])
     assert np.percentile(np.abs(pg - po) / np.abs(po), 99) < 1e-5
@@ -68,8 +88,9 @@ def test_fmm_parity_plummer_p4():
 def test_fmm_parity_orders_geometric(order):
     ps, q, box, aold, _ = _plummer(4000)
     kw = dict(criterion=1, theta=0.4, order_p=order)
-    ag, pg, _, _ = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), None)
-    ao, po, _ = oracle_fmm(ps, q, oracle_params(ps, box, **kw), None)
+    ag, pg, cg, _ = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), None)
+    ao, po, co, pc = oracle_fmm(ps, q, oracle_params(ps, box, **kw), None)
+    assert co[1] > 0 and same_counts(cg, pc)
     assert np.percentile(relerr(ag, ao), 99) < 1e-5
 
 
@@ -81,8 +102,9 @@ def test_fmm_parity_treepm_box():
     OP = oracle_params(ps, box, **kw)
     ad, _ = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP, r_max=OP.r_cut)
     aold = np.linalg.norm(ad, axis=1).astype(np.float32)
-    ag, pg, _, mom = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), aold)
-    ao, po, _ = oracle_fmm(ps, q, OP, aold.astype(np.float64))
+    ag, pg, cg, mom = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), aold)
+    ao, po, co, pc = oracle_fmm(ps, q, OP, aold.astype(np.float64))
+    assert same_counts(cg, pc)
     assert np.percentile(relerr(ag, ao), 99) < 1e-5
     # the FMM's own error against the hard-cutoff direct sum (shared by the oracle FMM):
     # node pairs straddling r_cut and the sink-side expansion (Sec. 3.1) at alpha = 0.0025
@@ -94,15 +116,16 @@ def test_fmm_alpha0_is_direct_sum():
     ps, q, box, aold, ad = _plummer(3000)
     kw = dict(alpha=0.0, order_p=4)
     ag, pg, cg, _ = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), aold)
-    assert np.all(cg[:, 1] == 0)
+    assert np.all(cg[:, 1] == 0) and np.all(cg[:, 2] == 0)
+    assert np.all(cg[:, 0] == ps.n - 1)   # every pair, directly
     ad2, pd = oracle.direct(q, ps.mass, None, np.arange(ps.n), oracle_params(ps, box))
     assert np.percentile(relerr(ag, ad2), 99) < 1e-5
 
 
 def test_fmm_inwalk_leaf_leaf_when_lists_are_full():
-    """With the deferred leaf-leaf lists almost empty (one entry per particle) the dual walk
-    evaluates the overflowing leaf-leaf work itself: same interactions, same forces to
-    rounding as the deferred pass."""
+    """With the deferred particle-pair lists almost empty (one entry per particle) the dual walk
+    evaluates the overflowing pairs itself: same interactions, same forces to rounding as the
+    deferred pass."""
     L = 24 * 1.953125
     ps = synth.zeldovich(24, L, 2.0, 1003)
     q, box = int_coords(ps)
@@ -115,16 +138,53 @@ def test_fmm_inwalk_leaf_leaf_when_lists_are_full():
 
 def test_fmm_sparse_leaves_keep_pairs_near_cutoff():
     """Sparse pairs 0.99 r_cut apart: sink leaves span many r_cut, beyond the range where the
-    FP16 candidate test is exact; the leaf-leaf pass must still keep every pair."""
+    FP16 candidate test is exact; the particle-pair pass must still keep every pair."""
     L = 1.0
     rc = L / 1000
     ps = synth.sparse_pairs(2048, L, 0.99 * rc, 7001)
     q, box = int_coords(ps)
     kw = dict(alpha=0.0, order_p=4, r_s=rc / 4.5, r_cut_factor=4.5)
-    aold = np.ones(ps.n, np.float32)   # alpha = 0: leaf-leaf pairs only
+    aold = np.ones(ps.n, np.float32)   # alpha = 0: particle pairs only
     ag, pg, cg, _ = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), aold)
-    assert np.all(cg[:, 1] == 0)
+    assert np.all(cg[:, 1] == 0) and np.all(cg[:, 2] == 0)
     OP = oracle_params(ps, box, **kw)
     ad, _ = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP, r_max=OP.r_cut)
     # a dropped partner would leave its particle with no force at all
     assert np.percentile(relerr(ag, ad), 99) < 1e-5 and relerr(ag, ad).max() < 1e-3
+
+
+def test_fmm_parity_two_softening_classes_leaf_above_32():
+    """Leaves of up to 48 particles (two 32-sink chunks per leaf: the particle walk and the
+    particle pairs per chunk) and two softening classes (eps_ij = max(eps_i, eps_j)); the
+    same interactions as the oracle."""
+    ps = synth.plummer(6000, 1101)
+    ps.eps_class[::3] = 1
+    ps.eps_table = np.array([0.01, 0.03])
+    q, box = int_coords(ps)
+    OPd = oracle_params(ps, box)
+    cls = ps.eps_class
+    ad, _ = oracle.direct(q, ps.mass, cls, np.arange(ps.n), OPd)
+    aold = np.linalg.norm(ad, axis=1).astype(np.float32)
+    kw = dict(alpha=0.001, order_p=3, leaf_max=48)
+    P = gpu_params(g4, ps, box, **kw)
+    tg = g4.TreeGravity(ps.n, P, with_cls=True)
+    tg.prepare(u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32),
+               to_dev(torch, cls, torch.uint8), to_dev(torch, aold, torch.float32), P)
+    acc, pot, cnt, _ = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, tg.cls_s, tg.aold_s, P)
+    torch.cuda.synchronize()
+    tg.tree.status()
+    perm = tg.perm.cpu().numpy()
+    ag = np.empty((ps.n, 3))
+    ag[perm] = acc.cpu().numpy().T
+    cg = np.empty((ps.n, 3), np.int64)
+    cg[perm] = cnt.cpu().numpy().T
+    OP = oracle_params(ps, box, **kw)
+    run = oracle.prepare(q, ps.mass, cls, aold.astype(np.float64), OP, 48)
+    acc_s, _, co, pc_s = run.tree.fmm(OP, per_particle=True)
+    ao = np.empty_like(acc_s)
+    ao[run.perm] = acc_s
+    pc = np.empty_like(pc_s)
+    pc[run.perm] = pc_s
+    assert co[1] > 0
+    assert same_counts(cg, pc)
+    assert np.percentile(relerr(ag, ao), 99) < 1e-5

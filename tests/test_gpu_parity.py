@@ -42,7 +42,10 @@ def test_int_coords_bit_exact(kind):
     else:
         q, fr = oracle.int_coords_isolated(ps.pos)
     assert np.array_equal(u32_host(qg), q)
-    assert np.array_equal(frame.cpu().numpy(), fr)
+    assert np.array_equal(frame.cpu().numpy()[:4], fr)
+    # a second call into the same frame buffer (its scratch part holds the first call's state)
+    qg2, frame2 = g4.g4_int_coords(pos, ps.periodic, ps.box_size, frame=frame)
+    assert np.array_equal(u32_host(qg2), q) and np.array_equal(frame2.cpu().numpy()[:4], fr)
 
 
 @pytest.mark.parametrize("n", [1, 2, 7, 4095, 4096, 4097, 100003])
@@ -146,8 +149,9 @@ def test_walk_parity_plummer_relative():
     assert np.percentile(ep, 99) < PARITY_P99
     same = np.all(cg == co, axis=1)
     assert same.mean() > 0.99, same.mean()
-    # accuracy against the FP64 direct sum (the method's own error at alpha = 0.0025)
-    assert np.percentile(relerr(ag, ad), 99) < 1e-2
+    # accuracy against the FP64 direct sum (the method's own error at alpha = 0.0025): the
+    # headline target, 99th percentile below 1e-3
+    assert np.percentile(relerr(ag, ad), 99) < 1e-3
 
 
 @pytest.mark.parametrize("order", [1, 2, 4, 5])

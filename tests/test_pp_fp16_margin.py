@@ -12,19 +12,27 @@ import re
 import numpy as np
 import pytest
 
-HDR = pathlib.Path(__file__).resolve().parents[1] / "paper_2010_03567_gb300" / "csrc" / "g4_pp.cuh"
+HDR = pathlib.Path(__file__).resolve().parents[1] / "paper_2010_03567_gb300" / "csrc" / "g4_pp_fp16.h"
+
+
+def _consts():
+    """The candidate test's constants, read from the header the kernel includes."""
+    c = dict(re.findall(r"#define G4_PP_FP16_(\w+) ([0-9.]+)f", HDR.read_text()))
+    keys = ("RMAX", "EA", "EB", "ULP", "C1", "C2", "SLACK_MUL", "SLACK_ADD")
+    assert all(k in c for k in keys), c
+    return {k: np.float32(float(c[k])) for k in keys}
 
 
 def _rmax():
-    m = re.search(r"constexpr float PP_FP16_RMAX = ([0-9.]+)f;", HDR.read_text())
-    assert m, "PP_FP16_RMAX not found"
-    return float(m.group(1))
+    return float(_consts()["RMAX"])
 
 
-def test_threshold_formula_matches_the_kernel():
-    src = " ".join(HDR.read_text().split())
-    assert "const float e16 = (2.f * R + 2.f) * (1.f / 2048.f);" in src
-    assert "__float2half_rd(-((1.f + 3.4642f * e16 + 3.f * e16 * e16) * 1.002f + 0.002f))" in src
+def test_threshold_constants_cover_the_error_bound():
+    """The slack terms are at least the bound's own coefficients: 2 sqrt(3) for e and 3 for
+    e^2 (the rest of this file checks the rounded result on random pairs)."""
+    c = _consts()
+    assert c["C1"] >= 2 * np.sqrt(3.0) - 1e-4 and c["C2"] >= 3.0
+    assert c["SLACK_MUL"] >= 1.0 and c["SLACK_ADD"] >= 0.0 and c["ULP"] == 2048.0
 
 
 def _h(x):
@@ -32,10 +40,12 @@ def _h(x):
 
 
 def _threshold(R):
-    """Negative FP16 threshold for radius R, rounded toward -inf as __float2half_rd does."""
-    e = np.float32((2.0 * R + 2.0) / 2048.0)
-    lim = np.float32((np.float32(1.0) + np.float32(3.4642) * e + np.float32(3.0) * e * e)
-                     * np.float32(1.002) + np.float32(0.002))
+    """Negative FP16 threshold for radius R (the kernel's formula with the header's constants),
+    rounded toward -inf as __float2half_rd does."""
+    c = _consts()
+    e = np.float32((c["EA"] * np.float32(R) + c["EB"]) / c["ULP"])
+    lim = np.float32((np.float32(1.0) + c["C1"] * e + c["C2"] * e * e) * c["SLACK_MUL"]
+                     + c["SLACK_ADD"])
     v = np.float16(-lim)
     if float(v) > -float(lim):
         v = np.nextafter(v, np.float16(-np.inf))
