@@ -40,12 +40,24 @@ SEED = 1003
 # count as one operation each)
 FLOPS_PP = 35
 FLOPS_PN = {1: 40, 2: 110, 3: 170, 4: 300, 5: 480}
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12      # SMs x FP32 lanes x FMA x max clock
-# DRAM bytes (read + write) of one k_walk launch of the headline workload, from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum, single-pass capture of the timed walk; the
-# command is in profiles/ncu_walk_dram_256cubed.md).  Reported as roofline.traffic for the
-# default workload only; re-measured whenever the walk kernel changes.
-WALK_DRAM_BYTES_256 = None   # walk kernel changed since the last capture
+FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (Blackwell)
+SM_CLOCK_MAX_GHZ = 2.070    # maximum SM clock of a GB300
+
+
+def fp32_peak_tflops():
+    """FP32 FMA peak of the current GPU: its SM count x 128 lanes x 2 flops x maximum clock
+    (no FP32 figure is measured for this GPU type, so the unit counts and clock are used)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * FP32_LANES_PER_SM * 2 * SM_CLOCK_MAX_GHZ * 1e9 / 1e12, \
+        f"{sms} SMs (device property) x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {SM_CLOCK_MAX_GHZ} GHz"
+
+
+# DRAM bytes (read + write) of one k_walk launch of the headline workload: the single-pass ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed walk, 611,016,960 +
+# 451,179,520 bytes.  Reported as roofline.traffic for the default workload only; set to
+# None whenever the walk kernel changes until it is captured again.
+WALK_DRAM_BYTES_256 = 1062196480
 
 
 def hbm_peak_gbs():
@@ -65,7 +77,7 @@ STAGE_BYTES = {"keys_sort": (20 + 8 * 2 * 12, 0), "gather": (44, 0), "build": (2
                "multipoles": (16, 128), "scatter": (36, 0)}
 
 
-LEAF_MAX = 32          # tuned on GB300 (profiles/autotune_leaf_256cubed.md)
+LEAF_MAX = 32          # tuned on GB300 with autotune.tune_leaf on the 256^3 box
 
 
 def workload_params(n_side=N_SIDE, L=L_BOX, leaf_max=None):
@@ -376,6 +388,7 @@ def run_gpu(args, rank, world):
             sample_ref = (sinks, ad)
         for name, fn in (("cost_model", lambda: extra_cost_model(tg, P, n)),
                          ("fmm", lambda: extra_fmm(pos_int, mass, aold, wp, n, sample_ref)),
+                         ("treepm", lambda: extra_treepm(pos_int, mass, aold, wp, n)),
                          ("fp64_walk", lambda: extra_fp64(tg, P, n, sample_ref)),
                          ("batched_systems", lambda: extra_forest(wp["leaf_max"])),
                          ("hierarchical_bins", lambda: extra_bins(wp["leaf_max"])),
@@ -396,6 +409,7 @@ def run_gpu(args, rank, world):
                "sample": csample + f" ({treal:.1f} s of CPU time measured)"}
 
     if rank == 0:
+        peak, peak_src = fp32_peak_tflops()
         value = job_throughput(world, n, ms)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -408,15 +422,16 @@ def run_gpu(args, rank, world):
                         "results_equal_device_run": e2e_same},
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "alu", "kernel": "k_walk (tree walk, p=3, TreePM)",
-                             "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
-                             "frac": achieved / FP32_PEAK_TFLOPS,
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "peak_source": peak_src, "frac": achieved / peak,
                              "traffic": WALK_DRAM_BYTES_256 if (n_side == N_SIDE and WALK_DRAM_BYTES_256) else None,
                              "traffic_per_sink_bytes": (WALK_DRAM_BYTES_256 / n) if (n_side == N_SIDE and WALK_DRAM_BYTES_256) else None,
                              "walk_ms": walk_ms,
                              "interactions_per_step": {"pp": int(counts[0]), "pn": int(counts[1])}},
                 "tree": {"nodes": nn, "max_level": ml},
-                "interactions_per_s": float((counts[0] + counts[1]) / (walk_ms * 1e-3)),
+                "interactions_per_s": {"pp": float(counts[0] / (walk_ms * 1e-3)),
+                                       "pn": float(counts[1] / (walk_ms * 1e-3)),
+                                       "nn": None},
                 "accuracy": accuracy, "stages": stages, "cpu_baseline": cpu, **extras}
         print(json.dumps(line), flush=True)
     if dist:
@@ -478,6 +493,38 @@ def extra_fmm(pos_int, mass, aold, wp, n, sample_ref):
         res["accuracy_vs_direct"] = {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99))}
     del ws
     return res
+
+
+def extra_treepm(pos_int, mass, aold, wp, n):
+    """Total TreePM forces on the headline box (Sec. 2.3): the tree's short-range walk plus
+    the PM long-range force on a 512^3 mesh (A_smth = r_s / (L / N_grid) = 1.25), with the
+    relative criterion fed the total |a| of the previous step; the PM call alone, and its
+    mesh traffic against the measured HBM bandwidth."""
+    import torch
+    from paper_2010_03567_gb300 import g4
+    ng = 2 * N_SIDE if n == N_SIDE ** 3 else 2 * round(n ** (1 / 3))
+    P = g4.params(**wp)
+    tp = g4.TreePMGravity(n, P, ng)
+    tp.forces(pos_int, mass, None, aold, P)
+    aold_tot = torch.linalg.vector_norm(tp.tg.acc, dim=0).contiguous()   # total |a|
+    ms_step = _time(lambda: tp.forces(pos_int, mass, None, aold_tot, P), 3)
+    tg = tp.tg
+    acc = torch.zeros_like(tg.acc_s)
+    pm = lambda: g4.g4_pm_long_range(tg.pos_s, tg.mass_s, P, ng, acc=acc, pot=None, workspace=tp.ws)
+    ms_pm = _time(pm, 5)
+    # mesh bytes per call: clear (8 N^3), 6 FFT passes and the Green's function (2 x 8 N^3 each),
+    # the CIC sums (8 atomics of 4 B per particle) and the interpolation reads (8 x 13 values
+    # of 8 B per sink, mostly from cache)
+    mesh = 8.0 * ng ** 3
+    bytes_alg = mesh + 7 * 2 * mesh + n * 8 * 4 + n * (12 + 4) + n * 16
+    peak, src = hbm_peak_gbs()
+    cnt = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+    return {"n_grid": ng, "A_smth": wp["r_s"] / (wp["box_size"] / ng), "ms_per_step": ms_step,
+            "forces_per_s": n / (ms_step * 1e-3), "pm_ms": ms_pm,
+            "pm_algorithmic_bytes": bytes_alg, "pm_GB/s": bytes_alg / (ms_pm * 1e-3) / 1e9,
+            "pm_frac_hbm": bytes_alg / (ms_pm * 1e-3) / 1e9 / peak, "hbm_peak_source": src,
+            "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
+            "aold": "total |a| (tree + PM) of the previous step"}
 
 
 def extra_forest(leaf_max):
@@ -739,8 +786,17 @@ def partition_gain(tg, P, n, step, reps=10, train_steps=400):
 
 
 def _errors(a, ref):
-    e = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
-    return {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99)), "max": float(e.max())}
+    """Relative error percentiles |a - ref| / |ref|; sinks whose reference force is exactly zero
+    (no source inside r_cut, e.g. in sparse active subsets) are counted apart, with the number
+    of them where a is not zero as well."""
+    rn = np.linalg.norm(ref, axis=1)
+    z = rn == 0
+    e = np.linalg.norm(a[~z] - ref[~z], axis=1) / rn[~z]
+    out = {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99)), "max": float(e.max())}
+    if z.any():
+        out["zero_reference"] = int(z.sum())
+        out["zero_reference_nonzero_result"] = int(np.count_nonzero(np.linalg.norm(a[z], axis=1)))
+    return out
 
 
 def extra_fp64(tg, P, n, sample_ref):

@@ -303,6 +303,56 @@ g4_status g4_gravity_fmm(g4_tree tree, const uint32_t *pos_sorted, const float *
                          double *momentum_out, void *workspace, size_t workspace_bytes,
                          void *stream);
 
+/* ---- long-range particle-mesh force of the TreePM split (Sec. 2.3) ------------------------ */
+
+/* Bytes of device workspace g4_pm_long_range needs for an n_grid^3 mesh (n_grid a power of two
+ * in [16, 1024]): a complex FP32 mesh (8 n_grid^3 bytes) and the FFT twiddles. */
+g4_status g4_pm_workspace(int32_t n_grid, size_t *bytes);
+
+/* Long-range accelerations and potentials of the TreePM split (Sec. 2.3: the Fourier sum of
+ * Eq. eqnksum, with the sign that makes it add to the short-range part of Eq. eqnpo4 to give
+ * the periodic potential of Eq. eqnpo1), by the particle-mesh steps the paper lists:
+ *   clouds-in-cell assignment of the n sources to a periodic n_grid^3 mesh (mesh points at
+ *   i * L / n_grid); FFT; multiplication with -4 pi G exp(-k^2 r_s^2) / k^2 divided by the
+ *   CIC assignment and interpolation transforms, prod_i sinc^4(k_i Delta / 2) (Delta =
+ *   L / n_grid); inverse FFT; fourth-order differences of the potential; CIC interpolation
+ *   to the n_sinks sink positions.
+ *   pos: sources, 3 x n uint32 SoA (integer coordinates, unit box_size / 2^32); mass: n floats;
+ *   pos_sinks: 3 x n_sinks uint32 SoA (may be pos itself with n_sinks = n);
+ *   params: box_size (L), periodic (must be 1), r_s (> 0), G;
+ *   acc: 3 x n_sinks float SoA, pot: n_sinks floats (nullable); accumulate = 1 adds to them
+ *   (e.g. to the tree's short-range forces of the same sinks), 0 overwrites.
+ *   workspace: >= g4_pm_workspace(n_grid) bytes of device memory, 256-byte aligned.
+ * The mesh sums use FP32 atomics, so results are reproducible to rounding, not bitwise.
+ * Errors: G4_ERR_INVALID_ARG for a non-periodic box, r_s <= 0, a bad n_grid or workspace. */
+g4_status g4_pm_long_range(const uint32_t *pos, const float *mass, int64_t n,
+                           const uint32_t *pos_sinks, int64_t n_sinks, const g4_params *params,
+                           int32_t n_grid, float *acc, float *pot, int accumulate,
+                           void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---- hierarchical time integration (Sec. 4.2) --------------------------------------------- */
+
+/* Kick operator K: vel[i] += dt * acc[i] for the particles listed in idx (n_idx sorted or
+ * unsorted indices; idx = NULL: all n).  vel, acc: 3 x n float SoA (device). */
+g4_status g4_kick(float *vel, const float *acc, const int32_t *idx, int64_t n_idx, int64_t n,
+                  double dt, void *stream);
+
+/* Drift operator D: pos[i] += rint(vel[i] * dt * 2^32 / box_size) for the listed particles, on
+ * the integer coordinates (3 x n uint32 SoA): positions stay exact integers and a periodic box
+ * wraps through the 32-bit overflow (Sec. 2.10).  For an isolated set (periodic = 0) a step that
+ * would leave the central half of the integer cube is not applied and sets *flag (1 int32 of
+ * device memory, required then) to 1. */
+g4_status g4_drift(uint32_t *pos, const float *vel, const int32_t *idx, int64_t n_idx, int64_t n,
+                   double dt, const g4_params *params, int32_t *flag, void *stream);
+
+/* Timestep bins: dt_i = sqrt(2 eta eps_i / |a_i|) (eps_i from the particle's softening class,
+ * cls NULL = class 0), bins[i] = the smallest k <= max_bin with dt_max / 2^k <= dt_i (0 for
+ * |a_i| = 0): the power-of-two hierarchy in which the hierarchical scheme splits a system into
+ * slow and fast particles.  acc 3 x n float, bins n uint8 (written at the listed indices). */
+g4_status g4_timestep_bins(const float *acc, const uint8_t *cls, const int32_t *idx, int64_t n_idx,
+                           int64_t n, const g4_params *params, double eta, double dt_max,
+                           int32_t max_bin, uint8_t *bins, void *stream);
+
 /* ---- learned cost model for scheduling the walk (no counterpart in the paper's method; its
  *      load-balancing cost q_i is the interaction count of the last force computation,
  *      Sec. 6.1, which these calls learn to predict) --------------------------------------- */

@@ -112,6 +112,10 @@ def _declare(L):
     L.or_direct.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(_Params), d, vp, vp]
     L.or_fmm.argtypes = [vp, vp, i64, vp, vp, vp, C.POINTER(_Params), vp, vp, vp, vp]
     L.or_moments_points.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.or_ewald_psi.argtypes = [vp, d, d, i32, i32]
+    L.or_ewald_psi.restype = d
+    L.or_ewald_force.argtypes = [vp, d, d, i32, i32, i32, vp]
+    L.or_ewald_force_many.argtypes = [vp, i64, vp, vp, i64, d, d, i32, i32, i32, vp]
     L.or_two_node_tree.argtypes = [vp, i64, vp, vp, i64, i32, d, d, vp, vp]
     L.or_two_node_fmm.argtypes = [vp, vp, i64, vp, vp, i64, i32, d, d, i32, vp, vp, vp, vp]
 
@@ -303,6 +307,29 @@ def two_node_fmm(xa, ma, xb, mb, order: int, r_s: float = 0.0, G: float = 1.0,
     lib().or_two_node_fmm(_p(xa), _p(ma), xa.shape[0], _p(xb), _p(mb), xb.shape[0], int(order),
                           float(r_s), float(G), int(keep_qp), _p(aa), _p(pa), _p(ab), _p(pb))
     return aa, pa, ab, pb
+
+
+# ---- periodic Ewald reference (Sec. 2.1) ------------------------------------------------------
+
+def ewald_psi(x, L: float, alpha: float | None = None, nr: int = 4, nk: int = 8) -> float:
+    """Correction potential psi(x) of Eq. (eqnewal) for a cubic box of side L."""
+    a = 2.0 / L if alpha is None else alpha
+    xx = np.ascontiguousarray(x, np.float64)
+    return float(lib().or_ewald_psi(_p(xx), float(L), float(a), int(nr), int(nk)))
+
+
+def ewald_force(xe, ys, m, L: float, alpha: float | None = None, nr: int = 4, nk: int = 8,
+                kspace_only: bool = False):
+    """Periodic accelerations (G = 1) at the points xe (ne,3) due to masses m at ys (ns,3), by
+    Ewald summation; kspace_only with alpha = 1/(2 r_s): the exact long-range TreePM force."""
+    a = 2.0 / L if alpha is None else alpha
+    xe = np.ascontiguousarray(np.atleast_2d(xe), np.float64)
+    ys = np.ascontiguousarray(np.atleast_2d(ys), np.float64)
+    m = np.ascontiguousarray(np.atleast_1d(m), np.float64)
+    out = np.empty_like(xe)
+    lib().or_ewald_force_many(_p(xe), xe.shape[0], _p(ys), _p(m), ys.shape[0], float(L), float(a),
+                              int(nr), int(nk), int(kspace_only), _p(out))
+    return out
 
 
 def direct(pos_int: np.ndarray, mass, cls, sinks, params: OracleParams, r_max: float = 0.0):

@@ -1197,3 +1197,96 @@ void or_two_node_fmm(const double *xa, const double *ma, int64_t na, const doubl
     free(fA);
     free(fB);
 }
+
+/* ===================================================================================== */
+/* Periodic point-mass potential and force by Ewald summation (Sec. 2.1, Eq. eqnewal): the   */
+/* exact reference for the long-range (PM) part of the TreePM split, Sec. 2.3.             */
+/* ===================================================================================== */
+
+/* Sum over real-space images n with |n_i| <= nr and over wave vectors k = 2 pi m / L,
+ * m != 0, |m_i| <= nk.  alpha: the Ewald split parameter (any value; the result does not
+ * depend on it once both sums have converged). */
+
+/* Correction potential psi(x) of Eq. (eqnewal) for a cubic box of side L:
+ *   psi = 1/|x| + pi/(alpha^2 V) - sum_n erfc(alpha |x + q_n|)/|x + q_n|
+ *         - (4 pi / V) sum_{k != 0} exp(-k^2 / (4 alpha^2)) / k^2 cos(k . x),
+ * with the n = 0 term combined with 1/|x| as erf(alpha |x|)/|x| (finite at x = 0). */
+double or_ewald_psi(const double *x, double L, double alpha, int nr, int nk)
+{
+    const double V = L * L * L, pi = 3.14159265358979323846;
+    double r0 = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    double s = (r0 > 0.0) ? erf(alpha * r0) / r0 : 2.0 * alpha / sqrt(pi);
+    s += pi / (alpha * alpha * V);
+    for (int a = -nr; a <= nr; a++)
+        for (int b = -nr; b <= nr; b++)
+            for (int c = -nr; c <= nr; c++) {
+                if (a == 0 && b == 0 && c == 0) continue;
+                double d[3] = {x[0] + a * L, x[1] + b * L, x[2] + c * L};
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                s -= erfc(alpha * r) / r;
+            }
+    for (int a = -nk; a <= nk; a++)
+        for (int b = -nk; b <= nk; b++)
+            for (int c = -nk; c <= nk; c++) {
+                if (a == 0 && b == 0 && c == 0) continue;
+                double k[3] = {2 * pi * a / L, 2 * pi * b / L, 2 * pi * c / L};
+                double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                s -= 4 * pi / V * exp(-k2 / (4 * alpha * alpha)) / k2 *
+                     cos(k[0] * x[0] + k[1] * x[1] + k[2] * x[2]);
+            }
+    return s;
+}
+
+/* Acceleration of a unit test mass at x due to a unit point mass at the origin in the
+ * periodic box (with the neutralising background), a = -grad Phi with
+ * Phi(x) = pi/(alpha^2 V) - sum_n erfc(alpha s_n)/s_n - (4 pi/V) sum_k e^{-k^2/4alpha^2}/k^2 cos(k.x),
+ * s_n = |x + q_n|:
+ *   a = - sum_n s_vec [erfc(alpha s) + (2 alpha s / sqrt(pi)) exp(-alpha^2 s^2)] / s^3
+ *       - (4 pi / V) sum_k (k / k^2) exp(-k^2 / 4 alpha^2) sin(k . x).
+ * kspace_only = 1 returns only the second sum: with alpha = 1/(2 r_s) that is the exact
+ * long-range force of the TreePM split (the Fourier sum of Eq. eqnksum). */
+void or_ewald_force(const double *x, double L, double alpha, int nr, int nk, int kspace_only,
+                    double *acc)
+{
+    const double V = L * L * L, pi = 3.14159265358979323846;
+    acc[0] = acc[1] = acc[2] = 0.0;
+    if (!kspace_only)
+        for (int a = -nr; a <= nr; a++)
+            for (int b = -nr; b <= nr; b++)
+                for (int c = -nr; c <= nr; c++) {
+                    double d[3] = {x[0] + a * L, x[1] + b * L, x[2] + c * L};
+                    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    if (r == 0.0) continue;
+                    double f = (erfc(alpha * r) + 2.0 * alpha * r / sqrt(pi) * exp(-alpha * alpha * r * r))
+                               / (r * r * r);
+                    for (int i = 0; i < 3; i++) acc[i] -= f * d[i];
+                }
+    for (int a = -nk; a <= nk; a++)
+        for (int b = -nk; b <= nk; b++)
+            for (int c = -nk; c <= nk; c++) {
+                if (a == 0 && b == 0 && c == 0) continue;
+                double k[3] = {2 * pi * a / L, 2 * pi * b / L, 2 * pi * c / L};
+                double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                double f = 4 * pi / V * exp(-k2 / (4 * alpha * alpha)) / k2 *
+                           sin(k[0] * x[0] + k[1] * x[1] + k[2] * x[2]);
+                for (int i = 0; i < 3; i++) acc[i] -= f * k[i];
+            }
+}
+
+/* Many evaluations: acc[i] = sum_j m_j a(x_i - y_j) (OpenMP over the evaluation points). */
+void or_ewald_force_many(const double *xe, int64_t ne, const double *ys, const double *m,
+                         int64_t ns, double L, double alpha, int nr, int nk, int kspace_only,
+                         double *acc)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < ne; i++) {
+        double s[3] = {0, 0, 0};
+        for (int64_t j = 0; j < ns; j++) {
+            double d[3], a[3];
+            for (int ax = 0; ax < 3; ax++) d[ax] = xe[3 * i + ax] - ys[3 * j + ax];
+            or_ewald_force(d, L, alpha, nr, nk, kspace_only, a);
+            for (int ax = 0; ax < 3; ax++) s[ax] += m[j] * a[ax];
+        }
+        for (int ax = 0; ax < 3; ax++) acc[3 * i + ax] = s[ax];
+    }
+}

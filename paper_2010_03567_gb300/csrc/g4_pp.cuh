@@ -55,8 +55,9 @@ __device__ __forceinline__ int cand_bit(int u)
 // positions relative to the group centre in units of r_cut, threshold from the group's FP16
 // error bound, so no pair inside r_cut is missed) and keeps a candidate bit per source; then
 // each lane evaluates only its own candidates with exact integer separations, the exact
-// cutoff and the full kernel.  Without the pair cutoff, or for a group spread wider than
-// PP_FP16_RMAX, every staged source is a candidate.  Leaf masks (lanes that used an
+// cutoff and the full kernel.  Without the pair cutoff, for a group spread wider than
+// PP_FP16_RMAX, or for one reaching within r_cut of half the periodic box from its centre,
+// every staged source is a candidate.  Leaf masks (lanes that used an
 // ancestor's multipole must not see the leaf) are applied per source when a staged leaf does
 // not reach the whole group.  INTU (FP32 TreePM): the pair terms are summed in integer-grid
 // length units with the fast kernel; the caller rescales the sums.  Part kp of Kp (a group
@@ -112,7 +113,12 @@ __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf
     // group radius R in units of r_cut (non-negative floats order like their bit patterns)
     const float R = __uint_as_float(__reduce_max_sync(
         0xffffffffu, __float_as_uint(fmaxf(fabsf(xr), fmaxf(fabsf(yr), fabsf(zr))) * inv_rc)));
-    const bool test16 = TREEPM && A.pp_cut && R <= PP_FP16_RMAX;
+    // The FP16 positions are nearest-image offsets from the group centre, so a source within
+    // r_cut of a sink keeps its true offset only while R + 1 stays below half the box (in r_cut
+    // units); a group reaching that far in a periodic box (a sparse subset, say) would see
+    // such sources wrapped to the other side, so it skips the FP16 test.
+    const float half_box = 2147483648.f * fscale * inv_rc;
+    const bool test16 = TREEPM && A.pp_cut && R <= PP_FP16_RMAX && R + 1.01f < half_box;
     const float e16 = (G4_PP_FP16_EA * R + G4_PP_FP16_EB) * (1.f / G4_PP_FP16_ULP);
     const __half2 nlim = __half2half2(__float2half_rd(
         -((1.f + G4_PP_FP16_C1 * e16 + G4_PP_FP16_C2 * e16 * e16) * G4_PP_FP16_SLACK_MUL +

@@ -86,6 +86,11 @@ def _declare(L):
         "g4_fmm_workspace": ([vp, P, C.POINTER(C.c_size_t)], i32),
         "g4_gravity_fmm": ([vp, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, C.c_size_t, vp], i32),
         "g4_direct": ([vp, vp, vp, i64, vp, i64, P, vp, vp, vp], i32),
+        "g4_pm_workspace": ([C.c_int32, C.POINTER(C.c_size_t)], i32),
+        "g4_kick": ([vp, vp, vp, i64, i64, d, vp], i32),
+        "g4_drift": ([vp, vp, vp, i64, i64, d, P, vp, vp], i32),
+        "g4_timestep_bins": ([vp, vp, vp, i64, i64, P, d, d, C.c_int32, vp, vp], i32),
+        "g4_pm_long_range": ([vp, vp, i64, vp, i64, P, C.c_int32, vp, vp, i32, vp, C.c_size_t, vp], i32),
         "g4_mlp_param_count": ([], C.c_int32),
         "g4_cost_features": ([vp, vp, vp, P, vp, vp, vp], i32),
         "g4_cost_labels": ([vp, i64, C.c_float, vp, vp], i32),
@@ -351,6 +356,34 @@ def g4_direct(pos, mass, cls, p: G4Params, sinks=None, acc=None, pot=None, strea
     return acc, pot
 
 
+# ---- long-range particle-mesh force (TreePM) -------------------------------------------------------
+
+def g4_pm_workspace(n_grid: int) -> int:
+    b = C.c_size_t()
+    _check(lib().g4_pm_workspace(int(n_grid), C.byref(b)), "g4_pm_workspace")
+    return int(b.value)
+
+
+def g4_pm_long_range(pos, mass, p: G4Params, n_grid: int, sinks=None, acc=None, pot=None,
+                     accumulate: bool = False, workspace=None, stream=None):
+    """Long-range PM accelerations (3, ns) and potentials (ns,) at the sinks' integer positions
+    (3, ns) (default: the sources pos (3, n)); accumulate adds into the given acc/pot."""
+    sinks = pos if sinks is None else sinks
+    ns = sinks.shape[1]
+    dev = pos.device
+    acc = acc if acc is not None else torch.zeros((3, ns), dtype=torch.float32, device=dev)
+    pot = pot if pot is not None else torch.zeros(ns, dtype=torch.float32, device=dev)
+    if workspace is None:
+        workspace = torch.empty(g4_pm_workspace(n_grid) + 256, dtype=torch.uint8, device=dev)
+    wp = workspace.data_ptr()
+    off = (-wp) % 256
+    _check(lib().g4_pm_long_range(_ptr(pos), _ptr(mass), int(pos.shape[1]), _ptr(sinks), ns,
+                                  C.byref(p), int(n_grid), _ptr(acc), _ptr(pot), int(bool(accumulate)),
+                                  C.c_void_p(wp + off), workspace.numel() - off, _stream(stream)),
+           "g4_pm_long_range")
+    return acc, pot
+
+
 # ---- whole pipeline ------------------------------------------------------------------------------
 
 class TreeGravity:
@@ -401,6 +434,31 @@ class TreeGravity:
     def forces(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None):
         self.prepare(pos_int, mass, cls, aold, p, stream)
         return self.walk(p, use_aold=aold is not None, stream=stream)
+
+
+class TreePMGravity:
+    """Total TreePM forces (Sec. 2.3): the tree walk's short-range forces plus the PM long-range
+    forces, both on the PH-sorted particles, then one scatter to input order.  The relative
+    opening criterion takes |a_old| of the total force (the paper compares the node error
+    with the total acceleration, PM included)."""
+
+    def __init__(self, n: int, p: G4Params, n_grid: int, node_capacity: int = 0, with_cls: bool = False):
+        self.tg = TreeGravity(n, p, node_capacity, with_cls)
+        self.p = p
+        self.n_grid = n_grid
+        self.ws = torch.empty(g4_pm_workspace(n_grid) + 256, dtype=torch.uint8, device="cuda")
+
+    def forces(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None):
+        p = p or self.p
+        tg = self.tg
+        tg.prepare(pos_int, mass, cls, aold, p, stream)
+        tg.tree.gravity_tree(tg.pos_s, tg.mass_s, tg.cls_s if cls is not None else None,
+                             tg.aold_s if aold is not None else None, p, acc=tg.acc_s, pot=tg.pot_s,
+                             counts=tg.counts, stream=stream)
+        g4_pm_long_range(tg.pos_s, tg.mass_s, p, self.n_grid, acc=tg.acc_s, pot=tg.pot_s,
+                         accumulate=True, workspace=self.ws, stream=stream)
+        g4_scatter(tg.perm, tg.acc_s, tg.pot_s, out=(tg.acc, tg.pot), stream=stream)
+        return tg.acc, tg.pot
 
 
 class HostPipeline:
@@ -732,3 +790,163 @@ class BinnedForces:
     def replay(self):
         self.graph.replay()
         return self.acc, self.pot
+
+
+# ---- hierarchical time integration (Sec. 4.2) -------------------------------------------------------
+
+def g4_kick(vel, acc, dt: float, idx=None, stream=None):
+    n = vel.shape[1]
+    m = n if idx is None else int(idx.shape[0])
+    _check(lib().g4_kick(_ptr(vel), _ptr(acc), _ptr(idx), m, n, float(dt), _stream(stream)), "g4_kick")
+
+
+def g4_drift(pos_int, vel, dt: float, p: G4Params, idx=None, flag=None, stream=None):
+    n = vel.shape[1]
+    m = n if idx is None else int(idx.shape[0])
+    _check(lib().g4_drift(_ptr(pos_int), _ptr(vel), _ptr(idx), m, n, float(dt), C.byref(p), _ptr(flag),
+                          _stream(stream)), "g4_drift")
+
+
+def g4_timestep_bins(acc, p: G4Params, eta: float, dt_max: float, max_bin: int, bins, cls=None, idx=None,
+                     stream=None):
+    n = acc.shape[1]
+    m = n if idx is None else int(idx.shape[0])
+    _check(lib().g4_timestep_bins(_ptr(acc), _ptr(cls), _ptr(idx), m, n, C.byref(p), float(eta),
+                                  float(dt_max), int(max_bin), _ptr(bins), _stream(stream)),
+           "g4_timestep_bins")
+
+
+class SubsetForces:
+    """Forces of a particle subset on itself: the subset is gathered, sorted, gets its own tree
+    (the hierarchical scheme builds the tree over the particles of the current force
+    computation only) and its tree walk or FMM; the results are written into full-size arrays
+    at the subset's indices.  One handle and one set of buffers sized for all n particles."""
+
+    def __init__(self, n: int, p: G4Params, method: str = "fmm", with_cls: bool = False):
+        if method not in ("fmm", "tree"):
+            raise G4Error("method must be 'fmm' or 'tree'")
+        dev = torch.device("cuda")
+        self.n, self.p, self.method = n, p, method
+        self.tree = Tree(n, 4096 + int(n * max(1.5, 3.5 / max(1, int(p.leaf_max)))))
+        self.keys = torch.empty(n, dtype=torch.int64, device=dev)
+        self.perm = torch.empty(n, dtype=torch.int32, device=dev)
+        self.ws = torch.empty(g4_keys_sort_workspace(n) + 256, dtype=torch.uint8, device=dev)
+        f = lambda dt, k=1: torch.empty(k * n, dtype=dt, device=dev)
+        self.pos_sub, self.pos_s = f(torch.int32, 3), f(torch.int32, 3)
+        self.mass_sub, self.mass_s = f(torch.float32), f(torch.float32)
+        self.aold_sub, self.aold_s = f(torch.float32), f(torch.float32)
+        self.cls_sub = f(torch.uint8) if with_cls else None
+        self.cls_s = f(torch.uint8) if with_cls else None
+        self.acc_s, self.acc_sub = f(torch.float32, 3), f(torch.float32, 3)
+        self.pot_s, self.pot_sub = f(torch.float32), f(torch.float32)
+        self.counts = torch.zeros(3 * n, dtype=torch.int32, device=dev)
+        self.fmm_ws = (torch.empty(self.tree.fmm_workspace(p) + 256, dtype=torch.uint8, device=dev)
+                       if method == "fmm" else None)
+
+    def __call__(self, pos_all, mass_all, cls_all, aold_all, idx, acc_out, pot_out, p=None, stream=None):
+        p = p or self.p
+        k = int(idx.shape[0])
+        n_all = int(pos_all.shape[1])
+        v3 = lambda t: t[:3 * k].view(3, k)
+        cls_sub = self.cls_sub[:k] if cls_all is not None else None
+        aold_sub = self.aold_sub[:k] if aold_all is not None else None
+        _check(lib().g4_gather_subset(_ptr(idx), k, n_all, _ptr(pos_all), _ptr(mass_all), _ptr(cls_all),
+                                      _ptr(aold_all), _ptr(v3(self.pos_sub)), _ptr(self.mass_sub[:k]),
+                                      _ptr(cls_sub), _ptr(aold_sub), _stream(stream)), "g4_gather_subset")
+        g4_keys_sort(v3(self.pos_sub), self.keys[:k], self.perm[:k], self.ws, stream)
+        cls_s = self.cls_s[:k] if cls_all is not None else None
+        aold_s = self.aold_s[:k] if aold_all is not None else None
+        g4_gather(self.perm[:k], v3(self.pos_sub), self.mass_sub[:k], cls_sub, aold_sub,
+                  out=(v3(self.pos_s), self.mass_s[:k], cls_s, aold_s), stream=stream)
+        self.tree.build(self.keys[:k], v3(self.pos_s), p, stream)
+        self.tree.multipoles(v3(self.pos_s), self.mass_s[:k], cls_s, aold_s, p, stream)
+        if self.method == "fmm":
+            self.tree.gravity_fmm(v3(self.pos_s), self.mass_s[:k], cls_s, aold_s, p, workspace=self.fmm_ws,
+                                  acc=v3(self.acc_s), pot=self.pot_s[:k], counts=v3(self.counts),
+                                  stream=stream)
+        else:
+            self.tree.gravity_tree(v3(self.pos_s), self.mass_s[:k], cls_s, aold_s, p, acc=v3(self.acc_s),
+                                   pot=self.pot_s[:k], counts=self.counts[:2 * k].view(2, k), stream=stream)
+        g4_scatter(self.perm[:k], v3(self.acc_s), self.pot_s[:k], out=(v3(self.acc_sub), self.pot_sub[:k]),
+                   stream=stream)
+        _check(lib().g4_scatter_subset(_ptr(idx), k, n_all, _ptr(v3(self.acc_sub)), _ptr(self.pot_sub[:k]),
+                                       _ptr(acc_out), _ptr(pot_out), _stream(stream)), "g4_scatter_subset")
+
+
+class HierarchicalKDK:
+    """Hierarchical time integration (Sec. 4.2) on the GPU.  A step dt of a set P with known
+    forces a_P (sourced by P): kick P by a_P dt/2; split P into fast particles F (timestep
+    criterion sqrt(2 eta eps_i / |a_i|) < dt, g4_timestep_bins) and slow S; no F: drift P by dt,
+    forces of P, kick by dt/2; otherwise forces of F on F, kick F by -dt/2, two recursive steps
+    of F over dt/2 with the drift of S by dt between them, kick F by -dt/2 with F's final
+    forces, forces of P, kick P by dt/2.  Every force computation has equal source and sink sets
+    (SubsetForces: a tree over that set only), so with the FMM the total momentum is conserved
+    to the rounding of the kicks.  pos_int (3, n) int32 (uint32 bits) and vel (3, n) float32 are
+    updated in place.  criterion 0 (relative) takes |a_old| from each particle's latest force."""
+
+    def __init__(self, pos_int, vel, mass, p: G4Params, eta: float = 0.025, method: str = "fmm",
+                 cls=None, max_level: int = 10):
+        dev = torch.device("cuda")
+        self.pos, self.vel, self.mass, self.cls = pos_int, vel, mass, cls
+        self.n = n = int(pos_int.shape[1])
+        self.p, self.eta, self.max_level = p, eta, max_level
+        self.forces = SubsetForces(n, p, method, cls is not None)
+        self.acc = [torch.zeros((3, n), dtype=torch.float32, device=dev) for _ in range(max_level + 2)]
+        self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.aold = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.bins = torch.zeros(n, dtype=torch.uint8, device=dev)
+        self.flag = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.all = torch.arange(n, dtype=torch.int32, device=dev)
+        self.n_force = 0
+        self.started = False
+
+    def _force(self, idx, level):
+        use_aold = self.p.criterion == 0
+        self.forces(self.pos, self.mass, self.cls, self.aold if use_aold else None, idx,
+                    self.acc[level], self.pot)
+        if use_aold:
+            a = torch.linalg.vector_norm(self.acc[level][:, idx.long()], dim=0)
+            self.aold[idx.long()] = a
+        self.n_force += int(idx.shape[0])
+
+    def start(self, p_bootstrap: G4Params | None = None):
+        """Forces of all particles (with p_bootstrap, e.g. the geometric criterion, when the
+        relative criterion has no |a_old| yet)."""
+        if p_bootstrap is not None:
+            self.forces(self.pos, self.mass, self.cls, None, self.all, self.acc[0], self.pot, p_bootstrap)
+            self.aold = torch.linalg.vector_norm(self.acc[0], dim=0).contiguous()
+        self._force(self.all, 0)
+        self.started = True
+
+    def step(self, dt: float):
+        if not self.started:
+            self.start()
+        self._step(self.all, dt, 0)
+
+    def _step(self, P, dt, level):
+        acc = self.acc[level]
+        g4_kick(self.vel, acc, 0.5 * dt, P)
+        F = None
+        if level < self.max_level:
+            g4_timestep_bins(acc, self.p, self.eta, dt, 1, self.bins, self.cls, P)
+            fast = self.bins[P.long()] > 0
+            if bool(fast.any()):
+                F, S = P[fast].contiguous(), P[~fast].contiguous()
+        if F is None:
+            g4_drift(self.pos, self.vel, dt, self.p, P, self.flag)
+            self._force(P, level)
+            g4_kick(self.vel, acc, 0.5 * dt, P)
+            return
+        self._force(F, level + 1)
+        g4_kick(self.vel, self.acc[level + 1], -0.5 * dt, F)
+        self._step(F, 0.5 * dt, level + 1)
+        if S.numel():
+            g4_drift(self.pos, self.vel, dt, self.p, S, self.flag)
+        self._step(F, 0.5 * dt, level + 1)
+        g4_kick(self.vel, self.acc[level + 1], -0.5 * dt, F)
+        self._force(P, level)
+        g4_kick(self.vel, acc, 0.5 * dt, P)
+
+    def momentum(self):
+        """Total momentum sum m v (FP64)."""
+        return (self.mass.double()[None, :] * self.vel.double()).sum(dim=1)

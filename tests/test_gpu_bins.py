@@ -53,7 +53,10 @@ def test_binned_subsets_two_softening_classes_match_oracle():
         ao, po, co = oracle.tree_forces(run, np.arange(len(ix)))
         e = relerr(ag, ao)
         assert np.percentile(e, 99) < PARITY_P99, (b, np.percentile(e, [50, 99, 100]))
-        assert np.percentile(np.abs(pg - po) / np.abs(po), 99) < PARITY_P99
+        # sinks with no source inside r_cut (a sparse subset has some): exactly zero on both
+        z = np.linalg.norm(ao, axis=1) == 0
+        assert np.all(ag[z] == 0) and np.all(pg[z] == 0)
+        assert np.percentile(np.abs(pg[~z] - po[~z]) / np.abs(po[~z]), 99) < PARITY_P99
         assert np.mean(np.all(cg == co, axis=1)) > 0.99
         # both softening classes are present among the bin's sinks
         assert len(np.unique(ps.eps_class[ix])) == 2 or len(ix) < 64

@@ -112,6 +112,24 @@ def test_fmm_parity_treepm_box():
     assert np.percentile(relerr(ag, ad), 99) < 1.1 * eo + 1e-5 and eo < 1e-2
 
 
+def test_fmm_parity_treepm_box_bench_leaf():
+    """The bench's FMM configuration (leaf 32, p = 4, alpha = 0.0025, the same spacing and split
+    as the 256^3 box) on a 40^3 box the oracle's FMM finishes in seconds."""
+    L = 40 * 1.953125
+    ps = synth.zeldovich(40, L, 2.0, 1013)
+    q, box = int_coords(ps)
+    kw = dict(alpha=0.0025, order_p=4, r_s=1.25 * L / 80, r_cut_factor=4.5, leaf_max=32)
+    OP = oracle_params(ps, box, **kw)
+    ad, _ = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP, r_max=OP.r_cut)
+    aold = np.linalg.norm(ad, axis=1).astype(np.float32)
+    ag, pg, cg, mom = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), aold)
+    ao, po, co, pc = oracle_fmm(ps, q, OP, aold.astype(np.float64), leaf=32)
+    assert same_counts(cg, pc)
+    assert np.percentile(relerr(ag, ao), 99) < 1e-5
+    rel = np.linalg.norm(mom) / np.sum(ps.mass * np.linalg.norm(ag, axis=1))
+    assert rel < 1e-5, rel
+
+
 def test_fmm_alpha0_is_direct_sum():
     ps, q, box, aold, ad = _plummer(3000)
     kw = dict(alpha=0.0, order_p=4)

@@ -108,3 +108,20 @@ def test_fp16_test_compact_group(r):
     nlim = _threshold(1.0)
     assert np.all(_candidates(sink, sink + r * u, nlim))
     assert not np.any(_candidates(sink, sink + 1.03 * u, nlim))
+
+
+def test_fp16_test_needs_groups_inside_half_the_box():
+    """The FP16 positions are nearest-image offsets from the group centre.  A sink R r_cut from
+    the centre and a source r_cut beyond it stay on the same side only while R + 1 < L / (2
+    r_cut); past that, the source's offset wraps by a box length and the FP16 test would reject
+    a pair inside r_cut -- so the kernel skips the test for such groups (R + 1.01 < half box)."""
+    half_box = 10.0                      # L = 20 r_cut
+    R = half_box - 0.5                   # a sink 9.5 r_cut from the group centre
+    sink = np.array([[R, 0.0, 0.0]])
+    true_src = sink + np.array([[0.99, 0.0, 0.0]])           # 10.49: across the boundary
+    wrapped = true_src - np.array([[2 * half_box, 0.0, 0.0]])   # its nearest-image offset
+    assert not np.all(_candidates(sink, wrapped, _threshold(R)))   # the pair would be lost
+    assert np.all(_candidates(sink, true_src, _threshold(R)))
+    assert not (R + 1.01 < half_box)     # the kernel's rule turns the FP16 test off here
+    R_ok = half_box - 1.02
+    assert R_ok + 1.01 < half_box        # ... and keeps it where no source can wrap
