@@ -386,15 +386,19 @@ def run_gpu(args, rank, world):
         sample_ref = None
         if accuracy is not None:
             sample_ref = (sinks, ad)
+        collect_cost_samples("C3_256cubed", tg.tree, P, n, tg.aold_s, tg.counts)
         for name, fn in (("cost_model", lambda: extra_cost_model(tg, P, n)),
                          ("fmm", lambda: extra_fmm(pos_int, mass, aold, wp, n, sample_ref)),
                          ("treepm", lambda: extra_treepm(pos_int, mass, aold, wp, n)),
                          ("fp64_walk", lambda: extra_fp64(tg, P, n, sample_ref)),
                          ("batched_systems", lambda: extra_forest(wp["leaf_max"])),
-                         ("hierarchical_bins", lambda: extra_bins(wp["leaf_max"])),
                          ("plummer_16k", lambda: extra_plummer(wp["leaf_max"])),
                          ("box_128cubed", lambda: extra_box128(wp["leaf_max"])),
+                         ("cost_model_frozen", extra_frozen_model),
+                         ("hierarchical_bins", lambda: extra_bins(wp["leaf_max"])),
                          ("cost_model_512cubed", lambda: extra_c5(wp["leaf_max"]))):
+            if args.extras and name not in args.extras.split(","):
+                continue
             try:
                 extras[name] = fn()
             except Exception as ex:           # report, keep the headline line
@@ -598,6 +602,16 @@ def extra_forest(leaf_max):
         for k in range(len(sizes)):
             one_system(k)
     ms_sys_graph = _time(g.replay, 3)
+    # the leaf threshold tuned for the forest (one complete forest step per candidate)
+    leaf_ms = {}
+    for lm in (8, 16, 32, 64):
+        Pl = g4.params(periodic=0, eps=[0.01], alpha=0.0025, leaf_max=lm)
+        fl = g4.ForestGravity(sizes, Pl)
+        fl.forces(pos, mass, box, aold, Pl)
+        leaf_ms[lm] = _time(lambda: fl.forces(pos, mass, box, aold, Pl), 2)
+        del fl
+    res["leaf_autotune"] = {"best": min(leaf_ms, key=leaf_ms.get), "step_ms": leaf_ms,
+                            "forces_per_s_best": n / (min(leaf_ms.values()) * 1e-3)}
     res["per_system_launches"] = {"ms_per_step": ms_sys, "ms_per_step_graphs": ms_sys_graph,
                                   "forest_speedup": ms_sys / ms,
                                   "forest_speedup_vs_graphs": ms_sys_graph / ms}
@@ -666,30 +680,36 @@ def extra_bins(leaf_max):
     same = all(torch.equal(a, b) for a, b in zip(ref, bf.acc))
     per_bin = [_time(lambda b=b: bf.run_bin(b, q, mass, cls, aold), 3) for b in range(len(lists))]
     ref_counts = [tgb.counts.clone() for tgb, _ in bf.bins]
-    # the cost model trained on the counts of the full-set call partitions every bin's walk
-    tga = bf.bins[-1][0]
-    feats = g4.cost_features(tga.tree, P, n, tga.aold_s)
-    labels = g4.cost_labels(tga.counts)
-    gen = torch.Generator(device="cuda").manual_seed(7)
-    sub = torch.randperm(n, device="cuda", generator=gen)[: 1 << 18]
-    cm = g4.CostModel(seed=1)
-    cm.train(feats[sub].contiguous(), labels[sub].contiguous(), steps=400, lr=3e-3)
-    bf.set_cost_model(cm)
-    eager_m = _time(lambda: bf.run(q, mass, cls, aold), 3)
-    per_bin_m = [_time(lambda b=b: bf.run_bin(b, q, mass, cls, aold), 3) for b in range(len(lists))]
-    counts_same = all(torch.equal(tgb.counts, c) for (tgb, _), c in zip(bf.bins, ref_counts))
-    bf.capture(q, mass, cls, aold)
-    graph_m = _time(bf.replay, 3)
+    # partition of every bin's walk (g4_schedule_items) by (a) the cost model trained on C1-C3
+    # and frozen (it has never seen this box), (b) the paper's q_i: the measured interactions
+    # of the bin's previous force computation; against the plain 32-sink groups
+    part = {}
+    qi = [c.clone() for c in bf.measured_costs()]
+    schemes = [("q_i_measured", qi)]
+    cm = FROZEN.get("model")
+    if cm is not None:
+        preds = [cm.predict(g4.cost_features(tgb.tree, P, int(ix.shape[0]), tgb.aold_s))
+                 for ix, (tgb, _) in zip(bf.idx, bf.bins)]
+        schemes.insert(0, ("mlp_frozen", preds))
+        part["mlp_frozen_vs_measured"] = [_rank_and_err(pr, lb) for pr, lb in zip(preds, qi)]
+    counts_same = True
+    for name, pr in schemes:
+        bf.set_partition(pr)
+        e_ms = _time(lambda: bf.run(q, mass, cls, aold), 3)
+        pb = [_time(lambda b=b: bf.run_bin(b, q, mass, cls, aold), 3) for b in range(len(lists))]
+        counts_same = counts_same and all(torch.equal(tgb.counts, c) for (tgb, _), c in zip(bf.bins, ref_counts))
+        bf.capture(q, mass, cls, aold)
+        g_ms = _time(bf.replay, 3)
+        part[name] = {"eager_ms": e_ms, "graph_ms": g_ms, "per_bin_ms": pb,
+                      "forces_per_s_graph": forces / (g_ms * 1e-3), "speedup_graph": graph / g_ms}
+    part["interaction_counts_identical"] = bool(counts_same)
     bf.set_cost_model(None)
     return {"particles": n, "active_fractions": fracs, "forces_per_step": forces,
             "accuracy_vs_direct": acc_bins,
             "eager_ms": eager, "graph_ms": graph, "forces_per_s_eager": forces / (eager * 1e-3),
             "forces_per_s_graph": forces / (graph * 1e-3), "graph_equals_eager": bool(same),
             "per_bin_ms": per_bin,
-            "cost_partition": {"eager_ms": eager_m, "graph_ms": graph_m, "per_bin_ms": per_bin_m,
-                               "forces_per_s_graph": forces / (graph_m * 1e-3),
-                               "speedup_graph": graph / graph_m,
-                               "interaction_counts_identical": bool(counts_same)}}
+            "cost_partition": part}
 
 
 def extra_cost_model(tg, P, n):
@@ -799,6 +819,48 @@ def _errors(a, ref):
     return out
 
 
+# Cost-model training samples logged from the walks of C1 (Plummer sphere), C2 (128^3 box) and
+# C3 (the headline 256^3 box); the network trained once on them is frozen and applied to the
+# time bins of the zoom box and to the 512^3 box, which it has never seen.
+TRAIN_SAMPLES = {}
+FROZEN = {}
+
+
+def collect_cost_samples(name, tree, P, n, aold_s, counts, k=1 << 16):
+    """Tree features and measured-cost labels (log(1 + PP + 5 PN)) of k sampled sinks."""
+    import torch
+    from paper_2010_03567_gb300 import g4
+    feats = g4.cost_features(tree, P, n, aold_s)
+    labels = g4.cost_labels(counts)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    sub = torch.randperm(n, device="cuda", generator=gen)[: min(n, k)]
+    TRAIN_SAMPLES[name] = (feats[sub].contiguous().clone(), labels[sub].contiguous().clone())
+
+
+def extra_frozen_model():
+    """Train the cost model once on the samples of C1-C3 and freeze it."""
+    import torch
+    from paper_2010_03567_gb300 import g4
+    if not TRAIN_SAMPLES:
+        return {"error": "no training samples"}
+    f = torch.cat([v[0] for v in TRAIN_SAMPLES.values()]).contiguous()
+    lab = torch.cat([v[1] for v in TRAIN_SAMPLES.values()]).contiguous()
+    cm = g4.CostModel(seed=1)
+    losses = cm.train(f, lab, steps=600, lr=3e-3)
+    FROZEN["model"] = cm
+    return {"trained_on": {k: int(v[1].shape[0]) for k, v in TRAIN_SAMPLES.items()},
+            "steps": 600, "loss_first_last": [float(losses[0]), float(losses[-1])]}
+
+
+def _rank_and_err(pred, labels):
+    p_np, l_np = pred.cpu().numpy(), labels.cpu().numpy()
+    rk = lambda a: np.argsort(np.argsort(a))
+    return {"rank_corr": float(np.corrcoef(rk(p_np), rk(l_np))[0, 1]),
+            "mean_abs_err_log_cost": float(np.mean(np.abs(p_np - l_np))),
+            "mean_rel_err_cost": float(np.mean(np.abs(np.expm1(p_np) - np.expm1(l_np)) /
+                                               np.maximum(np.expm1(l_np), 1.0)))}
+
+
 def extra_fp64(tg, P, n, sample_ref):
     """The same walk in FP64 (FP64 multipoles and interactions) on the headline box: the FP32
     walk's error against it, and both against the FP64 direct sum on the sample."""
@@ -844,11 +906,17 @@ def extra_plummer(leaf_max):
     OP = oracle.OracleParams(box=box, periodic=False, eps=np.array([0.01]))
     ad, _ = oracle.direct(q.cpu().numpy().view(np.uint32), ps.mass, None, np.arange(ps.n), OP)
     cnt = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+    collect_cost_samples("C1_plummer16k", tg.tree, P, ps.n, tg.aold_s, tg.counts)
     part = partition_gain(tg, P, ps.n, lambda: tg.forces(q, mass, None, aold, P))
+    # the leaf threshold tuned for this workload (one complete force computation per candidate)
+    from paper_2010_03567_gb300 import autotune
+    best_leaf, leaf_ms = autotune.tune(autotune.gpu_step_timer(q, mass, aold, P),
+                                       torch.cuda.get_device_name(), ps.n, P, use_cache=False)
     return {"particles": ps.n, "ms_per_step": ms, "forces_per_s": ps.n / (ms * 1e-3),
             "ms_per_step_graph": ms_graph, "forces_per_s_graph": ps.n / (ms_graph * 1e-3),
             "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
             "accuracy_vs_direct": _errors(acc, ad), "cost_partition": part,
+            "leaf_autotune": {"best": best_leaf, "step_ms": leaf_ms},
             "forces_per_s_graph_model_items": ps.n / (part["model"]["step_ms_graph"] * 1e-3)}
 
 
@@ -876,6 +944,7 @@ def extra_box128(leaf_max):
     ad, _ = oracle.direct(q.cpu().numpy().view(np.uint32), ps.mass, None, sinks, OP, r_max=OP.r_cut)
     acc = tg.acc.double().cpu().numpy().T[sinks]
     cnt = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+    collect_cost_samples("C2_128cubed", tg.tree, P, ps.n, tg.aold_s, tg.counts)
     return {"particles": ps.n, "ms_per_step": ms, "forces_per_s": ps.n / (ms * 1e-3),
             "ms_per_step_graph": ms_graph, "forces_per_s_graph": ps.n / (ms_graph * 1e-3),
             "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
@@ -914,11 +983,58 @@ def extra_c5(leaf_max):
     del q_np
     accuracy = {**_errors(tg.acc[:, torch.from_numpy(sinks).cuda().long()].double().cpu().numpy().T, ad),
                 "sample": len(sinks)}
-    res = extra_cost_model(tg, P, n)
+    # the cost model frozen after training on C1-C3 (it has never seen this box) against the
+    # paper's q_i (the measured interactions of the previous walk): prediction quality and the
+    # walk with groups ordered heaviest first (chunks of 64 groups) by either, against PH order
+    walk = lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, acc=tg.acc_s,
+                                        pot=tg.pot_s, counts=tg.counts)
+    labels = g4.cost_labels(tg.counts).clone()
+    frozen = {}
+    cm = FROZEN.get("model")
+    ph_ms = _time(walk, 3)
+    ref = tg.acc_s.clone()
+    sources = [("q_i_measured", labels)]
+    if cm is not None:
+        pred = cm.predict(g4.cost_features(tg.tree, P, n, tg.aold_s))
+        frozen["mlp_frozen_vs_measured"] = _rank_and_err(pred, labels)
+        sources.insert(0, ("mlp_frozen", pred))
+    for name, src in sources:
+        g4.set_group_order(tg.tree, g4.schedule_lpt(src, 64))
+        frozen[name] = {"walk_ms_lpt_chunk64": _time(walk, 3),
+                        "forces_identical": bool(torch.equal(ref, tg.acc_s))}
+    g4.set_group_order(tg.tree, None)
+    frozen["walk_ms_ph_order"] = ph_ms
+    res = {"out_of_sample": frozen, "in_sample": extra_cost_model(tg, P, n)}
     res.update({"particles": n, "ms_per_step_ph_order": plain,
                 "forces_per_s_ph_order": n / (plain * 1e-3), "accuracy_vs_direct": accuracy})
     del tg
     return res
+
+
+def run_pm_only(args):
+    """PM long-range calls on the bench workload (for launch lists and captures of the PM
+    kernels): mesh 2 N_side per axis."""
+    import torch
+    from paper_2010_03567_gb300 import g4, synth
+    n_side = args.n_side
+    L = L_BOX * n_side / N_SIDE
+    ps = synth.zeldovich(n_side, L, RMS, SEED)
+    wp = workload_params(n_side, L, args.leaf_max)
+    pos = torch.from_numpy(ps.pos).cuda()
+    q, _ = g4.g4_int_coords(pos, True, L)
+    del pos
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    P = g4.params(**wp)
+    tg = g4.TreeGravity(ps.n, P)
+    tg.prepare(q, mass, None, None, P)          # PH order, as TreePMGravity calls it
+    ng = 2 * n_side
+    ws = torch.empty(g4.g4_pm_workspace(ng) + 256, dtype=torch.uint8, device="cuda")
+    acc = torch.zeros((3, ps.n), dtype=torch.float32, device="cuda")
+    call = lambda: g4.g4_pm_long_range(tg.pos_s, tg.mass_s, P, ng, acc=acc, workspace=ws)
+    ms = _time(call, max(1, args.steps), warm=1)
+    print(json.dumps({"pm_only": True, "n_particles": ps.n, "n_grid": ng, "calls": args.steps,
+                      "ms_per_call": ms}), flush=True)
+    return 0
 
 
 def run_fmm_only(args):
@@ -959,8 +1075,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FMM, batched-systems, time-bin and cost-model measurements")
+    ap.add_argument("--extras", default=None,
+                    help="comma-separated names of the extra entries to run (default: all)")
     ap.add_argument("--leaf-max", type=int, default=None,
                     help="leaf threshold of the tree (default: the tuned value)")
+    ap.add_argument("--pm-only", action="store_true",
+                    help="profiling aid: --steps PM long-range calls on the workload's particles "
+                         "(mesh 2 N_side per axis); prints their mean time, not the bench line")
     ap.add_argument("--fmm-only", action="store_true",
                     help="profiling aid: bootstrap walk, then --steps FMM calls (p = 4) on the workload; "
                          "prints their mean time, not the bench line")
@@ -977,6 +1098,8 @@ def main():
         tdist.init_process_group("nccl")
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.pm_only:
+        return run_pm_only(args)
     if args.fmm_only:
         return run_fmm_only(args)
     return run_gpu(args, rank, world)

@@ -155,11 +155,20 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// the rare softened / beyond-the-fit pairs of pair_treepm_fast, kept out of line so that the
+// common path stays a short branch-free sequence (an inlined copy could be if-converted into
+// every evaluation)
+static __device__ __noinline__ void pair_treepm_slow(float r2, float h, float as, float &g0,
+                                                    float &g1)
+{
+    pair_kernel<float, true>(r2, h, as, g0, g1);
+}
+
 __device__ __forceinline__ void pair_treepm_fast(float r2, float h, const PairF &c, float &g0,
                                                  float &g1)
 {
     if (r2 < h * h || r2 > c.fit2) {
-        pair_kernel<float, true>(r2, h, c.as, g0, g1);
+        pair_treepm_slow(r2, h, c.as, g0, g1);
         return;
     }
     const float rinv = rsqrt_approx(r2), r = r2 * rinv;   // r2 > 0 here, never subnormal

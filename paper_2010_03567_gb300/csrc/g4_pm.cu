@@ -6,7 +6,8 @@
 //      consecutive x, so every global access is coalesced along x);
 //   3. multiplication by the Green's function -4 pi G exp(-k^2 r_s^2) / k^2, divided by the
 //      CIC assignment and interpolation transforms prod_i sinc^4(k_i Delta / 2) and by N^3
-//      (the inverse transform is unnormalised); zero at k = 0;
+//      (the inverse transform is unnormalised); zero at k = 0.  Everything but 1/k^2 factorises
+//      over the axes: per-axis tables in FP64, one FP32 product and division per mesh cell;
 //   4. inverse 3-D FFT: the long-range potential on the mesh (real parts);
 //   5-6. at each sink, fourth-order differences of the potential at the 8 CIC mesh points,
 //      weighted with the CIC weights: a = -grad phi, and phi itself.
@@ -18,6 +19,11 @@ namespace {
 
 constexpr int PM_THREADS = 256;
 constexpr int PM_TILE = 4096;   // complex values per block tile (32 KB of shared memory)
+// shared-memory slot of tile element i: one float2 of padding after every 16, so that the
+// bit-reversed scatter of a warp (indices that differ by multiples of n/32) and the strided
+// butterflies of the first stages spread over the banks
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+constexpr int PM_SMEM = PM_TILE + PM_TILE / 16;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
@@ -37,18 +43,74 @@ __global__ void k_pm_twiddles(float2 *__restrict__ tw, int n)
 __device__ __forceinline__ int bitrev(int j, int logn) { return (int)(__brev((unsigned)j) >> (32 - logn)); }
 
 // In-place radix-2 decimation-in-time transforms of `lines` lines of length n held in shared
-// memory (line l at s[l * n], already in bit-reversed order).  inverse: conjugate twiddles.
-__device__ void fft_lines_smem(float2 *s, int lines, int n, int logn, const float2 *__restrict__ tw,
-                               bool inverse)
+// memory in bit-reversed order: element j of line l at s[pad(l * ls + j * js)]; stage st joins
+// blocks of 2^st with twiddles W_{2^(st+1)}^k = tw[k n / 2^(st+1)].  Contiguous lines (ls = n,
+// js = 1) give consecutive threads consecutive butterflies of one line; interleaved columns
+// (ls = 1, js = lines) give them the same butterfly of consecutive lines, so a warp's accesses
+// stay on consecutive slots either way.  inverse: conjugate twiddles.
+__device__ void fft_lines_smem(float2 *s, int lines, int n, int logn, int ls, int js,
+                               const float2 *__restrict__ tw, bool inverse)
 {
-    const int nb = lines * (n >> 1);   // butterflies per stage
-    for (int st = 0; st < logn; st++) {
-        const int half = 1 << st;
-        const int tstep = n >> (st + 1);   // twiddle index stride
+    const bool lfast = ls == 1;
+    int st = 0;
+    // pairs of radix-2 stages (st, st + 1) fused: each thread loads 4 elements, applies both
+    // stages in registers (the same operations as two separate stages) and stores them back
+    for (; st + 1 < logn; st += 2) {
+        const int h = 1 << st;
+        const int nq = n >> 2, nb = lines * nq;
+        const int t1 = n >> (st + 1), t2 = n >> (st + 2);   // twiddle strides of both stages
         for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const int line = b / (n >> 1), bb = b - line * (n >> 1);
+            int line, bb;
+            if (lfast) {
+                line = b % lines;
+                bb = b / lines;
+            } else {
+                line = b / nq;
+                bb = b - line * nq;
+            }
+            const int g = bb >> st, k = bb & (h - 1);
+            const int j0 = g * 4 * h + k, base = line * ls;
+            const int a0 = pad(base + j0 * js), a1 = pad(base + (j0 + h) * js);
+            const int a2 = pad(base + (j0 + 2 * h) * js), a3 = pad(base + (j0 + 3 * h) * js);
+            float2 w1 = __ldg(tw + k * t1), w2 = __ldg(tw + k * t2), w3 = __ldg(tw + (k + h) * t2);
+            if (inverse) {
+                w1.y = -w1.y;
+                w2.y = -w2.y;
+                w3.y = -w3.y;
+            }
+            float2 x0 = s[a0], x1 = s[a1], x2 = s[a2], x3 = s[a3];
+            // stage st: (x0, x1) and (x2, x3) with W_{2h}^k
+            float2 t = cmul(w1, x1);
+            float2 y0 = make_float2(x0.x + t.x, x0.y + t.y), y1 = make_float2(x0.x - t.x, x0.y - t.y);
+            t = cmul(w1, x3);
+            float2 y2 = make_float2(x2.x + t.x, x2.y + t.y), y3 = make_float2(x2.x - t.x, x2.y - t.y);
+            // stage st + 1: (y0, y2) with W_{4h}^k, (y1, y3) with W_{4h}^(k + h)
+            t = cmul(w2, y2);
+            s[a0] = make_float2(y0.x + t.x, y0.y + t.y);
+            s[a2] = make_float2(y0.x - t.x, y0.y - t.y);
+            t = cmul(w3, y3);
+            s[a1] = make_float2(y1.x + t.x, y1.y + t.y);
+            s[a3] = make_float2(y1.x - t.x, y1.y - t.y);
+        }
+        __syncthreads();
+    }
+    // a last single radix-2 stage when log2 n is odd
+    for (; st < logn; st++) {
+        const int half = 1 << st;
+        const int tstep = n >> (st + 1);
+        const int nh = n >> 1, nb = lines * nh;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            int line, bb;
+            if (lfast) {
+                line = b % lines;
+                bb = b / lines;
+            } else {
+                line = b / nh;
+                bb = b - line * nh;
+            }
             const int g = bb >> st, k = bb & (half - 1);
-            const int i0 = line * n + g * 2 * half + k, i1 = i0 + half;
+            const int j0 = g * 2 * half + k;
+            const int i0 = pad(line * ls + j0 * js), i1 = pad(line * ls + (j0 + half) * js);
             float2 w = __ldg(tw + k * tstep);
             if (inverse) w.y = -w.y;
             const float2 a = s[i0], t = cmul(w, s[i1]);
@@ -63,30 +125,31 @@ __device__ void fft_lines_smem(float2 *s, int lines, int n, int logn, const floa
 __global__ void __launch_bounds__(PM_THREADS) k_pm_fft_x(float2 *__restrict__ g, int n, int logn,
                                                          const float2 *__restrict__ tw, int inverse)
 {
-    __shared__ float2 s[PM_TILE];
+    __shared__ float2 s[PM_SMEM];
     const int lines = PM_TILE / n;
     const long long nlines = (long long)n * n;
     for (long long l0 = (long long)blockIdx.x * lines; l0 < nlines; l0 += (long long)gridDim.x * lines) {
         float2 *base = g + l0 * n;
         for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
             const int line = e / n, j = e - line * n;
-            s[line * n + bitrev(j, logn)] = base[e];
+            s[pad(line * n + bitrev(j, logn))] = base[e];
         }
         __syncthreads();
-        fft_lines_smem(s, lines, n, logn, tw, inverse != 0);
-        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) base[e] = s[e];
+        fft_lines_smem(s, lines, n, logn, n, 1, tw, inverse != 0);
+        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) base[e] = s[pad(e)];
         __syncthreads();
     }
 }
 
 // y / z pass: tiles of `cols` consecutive x columns (cols = min(n, PM_TILE / n)), transform
 // along the axis with element stride `stride` (n for y, n^2 for z); `outer` indexes the
-// remaining axis with stride `ostride`.
+// remaining axis with stride `ostride`.  The tile is kept column-interleaved in shared memory
+// (element j of column c at j * cols + c), as it is in the mesh.
 __global__ void __launch_bounds__(PM_THREADS) k_pm_fft_col(float2 *__restrict__ g, int n, int logn,
                                                            long long stride, long long ostride,
                                                            const float2 *__restrict__ tw, int inverse)
 {
-    __shared__ float2 s[PM_TILE];
+    __shared__ float2 s[PM_SMEM];
     const int cols = min(n, PM_TILE / n);
     const int ntx = n / cols;                       // column tiles per row of x
     const long long ntiles = (long long)ntx * n;    // times the other axis
@@ -96,13 +159,13 @@ __global__ void __launch_bounds__(PM_THREADS) k_pm_fft_col(float2 *__restrict__ 
         float2 *base = g + o * ostride + (long long)xt * cols;
         for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
             const int j = e / cols, c = e - j * cols;   // consecutive threads: consecutive x
-            s[c * n + bitrev(j, logn)] = base[(long long)j * stride + c];
+            s[pad(bitrev(j, logn) * cols + c)] = base[(long long)j * stride + c];
         }
         __syncthreads();
-        fft_lines_smem(s, cols, n, logn, tw, inverse != 0);
+        fft_lines_smem(s, cols, n, logn, 1, cols, tw, inverse != 0);
         for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
             const int j = e / cols, c = e - j * cols;
-            base[(long long)j * stride + c] = s[c * n + j];
+            base[(long long)j * stride + c] = s[pad(e)];
         }
         __syncthreads();
     }
@@ -141,32 +204,35 @@ __global__ void k_pm_assign(const uint32_t *__restrict__ pos, const float *__res
     }
 }
 
-// multiplication by the Green's function with the CIC deconvolution (and 1/N^3)
-__global__ void k_pm_green(float2 *__restrict__ g, int n, int logn, double two_pi_over_L,
-                           double rs2, double scale, double half_delta)
+// Per-axis factors of the Green's function (FP64, rounded to FP32), for wave number index i:
+// k_i = 2 pi n_i / L with n_i = i for i < N/2, i - N otherwise;
+//   kk[i] = k_i^2,  ew[i] = exp(-k_i^2 r_s^2) / sinc^4(k_i Delta / 2)
+// (exp(-k^2 r_s^2) factorises over the axes, and so does the CIC deconvolution).
+__global__ void k_pm_green_tables(float *__restrict__ kk, float *__restrict__ ew, int n,
+                                  double two_pi_over_L, double rs2, double half_delta)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ni = i < n / 2 ? i : i - n;
+        const double k = ni * two_pi_over_L, x = k * half_delta;
+        const double sc = x == 0.0 ? 1.0 : sin(x) / x;
+        kk[i] = (float)(k * k);
+        ew[i] = (float)(exp(-k * k * rs2) / (sc * sc * sc * sc));
+    }
+}
+
+// multiplication by the Green's function -4 pi G exp(-k^2 r_s^2) / k^2 with the CIC
+// deconvolution and 1/N^3: scale * ew[ix] ew[iy] ew[iz] / (kk[ix] + kk[iy] + kk[iz])
+__global__ void k_pm_green(float2 *__restrict__ g, int n, int logn, const float *__restrict__ kk,
+                           const float *__restrict__ ew, float scale)
 {
     const long long total = (long long)n * n * n;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
          c += (long long)gridDim.x * blockDim.x) {
         const int ix = (int)(c & (n - 1)), iy = (int)((c >> logn) & (n - 1)), iz = (int)(c >> (2 * logn));
-        const int kx = ix < n / 2 ? ix : ix - n, ky = iy < n / 2 ? iy : iy - n, kz = iz < n / 2 ? iz : iz - n;
-        if (kx == 0 && ky == 0 && kz == 0) {
-            g[c] = make_float2(0.f, 0.f);
-            continue;
-        }
-        const double qx = kx * two_pi_over_L, qy = ky * two_pi_over_L, qz = kz * two_pi_over_L;
-        const double k2 = qx * qx + qy * qy + qz * qz;
-        double w = 1.0;
-        const double q[3] = {qx, qy, qz};
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const double x = q[a] * half_delta;
-            const double sc = x == 0.0 ? 1.0 : sin(x) / x;
-            w *= sc * sc;
-        }
-        const double f = scale * exp(-k2 * rs2) / (k2 * w * w);
+        const float k2 = __ldg(kk + ix) + __ldg(kk + iy) + __ldg(kk + iz);
+        const float f = (c == 0) ? 0.f : scale * __ldg(ew + ix) * __ldg(ew + iy) * __ldg(ew + iz) / k2;
         const float2 v = g[c];
-        g[c] = make_float2((float)(v.x * f), (float)(v.y * f));
+        g[c] = make_float2(v.x * f, v.y * f);
     }
 }
 
@@ -244,7 +310,8 @@ extern "C" g4_status g4_pm_workspace(int32_t n_grid, size_t *bytes)
     if (!bytes || !pm_grid_ok(n_grid))
         return g4_fail(G4_ERR_INVALID_ARG, "g4_pm_workspace: n_grid=%d (a power of two in [16, 1024])", n_grid);
     const size_t n = (size_t)n_grid;
-    *bytes = al256(sizeof(float2) * n * n * n) + al256(sizeof(float2) * (n / 2));
+    *bytes = al256(sizeof(float2) * n * n * n) + al256(sizeof(float2) * (n / 2)) +
+             2 * al256(sizeof(float) * n);
     return G4_OK;
 }
 
@@ -275,12 +342,16 @@ extern "C" g4_status g4_pm_long_range(const uint32_t *pos, const float *mass, in
     const size_t cells = (size_t)N * N * N;
     float2 *grid = (float2 *)workspace;
     float2 *tw = (float2 *)((char *)workspace + al256(sizeof(float2) * cells));
+    float *kk = (float *)((char *)tw + al256(sizeof(float2) * (N / 2)));
+    float *ew = (float *)((char *)kk + al256(sizeof(float) * N));
     const double L = P->box_size, delta = L / N;
     int launches = 0;
     if (cudaMemsetAsync(grid, 0, sizeof(float2) * cells, st) != cudaSuccess)
         return g4_cuda_check(cudaGetLastError(), "g4_pm_long_range: clear mesh");
+    const double two_pi = 6.283185307179586;
     k_pm_twiddles<<<(N / 2 + 255) / 256, 256, 0, st>>>(tw, N);
-    launches++;
+    k_pm_green_tables<<<(N + 255) / 256, 256, 0, st>>>(kk, ew, N, two_pi / L, P->r_s * P->r_s, 0.5 * delta);
+    launches += 2;
     if (n > 0) {
         k_pm_assign<<<g4_blocks_for(n, 256), 256, 0, st>>>(pos, mass, (int)n, grid, N, logn,
                                                             (float)(1.0 / (delta * delta * delta)));
@@ -294,10 +365,8 @@ extern "C" g4_status g4_pm_long_range(const uint32_t *pos, const float *mass, in
         k_pm_fft_col<<<gx, PM_THREADS, 0, st>>>(grid, N, logn, n2, N, tw, inv);      // z
         launches += 3;
         if (inv == 0) {
-            const double two_pi = 6.283185307179586;
             k_pm_green<<<g4_blocks_for((int64_t)cells, 256), 256, 0, st>>>(
-                grid, N, logn, two_pi / L, P->r_s * P->r_s, -2.0 * two_pi * P->G / (double)cells,
-                0.5 * delta);
+                grid, N, logn, kk, ew, (float)(-2.0 * two_pi * P->G / (double)cells));
             launches++;
         }
     }

@@ -763,14 +763,26 @@ class BinnedForces:
     def set_cost_model(self, model, stream=None):
         """Partition every bin's walk by the model's predicted costs (g4_schedule_items), from
         the features of the bin's current tree; None restores the plain groups."""
-        for ix, (tg, sub) in zip(self.idx, self.bins):
-            k = int(ix.shape[0])
-            if model is None:
+        if model is None:
+            self.set_partition(None)
+            return
+        self.set_partition([model.predict(cost_features(tg.tree, self.p, int(ix.shape[0]), tg.aold_s,
+                                                        stream=stream), stream=stream)
+                            for ix, (tg, sub) in zip(self.idx, self.bins)], stream)
+
+    def measured_costs(self):
+        """log(1 + cost) per sorted sink of every bin from the interaction counts of its last
+        walk: the paper's q_i, the interactions of the last force computation (Sec. 6.1)."""
+        return [cost_labels(tg.counts) for tg, _ in self.bins]
+
+    def set_partition(self, preds, stream=None):
+        """Partition bin b's walk by preds[b] (log(1 + cost) per sorted sink); None: plain."""
+        for b, (ix, (tg, sub)) in enumerate(zip(self.idx, self.bins)):
+            if preds is None:
                 set_work_items(tg.tree, None)
                 continue
-            feats = cost_features(tg.tree, self.p, k, tg.aold_s, stream=stream)
-            items, ni = schedule_items(model.predict(feats, stream=stream), stream=stream)
-            set_work_items(tg.tree, items, ni, k)
+            items, ni = schedule_items(preds[b], stream=stream)
+            set_work_items(tg.tree, items, ni, int(ix.shape[0]))
         self.graph = None
 
     def capture(self, pos_int, mass, cls, aold):
