@@ -396,6 +396,7 @@ def run_gpu(args, rank, world):
                          ("box_128cubed", lambda: extra_box128(wp["leaf_max"])),
                          ("cost_model_frozen", extra_frozen_model),
                          ("hierarchical_bins", lambda: extra_bins(wp["leaf_max"])),
+                         ("softened_nodes", lambda: extra_softened(wp["leaf_max"])),
                          ("cost_model_512cubed", lambda: extra_c5(wp["leaf_max"]))):
             if args.extras and name not in args.extras.split(","):
                 continue
@@ -674,7 +675,14 @@ def extra_bins(leaf_max):
         ad, _ = oracle.direct(np.ascontiguousarray(q_np[:, ix]), ps.mass[ix], ps.eps_class[ix], sel,
                               OPb, r_max=OPb.r_cut)
         ag = ref[b].double().cpu().numpy().T[ix[sel]]
-        acc_bins.append({"fraction": fracs[b], **_errors(ag, ad), "sample": int(len(sel))})
+        # the relative criterion bounds each node's error by alpha |a_old| with |a_old| the
+        # total acceleration, while a bin's force (from the bin's own particles) can be far
+        # smaller: the error in units of |a_old| is the quantity the criterion controls
+        a_o = aold.double().cpu().numpy()[ix[sel]]
+        e_o = np.linalg.norm(ag - ad, axis=1) / a_o
+        acc_bins.append({"fraction": fracs[b], **_errors(ag, ad), "sample": int(len(sel)),
+                         "err_over_aold_p99": float(np.percentile(e_o, 99)),
+                         "err_over_aold_max": float(e_o.max())})
     bf.capture(q, mass, cls, aold)
     graph = _time(bf.replay, 3)
     same = all(torch.equal(a, b) for a, b in zip(ref, bf.acc))
@@ -908,6 +916,16 @@ def extra_plummer(leaf_max):
     cnt = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
     collect_cost_samples("C1_plummer16k", tg.tree, P, ps.n, tg.aold_s, tg.counts)
     part = partition_gain(tg, P, ps.n, lambda: tg.forces(q, mass, None, aold, P))
+    # expansion orders p = 1..5 at the same alpha: time of a step and accuracy (Sec. 2.2.2)
+    orders = {}
+    for po in (1, 2, 3, 4, 5):
+        Po = g4.params(box_size=box, periodic=0, eps=[0.01], alpha=0.0025, leaf_max=leaf_max, order_p=po)
+        tgo = g4.TreeGravity(ps.n, Po)
+        mso = _time(lambda: tgo.forces(q, mass, None, aold, Po), 5)
+        co = tgo.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+        orders[po] = {"ms_per_step": mso, "pn_per_step": int(co[1]),
+                      "accuracy_vs_direct": _errors(tgo.acc.double().cpu().numpy().T, ad)}
+        del tgo
     # the leaf threshold tuned for this workload (one complete force computation per candidate)
     from paper_2010_03567_gb300 import autotune
     best_leaf, leaf_ms = autotune.tune(autotune.gpu_step_timer(q, mass, aold, P),
@@ -916,8 +934,77 @@ def extra_plummer(leaf_max):
             "ms_per_step_graph": ms_graph, "forces_per_s_graph": ps.n / (ms_graph * 1e-3),
             "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
             "accuracy_vs_direct": _errors(acc, ad), "cost_partition": part,
-            "leaf_autotune": {"best": best_leaf, "step_ms": leaf_ms},
+            "leaf_autotune": {"best": best_leaf, "step_ms": leaf_ms}, "orders": orders,
             "forces_per_s_graph_model_items": ps.n / (part["model"]["step_ms_graph"] * 1e-3)}
+
+
+def extra_softened(leaf_max):
+    """Softened node interactions (Sec. 2.7) where they matter: a zoom box (low-resolution
+    128^3 lattice, L = 100, a central sphere 64 times denser) whose heavy low-resolution
+    particles carry a softening of half their spacing next to the high-resolution region.
+    Tree walk (p = 3) and FMM (p = 4), alpha = 0.0025, under the GADGET-3 rule (every pair
+    closer than 2.8 eps_ij opened) and the GADGET-4 rule (the softened kernel's expansion
+    unless both sides are mixed): time, interactions, accuracy on sampled sinks against the
+    oracle's FP64 direct sum (r < r_cut, pair softening max(eps_i, eps_j))."""
+    import torch
+    import oracle
+    from paper_2010_03567_gb300 import g4, synth
+    L, ns = 100.0, 128
+    ps = synth.zoom(ns, L, 1007)
+    n = ps.n
+    ps.eps_table = np.array([0.5 * L / ns, ps.eps_table[1]])
+    base = dict(box_size=L, periodic=1, r_s=1.25 * L / (2 * ns), r_cut_factor=4.5,
+                eps=list(ps.eps_table), leaf_max=leaf_max)
+    q, _ = g4.g4_int_coords(torch.from_numpy(ps.pos).cuda(), True, L)
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    cls = torch.from_numpy(ps.eps_class).cuda()
+    tg = g4.TreeGravity(n, g4.params(**base, criterion=1, theta=0.5), with_cls=True)
+    a0, _ = tg.forces(q, mass, cls, None)
+    aold = torch.linalg.vector_norm(a0, dim=0).contiguous()
+    # sampled sinks: random ones, and heavy particles within two low-resolution spacings of
+    # the sphere's surface (where the two species meet)
+    rng = np.random.default_rng(4107)
+    rad = np.linalg.norm(ps.pos - 0.5 * L, axis=1)
+    edge = np.flatnonzero((ps.eps_class == 0) & (np.abs(rad - 0.125 * L) < 2 * L / ns))
+    sinks = np.unique(np.concatenate([rng.choice(n, 1024, replace=False),
+                                      rng.choice(edge, min(1024, len(edge)), replace=False)]))
+    q_np = q.cpu().numpy().view(np.uint32)
+    OP = oracle.OracleParams(box=L, periodic=True, eps=ps.eps_table, r_s=base["r_s"],
+                             r_cut_factor=4.5)
+    ad, _ = oracle.direct(q_np, ps.mass, ps.eps_class, sinks, OP, r_max=OP.r_cut)
+    ws = None
+    out = {"particles": n, "eps": [float(e) for e in ps.eps_table], "sample": int(len(sinks))}
+    for soft in (0, 1):
+        P = g4.params(**base, alpha=0.0025, soft_nodes=soft)
+        ms = _time(lambda: tg.forces(q, mass, cls, aold, P), 3)
+        tg.tree.status()
+        c = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+        ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
+        tree = {"ms_per_step": ms, "forces_per_s": n / (ms * 1e-3), "pp_per_step": int(c[0]),
+                "pn_per_step": int(c[1]), "accuracy_vs_direct": _errors(ag, ad)}
+        P4 = g4.params(**base, alpha=0.0025, order_p=4, soft_nodes=soft)
+        tg.prepare(q, mass, cls, aold, P4)
+        if ws is None:
+            ws = torch.empty(tg.tree.fmm_workspace(P4) + 256, dtype=torch.uint8, device="cuda")
+        res = {}
+
+        def step():
+            tg.prepare(q, mass, cls, aold, P4)
+            res["r"] = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, tg.cls_s, tg.aold_s, P4, workspace=ws)
+            g4.g4_scatter(tg.perm, res["r"][0], res["r"][1], out=(tg.acc, tg.pot))
+
+        fms = _time(step, 3)
+        tg.tree.status()
+        cnt = res["r"][2].to(torch.int64).sum(dim=1).cpu().numpy()
+        af = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
+        fmm = {"ms_per_step": fms, "forces_per_s": n / (fms * 1e-3), "pp_per_step": int(cnt[0]),
+               "pn_per_step": int(cnt[1]), "accuracy_vs_direct": _errors(af, ad)}
+        out["gadget4_rule" if soft else "gadget3_rule"] = {"tree": tree, "fmm": fmm}
+    g3, g4r = out["gadget3_rule"], out["gadget4_rule"]
+    out["speedup_tree"] = g3["tree"]["ms_per_step"] / g4r["tree"]["ms_per_step"]
+    out["speedup_fmm"] = g3["fmm"]["ms_per_step"] / g4r["fmm"]["ms_per_step"]
+    del ws
+    return out
 
 
 def extra_box128(leaf_max):

@@ -76,9 +76,16 @@ typedef struct g4_params {
     int fp64_count;        /* nodes holding >= fp64_count particles accumulate moments in
                               FP64 (0 = 4096) */
     int keep_qp;           /* FMM: 1 keeps Q_p in the potential (Sec. 2.4 drops it) */
-    int fmm_p2p_per_particle; /* FMM: deferred leaf-leaf list entries per particle of the
-                              handle (0 = 16); beyond them the dual walk evaluates the
-                              leaf-leaf work itself */
+    int fmm_p2p_per_particle; /* FMM: deferred particle-pair list entries per particle of
+                              the handle (0 = 16); beyond them the dual walk evaluates the
+                              pairs itself */
+    int soft_nodes;        /* 0: a particle-node pair (tree walk, FMM) or node-node pair (FMM)
+                              closer than 2.8 eps_ij, eps_ij = the larger of the two sides'
+                              largest softenings, is opened (GADGET-3, multipoles unsoftened);
+                              1: the GADGET-4 rule of Sec. 2.7, such a pair is opened only if
+                              both sides' smallest softenings lie below eps_ij (a particle's
+                              smallest is its own), otherwise it interacts through the
+                              expansion of the softened kernel with eps_ij */
 } g4_params;
 
 typedef struct g4_tree_s *g4_tree;
@@ -95,8 +102,8 @@ int64_t g4_launch_count(void);
 
 /* Fills *p with the defaults: periodic=0, r_s=0, R_cut=4.5, pp_cut=1, alpha=0.0025,
  * theta=0.5, criterion=0, p=3, leaf_max=8, exclusion=1, precision=0, G=1, one class with
- * eps=0.01, group_size=32, fp64_count=4096, keep_qp=0, fmm_p2p_per_particle=0.  Host-only,
- * never fails for p!=NULL. */
+ * eps=0.01, group_size=32, fp64_count=4096, keep_qp=0, fmm_p2p_per_particle=0, soft_nodes=0.
+ * Host-only, never fails for p!=NULL. */
 g4_status g4_params_default(g4_params *p);
 
 /* ---- a1: integer coordinates (Sec. 2.10, Sec. 2.11) ----------------------------------- */
@@ -352,6 +359,14 @@ g4_status g4_drift(uint32_t *pos, const float *vel, const int32_t *idx, int64_t 
 g4_status g4_timestep_bins(const float *acc, const uint8_t *cls, const int32_t *idx, int64_t n_idx,
                            int64_t n, const g4_params *params, double eta, double dt_max,
                            int32_t max_bin, uint8_t *bins, void *stream);
+
+/* Random translation (Sec. 3.8): pos_out = pos_in + shift modulo 2^32 per axis, for n
+ * particles (3 x n uint32 SoA, device; pos_out may equal pos_in).  shift: 3 uint32 in HOST
+ * memory, read during the call.  With integer coordinates the shift is loss-less and exactly
+ * reversible (add 2^32 - shift); in a periodic box it moves the particle set relative to the
+ * root node, which decorrelates the tree's and the mesh's force errors between steps. */
+g4_status g4_translate(const uint32_t *pos_in, uint32_t *pos_out, int64_t n, const uint32_t *shift,
+                       void *stream);
 
 /* ---- learned cost model for scheduling the walk (no counterpart in the paper's method; its
  *      load-balancing cost q_i is the interaction count of the last force computation,

@@ -47,7 +47,7 @@ class _Params(C.Structure):
                 ("r_cut", C.c_double), ("pp_cut", C.c_int), ("alpha", C.c_double),
                 ("theta", C.c_double), ("criterion", C.c_int), ("order", C.c_int),
                 ("exclusion", C.c_int), ("G", C.c_double), ("n_eps", C.c_int),
-                ("eps", C.POINTER(C.c_double)), ("keep_qp", C.c_int)]
+                ("eps", C.POINTER(C.c_double)), ("keep_qp", C.c_int), ("soft_nodes", C.c_int)]
 
 
 @dataclass
@@ -65,6 +65,7 @@ class OracleParams:
     exclusion: bool = True
     G: float = 1.0
     keep_qp: bool = False
+    soft_nodes: bool = False
     _eps_buf: np.ndarray = field(default=None, repr=False)
 
     @property
@@ -81,7 +82,7 @@ class OracleParams:
                        int(self.criterion), int(self.order), int(self.exclusion),
                        float(self.G), int(len(self._eps_buf)),
                        self._eps_buf.ctypes.data_as(C.POINTER(C.c_double)),
-                       int(self.keep_qp))
+                       int(self.keep_qp), int(self.soft_nodes))
 
 
 def _p(a):
@@ -107,6 +108,8 @@ def _declare(L):
     L.or_soft_kernel.argtypes = [d, d, C.POINTER(d), C.POINTER(d)]
     L.or_pair_kernel.argtypes = [d, d, d, C.POINTER(d), C.POINTER(d)]
     L.or_gn.argtypes = [d, d, i32, vp]
+    L.or_gn_soft.argtypes = [d, d, d, i32, vp]
+    L.or_pn_soft_eval.argtypes = [vp, vp, i32, d, d, d, vp, vp]
     L.or_D_full.argtypes = [i32, vp, vp, vp]
     L.or_tree_walk.argtypes = [vp, vp, i64, vp, vp, vp, vp, i64, C.POINTER(_Params), vp, vp, vp]
     L.or_direct.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(_Params), d, vp, vp]
@@ -174,6 +177,24 @@ def gn(r: float, r_s: float, nmax: int) -> np.ndarray:
     g = np.zeros(8, np.float64)
     lib().or_gn(float(r), float(r_s), int(nmax), _p(g))
     return g[: nmax + 1].copy()
+
+
+def gn_soft(r: float, h: float, r_s: float, nmax: int) -> np.ndarray:
+    """g_n of the softened kernel (spline inside h, TreePM part when r_s > 0)."""
+    g = np.zeros(8, np.float64)
+    lib().or_gn_soft(float(r), float(h), float(r_s), int(nmax), _p(g))
+    return g[: nmax + 1].copy()
+
+
+def pn_soft(mono, rvec, order: int, r_s: float, h: float, G: float = 1.0):
+    """Particle-node term of the softened kernel: (acc (3,), pot)."""
+    mono = np.ascontiguousarray(mono, np.float64)
+    rv = np.ascontiguousarray(rvec, np.float64)
+    acc = np.zeros(3)
+    pot = C.c_double()
+    lib().or_pn_soft_eval(_p(mono), _p(rv), int(order), float(r_s), float(h), float(G), _p(acc),
+                          C.byref(pot))
+    return acc, pot.value
 
 
 def D_full(m: int, rvec, g) -> np.ndarray:

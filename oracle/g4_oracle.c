@@ -47,6 +47,9 @@ typedef struct {
     int n_eps;         /* number of softening classes */
     const double *eps; /* softening length eps_0 per class (Sec. 2.7) */
     int keep_qp;       /* FMM: 1 keeps Q_p in the potential (Sec. 2.4 drops it by default) */
+    int soft_nodes;    /* tree walk and FMM: 0 opens every pair closer than 2.8 max(eps)
+                          (GADGET-3); 1 applies the GADGET-4 rule of Sec. 2.7 (softened
+                          multipoles) */
 } or_params;
 
 /* ===================================================================================== */
@@ -181,6 +184,7 @@ typedef struct {
     double *com;                    /* nn x 3: (s - c) in physical units */
     double *mono;                   /* nn x nmono: monomial moments of orders 0..order */
     double *eps_max, *amin;         /* nn */
+    double *eps_min;                /* nn: smallest softening among the node's particles */
 } or_tree;
 
 static int64_t or_nmono(int order) { return (int64_t)(order + 1) * (order + 2) * (order + 3) / 6; }
@@ -262,7 +266,7 @@ void or_tree_free(or_tree *t)
 {
     if (!t) return;
     free(t->level); free(t->first); free(t->count); free(t->next); free(t->center);
-    free(t->mass); free(t->com); free(t->mono); free(t->eps_max); free(t->amin);
+    free(t->mass); free(t->com); free(t->mono); free(t->eps_max); free(t->amin); free(t->eps_min);
     free(t);
 }
 
@@ -296,17 +300,19 @@ void or_multipoles(or_tree *t, const uint32_t *pos, int64_t np, const double *ma
     t->com = (double *)realloc(t->com, sizeof(double) * 3 * (t->nn ? t->nn : 1));
     t->mono = (double *)realloc(t->mono, sizeof(double) * nm * (t->nn ? t->nn : 1));
     t->eps_max = (double *)realloc(t->eps_max, sizeof(double) * (t->nn ? t->nn : 1));
+    t->eps_min = (double *)realloc(t->eps_min, sizeof(double) * (t->nn ? t->nn : 1));
     t->amin = (double *)realloc(t->amin, sizeof(double) * (t->nn ? t->nn : 1));
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t k = 0; k < t->nn; k++) {
         int64_t f = t->first[k], e = f + t->count[k];
-        double M = 0.0, d[3] = {0, 0, 0}, em = 0.0, am = INFINITY;
+        double M = 0.0, d[3] = {0, 0, 0}, em = 0.0, am = INFINITY, en = INFINITY;
         for (int64_t j = f; j < e; j++) {
             M += mass[j];
             for (int ax = 0; ax < 3; ax++)
                 d[ax] += mass[j] * or_isep(pos[ax * np + j], t->center[3 * k + ax], 0) * scale;
             double ej = P->eps[cls ? cls[j] : 0];
             if (ej > em) em = ej;
+            if (ej < en) en = ej;
             double aj = aold ? aold[j] : 0.0;
             if (aj < am) am = aj;
         }
@@ -315,6 +321,7 @@ void or_multipoles(or_tree *t, const uint32_t *pos, int64_t np, const double *ma
         t->mass[k] = M;
         for (int ax = 0; ax < 3; ax++) t->com[3 * k + ax] = s[ax];
         t->eps_max[k] = em;
+        t->eps_min[k] = en;
         t->amin[k] = am;
         double *q = t->mono + nm * k;
         for (int64_t c = 0; c < nm; c++) q[c] = 0.0;
@@ -457,6 +464,40 @@ void or_gn(double r, double r_s, int nmax, double *g)
     }
 }
 
+/* g_n = (r^-1 d/dr)^n g for the softened kernel used by softened multipoles (Sec. 2.7):
+ * g = g_soft(r) for r_s <= 0, g = g_soft(r) - erf(r / 2 r_s) / r for TreePM, with
+ * g_soft = -W_2(u) / h (u = r / h < 1; W_2 the cubic-spline potential of or_soft_kernel) and
+ * 1/r beyond h.  On a piece W_2 = sum_k c_k u^k (k = -1, 0, 2, 3, 4, 5) the operator
+ * r^-1 d/dr maps u^k to (k / h^2) u^(k-2), so
+ *   g_n = -(1/h) sum_k c_k [k (k-2) ... (k-2n+2)] u^(k-2n) / h^(2n);
+ * the TreePM part is -erf/r = erfc/r - 1/r, i.e. or_gn with r_s minus or_gn without. */
+void or_gn_soft(double r, double h, double r_s, int nmax, double *g)
+{
+    if (r >= h) { or_gn(r, r_s, nmax, g); return; }
+    static const int kk[6] = {-1, 0, 2, 3, 4, 5};
+    const double c_in[6] = {0.0, -14.0 / 5.0, 16.0 / 3.0, 0.0, -48.0 / 5.0, 32.0 / 5.0};
+    const double c_out[6] = {1.0 / 15.0, -16.0 / 5.0, 32.0 / 3.0, -16.0, 48.0 / 5.0, -32.0 / 15.0};
+    const double *c = (r / h < 0.5) ? c_in : c_out;
+    double u = r / h;
+    for (int n = 0; n <= nmax; n++) {
+        double sum = 0.0;
+        for (int t = 0; t < 6; t++) {
+            if (c[t] == 0.0) continue;
+            double f = 1.0;
+            for (int m = 0; m < n; m++) f *= (double)(kk[t] - 2 * m);
+            if (f == 0.0) continue;
+            sum += c[t] * f * pow(u, (double)(kk[t] - 2 * n));
+        }
+        g[n] = -sum / h / pow(h, 2.0 * n);
+    }
+    if (r_s > 0.0) {
+        double ge[OR_MAXP + 2], gN[OR_MAXP + 2];
+        or_gn(r, r_s, nmax, ge);
+        or_gn(r, 0.0, nmax, gN);
+        for (int n = 0; n <= nmax; n++) g[n] += ge[n] - gN[n];
+    }
+}
+
 /* Full derivative tensor D_m = grad^(m) g(|r|) (3^m entries, index digit k of the flat index
  * is the k-th tensor index, little-endian in base 3).  Eqs. (eqngderiv0)-(eqngderiv): each
  * component is a sum over all partial pairings of its m index slots; a pairing with j pairs
@@ -515,12 +556,13 @@ static double or_factorial(int n)
 /* Particle-node term with r = s - x:
  *   phi += -G sum_{n=0}^{p}   (1/n!) Q_n . D_n        (Eq. eqonesidetreepotential)
  *   a   += -G sum_{n=0}^{p-1} (1/n!) Q_n . D_{n+1}    (Eq. eqonesidetreeacc)            */
-static void or_pn(const double *mono, const double *rv, int p, double r_s, double G,
-                  double *acc, double *pot)
+static void or_pn_h(const double *mono, const double *rv, int p, double r_s, double h, double G,
+                    double *acc, double *pot)
 {
     double r = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
     double g[OR_MAXP + 2];
-    or_gn(r, r_s, p, g);
+    if (h > 0.0) or_gn_soft(r, h, r_s, p, g);
+    else or_gn(r, r_s, p, g);
     double D[OR_MAXP + 1][729];
     for (int m = 0; m <= p; m++) or_D_full(m, rv, g, D[m]);
     double phi = 0.0, a[3] = {0, 0, 0};
@@ -538,6 +580,13 @@ static void or_pn(const double *mono, const double *rv, int p, double r_s, doubl
     for (int i = 0; i < 3; i++) acc[i] += -G * a[i];
 }
 
+/* the unsoftened particle-node term */
+static void or_pn(const double *mono, const double *rv, int p, double r_s, double G,
+                  double *acc, double *pot)
+{
+    or_pn_h(mono, rv, p, r_s, 0.0, G, acc, pot);
+}
+
 static double or_sep(uint32_t a, uint32_t b, const or_params *P)
 {
     return or_isep(a, b, P->periodic) * (P->box / 4294967296.0);
@@ -550,8 +599,10 @@ static double or_sep(uint32_t a, uint32_t b, const or_params *P)
  *     pp_cut is set);
  *   - an internal node is opened if the particle lies inside the node's cube, or inside the
  *     exclusion cube of half-width l around the geometric centre (Sec. 2.2.3, reading of
- *     Fig. FigTREESketch), or if r < 2.8 max(eps_i, eps_max(node)) (multipoles are always
- *     unsoftened, reading of Sec. 2.7), or if the opening criterion fails:
+ *     Fig. FigTREESketch), or if r < 2.8 max(eps_i, eps_max(node)) and either the
+ *     GADGET-3 rule is in force (multipoles always unsoftened) or, under the GADGET-4 rule of
+ *     Sec. 2.7, both eps_i and the node's smallest softening lie below eps_ij (otherwise the
+ *     multipole of the softened kernel with eps_ij is used), or if the criterion fails:
  *       relative  G M / r^2 (l / r)^p < alpha |a_old|     (Eq. eqnrelcriterion)
  *       geometric l / r < theta_c;
  *     otherwise its multipole expansion is used.                                          */
@@ -610,8 +661,15 @@ static void or_walk_one(const or_tree *t, const uint32_t *pos, int64_t np, const
         if (dmax <= 0.5 * side) open = 1;                     /* particle inside the node */
         if (P->exclusion && dmax < side) open = 1;             /* exclusion zone */
         double epsn = t->eps_max[k];
-        double h = 2.8 * (eps_i > epsn ? eps_i : epsn);
-        if (r2 < h * h) open = 1;                              /* softened: open */
+        double h = 2.8 * (eps_i > epsn ? eps_i : epsn);        /* 2.8 eps_ij */
+        int softened = r2 < h * h;
+        if (softened) {
+            if (!P->soft_nodes) open = 1;                      /* GADGET-3: always open */
+            /* GADGET-4 (Sec. 2.7): open only if both the particle's and the node's smallest
+             * softening are below eps_ij (a mixed node some of whose pairs would be
+             * oversoftened); otherwise use the multipole of the softened kernel */
+            else if (2.8 * eps_i < h && 2.8 * t->eps_min[k] < h) open = 1;
+        }
         if (!open) {
             if (P->criterion == 1) {
                 if (side * side >= P->theta * P->theta * r2) open = 1;
@@ -623,7 +681,7 @@ static void or_walk_one(const or_tree *t, const uint32_t *pos, int64_t np, const
             }
         }
         if (open) { k = k + 1; continue; }
-        or_pn(t->mono + nm * k, rv, p, P->r_s, P->G, acc, pot);
+        or_pn_h(t->mono + nm * k, rv, p, P->r_s, softened ? h : 0.0, P->G, acc, pot);
         cnt[1]++;
         k = t->next[k];
     }
@@ -782,6 +840,12 @@ static double or_cell_eps(const or_fmm_ctx *C, or_cell X)
     return C->P->eps[C->cls ? C->cls[X.k] : 0];
 }
 
+static double or_cell_eps_min(const or_fmm_ctx *C, or_cell X)
+{
+    if (!X.part) return C->t->eps_min[X.k];
+    return C->P->eps[C->cls ? C->cls[X.k] : 0];
+}
+
 static double or_cell_amin(const or_fmm_ctx *C, or_cell X)
 {
     if (!X.part) return C->t->amin[X.k];
@@ -814,15 +878,17 @@ static void or_pp(or_fmm_ctx *C, int64_t i, int64_t j)
  * 0..p about their centres of mass) and r = s_B - s_A (Sec. 2.4):
  *   fA_k = -G (-1)^k sum_{n=0}^{p-k} (1/n!) D_{n+k}(r) . Q^B_n      (field of B around s_A)
  *   fB_k = -G        sum_{n=0}^{p-k} ((-1)^n/n!) D_{n+k}(r) . Q^A_n (field of A around s_B)
- * Q_p is dropped unless keep_qp is set (it only shifts the potential by a constant).
- * fA, fB: full tensors of orders 0..p at offsets toff[k]. */
+ * Q_p is dropped unless keep_qp is set (it only shifts the potential by a constant).  h > 0
+ * takes the derivatives of the softened kernel with h = 2.8 eps_ij (or_gn_soft) instead of
+ * the unsoftened ones.  fA, fB: full tensors of orders 0..p at offsets toff[k]. */
 static void or_m2l_fields(const double *QA, const double *QB, const double *rv, int p,
-                          double r_s, double G, int keep_qp, const int *toff, double *fA,
-                          double *fB)
+                          double r_s, double h, double G, int keep_qp, const int *toff,
+                          double *fA, double *fB)
 {
     double r = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
     double g[OR_MAXP + 2];
-    or_gn(r, r_s, p, g);
+    if (h > 0.0) or_gn_soft(r, h, r_s, p, g);   /* softened multipoles (Sec. 2.7) */
+    else or_gn(r, r_s, p, g);
     static __thread double D[OR_MAXP + 1][729];
     for (int m = 0; m <= p; m++) or_D_full(m, rv, g, D[m]);
     for (int k = 0; k <= p; k++) {
@@ -859,8 +925,9 @@ static void or_deposit(or_fmm_ctx *C, or_cell X, const double *f)
     for (int c = 0; c < C->ntens; c++) T[c] += f[c];
 }
 
-/* Accepted interaction of two cells, both directions (node-node or particle-node). */
-static void or_m2l(or_fmm_ctx *C, or_cell A, or_cell B, const double *rv)
+/* Accepted interaction of two cells, both directions (node-node or particle-node); h > 0 for a
+ * softened interaction. */
+static void or_m2l(or_fmm_ctx *C, or_cell A, or_cell B, const double *rv, double h)
 {
     const or_tree *t = C->t;
     const or_params *P = C->P;
@@ -881,7 +948,7 @@ static void or_m2l(or_fmm_ctx *C, or_cell A, or_cell B, const double *rv)
     } else {
         QB = t->mono + nm * B.k;
     }
-    or_m2l_fields(QA, QB, rv, P->order, P->r_s, P->G, P->keep_qp, C->toff, fA, fB);
+    or_m2l_fields(QA, QB, rv, P->order, P->r_s, h, P->G, P->keep_qp, C->toff, fA, fB);
     or_deposit(C, A, fA);
     or_deposit(C, B, fB);
     if (A.part || B.part) {
@@ -952,7 +1019,10 @@ static int64_t or_daughters(const or_fmm_ctx *C, int64_t k, or_cell **out)
  *     within max(l_A, l_B) along every axis: touching equal-sized nodes, or a particle inside
  *     the exclusion cube of side 2l around a node (the tree's zone, Sec. 2.2.3); overlapping
  *     cubes never interact;
- *   - a pair with r < 2.8 max(eps) is opened (multipoles are unsoftened);
+ *   - a pair with r < 2.8 eps_ij, eps_ij = max(eps_max(A), eps_max(B)), is opened under the
+ *     GADGET-3 rule (multipoles unsoftened); under the GADGET-4 rule of Sec. 2.7 only if
+ *     eps_min(A) < eps_ij and eps_min(B) < eps_ij (both cells mixed), otherwise the pair
+ *     interacts through the expansion of the softened kernel with eps_ij;
  *   - relative criterion G M_max / r^2 (l_max / r)^(p-1) < alpha min(|a|_A, |a|_B), or the
  *     geometric one (l_A + l_B) / r < theta_c (Eq. eqnNodeDec); a particle contributes its
  *     own mass, side 0, softening and |a_old|.                                              */
@@ -979,8 +1049,12 @@ static void or_interact(or_fmm_ctx *C, or_cell A, or_cell B)
     double dmax = fmax(fabs(dc[0]), fmax(fabs(dc[1]), fabs(dc[2])));
     if (P->exclusion && dmax <= fmax(lA, lB)) accept = 0;   /* touching / exclusion zone */
     if (dmax < 0.5 * (lA + lB)) accept = 0;                  /* overlapping cubes */
-    double em = fmax(or_cell_eps(C, A), or_cell_eps(C, B));
-    if (r2 < (2.8 * em) * (2.8 * em)) accept = 0;
+    double em = fmax(or_cell_eps(C, A), or_cell_eps(C, B)), hsoft = 0.0;
+    if (r2 < (2.8 * em) * (2.8 * em)) {
+        if (!P->soft_nodes) accept = 0;
+        else if (or_cell_eps_min(C, A) < em && or_cell_eps_min(C, B) < em) accept = 0;
+        else hsoft = 2.8 * em;
+    }
     if (accept) {
         if (P->criterion == 1) {
             if ((lA + lB) * (lA + lB) >= P->theta * P->theta * r2) accept = 0;
@@ -993,7 +1067,7 @@ static void or_interact(or_fmm_ctx *C, or_cell A, or_cell B)
             if (!(lhs < rhs)) accept = 0;
         }
     }
-    if (accept) { or_m2l(C, A, B, rv); return; }
+    if (accept) { or_m2l(C, A, B, rv, hsoft); return; }
     or_cell *da = NULL, *db = NULL;
     int64_t na = 1, nb = 1;
     if (!A.part) na = or_daughters(C, A.k, &da);
@@ -1152,6 +1226,15 @@ void or_moments_points(const double *x, const double *m, int64_t n, int p, doubl
     }
 }
 
+/* The particle-node term of the softened kernel (or_pn_h with h = 2.8 eps), exported for pins. */
+void or_pn_soft_eval(const double *mono, const double *rv, int p, double r_s, double h, double G,
+                     double *acc, double *pot)
+{
+    acc[0] = acc[1] = acc[2] = 0.0;
+    *pot = 0.0;
+    or_pn_h(mono, rv, p, r_s, h, G, acc, pot);
+}
+
 /* One-sided tree: the particle-node term (or_pn) of group B at every particle of A. */
 void or_two_node_tree(const double *xa, int64_t na, const double *xb, const double *mb,
                       int64_t nb, int p, double r_s, double G, double *acc, double *pot)
@@ -1181,7 +1264,7 @@ void or_two_node_fmm(const double *xa, const double *ma, int64_t na, const doubl
     or_moments_points(xa, ma, na, p, sA, QA);
     or_moments_points(xb, mb, nb, p, sB, QB);
     for (int ax = 0; ax < 3; ax++) rv[ax] = sB[ax] - sA[ax];
-    or_m2l_fields(QA, QB, rv, p, r_s, G, keep_qp, toff, fA, fB);
+    or_m2l_fields(QA, QB, rv, p, r_s, 0.0, G, keep_qp, toff, fA, fB);
     for (int64_t i = 0; i < na; i++) {
         double a[3], grad[3];
         for (int ax = 0; ax < 3; ax++) a[ax] = xa[3 * i + ax] - sA[ax];

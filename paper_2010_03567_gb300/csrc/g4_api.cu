@@ -82,5 +82,6 @@ extern "C" g4_status g4_params_default(g4_params *p)
     p->fp64_count = 4096;
     p->keep_qp = 0;
     p->fmm_p2p_per_particle = 0;
+    p->soft_nodes = 0;
     return G4_OK;
 }

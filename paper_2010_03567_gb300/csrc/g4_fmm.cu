@@ -179,6 +179,7 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     A.exclusion = P->exclusion_zone;
     A.pp_cut = P->pp_cut;
     A.keep_qp = P->keep_qp;
+    A.soft_nodes = P->soft_nodes;
     A.rcut2f = (float)A.rcut2;
     A.asf = (float)A.as;
     const double igs = 4294967296.0 / P->box_size;

@@ -96,8 +96,10 @@ __device__ __forceinline__ int fmm_decide(const FmmArgs &A, const G4Node &na, in
     const float dmax = fmaxf(fabsf(dcx), fmaxf(fabsf(dcy), fabsf(dcz)));
     if (A.exclusion && dmax <= fmaxf(lA, lB)) accept = false;   // touching nodes never interact
     if (dmax < hl) accept = false;                              // overlapping cubes
+    // closer than 2.8 eps_ij: opened (GADGET-3 rule), or under the rule of Sec. 2.7 only if
+    // both nodes hold particles with softenings below eps_ij (else a softened interaction)
     const float h = fmaxf(na.hmax, nb.hmax);
-    if (r2 < h * h) accept = false;                             // multipoles are unsoftened
+    if (r2 < h * h && (!A.soft_nodes || (na.hmin < h && nb.hmin < h))) accept = false;
     if (accept) {
         if (GEOM) {
             accept = (lA + lB) * (lA + lB) < (float)A.theta2 * r2;
@@ -145,7 +147,7 @@ __device__ __forceinline__ int fmm_decide_pn(const FmmArgs &A, const G4Node &nz,
     if (A.exclusion && dmax <= l) accept = false;   // inside the node's exclusion cube
     if (dmax < hl) accept = false;                  // inside the node
     const float h = fmaxf(nz.hmax, x.h);
-    if (r2 < h * h) accept = false;
+    if (r2 < h * h && (!A.soft_nodes || (nz.hmin < h && x.h < h))) accept = false;
     if (accept) {
         if (GEOM) {
             accept = l * l < (float)A.theta2 * r2;
@@ -164,15 +166,24 @@ __device__ __forceinline__ int fmm_decide_pn(const FmmArgs &A, const G4Node &nz,
     return accept ? D_ACCEPT : D_OPEN;
 }
 
+// g_0..g_P of the interaction kernel: the softened one (h = 2.8 eps_ij) inside h when the
+// rule of Sec. 2.7 is in force (hs = h), the unsoftened one otherwise (hs = 0)
+template <int P, bool TREEPM>
+__device__ __forceinline__ void fmm_gn(const FmmArgs &A, float r2, float hs, float *g)
+{
+    if (hs > 0.f && r2 < hs * hs) gn_soft<P, float, TREEPM>(r2, hs, (float)A.as, g);
+    else gn_kernel<P, float, TREEPM>(r2, (float)A.as, g);
+}
+
 // lane-private M2L: T += field of node B at A's centre of mass (r = s_B - s_A)
 template <int P, bool TREEPM>
 __device__ __forceinline__ void m2l_add(const FmmArgs &A, float *T, int db, const G4Node &nb,
-                                        float rx, float ry, float rz)
+                                        float rx, float ry, float rz, float hs)
 {
     constexpr int NT = FT<P>::NT;
     const float r2 = rx * rx + ry * ry + rz * rz;
     float g[P + 1];
-    gn_kernel<P, float, TREEPM>(r2, (float)A.as, g);
+    fmm_gn<P, TREEPM>(A, r2, hs, g);
     float D[NT];
     dtensors<P, float>(rx, ry, rz, g, D);
     float Q[NT];
@@ -209,12 +220,12 @@ __device__ __forceinline__ void m2l_add(const FmmArgs &A, float *T, int db, cons
 // (the M2L with Q_0 = m only): T_k += -G (-1)^|k| m D_k(r)
 template <int P, bool TREEPM>
 __device__ __forceinline__ void p2l_add(const FmmArgs &A, float *T, float m, float rx, float ry,
-                                        float rz)
+                                        float rz, float hs)
 {
     constexpr int NT = FT<P>::NT;
     const float r2 = rx * rx + ry * ry + rz * rz;
     float g[P + 1];
-    gn_kernel<P, float, TREEPM>(r2, (float)A.as, g);
+    fmm_gn<P, TREEPM>(A, r2, hs, g);
     float D[NT];
     dtensors<P, float>(rx, ry, rz, g, D);
     const float mG = -(float)A.G * m;
@@ -234,11 +245,12 @@ __device__ __forceinline__ void p2l_add(const FmmArgs &A, float *T, float m, flo
 // when keep_qp); the caller multiplies both by -G.
 template <int P, bool TREEPM>
 __device__ __forceinline__ void m2p_add(const FmmArgs &A, int dz, const G4Node &nz, float x, float y,
-                                        float z, float &sx, float &sy, float &sz, float &sp)
+                                        float z, float hs, float &sx, float &sy, float &sz,
+                                        float &sp)
 {
     const float r2 = x * x + y * y + z * z;
     float g[P + 1];
-    gn_kernel<P, float, TREEPM>(r2, (float)A.as, g);
+    fmm_gn<P, TREEPM>(A, r2, hs, g);
     float D[g4_nmono(P)];
     dtensors<P, float>(x, y, z, g, D);
     const float M = nz.mass;
@@ -501,7 +513,8 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                             const PCell x = load_pcell(A, p0 + bit);
                             const int d = fmm_decide_pn<P, TREEPM, GEOM>(A, na, x, rx, ry, rz);
                             if (d == D_ACCEPT) {
-                                p2l_add<P, TREEPM>(A, T, x.m, -rx, -ry, -rz);
+                                p2l_add<P, TREEPM>(A, T, x.m, -rx, -ry, -rz,
+                                                   A.soft_nodes ? fmaxf(na.hmax, x.h) : 0.f);
                             } else if (d == D_OPEN) {
                                 keep |= 1u << bit;
                             }
@@ -515,7 +528,8 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                     }
                 }
                 if (dec == D_ACCEPT) {
-                    m2l_add<P, TREEPM>(A, T, ce.x, nb, rx, ry, rz);
+                    m2l_add<P, TREEPM>(A, T, ce.x, nb, rx, ry, rz,
+                                       A.soft_nodes ? fmaxf(na.hmax, nb.hmax) : 0.f);
                     nm2l++;
                 }
                 const int pre = warp_excl_i(e, lane);
@@ -600,7 +614,8 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                         if (dec == D_OPEN && !(nb.meta & 32u)) e = nb.nchild;   // B internal
                     }
                     if (ic == 0 && dec == D_ACCEPT) {
-                        m2l_add<P, TREEPM>(A, T, ce.x, nb, rx, ry, rz);
+                        m2l_add<P, TREEPM>(A, T, ce.x, nb, rx, ry, rz,
+                                           A.soft_nodes ? fmaxf(na.hmax, nb.hmax) : 0.f);
                         nm2l++;
                     }
                     // leaf pairs (A itself, or a leaf B that fails): all of A's particles
@@ -636,7 +651,9 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                                 const PCell x = load_pcell(A, y);
                                 float qx, qy, qz;
                                 const int d = fmm_decide_pn<P, TREEPM, GEOM>(A, na, x, qx, qy, qz);
-                                if (d == D_ACCEPT) p2l_add<P, TREEPM>(A, T, x.m, -qx, -qy, -qz);
+                                if (d == D_ACCEPT)
+                                    p2l_add<P, TREEPM>(A, T, x.m, -qx, -qy, -qz,
+                                                       A.soft_nodes ? fmaxf(na.hmax, x.h) : 0.f);
                                 op = d == D_OPEN;
                             }
                             push_pp(op, make_int4(y, 1, 0, 0));
@@ -655,7 +672,9 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                         if (((unsigned)se.y >> lane) & 1u)
                             d = fmm_decide_pn<P, TREEPM, GEOM>(A, nz, xs, qx, qy, qz);
                         if (d == D_ACCEPT) {
-                            m2p_add<P, TREEPM>(A, se.x, nz, qx, qy, qz, bx, by, bz, bp);
+                            m2p_add<P, TREEPM>(A, se.x, nz, qx, qy, qz,
+                                               A.soft_nodes ? fmaxf(nz.hmax, xs.h) : 0.f, bx, by,
+                                               bz, bp);
                             npn++;
                         }
                         const unsigned om = __ballot_sync(0xffffffffu, d == D_OPEN);

@@ -40,6 +40,7 @@ struct FmmArgs {
     double scale, G, alpha, theta2, rcut2, as, box;
     float h_cls[G4_MAX_EPS_CLASSES];
     int exclusion, pp_cut, keep_qp;
+    int soft_nodes;            // 1: softened multipoles under the rule of Sec. 2.7
     // particle-particle phase (shared with the tree walk)
     const uint4 *wpart;        // particles as (x, y, z, mass bits)
     float rcut2f, asf, figs, rc2i;

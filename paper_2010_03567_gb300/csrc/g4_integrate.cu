@@ -3,7 +3,8 @@
 // operator D moves the integer coordinates by v * dt (Sec. 2.10: positions stay exact integers,
 // a periodic box wraps through the 32-bit overflow), and the timestep criterion
 // dt_i = sqrt(2 eta eps_i / |a_i|) places every particle in the power-of-two bin k with
-// dt_max / 2^k <= dt_i.
+// dt_max / 2^k <= dt_i.  g4_translate shifts all integer coordinates by one vector (the random
+// translation of Sec. 3.8).
 #include "g4_internal.cuh"
 
 namespace {
@@ -66,9 +67,31 @@ __global__ void k_timebins(const float *__restrict__ acc, const uint8_t *__restr
     }
 }
 
+// out = in + shift (mod 2^32) per axis: the loss-less random translation of Sec. 3.8
+__global__ void k_translate(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
+                            uint32_t sx, uint32_t sy, uint32_t sz)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        out[i] = in[i] + sx;
+        out[n + i] = in[n + i] + sy;
+        out[2 * n + i] = in[2 * n + i] + sz;
+    }
+}
+
 }  // namespace
 
 g4_status g4_check_params(const g4_params *P, const char *who);
+
+extern "C" g4_status g4_translate(const uint32_t *pos_in, uint32_t *pos_out, int64_t n,
+                                  const uint32_t *shift, void *stream)
+{
+    if (n < 0 || n >= ((int64_t)1 << 31) || !shift || (n > 0 && (!pos_in || !pos_out)))
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_translate: bad arguments");
+    if (n == 0) return G4_OK;
+    k_translate<<<g4_blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(pos_in, pos_out, (int)n,
+                                                                         shift[0], shift[1], shift[2]);
+    return g4_launch_check("translate", 1);
+}
 
 extern "C" g4_status g4_kick(float *vel, const float *acc, const int32_t *idx, int64_t n_idx,
                              int64_t n, double dt, void *stream)

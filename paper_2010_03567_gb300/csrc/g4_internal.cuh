@@ -35,7 +35,7 @@ struct __align__(16) G4Node {
     int32_t first, count, next, parent;
     float amin;           // minimum |a_old| of the node's particles (FMM criterion)
     float hmax;           // 2.8 * largest softening among the node's particles
-    int32_t bfs;          // index in the level-ordered build arrays
+    float hmin;           // 2.8 * smallest softening among the node's particles
     int32_t nchild;       // number of daughters (0 for a leaf)
 };
 static_assert(sizeof(G4Node) == 64, "node record must be 64 bytes");

@@ -34,7 +34,7 @@ __device__ __forceinline__ G4Node load_node(const G4Node *p)
     nd.parent = c.w;
     nd.amin = __int_as_float(d.x);
     nd.hmax = __int_as_float(d.y);
-    nd.bfs = d.z;
+    nd.hmin = __int_as_float(d.z);
     nd.nchild = d.w;
     return nd;
 }
@@ -155,20 +155,11 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// the rare softened / beyond-the-fit pairs of pair_treepm_fast, kept out of line so that the
-// common path stays a short branch-free sequence (an inlined copy could be if-converted into
-// every evaluation)
-static __device__ __noinline__ void pair_treepm_slow(float r2, float h, float as, float &g0,
-                                                    float &g1)
-{
-    pair_kernel<float, true>(r2, h, as, g0, g1);
-}
-
 __device__ __forceinline__ void pair_treepm_fast(float r2, float h, const PairF &c, float &g0,
                                                  float &g1)
 {
     if (r2 < h * h || r2 > c.fit2) {
-        pair_treepm_slow(r2, h, c.as, g0, g1);
+        pair_kernel<float, true>(r2, h, c.as, g0, g1);
         return;
     }
     const float rinv = rsqrt_approx(r2), r = r2 * rinv;   // r2 > 0 here, never subnormal
@@ -197,6 +188,43 @@ __device__ __forceinline__ void gn_kernel(T r2, T as, T *g)
         B = (T(2 * n - 1) * B + t) * rinv2;
         if (TREEPM) t *= tw;
         g[n] = (n & 1) ? -B : B;
+    }
+}
+
+// g_0..g_N of the softened kernel for a softened multipole (Sec. 2.7), r < h: the spline part
+// -W_2(u)/h (u = r/h) differentiated term by term -- (r^-1 d/dr) u^k = (k / h^2) u^(k-2) --
+// plus, for TreePM, -erf(r/2r_s)/r = erfc/r - 1/r (the unsoftened erfc kernel's g_n minus the
+// Newtonian ones).  W_2 = sum c_k u^k on u < 1/2 and on 1/2 <= u < 1 (k = -1, 0, 2, 3, 4, 5).
+template <int N, typename T, bool TREEPM>
+__device__ __noinline__ void gn_soft(T r2, T h, T as, T *g)
+{
+    const T r = Math<T>::sqrt(r2), u = r / h, uinv = T(1) / u, hinv = T(1) / h, h2inv = hinv * hinv;
+    const bool inner = u < T(0.5);
+    const int kk[6] = {-1, 0, 2, 3, 4, 5};
+    const T ci[6] = {T(0), T(-14.0 / 5.0), T(16.0 / 3.0), T(0), T(-48.0 / 5.0), T(32.0 / 5.0)};
+    const T co[6] = {T(1.0 / 15.0), T(-16.0 / 5.0), T(32.0 / 3.0), T(-16.0), T(48.0 / 5.0),
+                     T(-32.0 / 15.0)};
+    T hp = hinv;   // h^-(2n+1)
+    for (int n = 0; n <= N; n++) {
+        T sum = T(0);
+        for (int t = 0; t < 6; t++) {
+            const T c = inner ? ci[t] : co[t];
+            T f = T(1);
+            for (int m = 0; m < n; m++) f *= T(kk[t] - 2 * m);
+            if (c == T(0) || f == T(0)) continue;
+            const int e = kk[t] - 2 * n;
+            T up = T(1);
+            for (int q = 0; q < (e > 0 ? e : -e); q++) up *= (e > 0 ? u : uinv);
+            sum += c * f * up;
+        }
+        g[n] = -sum * hp;
+        hp *= h2inv;
+    }
+    if (TREEPM) {
+        T ge[N + 1], gn[N + 1];
+        gn_kernel<N, T, true>(r2, as, ge);
+        gn_kernel<N, T, false>(r2, as, gn);
+        for (int n = 0; n <= N; n++) g[n] += ge[n] - gn[n];
     }
 }
 
@@ -235,13 +263,15 @@ __device__ __forceinline__ void dtensors(T x, T y, T z, const T *g, T *D)
 // Particle-node term of the one-sided expansion with r = s - x (Eqs. eqonesidetreepotential,
 // eqonesidetreeacc): sacc += sum_{n<P} Q_n . D_{n+1} / n!,  spot += sum_{n<=P} Q_n . D_n / n!
 // (the caller multiplies both by -G).  Qs holds moments of orders 2..P at g4_midx - 4.
+// hs > 0 with r^2 < hs^2: the multipole of the softened kernel with h = hs (Sec. 2.7).
 template <int P, typename T, bool TREEPM>
 __device__ __forceinline__ void pn_term(const T *Qs, T M, T x, T y, T z, T as, T &sx, T &sy,
-                                        T &sz, T &sp)
+                                        T &sz, T &sp, T hs = T(0))
 {
     const T r2 = x * x + y * y + z * z;
     T g[P + 1];
-    gn_kernel<P, T, TREEPM>(r2, as, g);
+    if (hs > T(0) && r2 < hs * hs) gn_soft<P, T, TREEPM>(r2, hs, as, g);
+    else gn_kernel<P, T, TREEPM>(r2, as, g);
     T D[g4_nmono(P)];
     dtensors<P, T>(x, y, z, g, D);
     T ax = M * D[g4_midx(1, 0, 0)], ay = M * D[g4_midx(0, 1, 0)], az = M * D[g4_midx(0, 0, 1)];

@@ -139,7 +139,7 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd, int slot
                                   (1.0 / 4294967296.0))
                             : (T)A.scale;
     T M = T(0), sx = T(0), sy = T(0), sz = T(0);
-    float hmax = 0.f, amin = 3.0e38f;
+    float hmax = 0.f, hmin = 3.0e38f, amin = 3.0e38f;
     const bool leaf = nd.meta & 32u;
     if (leaf) {
         const int f = nd.first, e = nd.first + nd.count;
@@ -150,7 +150,9 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd, int slot
             sx += m * ((T)(int32_t)(A.pos[j] - nd.cx) * scale);
             sy += m * ((T)(int32_t)(A.pos[A.n + j] - nd.cy) * scale);
             sz += m * ((T)(int32_t)(A.pos[2 * A.n + j] - nd.cz) * scale);
-            hmax = fmaxf(hmax, A.h_cls[A.cls ? A.cls[j] : 0]);
+            const float hj = A.h_cls[A.cls ? A.cls[j] : 0];
+            hmax = fmaxf(hmax, hj);
+            hmin = fminf(hmin, hj);
             amin = fminf(amin, A.aold ? A.aold[j] : 0.f);
         }
         const T inv = M > T(0) ? T(1) / M : T(0);
@@ -188,6 +190,7 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd, int slot
             sy += mc * ((T)(int32_t)(c.cy - nd.cy) * scale + oy);
             sz += mc * ((T)(int32_t)(c.cz - nd.cz) * scale + oz);
             hmax = fmaxf(hmax, c.hmax);
+            hmin = fminf(hmin, c.hmin);
             amin = fminf(amin, c.amin);
         }
         const T inv = M > T(0) ? T(1) / M : T(0);
@@ -230,6 +233,7 @@ __device__ void node_moments(const MomArgs &A, int d, const G4Node &nd, int slot
     o.sz = (float)sz;
     o.mass = (float)M;
     o.hmax = hmax;
+    o.hmin = hmin;
     o.amin = amin;
     float *dst = A.q + (size_t)d * A.nq;
 #pragma unroll
@@ -272,7 +276,7 @@ __device__ void node_moments_warp(const MomArgs &A, int d, const G4Node &nd, int
     T qc[NM];
 #pragma unroll
     for (int k = 0; k < NM; k++) qc[k] = T(0);
-    float hmax = 0.f, amin = 3.0e38f;
+    float hmax = 0.f, hmin = 3.0e38f, amin = 3.0e38f;
     if (has) {
         const int ch = A.b_dfs[A.b_child[slot] + lane];
         const G4Node c = A.node[ch];
@@ -296,6 +300,7 @@ __device__ void node_moments_warp(const MomArgs &A, int d, const G4Node &nd, int
         ey = (T)(int32_t)(c.cy - nd.cy) * scale + oy;
         ez = (T)(int32_t)(c.cz - nd.cz) * scale + oz;
         hmax = c.hmax;
+        hmin = c.hmin;
         amin = c.amin;
     }
     const T M = octet_sum(mc);
@@ -311,6 +316,7 @@ __device__ void node_moments_warp(const MomArgs &A, int d, const G4Node &nd, int
 #pragma unroll
     for (int s = 4; s >= 1; s >>= 1) {
         hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, s));
+        hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, s));
         amin = fminf(amin, __shfl_xor_sync(0xffffffffu, amin, s));
     }
     if (lane != 0) return;
@@ -320,6 +326,7 @@ __device__ void node_moments_warp(const MomArgs &A, int d, const G4Node &nd, int
     o.sz = (float)sz;
     o.mass = (float)M;
     o.hmax = hmax;
+    o.hmin = hmin;
     o.amin = amin;
     float *dst = A.q + (size_t)d * A.nq;
 #pragma unroll

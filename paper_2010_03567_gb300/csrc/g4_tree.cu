@@ -375,7 +375,7 @@ __global__ void k_build_emit(const int32_t *__restrict__ lvl, const int32_t *__r
         nd.parent = b_parent[b] >= 0 ? b_dfs[b_parent[b]] : -1;
         nd.amin = 0.f;
         nd.hmax = 0.f;
-        nd.bfs = b;
+        nd.hmin = 0.f;
         nd.nchild = b_child[b] < 0 ? 0 : b_nchild[b];
         node[d] = nd;
     }

@@ -59,6 +59,7 @@ struct WalkArgs {
     double inv_as, igs;                      // 1 / as; integer units per length unit (box)
     float h_cls[G4_MAX_EPS_CLASSES];
     int exclusion, pp_cut;
+    int soft_nodes;               // GADGET-4 softened-node rule (Sec. 2.7)
 };
 
 
@@ -116,8 +117,11 @@ __device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &n
     const T rx = dcx + ox, ry = dcy + oy, rz = dcz + oz;
     const T r2 = rx * rx + ry * ry + rz * rz;
     const T dmax = fmax(fabs(dcx), fmax(fabs(dcy), fabs(dcz)));
-    const T h = fmax(hi, (T)nd.hmax);
-    bool open = (dmax <= half) || (A.exclusion && dmax < side) || (r2 < h * h);
+    const T h = fmax(hi, (T)nd.hmax);   // 2.8 eps_ij
+    // closer than 2.8 eps_ij: GADGET-3 opens; GADGET-4 opens only a node that mixes smaller
+    // softenings when the particle's own is smaller too, else uses the softened multipole
+    const bool soft_open = r2 < h * h && (!A.soft_nodes || (hi < h && (T)nd.hmin < h));
+    bool open = (dmax <= half) || (A.exclusion && dmax < side) || soft_open;
     if (!open) {
         if (GEOM) open = side * side >= par<T>(A.theta2, A.theta2f) * r2;
         else open = !(par<T>(A.G, A.Gf) * M * ipow<P>(side) < crit * ipow<P + 2>(sqrt(r2)));
@@ -268,7 +272,7 @@ k_walk(const WalkArgs A)
                     const float fx = fabsf(dcx + nd.sx) + ghx, fy = fabsf(dcy + nd.sy) + ghy,
                                 fz = fabsf(dcz + nd.sz) + ghz;
                     const float rmax2 = (fx * fx + fy * fy + fz * fz) * 1.001f;
-                    if (rmax2 < nd.hmax * nd.hmax) none = true;
+                    if (!A.soft_nodes && rmax2 < nd.hmax * nd.hmax) none = true;
                     if (GEOM) {
                         if (side * side >= A.theta2f * rmax2) none = true;
                     } else {
@@ -332,7 +336,8 @@ k_walk(const WalkArgs A)
                     const T rx = (T)(int32_t)(n2.cx - xi) * (T)gscale + mx;
                     const T ry = (T)(int32_t)(n2.cy - yi) * (T)gscale + my;
                     const T rz = (T)(int32_t)(n2.cz - zi) * (T)gscale + mz;
-                    pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, par<T>(A.as, A.asf), bx, by, bz, bp);
+                    const T hs = A.soft_nodes ? fmax(hi, (T)n2.hmax) : T(0);
+                    pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, par<T>(A.as, A.asf), bx, by, bz, bp, hs);
                     npn++;
                 }
                 if (lane == src) m &= ~accm;
@@ -515,7 +520,6 @@ __global__ void k_walk_nodes(const int32_t *__restrict__ lvl, const int32_t *__r
         G4Node r = node[d];
         r.next = r.nchild > 0 ? b_child[b] : -1;
         r.parent = d;
-        r.bfs = b;
         wnode[b] = r;
     }
 }
@@ -691,6 +695,7 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
         A.h_cls[k] = k < P->n_eps_classes ? (float)(2.8 * P->eps_table[k]) : 0.f;
     A.exclusion = P->exclusion_zone;
     A.pp_cut = P->pp_cut;
+    A.soft_nodes = P->soft_nodes;
     if (!t->walk_queue) {
         // frontier rings, allocated on the handle's first walk (outside any graph capture)
         const size_t bytes = sizeof(int2) * (size_t)G4_WALK_QCAP * g4_num_sms() *

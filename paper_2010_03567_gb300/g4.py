@@ -33,7 +33,8 @@ class G4Params(C.Structure):
                 ("leaf_max", C.c_int), ("exclusion_zone", C.c_int), ("precision", C.c_int),
                 ("G", C.c_double), ("n_eps_classes", C.c_int),
                 ("eps_table", C.c_double * MAX_EPS), ("group_size", C.c_int),
-                ("fp64_count", C.c_int), ("keep_qp", C.c_int), ("fmm_p2p_per_particle", C.c_int)]
+                ("fp64_count", C.c_int), ("keep_qp", C.c_int), ("fmm_p2p_per_particle", C.c_int),
+                ("soft_nodes", C.c_int)]
 
     def copy(self) -> "G4Params":
         p = G4Params()
@@ -88,6 +89,7 @@ def _declare(L):
         "g4_direct": ([vp, vp, vp, i64, vp, i64, P, vp, vp, vp], i32),
         "g4_pm_workspace": ([C.c_int32, C.POINTER(C.c_size_t)], i32),
         "g4_kick": ([vp, vp, vp, i64, i64, d, vp], i32),
+        "g4_translate": ([vp, vp, i64, C.POINTER(C.c_uint32), vp], i32),
         "g4_drift": ([vp, vp, vp, i64, i64, d, P, vp, vp], i32),
         "g4_timestep_bins": ([vp, vp, vp, i64, i64, P, d, d, C.c_int32, vp, vp], i32),
         "g4_pm_long_range": ([vp, vp, i64, vp, i64, P, C.c_int32, vp, vp, i32, vp, C.c_size_t, vp], i32),
@@ -413,8 +415,15 @@ class TreeGravity:
         self.acc = torch.zeros((3, n), dtype=torch.float32, device=dev)
         self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
 
-    def prepare(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None):
+    def prepare(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None,
+                shift=None):
+        """Keys, sort, gather, tree and multipoles.  shift: optional integer vector added to all
+        positions first (the random translation of Sec. 3.8; periodic boxes), on a copy."""
         p = p or self.p
+        if shift is not None:
+            if getattr(self, "pos_shift", None) is None:
+                self.pos_shift = torch.empty_like(pos_int)
+            pos_int = g4_translate(pos_int, shift, out=self.pos_shift, stream=stream)
         g4_keys_sort(pos_int, self.keys, self.perm, self.ws, stream)
         g4_gather(self.perm, pos_int, mass, cls if self.cls_s is not None else None, aold,
                   out=(self.pos_s, self.mass_s, self.cls_s if cls is not None else None,
@@ -431,8 +440,9 @@ class TreeGravity:
         g4_scatter(self.perm, self.acc_s, self.pot_s, out=(self.acc, self.pot), stream=stream)
         return self.acc, self.pot
 
-    def forces(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None):
-        self.prepare(pos_int, mass, cls, aold, p, stream)
+    def forces(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None,
+               shift=None):
+        self.prepare(pos_int, mass, cls, aold, p, stream, shift)
         return self.walk(p, use_aold=aold is not None, stream=stream)
 
 
@@ -805,6 +815,15 @@ class BinnedForces:
 
 
 # ---- hierarchical time integration (Sec. 4.2) -------------------------------------------------------
+
+def g4_translate(pos_in, shift, out=None, stream=None):
+    """pos_in + shift modulo 2^32 (Sec. 3.8); shift: three integers (taken modulo 2^32)."""
+    n = pos_in.shape[1]
+    out = out if out is not None else torch.empty_like(pos_in)
+    sh = (C.c_uint32 * 3)(*[int(v) % (1 << 32) for v in shift])
+    _check(lib().g4_translate(_ptr(pos_in), _ptr(out), n, sh, _stream(stream)), "g4_translate")
+    return out
+
 
 def g4_kick(vel, acc, dt: float, idx=None, stream=None):
     n = vel.shape[1]

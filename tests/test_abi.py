@@ -47,3 +47,32 @@ def test_oracle_and_library_share_no_code():
         assert "oracle" not in open(f).read().lower().replace("oracle-free", "")
     txt = open(os.path.join(ROOT, "oracle", "g4_oracle.c")).read()
     assert "g4.h" not in txt and "g4_internal" not in txt
+
+
+def test_params_struct_layout_matches_header(tmp_path):
+    """The binding's ctypes mirror of g4_params has the header's size and field offsets (a
+    field missing on the Python side would let the library write past the caller's struct)."""
+    import shutil
+    import subprocess
+    from paper_2010_03567_gb300 import g4
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in g4.G4Params._fields_]
+    prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "g4.h"', "int main(void) {",
+            '  printf("%zu\\n", sizeof(g4_params));']
+    prog += [f'  printf("%zu\\n", offsetof(g4_params, {f}));' for f in fields]
+    prog += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    hdr = open(os.path.join(ROOT, "include", "g4.h")).read()
+    body = re.search(r"typedef struct g4_params \{(.*?)\} g4_params;", hdr, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    declared = re.findall(r"(\w+)\s*(?:\[[^\]]*\])?\s*;", body)
+    assert declared == fields, (declared, fields)
+    assert out[0] == C.sizeof(g4.G4Params)
+    assert out[1:] == [getattr(g4.G4Params, f).offset for f in fields]

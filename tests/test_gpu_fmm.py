@@ -16,13 +16,14 @@ from _helpers import gpu_params, int_coords, oracle_params, relerr, to_dev, u32_
 pytestmark = pytest.mark.gpu
 
 
-def gpu_fmm(ps, q, P, aold):
+def gpu_fmm(ps, q, P, aold, cls=False):
     """GPU FMM through the C ABI; caller order.  Counts (n, 3): particle pairs, particle-node
-    terms, node-node fields of each particle."""
-    tg = g4.TreeGravity(ps.n, P)
-    tg.prepare(u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32), None,
+    terms, node-node fields of each particle.  cls: pass the softening classes."""
+    tg = g4.TreeGravity(ps.n, P, with_cls=cls)
+    tg.prepare(u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32),
+               to_dev(torch, ps.eps_class, torch.uint8) if cls else None,
                None if aold is None else to_dev(torch, aold, torch.float32), P)
-    acc, pot, cnt, mom = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None,
+    acc, pot, cnt, mom = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, tg.cls_s if cls else None,
                                              None if aold is None else tg.aold_s, P)
     torch.cuda.synchronize()
     tg.tree.status()
@@ -36,10 +37,10 @@ def gpu_fmm(ps, q, P, aold):
     return a, p, c, mom.cpu().numpy()
 
 
-def oracle_fmm(ps, q, OP, aold, leaf=8):
+def oracle_fmm(ps, q, OP, aold, leaf=8, cls=False):
     """Oracle FMM; caller order.  Returns acc, pot, totals [NN, PN, PP], per-particle counts
     (n, 2): particle pairs, particle-node terms."""
-    run = oracle.prepare(q, ps.mass, None, aold, OP, leaf)
+    run = oracle.prepare(q, ps.mass, ps.eps_class if cls else None, aold, OP, leaf)
     acc_s, pot_s, cnt, pc_s = run.tree.fmm(OP, per_particle=True)
     a = np.empty_like(acc_s)
     a[run.perm] = acc_s
@@ -206,3 +207,31 @@ def test_fmm_parity_two_softening_classes_leaf_above_32():
     assert co[1] > 0
     assert same_counts(cg, pc)
     assert np.percentile(relerr(ag, ao), 99) < 1e-5
+
+
+def test_fmm_parity_softened_node_rule():
+    """The FMM under GADGET-4's softened-node rule (Sec. 2.7, soft_nodes = 1; node-node and
+    particle-node pairs closer than 2.8 eps_ij use the softened kernel unless both sides are
+    mixed) against the oracle's, with two softening classes mixed through every node; the
+    GADGET-3 rule on the same set evaluates more particle pairs."""
+    ps = synth.plummer(2000, 65)
+    ps.eps_table = np.array([0.08, 0.3])
+    ps.eps_class[::4] = 1
+    q, box = int_coords(ps)
+    ad, _ = oracle.direct(q, ps.mass, ps.eps_class, np.arange(ps.n), oracle_params(ps, box))
+    aold = np.linalg.norm(ad, axis=1).astype(np.float32)
+    pp = {}
+    for soft in (0, 1):
+        kw = dict(alpha=0.005, order_p=4, leaf_max=4, soft_nodes=soft)
+        ag, pg, cg, mom = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), aold, cls=True)
+        ao, po, co, pc = oracle_fmm(ps, q, oracle_params(ps, box, **kw), aold.astype(np.float64),
+                                    leaf=4, cls=True)
+        assert same_counts(cg, pc), soft
+        e = relerr(ag, ao)
+        assert np.percentile(e, 99) < 1e-5, (soft, np.percentile(e, [50, 99, 100]))
+        assert np.percentile(np.abs(pg - po) / np.abs(po), 99) < 1e-5
+        assert np.percentile(relerr(ag, ad), 99) < 0.01
+        amag = np.linalg.norm(ag, axis=1)
+        assert np.linalg.norm(mom) < 1e-5 * np.sum(ps.mass * amag)
+        pp[soft] = co[2]
+    assert pp[1] < pp[0], pp

@@ -401,3 +401,30 @@ def test_walk_group_sizes_same_interactions(gs):
     ags, pgs, cgs, _ = gpu_forces(torch, g4, ps, q, Pgs, aold)
     assert np.array_equal(c32, cgs)
     assert np.percentile(relerr(ags, a32), 99) < 2e-5
+
+
+def test_walk_parity_softened_node_rule():
+    """GADGET-4's softened node interactions (Sec. 2.7, soft_nodes = 1) against the oracle's:
+    softenings comparable to the node sizes and two classes, so that both the softened
+    multipoles and the forced opening of mixed nodes occur.  soft_nodes = 0 (the GADGET-3 rule,
+    every node within 2.8 max(eps) opened) on the same set evaluates more particle pairs."""
+    ps = synth.plummer(3000, 63)
+    ps.eps_table = np.array([0.3, 0.08])
+    ps.eps_class[::4] = 1
+    q, box = int_coords(ps)
+    ad, _ = oracle.direct(q, ps.mass, ps.eps_class, np.arange(ps.n), oracle_params(ps, box))
+    aold = np.linalg.norm(ad, axis=1).astype(np.float32)
+    pp = {}
+    for soft in (0, 1):
+        kw = dict(alpha=0.005, order_p=3, leaf_max=4, soft_nodes=soft)
+        ag, pg, cg, _ = gpu_forces(torch, g4, ps, q, gpu_params(g4, ps, box, **kw), aold)
+        run = oracle.prepare(q, ps.mass, ps.eps_class, aold.astype(np.float64),
+                             oracle_params(ps, box, **kw), 4)
+        ao, po, co = oracle.tree_forces(run, np.arange(ps.n))
+        e = relerr(ag, ao)
+        assert np.percentile(e, 99) < PARITY_P99, (soft, np.percentile(e, [50, 99, 100]))
+        assert np.percentile(np.abs(pg - po) / np.abs(po), 99) < PARITY_P99
+        assert np.mean(np.all(cg == co, axis=1)) > 0.99
+        assert np.percentile(relerr(ag, ad), 99) < 0.01
+        pp[soft] = cg[:, 0].sum()
+    assert pp[1] < 0.95 * pp[0], pp

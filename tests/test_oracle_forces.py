@@ -241,3 +241,102 @@ def test_fmm_converges_with_order_periodic_treepm():
         errs.append(np.median(_relerr(acc, ad)))
     assert errs[-1] < errs[0]
     assert errs[2] < errs[0] / 3
+
+
+def test_gadget4_softened_node_rule():
+    """Sec. 2.7: with softenings comparable to the node sizes, the GADGET-4 rule uses the
+    multipoles of the softened kernel where the GADGET-3 rule opens every node closer than
+    2.8 eps: fewer particle pairs, the same accuracy against the softened direct sum; with two
+    softening classes, mixed nodes are still opened; alpha -> 0 is still the direct sum."""
+    ps = synth.plummer(3000, 63)
+    ps.eps_table = np.array([0.3, 0.08])
+    ps.eps_class[::4] = 1
+    q, _, P = _iso(ps)
+    P.eps = ps.eps_table
+    ad, _ = oracle.direct(q, ps.mass, ps.eps_class, np.arange(ps.n), P)
+    amag = np.linalg.norm(ad, axis=1)
+    sinks = np.arange(0, ps.n, 3)
+    res = {}
+    for soft in (False, True):
+        P2 = oracle.OracleParams(box=P.box, periodic=False, eps=ps.eps_table, alpha=0.005, order=3,
+                                 soft_nodes=soft)
+        run = oracle.prepare(q, ps.mass, ps.eps_class, amag, P2, leaf_max=4)
+        acc, _, cnt = oracle.tree_forces(run, sinks)
+        res[soft] = (np.percentile(_relerr(acc, ad[sinks]), 90), cnt.sum(0))
+    assert res[True][1][0] < 0.9 * res[False][1][0], res        # fewer particle pairs
+    assert res[True][0] < 1.5 * res[False][0], res              # comparable accuracy
+    assert res[True][0] < 0.01
+    P0 = oracle.OracleParams(box=P.box, periodic=False, eps=ps.eps_table, alpha=0.0, order=3,
+                             soft_nodes=True)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, amag, P0, leaf_max=4)
+    acc, _, cnt = oracle.tree_forces(run, sinks)
+    assert np.all(cnt[:, 1] == 0) and np.max(_relerr(acc, ad[sinks])) < 1e-11
+
+
+def _softened_plummer(eps):
+    ps = synth.plummer(2000, 65)
+    ps.eps_table = np.array(eps)
+    ps.eps_class[::4] = len(eps) - 1
+    q, _, P = _iso(ps)
+    ad, _ = oracle.direct(q, ps.mass, ps.eps_class, np.arange(ps.n), P)
+    return ps, q, P, ad
+
+
+def test_softened_multipoles_converge_with_order():
+    """Sec. 2.7 with one softening class (eps comparable to the node sizes): every node closer
+    than 2.8 eps interacts through the expansion of the softened kernel, so the expansion
+    error has to fall with the order p like the unsoftened one (a wrong softened g_n, or the
+    unsoftened kernel used inside 2.8 eps, leaves an error that does not converge), in the
+    one-sided walk and in the FMM."""
+    ps, q, P, ad = _softened_plummer([0.3])
+    amag = np.linalg.norm(ad, axis=1)
+    e_tree, e_fmm, pp = [], [], {}
+    for p in (2, 3, 4, 5):
+        res = {}
+        for soft in (False, True):
+            Pp = oracle.OracleParams(box=P.box, periodic=False, eps=ps.eps_table, criterion=1,
+                                     theta=0.5, order=p, soft_nodes=soft)
+            run = oracle.prepare(q, ps.mass, ps.eps_class, amag, Pp, leaf_max=4)
+            at, _, ct = oracle.tree_forces(run, np.arange(ps.n))
+            af_s, _, cf = run.tree.fmm(Pp)
+            af = np.empty_like(af_s)
+            af[run.perm] = af_s
+            res[soft] = (np.percentile(_relerr(at, ad), 99), np.percentile(_relerr(af, ad), 99),
+                         ct[:, 0].sum(), cf[2])
+            if soft:
+                mom = np.sum(ps.mass[:, None] * af, axis=0)
+                assert np.linalg.norm(mom) < 1e-12 * np.sum(ps.mass * np.linalg.norm(af, axis=1))
+        e_tree.append(res[True][0])
+        e_fmm.append(res[True][1])
+        pp[p] = (res[False][2], res[True][2], res[False][3], res[True][3])
+        assert res[True][2] < 0.97 * res[False][2] and res[True][3] < 0.97 * res[False][3], pp
+    assert all(b < 0.7 * a for a, b in zip(e_tree, e_tree[1:])), e_tree
+    assert all(b < 0.7 * a for a, b in zip(e_fmm, e_fmm[1:])), e_fmm
+    assert e_tree[-1] < 3e-4 and e_fmm[-1] < 2e-4, (e_tree, e_fmm)
+
+
+def test_fmm_softened_rule_opens_mixed_pairs():
+    """Sec. 2.7 for the FMM (node-node pairs): with two softening classes mixed in every
+    node, pairs closer than 2.8 eps_ij are opened unless one side holds only the largest
+    softening; the result stays as accurate as the GADGET-3 rule's against the softened direct
+    sum, with fewer particle pairs, and alpha -> 0 is the direct sum."""
+    ps, q, P, ad = _softened_plummer([0.08, 0.3])
+    amag = np.linalg.norm(ad, axis=1)
+    res = {}
+    for soft in (False, True):
+        Pp = oracle.OracleParams(box=P.box, periodic=False, eps=ps.eps_table, alpha=0.005,
+                                 order=4, soft_nodes=soft)
+        run = oracle.prepare(q, ps.mass, ps.eps_class, amag, Pp, leaf_max=4)
+        af_s, _, cf = run.tree.fmm(Pp)
+        af = np.empty_like(af_s)
+        af[run.perm] = af_s
+        res[soft] = (np.percentile(_relerr(af, ad), 99), cf)
+    assert res[True][1][2] < res[False][1][2], res
+    assert res[True][0] < 1.5 * res[False][0] and res[True][0] < 0.01, res
+    P0 = oracle.OracleParams(box=P.box, periodic=False, eps=ps.eps_table, alpha=0.0, order=4,
+                             soft_nodes=True)
+    run = oracle.prepare(q, ps.mass, ps.eps_class, amag, P0, leaf_max=4)
+    af_s, _, cf = run.tree.fmm(P0)
+    af = np.empty_like(af_s)
+    af[run.perm] = af_s
+    assert cf[0] == 0 and cf[1] == 0 and np.max(_relerr(af, ad)) < 1e-11

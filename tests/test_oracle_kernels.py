@@ -177,3 +177,54 @@ def test_D2_printed_form():
         i, j, k = _full_index(t, 3)
         ref = g[2] * ((i == j) * rv[k] + (j == k) * rv[i] + (i == k) * rv[j]) + g[3] * rv[i] * rv[j] * rv[k]
         assert D3[t] == pytest.approx(ref, rel=1e-13, abs=1e-15)
+
+
+def test_softened_gn_matches_pair_kernel_and_differences():
+    """g_n of the softened kernel (softened multipoles, Sec. 2.7): g_0 and g_1 are the pair
+    kernel's g and g'/r (both pieces of the spline, with and without the TreePM part); each
+    g_(n+1) is (1/r) d g_n / dr by central differences; beyond h it is the unsoftened g_n;
+    g_0..g_2 are continuous at u = 1/2 and u = 1 (the spline potential is C^2)."""
+    h = 1.0
+    for r_s in (0.0, 0.4):
+        for r in (0.2, 0.35, 0.6, 0.85, 1.3):
+            g = oracle.gn_soft(r, h, r_s, 5)
+            g0, g1 = oracle.pair_kernel(r, h, r_s)
+            assert abs(g[0] - g0) < 1e-12 * abs(g0) and abs(g[1] - g1) < 1e-11 * abs(g1)
+            if r >= h:
+                assert np.allclose(g, oracle.gn(r, r_s, 5), rtol=1e-12)
+            for n in range(4):
+                d = 1e-5
+                fd = (oracle.gn_soft(r + d, h, r_s, n)[n] - oracle.gn_soft(r - d, h, r_s, n)[n]) / (2 * d) / r
+                assert abs(fd - g[n + 1]) < 1e-5 * max(1.0, abs(g[n + 1])), (r_s, r, n, fd, g[n + 1])
+        for ub in (0.5, 1.0):
+            lo = oracle.gn_soft(ub - 1e-9, h, r_s, 2)
+            hi = oracle.gn_soft(ub + 1e-9, h, r_s, 2)
+            assert np.allclose(lo, hi, rtol=1e-6, atol=1e-6), (ub, lo, hi)
+
+
+def test_softened_multipole_converges_inside_the_softening():
+    """The particle-node term of the softened kernel approximates the softened direct sum of a
+    small cluster at r < h, its error falling with the cluster size faster for higher order."""
+    rng = np.random.default_rng(4)
+    h, r_s = 1.0, 0.0
+    x = rng.uniform(-0.5, 0.5, (24, 3))
+    m = rng.uniform(0.5, 1.5, 24)
+    target = np.array([0.62, 0.1, -0.05])              # inside h of the cluster centre
+    errs = {}
+    for p in (1, 3, 5):
+        e = []
+        for size in (0.16, 0.08, 0.04):
+            pts = x * size
+            com, mono = oracle.moments_points(pts, m, p)
+            a_pn, _ = oracle.pn_soft(mono, com - target, p, r_s, h)
+            a_d = np.zeros(3)
+            for j in range(len(m)):
+                dvec = pts[j] - target
+                rr = np.linalg.norm(dvec)
+                _, g1 = oracle.pair_kernel(rr, h, r_s)
+                a_d += -m[j] * g1 * dvec
+            e.append(np.linalg.norm(a_pn - a_d) / np.linalg.norm(a_d))
+        errs[p] = e
+    for p in (1, 3):
+        assert errs[p][2] < errs[p][0]                   # shrinks with the cluster size
+    assert errs[3][1] < errs[1][1] and errs[5][1] < errs[3][1], errs
