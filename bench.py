@@ -742,14 +742,15 @@ def extra_cost_model(tg, P, n):
                                         pot=tg.pot_s, counts=tg.counts)
     g4.set_group_order(tg.tree, None)
     ph_ms = _time(walk, 5)
-    ref = tg.acc_s.clone()
+    ref, ref_cnt = tg.acc_s.clone(), tg.counts.clone()
     lpt = {}
-    same = True
+    same, dmax = True, 0.0
     for chunk in (1, 64, 512):
         order = g4.schedule_lpt(pred, chunk)
         g4.set_group_order(tg.tree, order)
         lpt[chunk] = _time(walk, 5)
-        same = same and bool(torch.equal(ref, tg.acc_s))
+        same = same and bool(torch.equal(ref_cnt, tg.counts))
+        dmax = max(dmax, _max_rel_diff(tg.acc_s, ref))
     g4.set_group_order(tg.tree, None)
     p_np, l_np = pred.cpu().numpy(), labels.cpu().numpy()
     rk = lambda a: np.argsort(np.argsort(a))
@@ -759,7 +760,16 @@ def extra_cost_model(tg, P, n):
             "mean_abs_err_log_cost": float(np.mean(np.abs(p_np - l_np))),
             "walk_ms_ph_order": ph_ms,
             "walk_ms_lpt_order": {f"chunk{c}": v for c, v in lpt.items()},
-            "forces_identical": same}
+            "interaction_counts_identical": same, "forces_max_rel_diff": dmax}
+
+
+def _max_rel_diff(a, b):
+    """Largest |a - b| / |b| over the particles (forces as (3, n) tensors): the PH-order walk
+    shares one walk among runs of groups, the scheduled orders walk every group on its own, so
+    the same interactions are summed in another order."""
+    import torch
+    d = torch.linalg.vector_norm((a - b).double(), dim=0) / torch.linalg.vector_norm(b.double(), dim=0).clamp_min(1e-30)
+    return float(d.max().item())
 
 
 def _graph_time(fn, reps):
@@ -942,10 +952,12 @@ def extra_softened(leaf_max):
     """Softened node interactions (Sec. 2.7) where they matter: a zoom box (low-resolution
     128^3 lattice, L = 100, a central sphere 64 times denser) whose heavy low-resolution
     particles carry a softening of half their spacing next to the high-resolution region.
-    Tree walk (p = 3) and FMM (p = 4), alpha = 0.0025, under the GADGET-3 rule (every pair
-    closer than 2.8 eps_ij opened) and the GADGET-4 rule (the softened kernel's expansion
-    unless both sides are mixed): time, interactions, accuracy on sampled sinks against the
-    oracle's FP64 direct sum (r < r_cut, pair softening max(eps_i, eps_j))."""
+    Tree walk (p = 3) and FMM (p = 4) with the geometric criterion (theta = 0.5: with the
+    relative criterion at alpha = 0.0025 no node within 2.8 eps of a sink passes anyway, so the
+    two rules coincide there), under the GADGET-3 rule (every pair closer than 2.8 eps_ij
+    opened) and the GADGET-4 rule (the softened kernel's expansion unless both sides are
+    mixed): time, interactions, accuracy on sampled sinks against the oracle's FP64 direct sum
+    (r < r_cut, pair softening max(eps_i, eps_j))."""
     import torch
     import oracle
     from paper_2010_03567_gb300 import g4, synth
@@ -975,14 +987,14 @@ def extra_softened(leaf_max):
     ws = None
     out = {"particles": n, "eps": [float(e) for e in ps.eps_table], "sample": int(len(sinks))}
     for soft in (0, 1):
-        P = g4.params(**base, alpha=0.0025, soft_nodes=soft)
+        P = g4.params(**base, criterion=1, theta=0.5, soft_nodes=soft)
         ms = _time(lambda: tg.forces(q, mass, cls, aold, P), 3)
         tg.tree.status()
         c = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
         ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
         tree = {"ms_per_step": ms, "forces_per_s": n / (ms * 1e-3), "pp_per_step": int(c[0]),
                 "pn_per_step": int(c[1]), "accuracy_vs_direct": _errors(ag, ad)}
-        P4 = g4.params(**base, alpha=0.0025, order_p=4, soft_nodes=soft)
+        P4 = g4.params(**base, criterion=1, theta=0.5, order_p=4, soft_nodes=soft)
         tg.prepare(q, mass, cls, aold, P4)
         if ws is None:
             ws = torch.empty(tg.tree.fmm_workspace(P4) + 256, dtype=torch.uint8, device="cuda")
@@ -1079,7 +1091,7 @@ def extra_c5(leaf_max):
     frozen = {}
     cm = FROZEN.get("model")
     ph_ms = _time(walk, 3)
-    ref = tg.acc_s.clone()
+    ref, ref_cnt = tg.acc_s.clone(), tg.counts.clone()
     sources = [("q_i_measured", labels)]
     if cm is not None:
         pred = cm.predict(g4.cost_features(tg.tree, P, n, tg.aold_s))
@@ -1088,7 +1100,8 @@ def extra_c5(leaf_max):
     for name, src in sources:
         g4.set_group_order(tg.tree, g4.schedule_lpt(src, 64))
         frozen[name] = {"walk_ms_lpt_chunk64": _time(walk, 3),
-                        "forces_identical": bool(torch.equal(ref, tg.acc_s))}
+                        "interaction_counts_identical": bool(torch.equal(ref_cnt, tg.counts)),
+                        "forces_max_rel_diff": _max_rel_diff(tg.acc_s, ref)}
     g4.set_group_order(tg.tree, None)
     frozen["walk_ms_ph_order"] = ph_ms
     res = {"out_of_sample": frozen, "in_sample": extra_cost_model(tg, P, n)}

@@ -2,7 +2,8 @@
 // (Eq. eqnrelcriterion) and the TreePM short-range kernel (Sec. 2.3), plus a GPU direct sum.
 //
 // Work decomposition: a warp owns a group of 32 PH-consecutive sinks (one per lane) and walks
-// the tree breadth-first for the whole group.  The frontier holds (node, mask of the lanes
+// the tree breadth-first for the whole group (TreePM: runs of UNION_G consecutive groups share
+// one walk where that gives each group exactly its own leaves, see union_walk).  The frontier holds (node, mask of the lanes
 // still walking there) entries in a per-warp ring; each step takes 32 entries, one per lane
 // (coalesced 64-byte records of the level-ordered node copy).  Group-level tests are
 // conservative (a cube beyond r_cut of the group's bounding box is skipped for all lanes); a
@@ -42,6 +43,8 @@ struct WalkArgs {
     int *work;                 // group counter
     int32_t *flags;            // tree error flags
     int2 *queue;               // per-warp frontier rings (level-ordered node, lane mask)
+    int4 *ul_cube;             // per-warp union leaf lists: cube centre, level / meta
+    int2 *ul_fc;               //   and (first particle, count); null: no union walks
     const int32_t *sys_first, *sys_goff;
     const double *sys_box;
     int n_sys;
@@ -80,12 +83,20 @@ constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in glob
 // minimum resident blocks per SM requested from the compiler for the FP32 walks of order <= 3
 // (caps their registers; other instances keep the compiler's choice)
 #ifndef G4_WALK_MIN_BLOCKS
-#define G4_WALK_MIN_BLOCKS 5
+#define G4_WALK_MIN_BLOCKS 4
 #endif
+// consecutive groups that share one union walk (1: every group walks on its own)
+#ifndef G4_WALK_UNION
+#define G4_WALK_UNION 4
+#endif
+constexpr int UNION_G = G4_WALK_UNION;
+constexpr int ULCAP = 2048;     // union leaves per warp
 
 // per-warp shared state: the pending leaf list of the group, the staged sources, the sinks
 struct WalkSmem : PPSmem<LEAF_BUF> {
     float4 sink[32];            // sinks relative to the group centre, opening threshold
+    int ul_n, ub;               // union leaf list: length (-1: none), next entry to take
+    int rg, rn, rq, rul;        // current run of groups: first, count, next, its union list
 };
 
 // Per-lane decision for an internal node (the single-particle walk's rule): skip beyond the
@@ -129,6 +140,122 @@ __device__ __forceinline__ int exact_decision(const WalkArgs &A, const G4Node &n
     return open ? ACT_OPEN : ACT_ACCEPT;
 }
 
+// Union walk for a run of consecutive groups (TreePM with the pair cutoff, plain sink order):
+// one breadth-first walk for the bounding box of all their sinks collects the leaves within
+// reach, with the single-group tests made slightly more conservative (cutoff slack 2e-4
+// instead of 1e-4, the multipole tests' margins doubled), so that whatever a group's own walk
+// would skip or find unusable the union walk skips or finds unusable too.  If no node could
+// serve any of the sinks as a multipole, a group's own walk expands every node it reaches and
+// keeps the leaves that pass its cutoff test, in breadth-first order; each group then takes
+// the union's leaves that pass its own cutoff test, in the union's (the same) order, instead
+// of walking.  Returns the number of leaves, or -1 if some node needs per-sink decisions or a
+// buffer would overflow (the groups then walk on their own).
+template <int P, bool GEOM>
+__device__ __noinline__ int union_walk(const WalkArgs &A, int2 *Q, int4 *UC, int2 *UF, int lane, int s0,
+                          int s_end)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    const double gscale = A.box * (1.0 / 4294967296.0);
+    const float fscale = (float)gscale, fbox = (float)A.box;
+    const uint4 p0 = A.wpart[s0];
+    int lox = 0x7fffffff, hix = -0x7fffffff - 1, loy = lox, hiy = hix, loz = lox, hiz = hix;
+    float critmax = 0.f;
+    for (int s = s0 + lane; s < s_end; s += 32) {
+        const uint4 p = A.wpart[s];
+        const int ox = (int32_t)(p.x - p0.x), oy = (int32_t)(p.y - p0.y), oz = (int32_t)(p.z - p0.z);
+        lox = min(lox, ox);
+        hix = max(hix, ox);
+        loy = min(loy, oy);
+        hiy = max(hiy, oy);
+        loz = min(loz, oz);
+        hiz = max(hiz, oz);
+        if (!GEOM) critmax = fmaxf(critmax, A.alphaf * (A.aold ? A.aold[s] : 0.f));
+    }
+    lox = __reduce_min_sync(0xffffffffu, lox);
+    hix = __reduce_max_sync(0xffffffffu, hix);
+    loy = __reduce_min_sync(0xffffffffu, loy);
+    hiy = __reduce_max_sync(0xffffffffu, hiy);
+    loz = __reduce_min_sync(0xffffffffu, loz);
+    hiz = __reduce_max_sync(0xffffffffu, hiz);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) critmax = fmaxf(critmax, __shfl_xor_sync(0xffffffffu, critmax, o));
+    critmax *= 1.002f;
+    const uint32_t gcx = p0.x + (uint32_t)(int)(((long long)lox + hix) >> 1);
+    const uint32_t gcy = p0.y + (uint32_t)(int)(((long long)loy + hiy) >> 1);
+    const uint32_t gcz = p0.z + (uint32_t)(int)(((long long)loz + hiz) >> 1);
+    const float ghx = (0.5f * (float)((long long)hix - lox) + 2.f) * fscale;
+    const float ghy = (0.5f * (float)((long long)hiy - loy) + 2.f) * fscale;
+    const float ghz = (0.5f * (float)((long long)hiz - loz) + 2.f) * fscale;
+    int head = 0, tail = 1, nl = 0;
+    if (lane == 0) Q[0] = make_int2(0, -1);
+    __syncwarp();
+    while (head < tail) {
+        const int cnt = min(32, tail - head);
+        const bool ve = lane < cnt;
+        int d = 0;
+        if (ve) d = Q[(head + lane) & (QCAP - 1)].x;
+        head += cnt;
+        __syncwarp();
+        G4Node nd;
+        if (ve) nd = load_node(A.wnode + d);
+        const bool leaf = ve && (nd.meta & 32u);
+        bool gskip = !ve, maybe = false;
+        if (ve) {
+            const float side = ldexpf(fbox, -(int)(nd.meta & 31u)), half = 0.5f * side;
+            const float dcx = (float)(int32_t)(nd.cx - gcx) * fscale;
+            const float dcy = (float)(int32_t)(nd.cy - gcy) * fscale;
+            const float dcz = (float)(int32_t)(nd.cz - gcz) * fscale;
+            const float ex = fmaxf(fabsf(dcx) - half - ghx, 0.f);
+            const float ey = fmaxf(fabsf(dcy) - half - ghy, 0.f);
+            const float ez = fmaxf(fabsf(dcz) - half - ghz, 0.f);
+            gskip = ex * ex + ey * ey + ez * ez > 1.0002f * A.rcut2f;
+            if (!gskip && !leaf) {
+                bool none = false;
+                if (A.exclusion && fmaxf(fabsf(dcx) + ghx, fmaxf(fabsf(dcy) + ghy, fabsf(dcz) + ghz)) < 0.998f * side)
+                    none = true;
+                const float fx = fabsf(dcx + nd.sx) + ghx, fy = fabsf(dcy + nd.sy) + ghy,
+                            fz = fabsf(dcz + nd.sz) + ghz;
+                const float rmax2 = (fx * fx + fy * fy + fz * fz) * 1.002f;
+                if (!A.soft_nodes && rmax2 < nd.hmax * nd.hmax) none = true;
+                // a sink can use the node only within r_cut of its cube, so its distance to the
+                // centre of mass is below r_cut + the cube's diagonal
+                const float rlim = fminf(sqrtf(rmax2), (sqrtf(A.rcut2f) + 1.7320509f * side) * 1.002f);
+                if (GEOM) {
+                    if (side * side >= A.theta2f * rlim * rlim) none = true;
+                } else {
+                    if (!(A.Gf * nd.mass * ipow<P>(side) < critmax * ipow<P + 2>(rlim))) none = true;
+                }
+                maybe = !none;
+            }
+        }
+        if (__any_sync(0xffffffffu, maybe)) return -1;
+        const bool addleaf = leaf && !gskip;
+        const unsigned lm = __ballot_sync(0xffffffffu, addleaf);
+        if (nl + __popc(lm) > ULCAP) return -1;
+        if (addleaf) {
+            const int pos = nl + __popc(lm & lt);
+            UC[pos] = make_int4((int)nd.cx, (int)nd.cy, (int)nd.cz, (int)nd.meta);
+            UF[pos] = make_int2(nd.first, nd.count);
+        }
+        nl += __popc(lm);
+        const bool expand = ve && !leaf && !gskip;
+        const int nch = expand ? nd.nchild : 0;
+        int pre = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, pre, 31);
+        pre -= nch;
+        if (tail + tot - head > QCAP) return -1;
+        for (int c = 0; c < nch; c++) Q[(tail + pre + c) & (QCAP - 1)] = make_int2(nd.next + c, -1);
+        tail += tot;
+        __syncwarp();
+    }
+    return nl;
+}
+
 // The group walk.  Nodes are scanned in depth-first order in windows of 32 (one node per lane,
 // coalesced loads).  A node is visited unless an earlier node of the window that the group
 // skipped covers it (prefix maximum of the skipped subtrees' ends).  Group-level tests are
@@ -149,12 +276,11 @@ k_walk(const WalkArgs A)
     int2 *Q = A.queue + (size_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * QCAP;
     const int ngroups = A.items ? *A.n_items
                                 : (A.n_sys ? A.sys_goff[A.n_sys] : (A.n_sinks + A.gs - 1) / A.gs);
-    for (;;) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(A.work, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= ngroups) break;
-        if (A.group_order) g = A.group_order[g];
+    // a run of UNION_G consecutive groups shares one union walk where that is exact (see
+    // union_walk); ul_n >= 0: the group takes its leaves from that walk's list
+    const bool uni = UNION_G > 1 && TREEPM && A.ul_cube && !A.items && !A.group_order && !A.n_sys &&
+                     !A.active && A.gs == 32 && A.pp_cut;
+    auto group = [&](int g, int ul_n) {
         // the group's sinks, node range and box (a forest walks only its own system's tree)
         int s0 = g * A.gs, s_end = min(A.n_sinks, s0 + A.gs), k = 0;   // k: root, level-ordered
         int kp = 0, Kp = 1, pslot = -1;               // part of a split group
@@ -168,7 +294,7 @@ k_walk(const WalkArgs A)
             if (s0 < 0 || s0 >= s_end || it.y > 32 || Kp < 1 || Kp > G4_ITEM_SPLIT_MAX ||
                 kp >= Kp || (Kp > 1 && (pslot < 0 || pslot >= A.part_cap))) {
                 if (lane == 0) atomicOr(A.flags, G4_FLAG_LISTCAP);   // malformed item: reported
-                continue;
+                return;
             }
         }
         double gbox = A.box;
@@ -226,18 +352,57 @@ k_walk(const WalkArgs A)
         T bx = T(0), by = T(0), bz = T(0), bp = T(0);     // particle-node sums
         uint32_t npp = 0, npn = 0;
         // breadth-first frontier of (node, lanes still walking there), 32 entries per step
-        int head = 0, tail = 1, nleaf = 0;
-        if (lane == 0) Q[0] = make_int2(k, (int)vmask);
+        int head = 0, tail = ul_n >= 0 ? 0 : 1, nleaf = 0;
+        if (lane == 0) {
+            if (ul_n < 0) Q[0] = make_int2(k, (int)vmask);
+            S.ul_n = ul_n;
+            S.ub = 0;
+        }
         __syncwarp();
         for (;;) {
+            // (the union list's state lives in shared memory, not in registers)
+            const int uln = S.ul_n, ub = S.ub;
+            const bool more = uln >= 0 ? ub < uln : head < tail;
             // a step adds at most 32 leaves: flush before the list could overflow, and at the end
-            if (nleaf > LEAF_BUF - 32 || (head >= tail && nleaf > 0)) {
+            if (nleaf > LEAF_BUF - 32 || (!more && nleaf > 0)) {
                 pp_flush<T, TREEPM>(A, S, nleaf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, vmask,
                                     INTU ? hi * (T)figs : hi, ax, ay, az, ap, npp, gscale, figs, pf, rc2i,
                                     kp, Kp);
                 nleaf = 0;
             }
-            if (head >= tail) break;
+            if (!more) break;
+            if (uln >= 0) {
+                // the union walk's leaves that pass this group's cutoff test (the test of the
+                // breadth-first walk below, on the same leaf records)
+                const size_t w0 = (size_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * ULCAP;
+                const int e = ub + lane;
+                __syncwarp();
+                if (lane == 0) S.ub = ub + 32;
+                bool keep = false;
+                int2 fc = make_int2(0, 0);
+                if (e < uln) {
+                    const int4 c = A.ul_cube[w0 + e];
+                    fc = A.ul_fc[w0 + e];
+                    const float side = ldexpf(fbox, -(int)((uint32_t)c.w & 31u)), half = 0.5f * side;
+                    const float dcx = (float)(int32_t)((uint32_t)c.x - gcx) * fscale;
+                    const float dcy = (float)(int32_t)((uint32_t)c.y - gcy) * fscale;
+                    const float dcz = (float)(int32_t)((uint32_t)c.z - gcz) * fscale;
+                    const float ex = fmaxf(fabsf(dcx) - half - ghx, 0.f);
+                    const float ey = fmaxf(fabsf(dcy) - half - ghy, 0.f);
+                    const float ez = fmaxf(fabsf(dcz) - half - ghz, 0.f);
+                    keep = !(ex * ex + ey * ey + ez * ez > 1.0001f * A.rcut2f);
+                }
+                const unsigned lm = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int pos = nleaf + __popc(lm & lt);
+                    S.first[pos] = fc.x;
+                    S.count[pos] = fc.y;
+                    S.mask[pos] = vmask;
+                }
+                nleaf += __popc(lm);
+                __syncwarp();
+                continue;
+            }
             const int cnt = min(32, tail - head);
             const bool ve = lane < cnt;
             int d = 0;
@@ -273,11 +438,14 @@ k_walk(const WalkArgs A)
                                 fz = fabsf(dcz + nd.sz) + ghz;
                     const float rmax2 = (fx * fx + fy * fy + fz * fz) * 1.001f;
                     if (!A.soft_nodes && rmax2 < nd.hmax * nd.hmax) none = true;
+                    // TreePM: a sink uses the node only within r_cut of its cube, so its distance
+                    // to the centre of mass is below r_cut + the cube's diagonal
+                    const float rlim = TREEPM ? fminf(sqrtf(rmax2), (sqrtf(A.rcut2f) + 1.7320509f * side) * 1.001f)
+                                              : sqrtf(rmax2);
                     if (GEOM) {
-                        if (side * side >= A.theta2f * rmax2) none = true;
+                        if (side * side >= A.theta2f * rlim * rlim) none = true;
                     } else {
-                        const float rmax = sqrtf(rmax2);
-                        if (!(A.Gf * nd.mass * ipow<P>(side) < critmax * ipow<P + 2>(rmax))) none = true;
+                        if (!(A.Gf * nd.mass * ipow<P>(side) < critmax * ipow<P + 2>(rlim))) none = true;
                     }
                     maybe = !none;
                 }
@@ -431,6 +599,37 @@ k_walk(const WalkArgs A)
                 }
                 if (lane == 0) A.part_cnt[pslot] = 0;   // ready for the next walk
             }
+        }
+    };
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(A.work, uni ? UNION_G : 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ngroups) break;
+        int ng = 1, ul_n = -1;
+        if (uni) {
+            const size_t w0 = (size_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * ULCAP;
+            ng = min(UNION_G, ngroups - g);
+            ul_n = union_walk<P, GEOM>(A, Q, A.ul_cube + w0, A.ul_fc + w0, lane, g * 32,
+                                       min(A.n_sinks, (g + ng) * 32));
+        } else if (A.group_order) {
+            g = A.group_order[g];
+        }
+        // the run's state lives in shared memory while its groups walk (register pressure)
+        if (lane == 0) {
+            S.rg = g;
+            S.rn = ng;
+            S.rq = 0;
+            S.rul = ul_n;
+        }
+        __syncwarp();
+        for (;;) {
+            const int q = S.rq;
+            if (q >= S.rn) break;
+            group(S.rg + q, S.rul);
+            __syncwarp();
+            if (lane == 0) S.rq = q + 1;
+            __syncwarp();
         }
     }
 }
@@ -696,10 +895,13 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     A.exclusion = P->exclusion_zone;
     A.pp_cut = P->pp_cut;
     A.soft_nodes = P->soft_nodes;
+    // per-warp frontier rings and union leaf lists, allocated on the handle's first walk
+    // (outside any graph capture)
+    const size_t nwarps = (size_t)g4_num_sms() * G4_WALK_BLOCKS_PER_SM * (WALK_THREADS / 32);
+    const size_t qbytes = sizeof(int2) * (size_t)G4_WALK_QCAP * nwarps;
+    const size_t ubytes = (sizeof(int4) + sizeof(int2)) * (size_t)ULCAP * nwarps;
     if (!t->walk_queue) {
-        // frontier rings, allocated on the handle's first walk (outside any graph capture)
-        const size_t bytes = sizeof(int2) * (size_t)G4_WALK_QCAP * g4_num_sms() *
-                             G4_WALK_BLOCKS_PER_SM * (WALK_THREADS / 32);
+        const size_t bytes = qbytes + ubytes;
         if (cudaMalloc(&t->walk_queue, bytes) != cudaSuccess) {
             cudaGetLastError();
             t->walk_queue = nullptr;
@@ -707,6 +909,8 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
         }
     }
     A.queue = (int2 *)t->walk_queue;
+    A.ul_cube = (int4 *)((char *)t->walk_queue + qbytes);
+    A.ul_fc = (int2 *)((char *)t->walk_queue + qbytes + sizeof(int4) * (size_t)ULCAP * nwarps);
     if (!t->wnode) {
         if (cudaMalloc(&t->wnode, sizeof(G4Node) * (size_t)t->cap) != cudaSuccess) {
             cudaGetLastError();
