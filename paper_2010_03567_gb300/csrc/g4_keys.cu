@@ -426,6 +426,7 @@ __global__ void k_gather(const int32_t *__restrict__ perm, int64_t n,
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t j = perm[k];
+        if ((uint64_t)j >= (uint64_t)n) j = 0;   // a corrupt permutation reads nothing outside
         pout[k] = pin[j];
         pout[n + k] = pin[n + j];
         pout[2 * n + k] = pin[2 * n + j];
@@ -441,7 +442,8 @@ __global__ void k_scatter(const int32_t *__restrict__ perm, int64_t n,
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        int64_t j = perm[k];
+        const int64_t j = perm[k];
+        if ((uint64_t)j >= (uint64_t)n) continue;   // a corrupt permutation writes nothing outside
         aout[j] = ain[k];
         aout[n + j] = ain[n + k];
         aout[2 * n + j] = ain[2 * n + k];
