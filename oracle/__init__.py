@@ -47,7 +47,8 @@ class _Params(C.Structure):
                 ("r_cut", C.c_double), ("pp_cut", C.c_int), ("alpha", C.c_double),
                 ("theta", C.c_double), ("criterion", C.c_int), ("order", C.c_int),
                 ("exclusion", C.c_int), ("G", C.c_double), ("n_eps", C.c_int),
-                ("eps", C.POINTER(C.c_double)), ("keep_qp", C.c_int), ("soft_nodes", C.c_int)]
+                ("eps", C.POINTER(C.c_double)), ("keep_qp", C.c_int), ("soft_nodes", C.c_int),
+                ("ewald", C.c_int)]
 
 
 @dataclass
@@ -66,6 +67,7 @@ class OracleParams:
     G: float = 1.0
     keep_qp: bool = False
     soft_nodes: bool = False
+    ewald: bool = False         # periodic, r_s = 0: Ewald-corrected pure tree (Sec. 2.2.4)
     _eps_buf: np.ndarray = field(default=None, repr=False)
 
     @property
@@ -82,7 +84,7 @@ class OracleParams:
                        int(self.criterion), int(self.order), int(self.exclusion),
                        float(self.G), int(len(self._eps_buf)),
                        self._eps_buf.ctypes.data_as(C.POINTER(C.c_double)),
-                       int(self.keep_qp), int(self.soft_nodes))
+                       int(self.keep_qp), int(self.soft_nodes), int(self.ewald))
 
 
 def _p(a):
@@ -113,6 +115,8 @@ def _declare(L):
     L.or_D_full.argtypes = [i32, vp, vp, vp]
     L.or_tree_walk.argtypes = [vp, vp, i64, vp, vp, vp, vp, i64, C.POINTER(_Params), vp, vp, vp]
     L.or_direct.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(_Params), d, vp, vp]
+    L.or_ewald_direct.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(_Params), vp, vp]
+    L.or_ewald_dpsi_flat.argtypes = [vp, d, i32, vp]
     L.or_fmm.argtypes = [vp, vp, i64, vp, vp, vp, C.POINTER(_Params), vp, vp, vp, vp]
     L.or_moments_points.argtypes = [vp, vp, i64, i32, vp, vp]
     L.or_ewald_psi.argtypes = [vp, d, d, i32, i32]
@@ -351,6 +355,36 @@ def ewald_force(xe, ys, m, L: float, alpha: float | None = None, nr: int = 4, nk
     lib().or_ewald_force_many(_p(xe), xe.shape[0], _p(ys), _p(m), ys.shape[0], float(L), float(a),
                               int(nr), int(nk), int(kspace_only), _p(out))
     return out
+
+
+def ewald_dpsi(x, L: float, mmax: int):
+    """Derivative tensors D_m[psi](x), m = 0..mmax (<= 6), of the Ewald correction potential
+    (full tensors: D[m] has shape (3,)*m)."""
+    xx = np.ascontiguousarray(x, np.float64)
+    n = sum(3 ** m for m in range(mmax + 1))
+    out = np.empty(n)
+    lib().or_ewald_dpsi_flat(_p(xx), float(L), int(mmax), _p(out))
+    res, o = [], 0
+    for m in range(mmax + 1):
+        res.append(out[o:o + 3 ** m].reshape((3,) * m) if m else out[o:o + 1].reshape(()))
+        o += 3 ** m
+    return res
+
+
+def ewald_direct(pos_int: np.ndarray, mass, cls, sinks, params: OracleParams):
+    """Exact periodic forces and potentials (Eq. eqnpo1): softened nearest-image pairs plus the
+    Ewald correction psi of every pair, and m_i psi(0) of each sink's own images."""
+    pos_int = np.ascontiguousarray(pos_int, dtype=np.uint32)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    cls = None if cls is None else np.ascontiguousarray(cls, dtype=np.uint8)
+    sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+    ns = sinks.shape[0]
+    acc = np.empty((ns, 3))
+    pot = np.empty(ns)
+    cp = params.c()
+    lib().or_ewald_direct(_p(pos_int), pos_int.shape[1], _p(mass), _p(cls), _p(sinks), ns,
+                          C.byref(cp), _p(acc), _p(pot))
+    return acc, pot
 
 
 def direct(pos_int: np.ndarray, mass, cls, sinks, params: OracleParams, r_max: float = 0.0):

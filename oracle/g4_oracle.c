@@ -50,6 +50,8 @@ typedef struct {
     int soft_nodes;    /* tree walk and FMM: 0 opens every pair closer than 2.8 max(eps)
                           (GADGET-3); 1 applies the GADGET-4 rule of Sec. 2.7 (softened
                           multipoles) */
+    int ewald;         /* tree walk, periodic and r_s = 0: 1 adds the Ewald correction psi to
+                          every interaction (Sec. 2.2.4, Eqs. eqnpo1, eqnewal) */
 } or_params;
 
 /* ===================================================================================== */
@@ -592,6 +594,45 @@ static double or_sep(uint32_t a, uint32_t b, const or_params *P)
     return or_isep(a, b, P->periodic) * (P->box / 4294967296.0);
 }
 
+/* Ewald correction tensors (defined with the Ewald sums below) */
+#define OR_EW_MMAX (OR_MAXP + 1)
+void or_ewald_dpsi(const double *x, double L, int mmax, double (*D)[729]);
+double or_ewald_psi(const double *x, double L, double alpha, int nr, int nk);
+
+/* Ewald correction of an accepted node (pure periodic tree, Sec. 2.2.4): the correction
+ * potential psi of Eq. (eqnpo1) expanded about the node's centre of mass like the Newtonian
+ * term, with r = s - x (nearest image):
+ *   phi += +G sum_{n=0}^{p}   (1/n!) Q_n . D_n[psi](r)
+ *   a   += +G sum_{n=0}^{p-1} (1/n!) Q_n . D_{n+1}[psi](r)                                */
+static void or_pn_ewald(const double *mono, const double *rv, int p, double L, double G,
+                        double *acc, double *pot)
+{
+    static __thread double D[OR_EW_MMAX + 1][729];
+    or_ewald_dpsi(rv, L, p, D);
+    double phi = 0.0, a[3] = {0, 0, 0};
+    for (int n = 0; n <= p; n++) {
+        double inv = 1.0 / or_factorial(n);
+        int n3 = or_pow3(n);
+        for (int t = 0; t < n3; t++) {
+            double q = or_Q_full(mono, n, t);
+            phi += inv * q * D[n][t];
+            if (n <= p - 1)
+                for (int i = 0; i < 3; i++) a[i] += inv * q * D[n + 1][i + 3 * t];
+        }
+    }
+    *pot += G * phi;
+    for (int i = 0; i < 3; i++) acc[i] += G * a[i];
+}
+
+/* Ewald correction of one particle pair, d = x_j - x (nearest image): m psi(d), m grad psi(d) */
+static void or_pp_ewald(const double *d, double m, double L, double G, double *acc, double *pot)
+{
+    static __thread double D[OR_EW_MMAX + 1][729];
+    or_ewald_dpsi(d, L, 1, D);
+    *pot += G * m * D[0][0];
+    for (int i = 0; i < 3; i++) acc[i] += G * m * D[1][i];
+}
+
 /* Walk for the particle at sorted index i.  Node handling, in this order:
  *   - TreePM: the node is dropped when the nearest point of its (nearest-image) cube is
  *     further than r_cut (Sec. 2.3, reading: Euclidean distance to the cube);
@@ -621,6 +662,11 @@ static void or_walk_one(const or_tree *t, const uint32_t *pos, int64_t np, const
     acc[0] = acc[1] = acc[2] = 0.0;
     *pot = 0.0;
     cnt[0] = cnt[1] = 0;
+    const int ewald = P->ewald && P->periodic && !treepm;
+    if (ewald) {   /* the particle's own periodic images: m_i psi(0) (no force) */
+        const double z[3] = {0.0, 0.0, 0.0};
+        *pot += P->G * mass[i] * or_ewald_psi(z, P->box, 2.0 / P->box, 2, 5);
+    }
     int64_t k = 0;
     while (k < t->nn) {
         double side = ldexp(P->box, -t->level[k]);
@@ -648,6 +694,7 @@ static void or_walk_one(const or_tree *t, const uint32_t *pos, int64_t np, const
                 or_pair_kernel(sqrt(r2), h, P->r_s, &g0, &g1);
                 *pot += -P->G * mass[j] * g0;
                 for (int ax = 0; ax < 3; ax++) acc[ax] += -P->G * mass[j] * g1 * d[ax];
+                if (ewald) or_pp_ewald(d, mass[j], P->box, P->G, acc, pot);
                 cnt[0]++;
             }
             k = t->next[k];
@@ -682,6 +729,7 @@ static void or_walk_one(const or_tree *t, const uint32_t *pos, int64_t np, const
         }
         if (open) { k = k + 1; continue; }
         or_pn_h(t->mono + nm * k, rv, p, P->r_s, softened ? h : 0.0, P->G, acc, pot);
+        if (ewald) or_pn_ewald(t->mono + nm * k, rv, p, P->box, P->G, acc, pot);
         cnt[1]++;
         k = t->next[k];
     }
@@ -1354,6 +1402,141 @@ void or_ewald_force(const double *x, double L, double alpha, int nr, int nk, int
                            sin(k[0] * x[0] + k[1] * x[1] + k[2] * x[2]);
                 for (int i = 0; i < 3; i++) acc[i] -= f * k[i];
             }
+}
+
+/* g_n = (r^-1 d/dr)^n of erf(alpha r) / r, n = 0..nmax.  With erf(a r)/r =
+ * (2 a/sqrt(pi)) sum_k (-1)^k (a r)^(2k) / (k! (2k+1)) and (r^-1 d/dr) r^(2k) = 2k r^(2k-2):
+ *   g_n = (-1)^n (2/sqrt(pi)) 2^n a^(2n+1) sum_j (-1)^j (a r)^(2j) / (j! (2j+2n+1)),
+ * summed for a r < 1.5; beyond, g_n of 1/r minus g_n of erfc(a r)/r (or_gn with
+ * r_s = 1/(2a)), where the two no longer cancel badly. */
+static void or_gn_erf(double r, double alpha, int nmax, double *g)
+{
+    const double pi = 3.14159265358979323846;
+    const double x = alpha * r;
+    if (x < 1.5) {
+        double pre = 2.0 / sqrt(pi) * alpha;
+        for (int n = 0; n <= nmax; n++) {
+            double s = 0.0, term = 1.0;   /* (-1)^j x^(2j) / j! */
+            for (int j = 0; j < 60; j++) {
+                s += term / (2.0 * j + 2.0 * n + 1.0);
+                term *= -x * x / (j + 1.0);
+            }
+            g[n] = ((n & 1) ? -1.0 : 1.0) * pre * s;
+            pre *= 2.0 * alpha * alpha;
+        }
+        return;
+    }
+    double gN[OR_EW_MMAX + 2], gE[OR_EW_MMAX + 2];
+    or_gn(r, 0.0, nmax, gN);
+    or_gn(r, 0.5 / alpha, nmax, gE);
+    for (int n = 0; n <= nmax; n++) g[n] = gN[n] - gE[n];
+}
+
+/* Full derivative tensors D_m[psi](x), m = 0..mmax (<= OR_EW_MMAX), of the correction
+ * potential psi of Eq. (eqnewal) for a cubic box of side L (Sec. 2.2.4), for separations in
+ * the primary cell (|x_i| <= L/2, as nearest-image separations are), term by term:
+ *   psi = pi/(a^2 V) + erf(a|x|)/|x| - sum_{n != 0} erfc(a|x+q_n|)/|x+q_n|
+ *         - (4 pi/V) sum_{k != 0} exp(-k^2/(4 a^2))/k^2 cos(k . x),
+ * radial terms through g_n and the pairing formula (or_D_full), the Fourier terms through
+ * d/dx_i cos(k.x + phase) = k_i cos(k.x + phase + pi/2), k and -k together (their terms are
+ * equal).  a = 3.5/L with |n_i| <= 1 (the first image left out lies beyond 1.5 L: erfc(5.25)
+ * ~ 1e-13) and |m_i| <= 7 (k = 2 pi m/L; exp(-pi^2 m^2/(aL)^2) ~ 1e-17 at m = 7). */
+#define OR_EW_NK 7
+void or_ewald_dpsi(const double *x, double L, int mmax, double (*D)[729])
+{
+    const double pi = 3.14159265358979323846, V = L * L * L, alpha = 3.5 / L;
+    const int nr = 1, nk = OR_EW_NK;
+    /* the half space of wave vectors with their weights, cached per thread for the last L */
+    enum { NKH = ((2 * OR_EW_NK + 1) * (2 * OR_EW_NK + 1) * (2 * OR_EW_NK + 1) - 1) / 2 };
+    static __thread double kc_L = -1.0, kc_k[NKH][3], kc_w[NKH];
+    if (kc_L != L) {
+        int q = 0;
+        for (int a = -nk; a <= nk; a++)
+            for (int b = -nk; b <= nk; b++)
+                for (int c = -nk; c <= nk; c++) {
+                    /* one of each pair k, -k: the first non-zero index positive */
+                    if (!(a > 0 || (a == 0 && (b > 0 || (b == 0 && c > 0))))) continue;
+                    double k[3] = {2 * pi * a / L, 2 * pi * b / L, 2 * pi * c / L};
+                    double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                    for (int i = 0; i < 3; i++) kc_k[q][i] = k[i];
+                    kc_w[q] = 2.0 * 4 * pi / V * exp(-k2 / (4 * alpha * alpha)) / k2;
+                    q++;
+                }
+        kc_L = L;
+    }
+    double g[OR_EW_MMAX + 2], tmp[729];
+    for (int m = 0; m <= mmax; m++)
+        for (int t = 0; t < or_pow3(m); t++) D[m][t] = 0.0;
+    D[0][0] = pi / (alpha * alpha * V);
+    for (int a = -nr; a <= nr; a++)
+        for (int b = -nr; b <= nr; b++)
+            for (int c = -nr; c <= nr; c++) {
+                double d[3] = {x[0] + a * L, x[1] + b * L, x[2] + c * L};
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                double sgn = 1.0;
+                if (a == 0 && b == 0 && c == 0) {
+                    or_gn_erf(r, alpha, mmax, g);
+                } else {
+                    or_gn(r, 0.5 / alpha, mmax, g);
+                    sgn = -1.0;
+                }
+                for (int m = 0; m <= mmax; m++) {
+                    or_D_full(m, d, g, tmp);
+                    for (int t = 0; t < or_pow3(m); t++) D[m][t] += sgn * tmp[t];
+                }
+            }
+    for (int q = 0; q < NKH; q++) {
+        const double *k = kc_k[q];
+        double th = k[0] * x[0] + k[1] * x[1] + k[2] * x[2];
+        double cs[4] = {cos(th), 0.0, 0.0, 0.0};
+        cs[1] = -sin(th);        /* cos(th + pi/2) */
+        cs[2] = -cs[0];          /* cos(th + pi) */
+        cs[3] = -cs[1];          /* cos(th + 3 pi/2) */
+        for (int m = 0; m <= mmax; m++) {
+            double cm = kc_w[q] * cs[m & 3];
+            for (int t = 0; t < or_pow3(m); t++) {
+                double prod = 1.0;
+                int v = t;
+                for (int u = 0; u < m; u++) { prod *= k[v % 3]; v /= 3; }
+                D[m][t] -= prod * cm;
+            }
+        }
+    }
+}
+
+/* Exact periodic forces and potentials with softened nearest-image pairs (Eq. eqnpo1): for
+ * each sink i, sum_{j != i} m_j [pair kernel of the nearest image, psi correction] plus
+ * m_i psi(0) in the potential: the reference of the Ewald-corrected pure periodic tree. */
+void or_ewald_direct(const uint32_t *pos, int64_t np, const double *mass, const uint8_t *cls,
+                     const int64_t *sinks, int64_t ns, const or_params *P, double *acc,
+                     double *pot)
+{
+    const double z[3] = {0.0, 0.0, 0.0};
+    const double psi0 = or_ewald_psi(z, P->box, 2.0 / P->box, 2, 5);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t s = 0; s < ns; s++) {
+        int64_t i = sinks[s];
+        double a[3] = {0, 0, 0}, ph = P->G * mass[i] * psi0;
+        for (int64_t j = 0; j < np; j++) {
+            if (j == i) continue;
+            or_pair_acc(pos, np, mass, cls, i, j, P, a, &ph, 0.0);
+            double d[3];
+            for (int ax = 0; ax < 3; ax++) d[ax] = or_sep(pos[ax * np + j], pos[ax * np + i], P);
+            or_pp_ewald(d, mass[j], P->box, P->G, a, &ph);
+        }
+        for (int ax = 0; ax < 3; ax++) acc[3 * s + ax] = a[ax];
+        pot[s] = ph;
+    }
+}
+
+/* D_m[psi](x) for m = 0..mmax as full tensors concatenated (1 + 3 + 9 + ... entries). */
+void or_ewald_dpsi_flat(const double *x, double L, int mmax, double *out)
+{
+    static __thread double D[OR_EW_MMAX + 1][729];
+    or_ewald_dpsi(x, L, mmax, D);
+    int64_t o = 0;
+    for (int m = 0; m <= mmax; m++)
+        for (int t = 0; t < or_pow3(m); t++) out[o++] = D[m][t];
 }
 
 /* Many evaluations: acc[i] = sum_j m_j a(x_i - y_j) (OpenMP over the evaluation points). */
