@@ -397,6 +397,7 @@ def run_gpu(args, rank, world):
                          ("cost_model_frozen", extra_frozen_model),
                          ("hierarchical_bins", lambda: extra_bins(wp["leaf_max"])),
                          ("softened_nodes", lambda: extra_softened(wp["leaf_max"])),
+                         ("ewald_periodic_tree", lambda: extra_ewald(wp["leaf_max"])),
                          ("cost_model_512cubed", lambda: extra_c5(wp["leaf_max"]))):
             if args.extras and name not in args.extras.split(","):
                 continue
@@ -1016,6 +1017,59 @@ def extra_softened(leaf_max):
     out["speedup_tree"] = g3["tree"]["ms_per_step"] / g4r["tree"]["ms_per_step"]
     out["speedup_fmm"] = g3["fmm"]["ms_per_step"] / g4r["fmm"]["ms_per_step"]
     del ws
+    return out
+
+
+def extra_ewald(leaf_max):
+    """The pure periodic tree with the Ewald correction (Sec. 2.2.4, no PM): a 64^3 periodic
+    box (L = 100, rms displacement 0.5 spacings), p = 3, relative criterion alpha = 0.0025 with
+    |a_old| from a geometric bootstrap walk; forces/s (keys to scatter), parity on sampled sinks
+    against the oracle's walk with exact Ewald tensors, and the method's accuracy on a 16^3
+    box against the exact periodic direct sum (with the nearest images alone for contrast)."""
+    import torch
+    import oracle
+    from paper_2010_03567_gb300 import g4, synth
+    L, ns = 100.0, 64
+    ps = synth.zeldovich(ns, L, 0.5, 1011)
+    base = dict(box_size=L, periodic=1, eps=list(ps.eps_table), order_p=3, leaf_max=leaf_max,
+                ewald=1)
+    q, _ = g4.g4_int_coords(torch.from_numpy(ps.pos).cuda(), True, L)
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    tg = g4.TreeGravity(ps.n, g4.params(**base, criterion=1, theta=0.5))
+    a0, _ = tg.forces(q, mass, None, None)
+    aold = torch.linalg.vector_norm(a0, dim=0).contiguous()
+    P = g4.params(**base, alpha=0.0025)
+    ms = _time(lambda: tg.forces(q, mass, None, aold, P), 3)
+    tg.tree.status()
+    c = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
+    sinks = np.sort(np.random.default_rng(4111).choice(ps.n, 64, replace=False))
+    q_np = q.cpu().numpy().view(np.uint32)
+    OP = oracle.OracleParams(box=L, periodic=True, eps=ps.eps_table, alpha=0.0025, order=3,
+                             ewald=True)
+    run = oracle.prepare(q_np, ps.mass, None, aold.double().cpu().numpy(), OP, leaf_max)
+    ao, _, _ = oracle.tree_forces(run, sinks)
+    ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
+    out = {"particles": ps.n, "ms_per_step": ms, "forces_per_s": ps.n / (ms * 1e-3),
+           "pp_per_step": int(c[0]), "pn_per_step": int(c[1]),
+           "parity_vs_oracle_walk": {**_errors(ag, ao), "sample": int(len(sinks))}}
+    # the method's accuracy against the exact periodic sum, 16^3 box
+    ps2 = synth.zeldovich(16, L, 0.5, 1012)
+    q2, _ = g4.g4_int_coords(torch.from_numpy(ps2.pos).cuda(), True, L)
+    m2 = torch.from_numpy(ps2.mass.astype(np.float32)).cuda()
+    s2 = np.sort(np.random.default_rng(4112).choice(ps2.n, 128, replace=False))
+    q2_np = q2.cpu().numpy().view(np.uint32)
+    ad, _ = oracle.ewald_direct(q2_np, ps2.mass, None, s2,
+                                oracle.OracleParams(box=L, periodic=True, eps=ps2.eps_table))
+    acc_small = {}
+    for ew in (1, 0):
+        b2 = dict(base, ewald=ew)
+        t2 = g4.TreeGravity(ps2.n, g4.params(**b2, criterion=1, theta=0.5))
+        x0, _ = t2.forces(q2, m2, None, None)
+        ao2 = torch.linalg.vector_norm(x0, dim=0).contiguous()
+        a2, _ = t2.forces(q2, m2, None, ao2, g4.params(**b2, alpha=0.0025))
+        acc_small["ewald" if ew else "nearest_images_only"] = _errors(
+            a2.cpu().numpy().T[s2].astype(np.float64), ad)
+    out["accuracy_vs_exact_periodic_sum_16cubed"] = {**acc_small, "sample": int(len(s2))}
     return out
 
 

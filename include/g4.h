@@ -86,6 +86,16 @@ typedef struct g4_params {
                               both sides' smallest softenings lie below eps_ij (a particle's
                               smallest is its own), otherwise it interacts through the
                               expansion of the softened kernel with eps_ij */
+    int ewald;             /* tree walk, periodic=1 and r_s=0 only: 1 adds the Ewald
+                              correction psi of Eq. (eqnewal) to every interaction -- the
+                              pure periodic tree of Sec. 2.2.4: nearest-image Newtonian terms
+                              plus the correction, expanded like them about each accepted
+                              node's centre of mass, for every particle pair, and G m_i psi(0)
+                              of each particle's own images in its potential.  D_n[psi] come
+                              from a grid of the tensors up to order p + 4 (one octant, 32^3
+                              cells, FP64 from the Ewald sums, built in the handle on first
+                              use) by third-order Taylor expansion about the nearest cell
+                              centre.  0: nearest images only.  The FMM rejects 1. */
 } g4_params;
 
 typedef struct g4_tree_s *g4_tree;
@@ -102,9 +112,22 @@ int64_t g4_launch_count(void);
 
 /* Fills *p with the defaults: periodic=0, r_s=0, R_cut=4.5, pp_cut=1, alpha=0.0025,
  * theta=0.5, criterion=0, p=3, leaf_max=8, exclusion=1, precision=0, G=1, one class with
- * eps=0.01, group_size=32, fp64_count=4096, keep_qp=0, fmm_p2p_per_particle=0, soft_nodes=0.
+ * eps=0.01, group_size=32, fp64_count=4096, keep_qp=0, fmm_p2p_per_particle=0, soft_nodes=0,
+ * ewald=0.
  * Host-only, never fails for p!=NULL. */
 g4_status g4_params_default(g4_params *p);
+
+/* ---- pure periodic tree: the Ewald correction grid (Sec. 2.2.4) ---------------------- */
+
+/* Evaluates the derivative tensors D_abc[psi](x), a + b + c <= nmax (0..6), of the Ewald
+ * correction potential for a cubic box of side `box` at n separations x[n][3] (FP64,
+ * row-major, device, each component in [-box/2, box/2]: nearest-image separations), from the
+ * handle's grid (built or rebuilt for `box` first, as the walk does) by third-order Taylor
+ * expansion in FP64.  out: device, n x (nmax+1)(nmax+2)(nmax+3)/6 doubles, component
+ * (a, b, c) of order m at (m(m+1)(m+2)/6 + (b+c)(b+c+1)/2 + c).  Asynchronous on `stream`;
+ * errors: G4_ERR_INVALID_ARG, G4_ERR_OOM (grid allocation, first use only). */
+g4_status g4_ewald_eval(g4_tree t, const double *x, int64_t n, int nmax, double box, double *out,
+                        void *stream);
 
 /* ---- a1: integer coordinates (Sec. 2.10, Sec. 2.11) ----------------------------------- */
 

@@ -107,6 +107,8 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
                                     void *stream)
 {
     g4_status s = g4_check_params(P, "g4_gravity_fmm");
+    if (s == G4_OK && P->ewald)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: the Ewald correction is built for the tree walk only");
     if (s != G4_OK) return s;
     if (!t || !pos_sorted || !mass_sorted || !acc || !workspace)
         return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: NULL argument");
@@ -180,6 +182,8 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     A.pp_cut = P->pp_cut;
     A.keep_qp = P->keep_qp;
     A.soft_nodes = P->soft_nodes;
+    A.ewald = 0;
+    A.ew = G4EwaldView{nullptr, nullptr, 0, 1, 1.0};
     A.rcut2f = (float)A.rcut2;
     A.asf = (float)A.as;
     const double igs = 4294967296.0 / P->box_size;

@@ -3,6 +3,7 @@
 #pragma once
 #include "g4_internal.cuh"
 #include "g4_kernels.cuh"
+#include "g4_ewald.cuh"
 
 namespace g4fmm {
 
@@ -41,6 +42,8 @@ struct FmmArgs {
     float h_cls[G4_MAX_EPS_CLASSES];
     int exclusion, pp_cut, keep_qp;
     int soft_nodes;            // 1: softened multipoles under the rule of Sec. 2.7
+    int ewald;                 // always 0 (the FMM has no Ewald correction)
+    G4EwaldView ew;
     // particle-particle phase (shared with the tree walk)
     const uint4 *wpart;        // particles as (x, y, z, mass bits)
     float rcut2f, asf, figs, rc2i;

@@ -68,6 +68,7 @@ struct g4_tree_s {
     G4Node *node = nullptr;
     float *q = nullptr;           // cap x g4_nq(G4_MAX_ORDER) FP32 moments (orders 2..p)
     void *walk_queue = nullptr;   // walk frontier rings (allocated on the first walk)
+    int walk_qcap = 0;            // their capacity per warp
     // walk copies (allocated on the first walk): node records in level order with
     // next = first daughter (level order) and parent = depth-first index, and the particles
     // as 16-byte records (x, y, z, mass bits)
@@ -94,6 +95,11 @@ struct g4_tree_s {
     int part_cap = 0;
     int moments_order = -1;
     int moments_fp64 = 0;
+    // Ewald correction grid of the pure periodic tree (built on first use, see g4_ewald.cu)
+    double *ew64 = nullptr;
+    float *ew32 = nullptr;
+    double ew_L = 0.0;
+    int ew_nt = -1;
     // host copies filled by g4_tree_status
     int64_t n_nodes_host = -1;
 };

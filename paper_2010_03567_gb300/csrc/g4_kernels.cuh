@@ -260,6 +260,10 @@ __device__ __forceinline__ void dtensors(T x, T y, T z, const T *g, T *D)
             }
 }
 
+template <int P, typename T>
+__device__ __forceinline__ void pn_contract(const T *Qs, T M, const T *D, T &sx, T &sy, T &sz,
+                                            T &sp);
+
 // Particle-node term of the one-sided expansion with r = s - x (Eqs. eqonesidetreepotential,
 // eqonesidetreeacc): sacc += sum_{n<P} Q_n . D_{n+1} / n!,  spot += sum_{n<=P} Q_n . D_n / n!
 // (the caller multiplies both by -G).  Qs holds moments of orders 2..P at g4_midx - 4.
@@ -274,6 +278,15 @@ __device__ __forceinline__ void pn_term(const T *Qs, T M, T x, T y, T z, T as, T
     else gn_kernel<P, T, TREEPM>(r2, as, g);
     T D[g4_nmono(P)];
     dtensors<P, T>(x, y, z, g, D);
+    pn_contract<P, T>(Qs, M, D, sx, sy, sz, sp);
+}
+
+// The contraction of pn_term for given derivative tensors D (a + b + c <= P):
+// sacc += sum_{n<P} Q_n . D_{n+1} / n!,  spot += sum_{n<=P} Q_n . D_n / n!.
+template <int P, typename T>
+__device__ __forceinline__ void pn_contract(const T *Qs, T M, const T *D, T &sx, T &sy, T &sz,
+                                            T &sp)
+{
     T ax = M * D[g4_midx(1, 0, 0)], ay = M * D[g4_midx(0, 1, 0)], az = M * D[g4_midx(0, 0, 1)];
     T ph = M * D[0];
 #pragma unroll

@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 
 #include "g4_kernels.cuh"
+#include "g4_ewald.cuh"
 #include "g4_pp_fp16.h"
 
 namespace g4k {
@@ -302,6 +303,16 @@ __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf
                 ay += mg1 * dy;
                 az += mg1 * dz;
                 ap += m_ * g0;
+                if (!TREEPM && A.ewald) {
+                    // Ewald correction of the pair (Sec. 2.2.4): + G m psi(d) in the
+                    // potential, + G m grad psi(d) in the acceleration (sums carry -G)
+                    T Dp[4];
+                    ewald_dpsi<1, T>(A.ew, dx, dy, dz, Dp);
+                    ap -= m_ * Dp[0];
+                    ax -= m_ * Dp[g4_midx(1, 0, 0)];
+                    ay -= m_ * Dp[g4_midx(0, 1, 0)];
+                    az -= m_ * Dp[g4_midx(0, 0, 1)];
+                }
             }
             npp++;
         }

@@ -464,6 +464,8 @@ extern "C" void g4_tree_free(g4_tree t)
     if (t->qd) cudaFree(t->qd);
     if (t->sys_goff) cudaFree(t->sys_goff);
     if (t->walk_queue) cudaFree(t->walk_queue);
+    if (t->ew64) cudaFree(t->ew64);
+    if (t->ew32) cudaFree(t->ew32);
     if (t->wnode) cudaFree(t->wnode);
     if (t->wpart) cudaFree(t->wpart);
     if (t->part_buf) cudaFree(t->part_buf);

@@ -18,6 +18,7 @@
 
 #include "g4_internal.cuh"
 #include "g4_kernels.cuh"
+#include "g4_ewald.cuh"
 #include "g4_pp.cuh"
 
 namespace {
@@ -43,6 +44,7 @@ struct WalkArgs {
     int *work;                 // group counter
     int32_t *flags;            // tree error flags
     int2 *queue;               // per-warp frontier rings (level-ordered node, lane mask)
+    int qcap;                  // ring capacity per warp (a power of two)
     int4 *ul_cube;             // per-warp union leaf lists: cube centre, level / meta
     int2 *ul_fc;               //   and (first particle, count); null: no union walks
     const int32_t *sys_first, *sys_goff;
@@ -63,6 +65,8 @@ struct WalkArgs {
     float h_cls[G4_MAX_EPS_CLASSES];
     int exclusion, pp_cut;
     int soft_nodes;               // GADGET-4 softened-node rule (Sec. 2.7)
+    int ewald;                    // pure periodic tree with the Ewald correction (Sec. 2.2.4)
+    G4EwaldView ew;
 };
 
 
@@ -79,7 +83,8 @@ template <int P, typename T> __device__ __forceinline__ T ipow(T x)
 constexpr int WALK_THREADS = 128;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int LEAF_BUF = 256;   // pending leaves: a whole group's leaves usually fit (one flush)
-constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp (ring in global memory)
+constexpr int QCAP = G4_WALK_QCAP;   // frontier capacity per warp with the TreePM cutoff
+constexpr int QCAP_TREE = 4 * QCAP;  // without a cutoff (large sets: the frontier is wider)
 // minimum resident blocks per SM requested from the compiler for the FP32 walks of order <= 3
 // (caps their registers; other instances keep the compiler's choice)
 #ifndef G4_WALK_MIN_BLOCKS
@@ -193,7 +198,7 @@ __device__ __noinline__ int union_walk(const WalkArgs &A, int2 *Q, int4 *UC, int
         const int cnt = min(32, tail - head);
         const bool ve = lane < cnt;
         int d = 0;
-        if (ve) d = Q[(head + lane) & (QCAP - 1)].x;
+        if (ve) d = Q[(head + lane) & (A.qcap - 1)].x;
         head += cnt;
         __syncwarp();
         G4Node nd;
@@ -248,8 +253,8 @@ __device__ __noinline__ int union_walk(const WalkArgs &A, int2 *Q, int4 *UC, int
         }
         const int tot = __shfl_sync(0xffffffffu, pre, 31);
         pre -= nch;
-        if (tail + tot - head > QCAP) return -1;
-        for (int c = 0; c < nch; c++) Q[(tail + pre + c) & (QCAP - 1)] = make_int2(nd.next + c, -1);
+        if (tail + tot - head > A.qcap) return -1;
+        for (int c = 0; c < nch; c++) Q[(tail + pre + c) & (A.qcap - 1)] = make_int2(nd.next + c, -1);
         tail += tot;
         __syncwarp();
     }
@@ -273,7 +278,7 @@ k_walk(const WalkArgs A)
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     if (*A.flags & G4_FLAG_CAPACITY) return;   // incomplete tree: outputs left untouched
-    int2 *Q = A.queue + (size_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * QCAP;
+    int2 *Q = A.queue + (size_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * A.qcap;
     const int ngroups = A.items ? *A.n_items
                                 : (A.n_sys ? A.sys_goff[A.n_sys] : (A.n_sinks + A.gs - 1) / A.gs);
     // a run of UNION_G consecutive groups shares one union walk where that is exact (see
@@ -351,6 +356,12 @@ k_walk(const WalkArgs A)
         T ax = T(0), ay = T(0), az = T(0), ap = T(0);     // particle-particle sums
         T bx = T(0), by = T(0), bz = T(0), bp = T(0);     // particle-node sums
         uint32_t npp = 0, npn = 0;
+        if (!TREEPM && A.ewald && kp == 0) {
+            // the sink's own periodic images: + G m_i psi(0) in the potential, no force
+            T D0[1];
+            ewald_dpsi<0, T>(A.ew, T(0), T(0), T(0), D0);
+            bp -= (T)__uint_as_float(pi_.w) * D0[0];
+        }
         // breadth-first frontier of (node, lanes still walking there), 32 entries per step
         int head = 0, tail = ul_n >= 0 ? 0 : 1, nleaf = 0;
         if (lane == 0) {
@@ -408,7 +419,7 @@ k_walk(const WalkArgs A)
             int d = 0;
             unsigned m = 0u;
             if (ve) {
-                const int2 qe = Q[(head + lane) & (QCAP - 1)];
+                const int2 qe = Q[(head + lane) & (A.qcap - 1)];
                 d = qe.x;
                 m = (unsigned)qe.y;
             }
@@ -501,11 +512,21 @@ k_walk(const WalkArgs A)
 #pragma unroll
                         for (int c = 0; c < g4_nq_raw(P); c++) Qs[c] = (T)__ldg(qq + c);
                     }
-                    const T rx = (T)(int32_t)(n2.cx - xi) * (T)gscale + mx;
-                    const T ry = (T)(int32_t)(n2.cy - yi) * (T)gscale + my;
-                    const T rz = (T)(int32_t)(n2.cz - zi) * (T)gscale + mz;
+                    T rx = (T)(int32_t)(n2.cx - xi) * (T)gscale + mx;
+                    T ry = (T)(int32_t)(n2.cy - yi) * (T)gscale + my;
+                    T rz = (T)(int32_t)(n2.cz - zi) * (T)gscale + mz;
+                    if (!TREEPM && A.ewald) {
+                        // the Newtonian term plus the correction is the periodic potential,
+                        // the same at every image of the centre of mass: take the one in the
+                        // primary cell, which the correction grid covers
+                        const T Lb = (T)gbox;
+                        rx -= Lb * rint(rx / Lb);
+                        ry -= Lb * rint(ry / Lb);
+                        rz -= Lb * rint(rz / Lb);
+                    }
                     const T hs = A.soft_nodes ? fmax(hi, (T)n2.hmax) : T(0);
                     pn_term<P, T, TREEPM>(Qs, M, rx, ry, rz, par<T>(A.as, A.asf), bx, by, bz, bp, hs);
+                    if (!TREEPM && A.ewald) pn_ewald<P, T>(A.ew, Qs, M, rx, ry, rz, bx, by, bz, bp);
                     npn++;
                 }
                 if (lane == src) m &= ~accm;
@@ -530,13 +551,13 @@ k_walk(const WalkArgs A)
             }
             const int tot = __shfl_sync(0xffffffffu, pre, 31);
             pre -= nch;
-            if (tail + tot - head > QCAP) {
+            if (tail + tot - head > A.qcap) {
                 if (lane == 0) atomicOr(A.flags, G4_FLAG_LISTCAP);
             } else if (nch > 0) {
                 for (int c = 0; c < nch; c++)   // daughters are consecutive in level order
-                    Q[(tail + pre + c) & (QCAP - 1)] = make_int2(nd.next + c, (int)m);
+                    Q[(tail + pre + c) & (A.qcap - 1)] = make_int2(nd.next + c, (int)m);
             }
-            if (tail + tot - head <= QCAP) tail += tot;
+            if (tail + tot - head <= A.qcap) tail += tot;
             __syncwarp();
         }
         if (INTU) {
@@ -795,6 +816,8 @@ g4_status g4_check_params(const g4_params *P, const char *who)
         return g4_fail(G4_ERR_INVALID_ARG, "%s: precision=%d", who, P->precision);
     if (P->group_size != 0 && P->group_size != 8 && P->group_size != 16 && P->group_size != 32)
         return g4_fail(G4_ERR_INVALID_ARG, "%s: group_size=%d (8, 16 or 32)", who, P->group_size);
+    if (P->ewald && (!P->periodic || P->r_s > 0.0 || P->order_p > 5))
+        return g4_fail(G4_ERR_INVALID_ARG, "%s: the Ewald correction needs periodic=1, r_s=0", who);
     return G4_OK;
 }
 
@@ -895,11 +918,23 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     A.exclusion = P->exclusion_zone;
     A.pp_cut = P->pp_cut;
     A.soft_nodes = P->soft_nodes;
+    A.ewald = P->ewald;
+    if (P->ewald) {
+        s = g4_ewald_ensure(t, P->box_size, P->order_p + 1 + 3, (cudaStream_t)stream, &A.ew);
+        if (s != G4_OK) return s;
+    }
     // per-warp frontier rings and union leaf lists, allocated on the handle's first walk
     // (outside any graph capture)
+    // (the rings are four times wider for walks without the TreePM cutoff on large sets,
+    // whose breadth-first frontier is wider; a handle grows its rings when first asked)
+    const int qcap = (!treepm && n > (1 << 16)) ? QCAP_TREE : QCAP;
     const size_t nwarps = (size_t)g4_num_sms() * G4_WALK_BLOCKS_PER_SM * (WALK_THREADS / 32);
-    const size_t qbytes = sizeof(int2) * (size_t)G4_WALK_QCAP * nwarps;
+    const size_t qbytes = sizeof(int2) * (size_t)qcap * nwarps;
     const size_t ubytes = (sizeof(int4) + sizeof(int2)) * (size_t)ULCAP * nwarps;
+    if (t->walk_queue && t->walk_qcap < qcap) {
+        cudaFree(t->walk_queue);
+        t->walk_queue = nullptr;
+    }
     if (!t->walk_queue) {
         const size_t bytes = qbytes + ubytes;
         if (cudaMalloc(&t->walk_queue, bytes) != cudaSuccess) {
@@ -907,10 +942,13 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
             t->walk_queue = nullptr;
             return g4_fail(G4_ERR_OOM, "g4_gravity_tree: frontier buffers (%zu bytes)", bytes);
         }
+        t->walk_qcap = qcap;
     }
     A.queue = (int2 *)t->walk_queue;
-    A.ul_cube = (int4 *)((char *)t->walk_queue + qbytes);
-    A.ul_fc = (int2 *)((char *)t->walk_queue + qbytes + sizeof(int4) * (size_t)ULCAP * nwarps);
+    A.qcap = t->walk_qcap;
+    const size_t qoff = sizeof(int2) * (size_t)t->walk_qcap * nwarps;   // the rings as allocated
+    A.ul_cube = (int4 *)((char *)t->walk_queue + qoff);
+    A.ul_fc = (int2 *)((char *)t->walk_queue + qoff + sizeof(int4) * (size_t)ULCAP * nwarps);
     if (!t->wnode) {
         if (cudaMalloc(&t->wnode, sizeof(G4Node) * (size_t)t->cap) != cudaSuccess) {
             cudaGetLastError();

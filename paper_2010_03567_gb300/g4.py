@@ -34,7 +34,7 @@ class G4Params(C.Structure):
                 ("G", C.c_double), ("n_eps_classes", C.c_int),
                 ("eps_table", C.c_double * MAX_EPS), ("group_size", C.c_int),
                 ("fp64_count", C.c_int), ("keep_qp", C.c_int), ("fmm_p2p_per_particle", C.c_int),
-                ("soft_nodes", C.c_int)]
+                ("soft_nodes", C.c_int), ("ewald", C.c_int)]
 
     def copy(self) -> "G4Params":
         p = G4Params()
@@ -90,6 +90,7 @@ def _declare(L):
         "g4_pm_workspace": ([C.c_int32, C.POINTER(C.c_size_t)], i32),
         "g4_kick": ([vp, vp, vp, i64, i64, d, vp], i32),
         "g4_translate": ([vp, vp, i64, C.POINTER(C.c_uint32), vp], i32),
+        "g4_ewald_eval": ([vp, vp, i64, i32, d, vp, vp], i32),
         "g4_drift": ([vp, vp, vp, i64, i64, d, P, vp, vp], i32),
         "g4_timestep_bins": ([vp, vp, vp, i64, i64, P, d, d, C.c_int32, vp, vp], i32),
         "g4_pm_long_range": ([vp, vp, i64, vp, i64, P, C.c_int32, vp, vp, i32, vp, C.c_size_t, vp], i32),
@@ -981,3 +982,17 @@ class HierarchicalKDK:
     def momentum(self):
         """Total momentum sum m v (FP64)."""
         return (self.mass.double()[None, :] * self.vel.double()).sum(dim=1)
+
+
+# ---- pure periodic tree: the Ewald correction grid (Sec. 2.2.4) ------------------------------
+
+def g4_ewald_eval(tree: "Tree", x, nmax: int, box: float, stream=None):
+    """D_abc[psi] (a + b + c <= nmax) of the Ewald correction potential at separations x (n, 3)
+    FP64 (nearest-image range), from the handle's grid by Taylor expansion: (n, nmono) FP64."""
+    x = x.contiguous().to(torch.float64)
+    n = x.shape[0]
+    nm = (nmax + 1) * (nmax + 2) * (nmax + 3) // 6
+    out = torch.empty((n, nm), dtype=torch.float64, device=x.device)
+    _check(lib().g4_ewald_eval(tree.h, x.data_ptr(), n, int(nmax), float(box), out.data_ptr(),
+                               _stream(stream)), "g4_ewald_eval")
+    return out
