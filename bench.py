@@ -54,10 +54,10 @@ def fp32_peak_tflops():
 
 
 # DRAM bytes (read + write) of one k_walk launch of the headline workload: the single-pass ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed walk, 611,016,960 +
-# 451,179,520 bytes.  Reported as roofline.traffic for the default workload only; set to
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed walk, 622,315,776 +
+# 740,627,200 bytes.  Reported as roofline.traffic for the default workload only; set to
 # None whenever the walk kernel changes until it is captured again.
-WALK_DRAM_BYTES_256 = 1062196480
+WALK_DRAM_BYTES_256 = 1362942976
 
 
 def hbm_peak_gbs():
