@@ -952,7 +952,8 @@ def extra_plummer(leaf_max):
 def extra_softened(leaf_max):
     """Softened node interactions (Sec. 2.7) where they matter: a zoom box (low-resolution
     128^3 lattice, L = 100, a central sphere 64 times denser) whose heavy low-resolution
-    particles carry a softening of half their spacing next to the high-resolution region.
+    particles carry a softening of their spacing (2.8 eps about r_cut) next to the
+    high-resolution region.
     Tree walk (p = 3) and FMM (p = 4) with the geometric criterion (theta = 0.5: with the
     relative criterion at alpha = 0.0025 no node within 2.8 eps of a sink passes anyway, so the
     two rules coincide there), under the GADGET-3 rule (every pair closer than 2.8 eps_ij
@@ -965,7 +966,7 @@ def extra_softened(leaf_max):
     L, ns = 100.0, 128
     ps = synth.zoom(ns, L, 1007)
     n = ps.n
-    ps.eps_table = np.array([0.5 * L / ns, ps.eps_table[1]])
+    ps.eps_table = np.array([1.0 * L / ns, ps.eps_table[1]])
     base = dict(box_size=L, periodic=1, r_s=1.25 * L / (2 * ns), r_cut_factor=4.5,
                 eps=list(ps.eps_table), leaf_max=leaf_max)
     q, _ = g4.g4_int_coords(torch.from_numpy(ps.pos).cuda(), True, L)
