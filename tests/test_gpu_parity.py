@@ -428,3 +428,27 @@ def test_walk_parity_softened_node_rule():
         assert np.percentile(relerr(ag, ad), 99) < 0.01
         pp[soft] = cg[:, 0].sum()
     assert pp[1] < 0.95 * pp[0], pp
+
+
+def test_union_walk_equals_per_group_walks():
+    """The TreePM walk shares one walk among runs of four groups; with a group order set, every
+    group walks on its own (the union walk is off).  Both give every sink the same
+    interactions (identical counts) and the same forces up to the order of the sums."""
+    ps, tp = _treepm_box(40)
+    q, box = int_coords(ps)
+    aold = np.full(ps.n, 5.0, np.float32)
+    P = gpu_params(g4, ps, box, alpha=0.0025, leaf_max=32, **tp)
+    tg = g4.TreeGravity(ps.n, P)
+    pos, mass = u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32)
+    a = to_dev(torch, aold, torch.float32)
+    tg.forces(pos, mass, None, a)
+    acc_u, cnt_u = tg.acc.clone(), tg.counts.clone()
+    ng = (ps.n + 31) // 32
+    g4.set_group_order(tg.tree, torch.arange(ng, dtype=torch.int32, device="cuda"))
+    tg.forces(pos, mass, None, a)
+    acc_g, cnt_g = tg.acc.clone(), tg.counts.clone()
+    g4.set_group_order(tg.tree, None)
+    torch.cuda.synchronize()
+    assert torch.equal(cnt_u, cnt_g)
+    e = relerr(acc_u.cpu().numpy().T, acc_g.cpu().numpy().T)
+    assert np.percentile(e, 99) < 1e-6 and e.max() < 1e-4, np.percentile(e, [50, 99, 100])
