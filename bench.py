@@ -1025,8 +1025,9 @@ def extra_ewald(leaf_max):
     """The pure periodic tree with the Ewald correction (Sec. 2.2.4, no PM): a 64^3 periodic
     box (L = 100, rms displacement 0.5 spacings), p = 3, relative criterion alpha = 0.0025 with
     |a_old| from a geometric bootstrap walk; forces/s (keys to scatter), parity on sampled sinks
-    against the oracle's walk with exact Ewald tensors, and the method's accuracy on a 16^3
-    box against the exact periodic direct sum (with the nearest images alone for contrast)."""
+    against the oracle's walk with exact Ewald tensors, the pure periodic FMM (p = 4) on the
+    same box, and the tree's accuracy on a 16^3 box against the exact periodic direct sum (with
+    the nearest images alone for contrast)."""
     import torch
     import oracle
     from paper_2010_03567_gb300 import g4, synth
@@ -1053,6 +1054,26 @@ def extra_ewald(leaf_max):
     out = {"particles": ps.n, "ms_per_step": ms, "forces_per_s": ps.n / (ms * 1e-3),
            "pp_per_step": int(c[0]), "pn_per_step": int(c[1]),
            "parity_vs_oracle_walk": {**_errors(ag, ao), "sample": int(len(sinks))}}
+    # the pure periodic FMM (p = 4) on the same box and |a_old|
+    P4 = g4.params(**dict(base, order_p=4), alpha=0.0025)
+    tg.prepare(q, mass, None, aold, P4)
+    ws = torch.empty(tg.tree.fmm_workspace(P4) + 256, dtype=torch.uint8, device="cuda")
+    res = {}
+
+    def fstep():
+        tg.prepare(q, mass, None, aold, P4)
+        res["r"] = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, tg.aold_s, P4, workspace=ws)
+
+    fms = _time(fstep, 3)
+    tg.tree.status()
+    acc_s, _, cnt, mom = res["r"]
+    amag = torch.linalg.vector_norm(acc_s.double(), dim=0)
+    out["fmm"] = {"ms_per_step": fms, "forces_per_s": ps.n / (fms * 1e-3), "order_p": 4,
+                  "momentum_rel": float(torch.linalg.vector_norm(mom).item()
+                                        / (tg.mass_s.double() * amag).sum().item()),
+                  "pp_per_step": int(cnt[0].to(torch.int64).sum().item()),
+                  "pn_per_step": int(cnt[1].to(torch.int64).sum().item())}
+    del ws
     # the method's accuracy against the exact periodic sum, 16^3 box
     ps2 = synth.zeldovich(16, L, 0.5, 1012)
     q2, _ = g4.g4_int_coords(torch.from_numpy(ps2.pos).cuda(), True, L)

@@ -86,16 +86,17 @@ typedef struct g4_params {
                               both sides' smallest softenings lie below eps_ij (a particle's
                               smallest is its own), otherwise it interacts through the
                               expansion of the softened kernel with eps_ij */
-    int ewald;             /* tree walk, periodic=1 and r_s=0 only: 1 adds the Ewald
-                              correction psi of Eq. (eqnewal) to every interaction -- the
-                              pure periodic tree of Sec. 2.2.4: nearest-image Newtonian terms
-                              plus the correction, expanded like them about each accepted
-                              node's centre of mass, for every particle pair, and G m_i psi(0)
-                              of each particle's own images in its potential.  D_n[psi] come
+    int ewald;             /* periodic=1 and r_s=0 only: 1 adds the Ewald correction psi of
+                              Eq. (eqnewal) to every interaction -- the pure periodic tree and
+                              FMM of Sec. 2.2.4: nearest-image Newtonian terms plus the
+                              correction, expanded like them (tree: about each accepted node's
+                              centre of mass; FMM: in every mutual expansion, the kernel
+                              1/r - psi), for every particle pair, and G m_i psi(0) of each
+                              particle's own images in its potential.  D_n[psi] come
                               from a grid of the tensors up to order p + 4 (one octant, 32^3
                               cells, FP64 from the Ewald sums, built in the handle on first
                               use) by third-order Taylor expansion about the nearest cell
-                              centre.  0: nearest images only.  The FMM rejects 1. */
+                              centre.  0: nearest images only. */
 } g4_params;
 
 typedef struct g4_tree_s *g4_tree;

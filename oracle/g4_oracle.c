@@ -918,6 +918,17 @@ static void or_pp(or_fmm_ctx *C, int64_t i, int64_t j)
         C->acc[3 * i + ax] += -P->G * C->mass[j] * g1 * d[ax];
         C->acc[3 * j + ax] += P->G * C->mass[i] * g1 * d[ax];
     }
+    if (P->ewald && P->periodic && P->r_s <= 0.0) {
+        /* the Ewald correction of the pair (psi even, its gradient odd) */
+        double ai[3] = {0, 0, 0}, pi_ = 0.0;
+        or_pp_ewald(d, 1.0, P->box, P->G, ai, &pi_);
+        C->pot[i] += C->mass[j] * pi_;
+        C->pot[j] += C->mass[i] * pi_;
+        for (int ax = 0; ax < 3; ax++) {
+            C->acc[3 * i + ax] += C->mass[j] * ai[ax];
+            C->acc[3 * j + ax] -= C->mass[i] * ai[ax];
+        }
+    }
     C->n_p2p++;
     if (C->pcnt) { C->pcnt[2 * i]++; C->pcnt[2 * j]++; }
 }
@@ -931,7 +942,7 @@ static void or_pp(or_fmm_ctx *C, int64_t i, int64_t j)
  * the unsoftened ones.  fA, fB: full tensors of orders 0..p at offsets toff[k]. */
 static void or_m2l_fields(const double *QA, const double *QB, const double *rv, int p,
                           double r_s, double h, double G, int keep_qp, const int *toff,
-                          double *fA, double *fB)
+                          double *fA, double *fB, double L_ewald)
 {
     double r = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
     double g[OR_MAXP + 2];
@@ -939,6 +950,14 @@ static void or_m2l_fields(const double *QA, const double *QB, const double *rv, 
     else or_gn(r, r_s, p, g);
     static __thread double D[OR_MAXP + 1][729];
     for (int m = 0; m <= p; m++) or_D_full(m, rv, g, D[m]);
+    if (L_ewald > 0.0) {
+        /* pure periodic FMM (Sec. 2.2.4): the kernel is 1/r - psi, the correction expanded
+         * with the same tensors */
+        static __thread double Dp[OR_EW_MMAX + 1][729];
+        or_ewald_dpsi(rv, L_ewald, p, Dp);
+        for (int m = 0; m <= p; m++)
+            for (int t = 0; t < or_pow3(m); t++) D[m][t] -= Dp[m][t];
+    }
     for (int k = 0; k <= p; k++) {
         int k3 = or_pow3(k);
         double sk = (k & 1) ? -1.0 : 1.0;
@@ -996,7 +1015,8 @@ static void or_m2l(or_fmm_ctx *C, or_cell A, or_cell B, const double *rv, double
     } else {
         QB = t->mono + nm * B.k;
     }
-    or_m2l_fields(QA, QB, rv, P->order, P->r_s, h, P->G, P->keep_qp, C->toff, fA, fB);
+    or_m2l_fields(QA, QB, rv, P->order, P->r_s, h, P->G, P->keep_qp, C->toff, fA, fB,
+                  (P->ewald && P->periodic && P->r_s <= 0.0) ? P->box : 0.0);
     or_deposit(C, A, fA);
     or_deposit(C, B, fB);
     if (A.part || B.part) {
@@ -1063,6 +1083,8 @@ static int64_t or_daughters(const or_fmm_ctx *C, int64_t k, or_cell **out)
  *     interactions of the method's second phase);
  *   - pairs whose nearest faces are further apart than r_cut are dropped (Sec. 2.5); for a
  *     particle the "cube" is its position;
+ *   - in a periodic box the centres are taken at their nearest images and then the centre-of-
+ *     mass separation at its own nearest image (so both cells see the same image);
  *   - with the exclusion zone on, a pair does not interact when the centre separation is
  *     within max(l_A, l_B) along every axis: touching equal-sized nodes, or a particle inside
  *     the exclusion cube of side 2l around a node (the tree's zone, Sec. 2.2.3); overlapping
@@ -1092,6 +1114,8 @@ static void or_interact(or_fmm_ctx *C, or_cell A, or_cell B)
     }
     double rv[3];
     for (int ax = 0; ax < 3; ax++) rv[ax] = dc[ax] + or_cell_com(C, B, ax) - or_cell_com(C, A, ax);
+    if (P->periodic)   /* the nearest image of the centre-of-mass separation */
+        for (int ax = 0; ax < 3; ax++) rv[ax] -= P->box * rint(rv[ax] / P->box);
     double r2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
     int accept = 1;
     double dmax = fmax(fabs(dc[0]), fmax(fabs(dc[1]), fabs(dc[2])));
@@ -1238,6 +1262,11 @@ void or_fmm(const or_tree *t, const uint32_t *pos, int64_t np, const double *mas
         or_self(&C, root);   /* the root interacting with itself */
         or_down(&C, 0);
     }
+    if (P->ewald && P->periodic && P->r_s <= 0.0) {   /* each particle's own images */
+        const double z[3] = {0.0, 0.0, 0.0};
+        const double psi0 = or_ewald_psi(z, P->box, 2.0 / P->box, 2, 5);
+        for (int64_t i = 0; i < np; i++) pot[i] += P->G * mass[i] * psi0;
+    }
     counts[0] = C.n_m2l;
     counts[1] = C.n_pn;
     counts[2] = C.n_p2p;
@@ -1312,7 +1341,7 @@ void or_two_node_fmm(const double *xa, const double *ma, int64_t na, const doubl
     or_moments_points(xa, ma, na, p, sA, QA);
     or_moments_points(xb, mb, nb, p, sB, QB);
     for (int ax = 0; ax < 3; ax++) rv[ax] = sB[ax] - sA[ax];
-    or_m2l_fields(QA, QB, rv, p, r_s, 0.0, G, keep_qp, toff, fA, fB);
+    or_m2l_fields(QA, QB, rv, p, r_s, 0.0, G, keep_qp, toff, fA, fB, 0.0);
     for (int64_t i = 0; i < na; i++) {
         double a[3], grad[3];
         for (int ax = 0; ax < 3; ax++) a[ax] = xa[3 * i + ax] - sA[ax];

@@ -107,8 +107,6 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
                                     void *stream)
 {
     g4_status s = g4_check_params(P, "g4_gravity_fmm");
-    if (s == G4_OK && P->ewald)
-        return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: the Ewald correction is built for the tree walk only");
     if (s != G4_OK) return s;
     if (!t || !pos_sorted || !mass_sorted || !acc || !workspace)
         return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: NULL argument");
@@ -182,7 +180,8 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     A.pp_cut = P->pp_cut;
     A.keep_qp = P->keep_qp;
     A.soft_nodes = P->soft_nodes;
-    A.ewald = 0;
+    A.ewald = P->ewald;
+    A.periodic = P->periodic;
     A.ew = G4EwaldView{nullptr, nullptr, 0, 1, 1.0};
     A.rcut2f = (float)A.rcut2;
     A.asf = (float)A.as;
@@ -191,6 +190,10 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     A.rc2i = (float)(A.rcut2 * igs * igs);
     A.pf = g4k::make_pairf(A.as * A.scale, treepm ? 2.0 * P->r_s * igs : 0.0);
     cudaStream_t st = (cudaStream_t)stream;
+    if (P->ewald) {
+        s = g4_ewald_ensure(t, P->box_size, P->order_p + 3, st, &A.ew);
+        if (s != G4_OK) return s;
+    }
     s = g4_particle_records(t, pos_sorted, mass_sorted, n, st);
     if (s != G4_OK) return s;
     A.wpart = t->wpart;

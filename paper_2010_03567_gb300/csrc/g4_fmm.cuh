@@ -70,6 +70,20 @@ __device__ __forceinline__ PCell load_pcell(const FmmArgs &A, int j)
     return c;
 }
 
+// Periodic box: the nearest image of a centre-of-mass separation.  The centres' separation
+// is already the nearest image, but with the centres of mass it can pass half the box; taking
+// the separation's own nearest image keeps the two directions of a pair mirror images
+// (centres exactly half a box apart get the same image sign from both sides), so both take
+// the same decision.  Without a cutoff only: within r_cut it changes nothing.
+__device__ __forceinline__ void periodic_wrap(const FmmArgs &A, float &rx, float &ry, float &rz)
+{
+    if (!A.periodic) return;
+    const float L = (float)A.box;
+    rx -= L * rintf(rx / L);
+    ry -= L * rintf(ry / L);
+    rz -= L * rintf(rz / L);
+}
+
 // decision for the node pair (A <- B), identical to the symmetric rule of the dual walk
 template <int P, bool TREEPM, bool GEOM>
 __device__ __forceinline__ int fmm_decide(const FmmArgs &A, const G4Node &na, int da,
@@ -91,6 +105,7 @@ __device__ __forceinline__ int fmm_decide(const FmmArgs &A, const G4Node &na, in
     rx = dcx + (nb.sx - na.sx);
     ry = dcy + (nb.sy - na.sy);
     rz = dcz + (nb.sz - na.sz);
+    if (!TREEPM) periodic_wrap(A, rx, ry, rz);   // (a no-op within r_cut)
     const float r2 = rx * rx + ry * ry + rz * rz;
     bool accept = true;
     const float dmax = fmaxf(fabsf(dcx), fmaxf(fabsf(dcy), fabsf(dcz)));
@@ -141,6 +156,7 @@ __device__ __forceinline__ int fmm_decide_pn(const FmmArgs &A, const G4Node &nz,
     rx = dcx + nz.sx;
     ry = dcy + nz.sy;
     rz = dcz + nz.sz;
+    if (!TREEPM) periodic_wrap(A, rx, ry, rz);   // (a no-op within r_cut)
     const float r2 = rx * rx + ry * ry + rz * rz;
     bool accept = true;
     const float dmax = fmaxf(fabsf(dcx), fmaxf(fabsf(dcy), fabsf(dcz)));
@@ -176,16 +192,39 @@ __device__ __forceinline__ void fmm_gn(const FmmArgs &A, float r2, float hs, flo
 }
 
 // lane-private M2L: T += field of node B at A's centre of mass (r = s_B - s_A)
+// Pure periodic FMM (Sec. 2.2.4): the separation moved to its image in the primary cell (the
+// periodic kernel 1/r - psi is the same at every image), and the correction tensors D_n[psi]
+// subtracted from the Newtonian ones there.
+__device__ __forceinline__ void ewald_wrap(const FmmArgs &A, float &rx, float &ry, float &rz)
+{
+    if (!A.ewald) return;
+    const float L = (float)A.box;
+    rx -= L * rintf(rx / L);
+    ry -= L * rintf(ry / L);
+    rz -= L * rintf(rz / L);
+}
+template <int P>
+__device__ __forceinline__ void ewald_sub(const FmmArgs &A, float rx, float ry, float rz, float *D)
+{
+    if (!A.ewald) return;
+    float Dp[g4_nmono(P)];
+    ewald_dpsi<P, float>(A.ew, rx, ry, rz, Dp);
+#pragma unroll
+    for (int k = 0; k < g4_nmono(P); k++) D[k] -= Dp[k];
+}
+
 template <int P, bool TREEPM>
 __device__ __forceinline__ void m2l_add(const FmmArgs &A, float *T, int db, const G4Node &nb,
                                         float rx, float ry, float rz, float hs)
 {
     constexpr int NT = FT<P>::NT;
+    if (!TREEPM) ewald_wrap(A, rx, ry, rz);
     const float r2 = rx * rx + ry * ry + rz * rz;
     float g[P + 1];
     fmm_gn<P, TREEPM>(A, r2, hs, g);
     float D[NT];
     dtensors<P, float>(rx, ry, rz, g, D);
+    if (!TREEPM) ewald_sub<P>(A, rx, ry, rz, D);
     float Q[NT];
     Q[0] = nb.mass;
     const float *qq = A.q + (size_t)db * A.nq;
@@ -223,11 +262,13 @@ __device__ __forceinline__ void p2l_add(const FmmArgs &A, float *T, float m, flo
                                         float rz, float hs)
 {
     constexpr int NT = FT<P>::NT;
+    if (!TREEPM) ewald_wrap(A, rx, ry, rz);
     const float r2 = rx * rx + ry * ry + rz * rz;
     float g[P + 1];
     fmm_gn<P, TREEPM>(A, r2, hs, g);
     float D[NT];
     dtensors<P, float>(rx, ry, rz, g, D);
+    if (!TREEPM) ewald_sub<P>(A, rx, ry, rz, D);
     const float mG = -(float)A.G * m;
 #pragma unroll
     for (int kn = 0; kn <= P; kn++)
@@ -248,11 +289,13 @@ __device__ __forceinline__ void m2p_add(const FmmArgs &A, int dz, const G4Node &
                                         float z, float hs, float &sx, float &sy, float &sz,
                                         float &sp)
 {
+    if (!TREEPM) ewald_wrap(A, x, y, z);
     const float r2 = x * x + y * y + z * z;
     float g[P + 1];
     fmm_gn<P, TREEPM>(A, r2, hs, g);
     float D[g4_nmono(P)];
     dtensors<P, float>(x, y, z, g, D);
+    if (!TREEPM) ewald_sub<P>(A, x, y, z, D);
     const float M = nz.mass;
     float ax = M * D[g4_midx(1, 0, 0)], ay = M * D[g4_midx(0, 1, 0)], az = M * D[g4_midx(0, 0, 1)];
     float ph = M * D[0];
@@ -566,7 +609,16 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                 A.acc[i] = 0.f;
                 A.acc[A.n + i] = 0.f;
                 A.acc[2 * A.n + i] = 0.f;
-                if (A.pot) A.pot[i] = 0.f;
+                if (A.pot) {
+                    // each particle's own periodic images: + G m_i psi(0) (pure periodic FMM)
+                    float p0 = 0.f;
+                    if (!TREEPM && A.ewald) {
+                        float D0[1];
+                        ewald_dpsi<0, float>(A.ew, 0.f, 0.f, 0.f, D0);
+                        p0 = (float)A.G * A.mass[i] * D0[0];
+                    }
+                    A.pot[i] = p0;
+                }
                 if (A.counts) {
                     A.counts[i] = 0u;
                     A.counts[A.n + i] = 0u;

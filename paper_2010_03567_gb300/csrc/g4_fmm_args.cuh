@@ -42,7 +42,8 @@ struct FmmArgs {
     float h_cls[G4_MAX_EPS_CLASSES];
     int exclusion, pp_cut, keep_qp;
     int soft_nodes;            // 1: softened multipoles under the rule of Sec. 2.7
-    int ewald;                 // always 0 (the FMM has no Ewald correction)
+    int ewald;                 // pure periodic FMM with the Ewald correction (Sec. 2.2.4)
+    int periodic;
     G4EwaldView ew;
     // particle-particle phase (shared with the tree walk)
     const uint4 *wpart;        // particles as (x, y, z, mass bits)

@@ -111,3 +111,57 @@ def test_ewald_needs_a_periodic_tree_walk():
         tg.forces(torch.zeros((3, 16), dtype=torch.int32, device="cuda"),
                   torch.ones(16, device="cuda"), None, None,
                   g4.params(box_size=1.0, periodic=0, ewald=1, criterion=1))
+
+
+def _gpu_fmm(ps, q, P):
+    from _helpers import to_dev, u32_dev
+    tg = g4.TreeGravity(ps.n, P)
+    tg.prepare(u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32), None, None, P)
+    acc, pot, cnt, mom = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, None, P)
+    torch.cuda.synchronize()
+    tg.tree.status()
+    perm = tg.perm.cpu().numpy()
+    a = np.empty((ps.n, 3))
+    a[perm] = acc.cpu().numpy().T
+    p = np.empty(ps.n)
+    p[perm] = pot.cpu().numpy()
+    c = np.empty((ps.n, 3), np.int64)
+    c[perm] = cnt.cpu().numpy().T
+    return a, p, c, mom.cpu().numpy()
+
+
+def test_ewald_fmm_parity_and_momentum():
+    """The pure periodic FMM (kernel 1/r - psi in every expansion, psi for every particle
+    pair) against the oracle's FMM with exact tensors, its momentum, and its error against the
+    exact periodic sum."""
+    ps, q = _periodic_set(1024, 23)
+    kw = dict(criterion=1, theta=0.5, order_p=4, leaf_max=8, ewald=1)
+    ag, pg, cg, mom = _gpu_fmm(ps, q, gpu_params(g4, ps, ps.box_size, **kw))
+    OP = oracle_params(ps, ps.box_size, **kw)
+    run = oracle.prepare(q, ps.mass, None, None, OP, 8)
+    a_s, p_s, co, pc_s = run.tree.fmm(OP, per_particle=True)
+    ao = np.empty_like(a_s)
+    ao[run.perm] = a_s
+    po = np.empty_like(p_s)
+    po[run.perm] = p_s
+    pc = np.empty_like(pc_s)
+    pc[run.perm] = pc_s
+    assert co[0] > 0 and co[1] > 0
+    assert np.mean((cg[:, 0] == pc[:, 0]) & (cg[:, 1] == pc[:, 1])) >= 0.99
+    e = relerr(ag, ao)
+    assert np.percentile(e, 99) < PARITY_P99, np.percentile(e, [50, 99, 100])
+    assert np.percentile(np.abs(pg - po) / np.abs(po), 99) < PARITY_P99
+    assert np.linalg.norm(mom) < 1e-5 * np.sum(ps.mass * np.linalg.norm(ag, axis=1))
+    sinks = np.arange(0, ps.n, 4)
+    ad, _ = oracle.ewald_direct(q, ps.mass, None, sinks, oracle_params(ps, ps.box_size))
+    assert np.percentile(relerr(ag[sinks], ad), 99) < 0.02
+
+
+def test_ewald_fmm_opened_everywhere_is_the_exact_sum():
+    ps, q = _periodic_set(512, 24)
+    kw = dict(criterion=1, theta=1e-6, order_p=3, leaf_max=8, ewald=1)
+    ag, pg, cg, _ = _gpu_fmm(ps, q, gpu_params(g4, ps, ps.box_size, **kw))
+    ad, pd = oracle.ewald_direct(q, ps.mass, None, np.arange(ps.n), oracle_params(ps, ps.box_size))
+    assert np.all(cg[:, 1] == 0)
+    assert np.percentile(relerr(ag, ad), 99) < 2e-5
+    assert np.percentile(np.abs(pg - pd) / np.abs(pd), 99) < 2e-5

@@ -154,3 +154,55 @@ def test_ewald_tree_converges_with_order_and_needs_the_correction():
     run = oracle.prepare(q, ps.mass, None, None, OPn, 4)
     an, _, _ = oracle.tree_forces(run, sinks)
     assert np.percentile(_relerr(an, ad), 90) > 10 * err[3]
+
+
+def _fmm(ps, q, OP, leaf=4):
+    run = oracle.prepare(q, ps.mass, None, None, OP, leaf)
+    a_s, p_s, cnt = run.tree.fmm(OP)
+    a = np.empty_like(a_s)
+    a[run.perm] = a_s
+    p = np.empty_like(p_s)
+    p[run.perm] = p_s
+    return a, p, cnt
+
+
+def test_ewald_fmm_alpha0_is_the_exact_direct_sum():
+    """The FMM with the correction (kernel 1/r - psi in every mutual expansion, psi for every
+    pair, m_i psi(0) per particle): with alpha = 0 every pair is a particle pair, and the
+    result is the exact periodic direct sum."""
+    ps, q = _periodic_set(200, 13)
+    OP = oracle.OracleParams(box=ps.box_size, periodic=True, eps=ps.eps_table, alpha=0.0,
+                             order=3, ewald=True)
+    run = oracle.prepare(q, ps.mass, None, np.ones(ps.n), OP, 4)
+    a_s, p_s, cnt = run.tree.fmm(OP)
+    a = np.empty_like(a_s)
+    a[run.perm] = a_s
+    p = np.empty_like(p_s)
+    p[run.perm] = p_s
+    ad, pd = oracle.ewald_direct(q, ps.mass, None, np.arange(ps.n), OP)
+    assert cnt[0] == 0 and cnt[1] == 0
+    assert np.max(_relerr(a, ad)) < 1e-10
+    assert np.max(np.abs(p - pd) / np.abs(pd)) < 1e-10
+
+
+def test_ewald_fmm_converges_and_conserves_momentum():
+    """Geometric criterion theta = 0.6: the error against the exact periodic sum falls with the
+    order, total momentum is conserved to roundoff (the periodic kernel is even), and without
+    the correction the FMM is off by far more."""
+    ps, q = _periodic_set(400, 14)
+    OPd = oracle.OracleParams(box=ps.box_size, periodic=True, eps=ps.eps_table)
+    ad, _ = oracle.ewald_direct(q, ps.mass, None, np.arange(ps.n), OPd)
+    err = {}
+    for p in (2, 3, 4):
+        OP = oracle.OracleParams(box=ps.box_size, periodic=True, eps=ps.eps_table, criterion=1,
+                                 theta=0.6, order=p, ewald=True)
+        a, _, cnt = _fmm(ps, q, OP)
+        assert cnt[0] > 0 and cnt[1] > 0
+        err[p] = np.percentile(_relerr(a, ad), 90)
+        mom = np.sum(ps.mass[:, None] * a, axis=0)
+        assert np.linalg.norm(mom) < 1e-12 * np.sum(ps.mass * np.linalg.norm(a, axis=1))
+    assert err[3] < 0.6 * err[2] and err[4] < 0.6 * err[3], err
+    OPn = oracle.OracleParams(box=ps.box_size, periodic=True, eps=ps.eps_table, criterion=1,
+                              theta=0.6, order=3, ewald=False)
+    an, _, _ = _fmm(ps, q, OPn)
+    assert np.percentile(_relerr(an, ad), 90) > 10 * err[3]
