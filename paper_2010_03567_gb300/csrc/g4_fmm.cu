@@ -13,6 +13,20 @@ __global__ void k_fmm_reset(int32_t *dcount, double *mom)
     if (mom && threadIdx.x < 3) mom[threadIdx.x] = 0.0;
 }
 
+// kids[8 d + c]: depth-first index of daughter c of the node with depth-first index d (-1
+// past its daughters); the level-ordered build keeps a node's daughters consecutive
+__global__ void k_fmm_kids(const int32_t *__restrict__ lvl, const int32_t *__restrict__ b_dfs,
+                           const int32_t *__restrict__ b_child, const int32_t *__restrict__ b_nchild,
+                           int64_t cap, int32_t *__restrict__ kids)
+{
+    const int64_t nn = lvl[G4_NLEVELS];
+    for (int64_t lo = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lo < nn && lo < cap;
+         lo += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = b_dfs[lo], nc = b_nchild[lo], c0 = b_child[lo];
+        for (int c = 0; c < 8; c++) kids[(size_t)d * 8 + c] = c < nc ? b_dfs[c0 + c] : -1;
+    }
+}
+
 __global__ void k_momentum(const float *__restrict__ mass, const float *__restrict__ acc, int n,
                            double *__restrict__ mom)
 {
@@ -42,7 +56,7 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct FmmLayout {
     size_t T_own, T_tot, Doff, Dlen, m2l_own, m2l_cum, dcount, p2p_src, p2p_chunk, p2p_head,
-        p2p_sinks, p2p_fill, D0, D1, total;
+        p2p_sinks, p2p_fill, kids, D0, D1, total;
     int64_t dcap, p2p_cap, chunk_cap;
 };
 
@@ -73,6 +87,7 @@ FmmLayout fmm_layout(int64_t nodes, int64_t n_max, int nt, size_t ws_bytes, int 
     L.p2p_head = take(4 * nodes);
     L.p2p_sinks = take(4 * nodes);
     L.p2p_fill = take(16);
+    L.kids = take(32 * nodes);
     size_t fixed = o;
     int64_t dcap = 0;
     if (ws_bytes == 0) dcap = (int64_t)1 << 20 > 48 * nodes ? (int64_t)1 << 20 : 48 * nodes;
@@ -158,6 +173,7 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     A.p2p_head = (int32_t *)(w + L.p2p_head);
     A.p2p_sinks = (int32_t *)(w + L.p2p_sinks);
     A.p2p_fill = (int32_t *)(w + L.p2p_fill);
+    A.kids = (const int32_t *)(w + L.kids);
     A.p2p_cap = L.p2p_cap;
     A.chunk_cap = L.chunk_cap;
     A.flags = t->d_flags;
@@ -198,6 +214,10 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     if (s != G4_OK) return s;
     A.wpart = t->wpart;
     k_fmm_reset<<<1, 32, 0, st>>>(A.dcount, momentum_out);
+    // each node's daughters by depth-first index (daughters are consecutive in level order)
+    k_fmm_kids<<<g4_blocks_for(t->cap, 256), 256, 0, st>>>(t->lvl, t->b_dfs, t->b_child,
+                                                          t->b_nchild, t->cap,
+                                                          (int32_t *)(w + L.kids));
     if (cudaMemsetAsync(A.p2p_fill, 0, 16, st) != cudaSuccess)
         return g4_cuda_check(cudaGetLastError(), "g4_gravity_fmm: clear P2P counters");
     const bool geom = P->criterion == 1;
@@ -208,5 +228,5 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     default: dispatch_fmm<5>(A, treepm, geom, st); break;
     }
     if (momentum_out) k_momentum<<<g4_num_sms() * 4, 256, 0, st>>>(mass_sorted, acc, n, momentum_out);
-    return g4_launch_check("fmm", 2 + 2 * (G4_MAXLEVEL + 1) + (momentum_out ? 1 : 0));
+    return g4_launch_check("fmm", 3 + 2 * (G4_MAXLEVEL + 1) + (momentum_out ? 1 : 0));
 }

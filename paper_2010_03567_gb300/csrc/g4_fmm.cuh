@@ -587,11 +587,8 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                                                           (int)(nk >= 32 ? 0xffffffffu : ((1u << nk) - 1u)));
                         }
                     } else {
-                        int k = 0;
-                        for (int ch = ce.x + 1; ch < nb.next && k < e; k++) {
-                            Dout[w + pre + k] = make_int2(ch, 0);
-                            ch = max(A.node[ch].next, ch + 1);
-                        }
+                        for (int k = 0; k < e; k++)
+                            Dout[w + pre + k] = make_int2(__ldg(A.kids + (size_t)ce.x * 8 + k), 0);
                     }
                 }
                 w += warp_sum_i(e);
@@ -680,13 +677,9 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                     if (sp + tot > FMM_STACK) {
                         if (lane == 0) atomicOr(A.flags, G4_FLAG_LISTCAP);
                     } else {
-                        if (e > 0) {
-                            int k = 0;
-                            for (int ch = ce.x + 1; ch < nb.next && k < e; k++) {
-                                L.stack[sp + pre + k] = make_int2(ch, (int)vmask);
-                                ch = max(A.node[ch].next, ch + 1);
-                            }
-                        }
+                        for (int k = 0; k < e; k++)
+                            L.stack[sp + pre + k] =
+                                make_int2(__ldg(A.kids + (size_t)ce.x * 8 + k), (int)vmask);
                         sp += tot;
                     }
                     // particle candidates (taken once): accepted ones add to A's field, the
@@ -736,13 +729,9 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                             } else if (sp + nz.nchild > FMM_STACK) {
                                 if (lane == 0) atomicOr(A.flags, G4_FLAG_LISTCAP);
                             } else {
-                                if (lane == 0) {
-                                    int k = 0;
-                                    for (int ch = se.x + 1; ch < nz.next && k < nz.nchild; k++) {
-                                        L.stack[sp + k] = make_int2(ch, (int)om);
-                                        ch = max(A.node[ch].next, ch + 1);
-                                    }
-                                }
+                                if (lane < nz.nchild)   // one daughter per lane
+                                    L.stack[sp + lane] =
+                                        make_int2(__ldg(A.kids + (size_t)se.x * 8 + lane), (int)om);
                                 sp += nz.nchild;
                                 __syncwarp();
                             }

@@ -25,6 +25,7 @@ struct FmmArgs {
     const int32_t *lvl;
     const int32_t *b_dfs;
     const G4Node *node;
+    const int32_t *kids;       // per depth-first node: its daughters' depth-first indices (8)
     const float *q;
     int nq;
     float *T_own, *T_tot;
