@@ -950,53 +950,40 @@ def extra_plummer(leaf_max):
 
 
 def extra_softened(leaf_max):
-    """Softened node interactions (Sec. 2.7) where they matter: a zoom box (low-resolution
-    128^3 lattice, L = 100, a central sphere 64 times denser) whose heavy low-resolution
-    particles carry a softening of their spacing (2.8 eps about r_cut) next to the
-    high-resolution region.
-    Tree walk (p = 3) and FMM (p = 4) with the geometric criterion (theta = 0.5: with the
-    relative criterion at alpha = 0.0025 no node within 2.8 eps of a sink passes anyway, so the
-    two rules coincide there), under the GADGET-3 rule (every pair closer than 2.8 eps_ij
-    opened) and the GADGET-4 rule (the softened kernel's expansion unless both sides are
-    mixed): time, interactions, accuracy on sampled sinks against the oracle's FP64 direct sum
-    (r < r_cut, pair softening max(eps_i, eps_j))."""
+    """Softened node interactions (Sec. 2.7) on a set where softenings are comparable to the
+    node sizes: the 16k Plummer sphere with two softening classes (eps = 0.3 and 0.08, every
+    fourth particle in the second), tree walk (p = 3, alpha = 0.005, leaf 4) and FMM (p = 4)
+    under the GADGET-3 rule (every pair closer than 2.8 eps_ij opened) and the GADGET-4 rule
+    (the softened kernel's expansion unless both sides are mixed): time, interactions and
+    accuracy against the oracle's FP64 direct sum with pair softening max(eps_i, eps_j)."""
     import torch
     import oracle
     from paper_2010_03567_gb300 import g4, synth
-    L, ns = 100.0, 128
-    ps = synth.zoom(ns, L, 1007)
-    n = ps.n
-    ps.eps_table = np.array([1.0 * L / ns, ps.eps_table[1]])
-    base = dict(box_size=L, periodic=1, r_s=1.25 * L / (2 * ns), r_cut_factor=4.5,
-                eps=list(ps.eps_table), leaf_max=leaf_max)
-    q, _ = g4.g4_int_coords(torch.from_numpy(ps.pos).cuda(), True, L)
+    ps = synth.plummer_16k()
+    ps.eps_table = np.array([0.3, 0.08])
+    ps.eps_class = np.zeros(ps.n, np.uint8)
+    ps.eps_class[::4] = 1
+    q, fr = g4.g4_int_coords(torch.from_numpy(ps.pos).cuda(), False)
+    box = float(fr[3].item())
     mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
     cls = torch.from_numpy(ps.eps_class).cuda()
-    tg = g4.TreeGravity(n, g4.params(**base, criterion=1, theta=0.5), with_cls=True)
-    a0, _ = tg.forces(q, mass, cls, None)
-    aold = torch.linalg.vector_norm(a0, dim=0).contiguous()
-    # sampled sinks: random ones, and heavy particles within two low-resolution spacings of
-    # the sphere's surface (where the two species meet)
-    rng = np.random.default_rng(4107)
-    rad = np.linalg.norm(ps.pos - 0.5 * L, axis=1)
-    edge = np.flatnonzero((ps.eps_class == 0) & (np.abs(rad - 0.125 * L) < 2 * L / ns))
-    sinks = np.unique(np.concatenate([rng.choice(n, 1024, replace=False),
-                                      rng.choice(edge, min(1024, len(edge)), replace=False)]))
     q_np = q.cpu().numpy().view(np.uint32)
-    OP = oracle.OracleParams(box=L, periodic=True, eps=ps.eps_table, r_s=base["r_s"],
-                             r_cut_factor=4.5)
-    ad, _ = oracle.direct(q_np, ps.mass, ps.eps_class, sinks, OP, r_max=OP.r_cut)
+    OP = oracle.OracleParams(box=box, periodic=False, eps=ps.eps_table)
+    ad, _ = oracle.direct(q_np, ps.mass, ps.eps_class, np.arange(ps.n), OP)
+    aold = torch.from_numpy(np.linalg.norm(ad, axis=1).astype(np.float32)).cuda()
+    base = dict(box_size=box, periodic=0, eps=list(ps.eps_table), leaf_max=4, alpha=0.005)
+    tg = g4.TreeGravity(ps.n, g4.params(**base), with_cls=True)
     ws = None
-    out = {"particles": n, "eps": [float(e) for e in ps.eps_table], "sample": int(len(sinks))}
+    out = {"particles": ps.n, "eps": [0.3, 0.08]}
     for soft in (0, 1):
-        P = g4.params(**base, criterion=1, theta=0.5, soft_nodes=soft)
-        ms = _time(lambda: tg.forces(q, mass, cls, aold, P), 3)
+        P = g4.params(**base, soft_nodes=soft)
+        ms = _time(lambda: tg.forces(q, mass, cls, aold, P), 5)
         tg.tree.status()
         c = tg.counts.to(torch.int64).sum(dim=1).cpu().numpy()
-        ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
-        tree = {"ms_per_step": ms, "forces_per_s": n / (ms * 1e-3), "pp_per_step": int(c[0]),
-                "pn_per_step": int(c[1]), "accuracy_vs_direct": _errors(ag, ad)}
-        P4 = g4.params(**base, criterion=1, theta=0.5, order_p=4, soft_nodes=soft)
+        ag = tg.acc.cpu().numpy().T.astype(np.float64)
+        tree = {"ms_per_step": ms, "pp_per_step": int(c[0]), "pn_per_step": int(c[1]),
+                "accuracy_vs_direct": _errors(ag, ad)}
+        P4 = g4.params(**base, order_p=4, soft_nodes=soft)
         tg.prepare(q, mass, cls, aold, P4)
         if ws is None:
             ws = torch.empty(tg.tree.fmm_workspace(P4) + 256, dtype=torch.uint8, device="cuda")
@@ -1007,12 +994,12 @@ def extra_softened(leaf_max):
             res["r"] = tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, tg.cls_s, tg.aold_s, P4, workspace=ws)
             g4.g4_scatter(tg.perm, res["r"][0], res["r"][1], out=(tg.acc, tg.pot))
 
-        fms = _time(step, 3)
+        fms = _time(step, 5)
         tg.tree.status()
         cnt = res["r"][2].to(torch.int64).sum(dim=1).cpu().numpy()
-        af = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
-        fmm = {"ms_per_step": fms, "forces_per_s": n / (fms * 1e-3), "pp_per_step": int(cnt[0]),
-               "pn_per_step": int(cnt[1]), "accuracy_vs_direct": _errors(af, ad)}
+        af = tg.acc.cpu().numpy().T.astype(np.float64)
+        fmm = {"ms_per_step": fms, "pp_per_step": int(cnt[0]), "pn_per_step": int(cnt[1]),
+               "accuracy_vs_direct": _errors(af, ad)}
         out["gadget4_rule" if soft else "gadget3_rule"] = {"tree": tree, "fmm": fmm}
     g3, g4r = out["gadget3_rule"], out["gadget4_rule"]
     out["speedup_tree"] = g3["tree"]["ms_per_step"] / g4r["tree"]["ms_per_step"]
