@@ -14,7 +14,7 @@ import numpy as np
 from numpy.polynomial import chebyshev as C
 from scipy.special import erfcx
 
-XMAX, K, DEG = 4.0, 0.5, 8
+XMAX, K, DEG = 2.5, 0.5, 7
 
 
 def fit():
