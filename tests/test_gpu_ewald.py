@@ -165,3 +165,27 @@ def test_ewald_fmm_opened_everywhere_is_the_exact_sum():
     assert np.all(cg[:, 1] == 0)
     assert np.percentile(relerr(ag, ad), 99) < 2e-5
     assert np.percentile(np.abs(pg - pd) / np.abs(pd), 99) < 2e-5
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_ewald_single_particle_and_pair(n):
+    """One particle: no force, and the potential of its own images G m psi(0) with the
+    printed psi(0) L = 2.8372975; two particles: the exact periodic sum, tree and FMM."""
+    L = 10.0
+    g = np.random.default_rng(31 + n)
+    pos = g.uniform(0, L, (n, 3))
+    ps = synth.ParticleSet(pos=pos, mass=g.uniform(0.5, 1.5, n), eps_class=np.zeros(n, np.uint8),
+                           eps_table=np.array([0.01]), box_size=L, periodic=True)
+    q = oracle.int_coords_periodic(ps.pos, L)
+    kw = dict(criterion=1, theta=0.5, order_p=3, leaf_max=8, ewald=1)
+    P = gpu_params(g4, ps, L, **kw)
+    ag, pg, _, _ = gpu_forces(torch, g4, ps, q, P, None, cls=False)
+    af, pf, _, _ = _gpu_fmm(ps, q, P)
+    if n == 1:
+        assert np.all(ag == 0) and np.all(af == 0)
+        for p in (pg[0], pf[0]):
+            assert abs(p * L / ps.mass[0] - 2.8372975) < 1e-5
+    else:
+        ad, pd = oracle.ewald_direct(q, ps.mass, None, np.arange(n), oracle_params(ps, L))
+        for a, p in ((ag, pg), (af, pf)):
+            assert np.max(relerr(a, ad)) < 1e-5 and np.max(np.abs(p - pd) / np.abs(pd)) < 1e-5

@@ -235,3 +235,21 @@ def test_fmm_parity_softened_node_rule():
         assert np.linalg.norm(mom) < 1e-5 * np.sum(ps.mass * amag)
         pp[soft] = co[2]
     assert pp[1] < pp[0], pp
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 33])
+def test_fmm_small_and_degenerate_sets(n):
+    """One particle (no force, no potential), two, three, and 33 particles of which 20 share
+    one position (leaves at key resolution above leaf_max): the FMM against the oracle's."""
+    ps = synth.plummer(max(n, 1), 91 + n)
+    if n == 33:
+        ps.pos[1:20] = ps.pos[0]
+    q, box = int_coords(ps)
+    kw = dict(criterion=1, theta=0.5, order_p=3)
+    ag, pg, cg, mom = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), None)
+    ao, po, co, pc = oracle_fmm(ps, q, oracle_params(ps, box, **kw), None)
+    if n == 1:
+        assert np.all(ag == 0) and np.all(pg == 0)
+    else:
+        assert np.allclose(ag, ao, rtol=1e-5, atol=1e-6 * np.abs(ao).max())
+        assert np.allclose(pg, po, rtol=1e-5)
