@@ -126,6 +126,17 @@ __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf
           G4_PP_FP16_SLACK_ADD)));
     const __half2 sx2 = __float2half2_rn(xr * inv_rc), sy2 = __float2half2_rn(yr * inv_rc),
                   sz2 = __float2half2_rn(zr * inv_rc);
+    // Staged sources farther than r_cut from the sinks' bounding box (half extents gbx, gby,
+    // gbz about the centre) cannot pair with any sink: they are dropped before the per-lane
+    // tests (about half of the staged sources in a clustered box, whose leaves overhang the
+    // cutoff sphere).  Offsets and extents are rounded alike, and their FP32 error at
+    // R <= G4_PP_PRUNE_RMAX (64) is below 1e-5 r_cut, inside the G4_PP_PRUNE_MARGIN (2e-4)
+    // on r_cut^2.  Same nearest-image guard as the FP16 test.
+    const bool prune = TREEPM && A.pp_cut && R <= G4_PP_PRUNE_RMAX && R + 1.01f < half_box;
+    const float gbx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(xr))));
+    const float gby = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(yr))));
+    const float gbz = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(zr))));
+    const float plim = A.rcut2f * G4_PP_PRUNE_MARGIN;
     // Batch bb takes sources bb, bb + nbat, bb + 2 nbat, ...: every batch samples the whole
     // neighbourhood, so each lane's candidates spread evenly over the batches and the per-lane
     // evaluation loops below stay balanced across the warp.
@@ -165,31 +176,50 @@ __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf
         for (int q = 0; q < PP_STAGE / 32; q++) {
             const int u = q * 32 + lane;
             jq[q] = S.first[lq[q]] + (tq[q] - S.pref[lq[q]]);
-            if (u < nb) pq[q] = __ldg(A.wpart + jq[q]);
+            pq[q] = u < nb ? __ldg(A.wpart + jq[q]) : make_uint4(gcx, gcy, gcz, 0u);
         }
+        // staged sources kept (all of them without the prune), packed in staging order
+        int ns = 0;
 #pragma unroll
         for (int q = 0; q < PP_STAGE / 32; q++) {
-            const int u = q * 32 + lane, v = cand_bit(u);
-            if (u < nb) {
+            const int u = q * 32 + lane;
+            const uint32_t px = pq[q].x, py = pq[q].y, pz = pq[q].z;
+            const float ox = (float)(int32_t)(px - gcx) * fscale;
+            const float oy = (float)(int32_t)(py - gcy) * fscale;
+            const float oz = (float)(int32_t)(pz - gcz) * fscale;
+            bool keep = u < nb;
+            if (prune && keep) {
+                const float ex = fmaxf(fabsf(ox) - gbx, 0.f), ey = fmaxf(fabsf(oy) - gby, 0.f),
+                            ez = fmaxf(fabsf(oz) - gbz, 0.f);
+                keep = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= plim;
+            }
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int us = ns + __popc(km & ((1u << lane) - 1u)), v = cand_bit(us);
                 const int j = jq[q];
-                const uint32_t px = pq[q].x, py = pq[q].y, pz = pq[q].z;
                 const float hj = A.h_cls[A.cls ? __ldg(A.cls + j) : 0] * hconv;
                 const unsigned mk = S.mask[lq[q]];
                 S.ipos[v] = make_uint4(px, py, pz, __float_as_uint(hj));
                 S.mj[v] = make_float2(__uint_as_float(pq[q].w), __int_as_float(j));
                 S.smask[v] = mk;
-                S.hx[u] = __float2half_rn((float)(int32_t)(px - gcx) * fscale * inv_rc);
-                S.hy[u] = __float2half_rn((float)(int32_t)(py - gcy) * fscale * inv_rc);
-                S.hz[u] = __float2half_rn((float)(int32_t)(pz - gcz) * fscale * inv_rc);
+                S.hx[us] = __float2half_rn(ox * inv_rc);
+                S.hy[us] = __float2half_rn(oy * inv_rc);
+                S.hz[us] = __float2half_rn(oz * inv_rc);
                 partial |= (mk != vmask);
-            } else {
-                S.hx[u] = S.hy[u] = S.hz[u] = __float2half_rn(100.f);
-                S.smask[v] = 0xffffffffu;
+            }
+            ns += __popc(km);
+        }
+        {
+            // pad the last block of 32 with sources no test accepts
+            const int us = ns + lane;
+            if (us < ((ns + 31) & ~31)) {
+                S.hx[us] = S.hy[us] = S.hz[us] = __float2half_rn(100.f);
+                S.smask[cand_bit(us)] = 0xffffffffu;
             }
         }
         partial = __any_sync(0xffffffffu, partial);
         __syncwarp();
-        const int nw = (nb + 31) >> 5;
+        const int nw = (ns + 31) >> 5;
         uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
         if (test16) {
             const uint4 *X = reinterpret_cast<const uint4 *>(S.hx);
@@ -222,10 +252,10 @@ __device__ __forceinline__ void pp_flush(const Args &A, PPSmem<LB> &S, int nleaf
                 w3 = w == 3 ? m : w3;
             }
         } else {
-            // every staged source is a candidate; bit positions of sources u < nb
+            // every kept source is a candidate; bit positions of sources u < ns
 #pragma unroll
             for (int w = 0; w < 4; w++) {
-                const int r = min(max(nb - 32 * w, 0), 32);   // valid sources in block w
+                const int r = min(max(ns - 32 * w, 0), 32);   // valid sources in block w
                 const int ev = (r + 1) >> 1, od = r >> 1;      // even / odd ones
                 const uint32_t m = (ev >= 16 ? 0xffffu : ((1u << ev) - 1u)) |
                                    ((od >= 16 ? 0xffffu : ((1u << od) - 1u)) << 16);

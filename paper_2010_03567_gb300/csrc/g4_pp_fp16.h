@@ -7,7 +7,12 @@
  *   r^2 / r_cut^2 < (1 + G4_PP_FP16_C1 e + G4_PP_FP16_C2 e^2) G4_PP_FP16_SLACK_MUL
  *                   + G4_PP_FP16_SLACK_ADD                            (rounded up in FP16),
  * and groups wider than G4_PP_FP16_RMAX r_cut skip the test (every staged source is a
- * candidate).  Plain macros: the CPU test of the bound reads them from this file. */
+ * candidate).
+ * Before that test, staged sources farther than r_cut from the sinks' bounding box are dropped
+ * (FP32 offsets from the group centre, half extents = the sinks' largest |offset| per axis):
+ * kept when the squared distance is <= r_cut^2 G4_PP_PRUNE_MARGIN, for groups within
+ * G4_PP_PRUNE_RMAX r_cut of their centre (wider groups keep every staged source).
+ * Plain macros: the CPU tests of both bounds read them from this file. */
 #ifndef G4_PP_FP16_H
 #define G4_PP_FP16_H
 #define G4_PP_FP16_RMAX 2048.0f
@@ -18,4 +23,6 @@
 #define G4_PP_FP16_C2 3.0f
 #define G4_PP_FP16_SLACK_MUL 1.002f
 #define G4_PP_FP16_SLACK_ADD 0.002f
+#define G4_PP_PRUNE_RMAX 64.0f
+#define G4_PP_PRUNE_MARGIN 1.0002f
 #endif
