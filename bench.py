@@ -5,11 +5,11 @@ Workload (the headline configuration): periodic box L = 500 with 256^3 equal-mas
 lattice plus Zel'dovich displacements from a seeded Gaussian field with P(k) ~ k^-2 and rms
 displacement 2 grid spacings (strongly clustered), 32-bit integer coordinates, TreePM split
 r_s = 1.25 L / 512, cutoff 4.5 r_s, softening eps = L / 256 / 30, one-sided tree of order
-p = 3 with the relative opening criterion alpha = 0.0025, leaf threshold 8.
+p = 3 with the relative opening criterion alpha = 0.0025, leaf threshold 32.
 
 One step = one complete force computation through the C ABI: Peano-Hilbert keys + radix sort,
-PH-order gather, oct-tree build, upward moments, tree walk (with |a_old| of the previous step),
-scatter back to input order.  |a_old| comes from one geometric-criterion walk before timing
+PH-order gather, oct-tree build, upward moments, tree walk (with |a_old| of the previous step)
+writing its results in input order (the scatter fused into the walk's epilogue).  |a_old| comes from one geometric-criterion walk before timing
 (the paper's first-step bootstrap).  Inputs (about 335 MB) are larger than the 129 MB L2.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead.
@@ -54,10 +54,10 @@ def fp32_peak_tflops():
 
 
 # DRAM bytes (read + write) of one k_walk launch of the headline workload: the single-pass ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed walk, 622,315,776 +
-# 740,627,200 bytes.  Reported as roofline.traffic for the default workload only; set to
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed walk, 761,592,320 +
+# 762,985,984 bytes.  Reported as roofline.traffic for the default workload only; set to
 # None whenever the walk kernel changes until it is captured again.
-WALK_DRAM_BYTES_256 = 1362942976
+WALK_DRAM_BYTES_256 = 1524578304
 
 
 def hbm_peak_gbs():
@@ -72,9 +72,9 @@ def hbm_peak_gbs():
 # algorithmic bytes per particle / per node of the HBM-bound stages (keys: 12 B read + 8 B
 # written; sort: 8 passes of (8 + 4) B read and written; gather: perm + 20 B in, 20 B out;
 # build: keys and positions read plus ~64 B per node; multipoles: particles read once, node
-# records and p = 3 moments (64 + 64 B) written; scatter: perm + 16 B in, 16 B out)
+# records and p = 3 moments (64 + 64 B) written; the walk writes its results in input order)
 STAGE_BYTES = {"keys_sort": (20 + 8 * 2 * 12, 0), "gather": (44, 0), "build": (24, 64),
-               "multipoles": (16, 128), "scatter": (36, 0)}
+               "multipoles": (16, 128)}
 
 
 LEAF_MAX = 32          # tuned on GB300 with autotune.tune_leaf on the 256^3 box
@@ -188,9 +188,8 @@ def stage_breakdown(tg, pos_int, mass, aold, P, n, n_nodes, reps=3):
                                         out=(tg.pos_s, tg.mass_s, None, tg.aold_s))),
         ("build", lambda: tg.tree.build(tg.keys, tg.pos_s, P)),
         ("multipoles", lambda: tg.tree.multipoles(tg.pos_s, tg.mass_s, None, tg.aold_s, P)),
-        ("walk", lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, acc=tg.acc_s,
-                                              pot=tg.pot_s, counts=tg.counts)),
-        ("scatter", lambda: g4.g4_scatter(tg.perm, tg.acc_s, tg.pot_s, out=(tg.acc, tg.pot))),
+        ("walk", lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, acc=tg.acc,
+                                              pot=tg.pot, counts=tg.counts, perm=tg.perm)),
     ]
     s = torch.cuda.current_stream()
     tot = {k: 0.0 for k, _ in stages}
@@ -388,7 +387,8 @@ def run_gpu(args, rank, world):
             sample_ref = (sinks, ad)
         collect_cost_samples("C3_256cubed", tg.tree, P, n, tg.aold_s, tg.counts)
         for name, fn in (("cost_model", lambda: extra_cost_model(tg, P, n)),
-                         ("fmm", lambda: extra_fmm(pos_int, mass, aold, wp, n, sample_ref)),
+                         ("fmm", lambda: extra_fmm(pos_int, mass, aold, wp, n, sample_ref,
+                                                   cpu=not args.no_cpu)),
                          ("treepm", lambda: extra_treepm(pos_int, mass, aold, wp, n)),
                          ("fp64_walk", lambda: extra_fp64(tg, P, n, sample_ref)),
                          ("batched_systems", lambda: extra_forest(wp["leaf_max"])),
@@ -464,8 +464,30 @@ def _time(fn, reps, warm=1):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_fmm(pos_int, mass, aold, wp, n, sample_ref):
-    """Symmetric FMM (p = 4, relative criterion) on the headline box."""
+def oracle_fmm_throughput(n_side_cpu=40):
+    """The FP64 oracle's FMM (p = 4, relative criterion, leaf 32) on a box of the headline's
+    spacing, split and cutoff with n_side_cpu^3 particles (the FMM's work per particle does not
+    grow with N), on the host: forces/s."""
+    import oracle
+    from paper_2010_03567_gb300 import synth
+    L = 500.0 * n_side_cpu / N_SIDE
+    ps = synth.zeldovich(n_side_cpu, L, 2.0, 1003)
+    q = oracle.int_coords_periodic(ps.pos, L)
+    OP = oracle.OracleParams(box=L, periodic=True, eps=np.array([L / n_side_cpu / 30.0]),
+                             r_s=1.25 * L / (2 * n_side_cpu), r_cut_factor=4.5, alpha=0.0025, order=4)
+    t0 = time.perf_counter()
+    run = oracle.prepare(q, ps.mass, None, np.full(ps.n, 20.0), OP, LEAF_MAX)
+    run.tree.fmm(OP)
+    t = time.perf_counter() - t0
+    return {"value": ps.n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle FMM (keys, sort, tree, multipoles, dual walk; p = 4, alpha = 0.0025, "
+                      f"|a_old| = 20, leaf {LEAF_MAX}) on a {n_side_cpu}^3 box with the headline's spacing, "
+                      f"r_s / spacing and R_cut, one thread; {t:.1f} s"}
+
+
+def extra_fmm(pos_int, mass, aold, wp, n, sample_ref, cpu=True):
+    """Symmetric FMM (p = 4, relative criterion) on the headline box; the oracle's FMM on a
+    bounded sample of the same workload on the host."""
     import torch
     from paper_2010_03567_gb300 import g4
     P4 = g4.params(**{**wp, "order_p": 4})
@@ -498,6 +520,8 @@ def extra_fmm(pos_int, mass, aold, wp, n, sample_ref):
         e = np.linalg.norm(ag - ad, axis=1) / np.linalg.norm(ad, axis=1)
         res["accuracy_vs_direct"] = {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99))}
     del ws
+    if cpu:
+        res["cpu_oracle"] = oracle_fmm_throughput()
     return res
 
 
@@ -887,7 +911,7 @@ def extra_fp64(tg, P, n, sample_ref):
     from paper_2010_03567_gb300 import g4
     P64 = g4.G4Params.from_buffer_copy(P)
     P64.precision = 1
-    a32 = tg.acc_s.clone()
+    a32, _, _ = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P)   # FP32, sorted order
     tg.tree.multipoles(tg.pos_s, tg.mass_s, None, tg.aold_s, P64)
     acc64 = torch.zeros_like(tg.acc_s)
     ms = _time(lambda: tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P64, acc=acc64,

@@ -300,6 +300,19 @@ g4_status g4_gravity_tree(g4_tree tree, const uint32_t *pos_sorted, const float 
                           const int32_t *active, int64_t n_active, const g4_params *params,
                           float *acc, float *pot, uint32_t *counts, void *stream);
 
+/* g4_gravity_tree with the scatter back to input order fused into the walk's epilogue:
+ * perm (n int32, device; g4_keys_sort's permutation, perm[s] = input index of sorted particle
+ * s, a permutation of 0..n-1) sends sorted sink s's acceleration and potential to
+ * acc[:, perm[s]] and pot[perm[s]] (acc 3 x n SoA and pot n in input order); counts stay in
+ * sorted order.  Same results as g4_gravity_tree
+ * followed by g4_scatter, without the sorted-order copies.  Errors: those of
+ * g4_gravity_tree; G4_ERR_INVALID_ARG for a NULL perm. */
+g4_status g4_gravity_tree_perm(g4_tree tree, const uint32_t *pos_sorted, const float *mass_sorted,
+                               const uint8_t *cls_sorted, const float *aold_sorted,
+                               const int32_t *active, int64_t n_active, const g4_params *params,
+                               const int32_t *perm, float *acc, float *pot, uint32_t *counts,
+                               void *stream);
+
 /* ---- a8: symmetric Cartesian FMM (Sec. 2.4, Sec. 2.5) ----------------------------------- */
 
 /* Bytes of device workspace g4_gravity_fmm needs, sized from the handle's node capacity and

@@ -51,6 +51,7 @@ struct WalkArgs {
     const double *sys_box;
     int n_sys;
     const int32_t *group_order;   // optional schedule (longest predicted cost first)
+    const int32_t *operm;         // optional output order: acc/pot of sorted sink i go to operm[i]
     const int4 *items;            // optional work items (first sink, count, part | parts << 8,
     const int32_t *n_items;       //   split slot); their number on the device
     int gs;                       // sinks per group (8, 16 or 32)
@@ -570,10 +571,11 @@ k_walk(const WalkArgs A)
         if (Kp == 1) {
             if (valid) {
                 const T G = par<T>(A.G, A.Gf);
-                A.acc[i] = (float)(-G * (ax + bx));
-                A.acc[A.n + i] = (float)(-G * (ay + by));
-                A.acc[2 * A.n + i] = (float)(-G * (az + bz));
-                if (A.pot) A.pot[i] = (float)(-G * (ap + bp));
+                const int o = A.operm ? __ldg(A.operm + i) : i;
+                A.acc[o] = (float)(-G * (ax + bx));
+                A.acc[A.n + o] = (float)(-G * (ay + by));
+                A.acc[2 * A.n + o] = (float)(-G * (az + bz));
+                if (A.pot) A.pot[o] = (float)(-G * (ap + bp));
                 if (A.counts) {
                     A.counts[i] = npp;
                     A.counts[A.n + i] = npn;
@@ -609,10 +611,11 @@ k_walk(const WalkArgs A)
                 }
                 if (valid) {
                     const float G = A.Gf;
-                    A.acc[i] = -G * sx;
-                    A.acc[A.n + i] = -G * sy;
-                    A.acc[2 * A.n + i] = -G * sz;
-                    if (A.pot) A.pot[i] = -G * sp;
+                    const int o = A.operm ? __ldg(A.operm + i) : i;
+                    A.acc[o] = -G * sx;
+                    A.acc[A.n + o] = -G * sy;
+                    A.acc[2 * A.n + o] = -G * sz;
+                    if (A.pot) A.pot[o] = -G * sp;
                     if (A.counts) {
                         A.counts[i] = cp;
                         A.counts[A.n + i] = cn;
@@ -837,11 +840,11 @@ g4_status g4_particle_records(g4_tree t, const uint32_t *pos_sorted, const float
     return g4_launch_check("particle records", n > 0 ? 1 : 0);
 }
 
-extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
-                                     const float *mass_sorted, const uint8_t *cls_sorted,
-                                     const float *aold_sorted, const int32_t *active,
-                                     int64_t n_active, const g4_params *P, float *acc, float *pot,
-                                     uint32_t *counts, void *stream)
+static g4_status gravity_tree(g4_tree t, const uint32_t *pos_sorted, const float *mass_sorted,
+                              const uint8_t *cls_sorted, const float *aold_sorted,
+                              const int32_t *active, int64_t n_active, const g4_params *P,
+                              const int32_t *out_perm, float *acc, float *pot, uint32_t *counts,
+                              void *stream)
 {
     g4_status s = g4_check_params(P, "g4_gravity_tree");
     if (s != G4_OK) return s;
@@ -878,6 +881,7 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     A.acc = acc;
     A.pot = pot;
     A.counts = counts;
+    A.operm = out_perm;
     A.work = t->d_flags + 1;
     A.flags = t->d_flags;
     A.sys_first = t->sys_first;
@@ -973,6 +977,28 @@ extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
     if (P->precision == 1) dispatch_walk<double>(P->order_p, A, treepm, geom, st);
     else dispatch_walk<float>(P->order_p, A, treepm, geom, st);
     return g4_launch_check("tree walk", 2 + extra);
+}
+
+extern "C" g4_status g4_gravity_tree(g4_tree t, const uint32_t *pos_sorted,
+                                     const float *mass_sorted, const uint8_t *cls_sorted,
+                                     const float *aold_sorted, const int32_t *active,
+                                     int64_t n_active, const g4_params *P, float *acc, float *pot,
+                                     uint32_t *counts, void *stream)
+{
+    return gravity_tree(t, pos_sorted, mass_sorted, cls_sorted, aold_sorted, active, n_active, P,
+                        nullptr, acc, pot, counts, stream);
+}
+
+extern "C" g4_status g4_gravity_tree_perm(g4_tree t, const uint32_t *pos_sorted,
+                                          const float *mass_sorted, const uint8_t *cls_sorted,
+                                          const float *aold_sorted, const int32_t *active,
+                                          int64_t n_active, const g4_params *P,
+                                          const int32_t *perm, float *acc, float *pot,
+                                          uint32_t *counts, void *stream)
+{
+    if (!perm) return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_tree_perm: NULL perm");
+    return gravity_tree(t, pos_sorted, mass_sorted, cls_sorted, aold_sorted, active, n_active, P,
+                        perm, acc, pot, counts, stream);
 }
 
 extern "C" g4_status g4_direct(const uint32_t *pos, const float *mass, const uint8_t *cls,

@@ -84,6 +84,7 @@ def _declare(L):
         "g4_multipoles": ([vp, vp, vp, vp, vp, P, vp], i32),
         "g4_tree_moments": ([vp, vp, vp, vp, vp], i32),
         "g4_gravity_tree": ([vp, vp, vp, vp, vp, vp, i64, P, vp, vp, vp, vp], i32),
+        "g4_gravity_tree_perm": ([vp, vp, vp, vp, vp, vp, i64, P, vp, vp, vp, vp, vp], i32),
         "g4_fmm_workspace": ([vp, P, C.POINTER(C.c_size_t)], i32),
         "g4_gravity_fmm": ([vp, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, C.c_size_t, vp], i32),
         "g4_direct": ([vp, vp, vp, i64, vp, i64, P, vp, vp, vp], i32),
@@ -309,16 +310,24 @@ class Tree:
         return out
 
     def gravity_tree(self, pos_sorted, mass_sorted, cls_sorted, aold_sorted, p: G4Params,
-                     active=None, acc=None, pot=None, counts=None, stream=None):
+                     active=None, acc=None, pot=None, counts=None, stream=None, perm=None):
+        """Tree walk; outputs in sorted order, or in input order through perm
+        (g4_gravity_tree_perm: the scatter fused into the walk)."""
         n = pos_sorted.shape[1]
         dev = pos_sorted.device
         acc = acc if acc is not None else torch.zeros((3, n), dtype=torch.float32, device=dev)
         pot = pot if pot is not None else torch.zeros(n, dtype=torch.float32, device=dev)
         counts = counts if counts is not None else torch.zeros((2, n), dtype=torch.int32, device=dev)
         na = 0 if active is None else int(active.shape[0])
-        _check(lib().g4_gravity_tree(self.h, _ptr(pos_sorted), _ptr(mass_sorted), _ptr(cls_sorted),
-                                     _ptr(aold_sorted), _ptr(active), na, C.byref(p), _ptr(acc),
-                                     _ptr(pot), _ptr(counts), _stream(stream)), "g4_gravity_tree")
+        if perm is None:
+            _check(lib().g4_gravity_tree(self.h, _ptr(pos_sorted), _ptr(mass_sorted), _ptr(cls_sorted),
+                                         _ptr(aold_sorted), _ptr(active), na, C.byref(p), _ptr(acc),
+                                         _ptr(pot), _ptr(counts), _stream(stream)), "g4_gravity_tree")
+        else:
+            _check(lib().g4_gravity_tree_perm(self.h, _ptr(pos_sorted), _ptr(mass_sorted),
+                                              _ptr(cls_sorted), _ptr(aold_sorted), _ptr(active), na,
+                                              C.byref(p), _ptr(perm), _ptr(acc), _ptr(pot),
+                                              _ptr(counts), _stream(stream)), "g4_gravity_tree_perm")
         return acc, pot, counts
 
     def fmm_workspace(self, p: G4Params) -> int:
@@ -390,7 +399,8 @@ def g4_pm_long_range(pos, mass, p: G4Params, n_grid: int, sinks=None, acc=None, 
 # ---- whole pipeline ------------------------------------------------------------------------------
 
 class TreeGravity:
-    """Preallocated pipeline: keys + sort -> gather -> tree -> moments -> walk -> scatter.
+    """Preallocated pipeline: keys + sort -> gather -> tree -> moments -> walk (writing its
+    results in input order: the scatter is fused into the walk).
 
     All buffers are allocated once (torch, on the current device), so ``forces`` performs no
     allocation and no host synchronisation and can be captured in a CUDA graph.
@@ -434,11 +444,11 @@ class TreeGravity:
                              self.aold_s if aold is not None else None, p, stream)
 
     def walk(self, p: G4Params | None = None, use_aold: bool = True, stream=None):
+        """The walk, writing accelerations and potentials straight to input order."""
         p = p or self.p
         self.tree.gravity_tree(self.pos_s, self.mass_s, self.cls_s,
-                               self.aold_s if use_aold else None, p, acc=self.acc_s, pot=self.pot_s,
-                               counts=self.counts, stream=stream)
-        g4_scatter(self.perm, self.acc_s, self.pot_s, out=(self.acc, self.pot), stream=stream)
+                               self.aold_s if use_aold else None, p, acc=self.acc, pot=self.pot,
+                               counts=self.counts, stream=stream, perm=self.perm)
         return self.acc, self.pot
 
     def forces(self, pos_int, mass, cls=None, aold=None, p: G4Params | None = None, stream=None,
@@ -514,9 +524,8 @@ class HostPipeline:
         tg = self.tg
         tg.prepare(d_pos, d_mass, None, d_aold, p)
         self.in_free[b].record(ms)
-        tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, p, acc=tg.acc_s, pot=tg.pot_s,
-                             counts=tg.counts)
-        g4_scatter(tg.perm, tg.acc_s, tg.pot_s, out=(d_acc, d_pot))
+        tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, p, acc=d_acc, pot=d_pot,
+                             counts=tg.counts, perm=tg.perm)
         self.out_ready[b].record(ms)
         ds.wait_event(self.out_ready[b])
         done = torch.cuda.Event(enable_timing=True)
@@ -579,8 +588,8 @@ class ForestGravity:
         self.tree.multipoles(self.pos_s, self.mass_s, None, self.aold_s if aold is not None else None,
                              p, stream)
         self.tree.gravity_tree(self.pos_s, self.mass_s, None, self.aold_s if aold is not None else None,
-                               p, acc=self.acc_s, pot=self.pot_s, counts=self.counts, stream=stream)
-        g4_scatter(self.perm, self.acc_s, self.pot_s, out=(self.acc, self.pot), stream=stream)
+                               p, acc=self.acc, pot=self.pot, counts=self.counts, stream=stream,
+                               perm=self.perm)
         return self.acc, self.pot
 
 
@@ -896,11 +905,12 @@ class SubsetForces:
             self.tree.gravity_fmm(v3(self.pos_s), self.mass_s[:k], cls_s, aold_s, p, workspace=self.fmm_ws,
                                   acc=v3(self.acc_s), pot=self.pot_s[:k], counts=v3(self.counts),
                                   stream=stream)
+            g4_scatter(self.perm[:k], v3(self.acc_s), self.pot_s[:k], out=(v3(self.acc_sub), self.pot_sub[:k]),
+                       stream=stream)
         else:
-            self.tree.gravity_tree(v3(self.pos_s), self.mass_s[:k], cls_s, aold_s, p, acc=v3(self.acc_s),
-                                   pot=self.pot_s[:k], counts=self.counts[:2 * k].view(2, k), stream=stream)
-        g4_scatter(self.perm[:k], v3(self.acc_s), self.pot_s[:k], out=(v3(self.acc_sub), self.pot_sub[:k]),
-                   stream=stream)
+            self.tree.gravity_tree(v3(self.pos_s), self.mass_s[:k], cls_s, aold_s, p, acc=v3(self.acc_sub),
+                                   pot=self.pot_sub[:k], counts=self.counts[:2 * k].view(2, k), stream=stream,
+                                   perm=self.perm[:k])
         _check(lib().g4_scatter_subset(_ptr(idx), k, n_all, _ptr(v3(self.acc_sub)), _ptr(self.pot_sub[:k]),
                                        _ptr(acc_out), _ptr(pot_out), _stream(stream)), "g4_scatter_subset")
 

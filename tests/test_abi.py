@@ -40,6 +40,31 @@ def test_host_side_calls():
         g4.params(no_such_field=1)
 
 
+def test_binding_argument_counts_match_header():
+    """Every entry point the binding declares takes as many arguments as its prototype in
+    include/g4.h (a missing argument would shift every later pointer)."""
+    from paper_2010_03567_gb300 import g4
+    src = open(os.path.join(ROOT, "include", "g4.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = dict(re.findall(r"\b(g4_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", src))
+    L = g4.lib()
+    checked = 0
+    for name, args in protos.items():
+        at = getattr(L, name).argtypes
+        if at is None:
+            continue
+        a = args.strip()
+        n = 0 if a in ("", "void") else a.count(",") + 1
+        assert len(at) == n, (name, len(at), n)
+        checked += 1
+    assert checked >= 30 and "g4_gravity_tree_perm" in protos
+    # the fused-scatter walk rejects a NULL permutation before touching a GPU
+    p = g4.params()
+    st = L.g4_gravity_tree_perm(None, None, None, None, None, None, 0, C.byref(p), None, None,
+                                None, None, None)
+    assert st == 1 and b"NULL perm" in L.g4_last_error()
+
+
 def test_oracle_and_library_share_no_code():
     # the oracle is plain C under oracle/, the library CUDA under the package: no includes across
     import glob

@@ -247,6 +247,40 @@ def test_active_subset_bitwise_equal_and_deterministic():
     assert torch.max(torch.abs(a - b)) <= 1e-6 * torch.max(torch.abs(b))
 
 
+def test_walk_with_fused_scatter_equals_walk_then_scatter():
+    """g4_gravity_tree_perm (the walk writing its results in input order) gives bitwise the
+    results of g4_gravity_tree followed by g4_scatter, for all sinks and for an active subset,
+    and is what TreeGravity.forces returns."""
+    ps, q, box, aold, _ = _plummer_c1()
+    P = gpu_params(g4, ps, box, alpha=0.0025)
+    tg = g4.TreeGravity(ps.n, P)
+    pos = u32_dev(torch, q)
+    mass = to_dev(torch, ps.mass, torch.float32)
+    a = to_dev(torch, aold, torch.float32)
+    tg.prepare(pos, mass, None, a)
+    acc_s, pot_s, cnt = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P)
+    ref_acc, ref_pot = g4.g4_scatter(tg.perm, acc_s, pot_s)
+    acc = torch.full((3, ps.n), float("nan"), device="cuda")
+    pot = torch.full((ps.n,), float("nan"), device="cuda")
+    _, _, cnt2 = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, acc=acc, pot=pot,
+                                      perm=tg.perm)
+    assert torch.equal(acc, ref_acc) and torch.equal(pot, ref_pot) and torch.equal(cnt, cnt2)
+    af, pf = tg.forces(pos, mass, None, a, P)
+    assert torch.equal(af, ref_acc) and torch.equal(pf, ref_pot)
+    # an active subset: only the listed sinks' input-order slots are written
+    active = torch.arange(5, ps.n, 37, dtype=torch.int32, device="cuda")
+    acc3, pot3, _ = tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, active=active)
+    acc4 = torch.full((3, ps.n), float("nan"), device="cuda")
+    pot4 = torch.full((ps.n,), float("nan"), device="cuda")
+    tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, tg.aold_s, P, active=active, acc=acc4, pot=pot4,
+                         perm=tg.perm)
+    out = tg.perm[active.long()].long()
+    assert torch.equal(acc4[:, out], acc3[:, active.long()]) and torch.equal(pot4[out], pot3[active.long()])
+    written = torch.zeros(ps.n, dtype=torch.bool, device="cuda")
+    written[out] = True
+    assert bool(torch.isnan(pot4[~written]).all()) and not bool(torch.isnan(pot4[written]).any())
+
+
 def _sparse_pairs():
     """2,048 pairs 0.99 r_cut apart in a box of 1,000 r_cut: every 32-sink group spans ~120
     r_cut, where FP16 positions relative to the group centre err by more than the candidate
