@@ -486,8 +486,9 @@ def oracle_fmm_throughput(n_side_cpu=40):
 
 
 def extra_fmm(pos_int, mass, aold, wp, n, sample_ref, cpu=True):
-    """Symmetric FMM (p = 4, relative criterion) on the headline box; the oracle's FMM on a
-    bounded sample of the same workload on the host."""
+    """Symmetric FMM (p = 4, relative criterion) on the headline box; the same FMM run all in
+    FP64 on the GPU, and the FP32 run's error against it; the oracle's FMM on a bounded sample
+    of the same workload on the host."""
     import torch
     from paper_2010_03567_gb300 import g4
     P4 = g4.params(**{**wp, "order_p": 4})
@@ -520,6 +521,31 @@ def extra_fmm(pos_int, mass, aold, wp, n, sample_ref, cpu=True):
         e = np.linalg.norm(ag - ad, axis=1) / np.linalg.norm(ad, axis=1)
         res["accuracy_vs_direct"] = {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99))}
     del ws
+    # the all-FP64 GPU run of the same FMM (precision 1: FP64 node data, expansions, fields and
+    # pairs; the decisions as in FP32): the FP32 run's error against it
+    a32 = acc_s.clone()
+    P4d = g4.G4Params.from_buffer_copy(P4)
+    P4d.precision = 1
+    tg.tree.multipoles(tg.pos_s, tg.mass_s, None, tg.aold_s, P4d)
+    ws64 = torch.empty(tg.tree.fmm_workspace(P4d) + 256, dtype=torch.uint8, device="cuda")
+    r64 = {}
+    ms64 = _time(lambda: r64.__setitem__("r", tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, tg.aold_s,
+                                                                   P4d, workspace=ws64)), 1)
+    tg.tree.status()
+    a64, _, c64, mom64 = r64["r"]
+    amag64 = torch.linalg.vector_norm(a64.double(), dim=0)
+    fp64 = {"ms_per_step": ms64,
+            "momentum_rel": float(torch.linalg.vector_norm(mom64).item() / (ms_s * amag64).sum().item()),
+            "counts_identical_frac": float((c64 == cnt).all(dim=0).double().mean().item()),
+            "fp32_vs_fp64_gpu": _errors(a32.double().cpu().numpy().T, a64.double().cpu().numpy().T)}
+    if sample_ref is not None:
+        sinks, ad = sample_ref
+        inv = torch.empty_like(tg.perm)
+        inv[tg.perm.long()] = torch.arange(n, dtype=torch.int32, device="cuda")
+        rows = inv[torch.from_numpy(sinks).cuda().long()].long()
+        fp64["fp64_gpu_vs_direct"] = _errors(a64[:, rows].double().cpu().numpy().T, ad)
+    res["fp64_gpu"] = fp64
+    del ws64
     if cpu:
         res["cpu_oracle"] = oracle_fmm_throughput()
     return res

@@ -340,6 +340,10 @@ g4_status g4_fmm_workspace(g4_tree tree, const g4_params *params, size_t *bytes)
  *   counts: 3 x n uint32 (nullable): particle pairs of the particle, particle-node terms
  *          evaluated at the particle, node-node fields reaching its leaf.
  *   momentum_out: 3 doubles of device memory (nullable), receives sum m a in FP64.
+ *   precision 1 (order_p 4 only; needs g4_multipoles with precision 1): the FP64 reference
+ *          mode -- the decisions as in FP32, every expansion, field, downward shift and
+ *          particle pair in FP64 from the FP64 node data; outputs still float.  Other orders:
+ *          G4_ERR_INVALID_ARG; FP32 multipoles: G4_ERR_STATE.
  * Outputs otherwise as for g4_gravity_tree. */
 g4_status g4_gravity_fmm(g4_tree tree, const uint32_t *pos_sorted, const float *mass_sorted,
                          const uint8_t *cls_sorted, const float *aold_sorted,

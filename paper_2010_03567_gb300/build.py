@@ -35,7 +35,9 @@ def nvcc() -> str:
 # (order, TreePM) variants compile in parallel instead of in one long translation unit
 VARIANTS = {
     "g4_fmm_variant.cu": [([f"-DG4_FMM_P={p}", f"-DG4_FMM_TREEPM={t}"], f"_p{p}t{t}")
-                          for p in (2, 3, 4, 5) for t in (0, 1)],
+                          for p in (2, 3, 4, 5) for t in (0, 1)] +
+                         [([f"-DG4_FMM_P=4", f"-DG4_FMM_TREEPM={t}", "-DG4_FMM_FP64=1"], f"_p4t{t}d")
+                          for t in (0, 1)],
 }
 
 

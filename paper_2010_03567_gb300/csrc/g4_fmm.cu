@@ -45,11 +45,11 @@ __global__ void k_momentum(const float *__restrict__ mass, const float *__restri
 }
 
 
-template <int P>
+template <int P, typename R>
 void dispatch_fmm(const FmmArgs &A, bool treepm, bool geom, cudaStream_t st)
 {
-    if (treepm) g4fmm::run_variant<P, true>(A, geom, st);
-    else g4fmm::run_variant<P, false>(A, geom, st);
+    if (treepm) g4fmm::run_variant<P, true, R>(A, geom, st);
+    else g4fmm::run_variant<P, false, R>(A, geom, st);
 }
 
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -62,13 +62,14 @@ struct FmmLayout {
 
 // deferred particle-pair lists: 16 entries (16 bytes each) and 1.25 chunks per particle of the
 // handle (plus a floor for small sets); overflowing chunks are evaluated by the dual walk itself
-FmmLayout fmm_layout(int64_t nodes, int64_t n_max, int nt, size_t ws_bytes, int per_particle)
+FmmLayout fmm_layout(int64_t nodes, int64_t n_max, int nt, size_t ws_bytes, int per_particle,
+                     size_t tbytes)
 {
     FmmLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += al256(bytes); return r; };
-    L.T_own = take(sizeof(float) * nt * nodes);
-    L.T_tot = take(sizeof(float) * nt * nodes);
+    L.T_own = take(tbytes * nt * nodes);   // field tensors: float, or double (FP64 mode)
+    L.T_tot = take(tbytes * nt * nodes);
     L.Doff = take(4 * nodes);
     L.Dlen = take(4 * nodes);
     L.m2l_own = take(4 * nodes);
@@ -111,7 +112,8 @@ extern "C" g4_status g4_fmm_workspace(g4_tree t, const g4_params *P, size_t *byt
     if (s != G4_OK) return s;
     if (!t || !bytes) return g4_fail(G4_ERR_INVALID_ARG, "g4_fmm_workspace: NULL argument");
     // sized for the handle's node capacity, so no host synchronisation is needed
-    *bytes = fmm_layout(t->cap, t->n_max, g4_nmono(P->order_p), 0, P->fmm_p2p_per_particle).total;
+    *bytes = fmm_layout(t->cap, t->n_max, g4_nmono(P->order_p), 0, P->fmm_p2p_per_particle,
+                        P->precision == 1 ? sizeof(double) : sizeof(float)).total;
     return G4_OK;
 }
 
@@ -136,13 +138,17 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
                        t->moments_order, P->order_p);
     if (P->order_p < 2 || P->order_p > 5)
         return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: order_p must be in [2,5]");
-    if (P->precision != 0)
-        return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: only FP32 interactions (precision 0)");
+    if (P->precision == 1 && P->order_p != 4)
+        return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: the FP64 mode is built for order_p 4");
+    if (P->precision == 1 && !t->moments_fp64)
+        return g4_fail(G4_ERR_STATE, "g4_gravity_fmm: FP64 mode needs FP64 multipoles");
     const int n = t->built_n;
     if (n == 0) return G4_OK;
     const int nt = g4_nmono(P->order_p);
     // node count bound: the handle's capacity (no host synchronisation here)
-    FmmLayout L = fmm_layout(t->cap, t->n_max, nt, workspace_bytes, P->fmm_p2p_per_particle);
+    const bool fp64 = P->precision == 1;
+    FmmLayout L = fmm_layout(t->cap, t->n_max, nt, workspace_bytes, P->fmm_p2p_per_particle,
+                             fp64 ? sizeof(double) : sizeof(float));
     if (L.dcap < 1024 || L.total > workspace_bytes)
         return g4_fail(G4_ERR_INVALID_ARG, "g4_gravity_fmm: workspace too small (%zu bytes)",
                        workspace_bytes);
@@ -157,9 +163,10 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     A.b_dfs = t->b_dfs;
     A.node = t->node;
     A.q = t->q;
+    A.qd = fp64 ? t->qd : nullptr;
     A.nq = g4_nq(P->order_p);
-    A.T_own = (float *)(w + L.T_own);
-    A.T_tot = (float *)(w + L.T_tot);
+    A.T_own = (void *)(w + L.T_own);
+    A.T_tot = (void *)(w + L.T_tot);
     A.Doff = (int32_t *)(w + L.Doff);
     A.Dlen = (int32_t *)(w + L.Dlen);
     A.m2l_own = (uint32_t *)(w + L.m2l_own);
@@ -221,11 +228,15 @@ extern "C" g4_status g4_gravity_fmm(g4_tree t, const uint32_t *pos_sorted, const
     if (cudaMemsetAsync(A.p2p_fill, 0, 16, st) != cudaSuccess)
         return g4_cuda_check(cudaGetLastError(), "g4_gravity_fmm: clear P2P counters");
     const bool geom = P->criterion == 1;
-    switch (P->order_p) {
-    case 2: dispatch_fmm<2>(A, treepm, geom, st); break;
-    case 3: dispatch_fmm<3>(A, treepm, geom, st); break;
-    case 4: dispatch_fmm<4>(A, treepm, geom, st); break;
-    default: dispatch_fmm<5>(A, treepm, geom, st); break;
+    if (fp64) {
+        dispatch_fmm<4, double>(A, treepm, geom, st);
+    } else {
+        switch (P->order_p) {
+        case 2: dispatch_fmm<2, float>(A, treepm, geom, st); break;
+        case 3: dispatch_fmm<3, float>(A, treepm, geom, st); break;
+        case 4: dispatch_fmm<4, float>(A, treepm, geom, st); break;
+        default: dispatch_fmm<5, float>(A, treepm, geom, st); break;
+        }
     }
     if (momentum_out) k_momentum<<<g4_num_sms() * 4, 256, 0, st>>>(mass_sorted, acc, n, momentum_out);
     return g4_launch_check("fmm", 3 + 2 * (G4_MAXLEVEL + 1) + (momentum_out ? 1 : 0));

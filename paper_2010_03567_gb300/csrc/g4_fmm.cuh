@@ -75,13 +75,20 @@ __device__ __forceinline__ PCell load_pcell(const FmmArgs &A, int j)
 // the separation's own nearest image keeps the two directions of a pair mirror images
 // (centres exactly half a box apart get the same image sign from both sides), so both take
 // the same decision.  Without a cutoff only: within r_cut it changes nothing.
-__device__ __forceinline__ void periodic_wrap(const FmmArgs &A, float &rx, float &ry, float &rz)
+template <typename R>
+__device__ __forceinline__ void periodic_wrap(const FmmArgs &A, R &rx, R &ry, R &rz)
 {
     if (!A.periodic) return;
-    const float L = (float)A.box;
-    rx -= L * rintf(rx / L);
-    ry -= L * rintf(ry / L);
-    rz -= L * rintf(rz / L);
+    const R L = (R)A.box;
+    rx -= L * rint(rx / L);
+    ry -= L * rint(ry / L);
+    rz -= L * rint(rz / L);
+}
+
+// FP64 node data of node d (precision 1): centre-of-mass offset [0..2], mass [3], moments [4..]
+__device__ __forceinline__ const double *node_fp64(const FmmArgs &A, int d)
+{
+    return A.qd + (size_t)d * (4 + A.nq);
 }
 
 // decision for the node pair (A <- B), identical to the symmetric rule of the dual walk
@@ -184,53 +191,61 @@ __device__ __forceinline__ int fmm_decide_pn(const FmmArgs &A, const G4Node &nz,
 
 // g_0..g_P of the interaction kernel: the softened one (h = 2.8 eps_ij) inside h when the
 // rule of Sec. 2.7 is in force (hs = h), the unsoftened one otherwise (hs = 0)
-template <int P, bool TREEPM>
-__device__ __forceinline__ void fmm_gn(const FmmArgs &A, float r2, float hs, float *g)
+template <int P, bool TREEPM, typename R>
+__device__ __forceinline__ void fmm_gn(const FmmArgs &A, R r2, R hs, R *g)
 {
-    if (hs > 0.f && r2 < hs * hs) gn_soft<P, float, TREEPM>(r2, hs, (float)A.as, g);
-    else gn_kernel<P, float, TREEPM>(r2, (float)A.as, g);
+    if (hs > R(0) && r2 < hs * hs) gn_soft<P, R, TREEPM>(r2, hs, (R)A.as, g);
+    else gn_kernel<P, R, TREEPM>(r2, (R)A.as, g);
 }
 
 // lane-private M2L: T += field of node B at A's centre of mass (r = s_B - s_A)
 // Pure periodic FMM (Sec. 2.2.4): the separation moved to its image in the primary cell (the
 // periodic kernel 1/r - psi is the same at every image), and the correction tensors D_n[psi]
 // subtracted from the Newtonian ones there.
-__device__ __forceinline__ void ewald_wrap(const FmmArgs &A, float &rx, float &ry, float &rz)
+template <typename R>
+__device__ __forceinline__ void ewald_wrap(const FmmArgs &A, R &rx, R &ry, R &rz)
 {
     if (!A.ewald) return;
-    const float L = (float)A.box;
-    rx -= L * rintf(rx / L);
-    ry -= L * rintf(ry / L);
-    rz -= L * rintf(rz / L);
+    const R L = (R)A.box;
+    rx -= L * rint(rx / L);
+    ry -= L * rint(ry / L);
+    rz -= L * rint(rz / L);
 }
-template <int P>
-__device__ __forceinline__ void ewald_sub(const FmmArgs &A, float rx, float ry, float rz, float *D)
+template <int P, typename R>
+__device__ __forceinline__ void ewald_sub(const FmmArgs &A, R rx, R ry, R rz, R *D)
 {
     if (!A.ewald) return;
-    float Dp[g4_nmono(P)];
-    ewald_dpsi<P, float>(A.ew, rx, ry, rz, Dp);
+    R Dp[g4_nmono(P)];
+    ewald_dpsi<P, R>(A.ew, rx, ry, rz, Dp);
 #pragma unroll
     for (int k = 0; k < g4_nmono(P); k++) D[k] -= Dp[k];
 }
 
-template <int P, bool TREEPM>
-__device__ __forceinline__ void m2l_add(const FmmArgs &A, float *T, int db, const G4Node &nb,
-                                        float rx, float ry, float rz, float hs)
+template <int P, bool TREEPM, typename R>
+__device__ __forceinline__ void m2l_add(const FmmArgs &A, R *T, int db, const G4Node &nb,
+                                        R rx, R ry, R rz, R hs)
 {
     constexpr int NT = FT<P>::NT;
     if (!TREEPM) ewald_wrap(A, rx, ry, rz);
-    const float r2 = rx * rx + ry * ry + rz * rz;
-    float g[P + 1];
+    const R r2 = rx * rx + ry * ry + rz * rz;
+    R g[P + 1];
     fmm_gn<P, TREEPM>(A, r2, hs, g);
-    float D[NT];
-    dtensors<P, float>(rx, ry, rz, g, D);
+    R D[NT];
+    dtensors<P, R>(rx, ry, rz, g, D);
     if (!TREEPM) ewald_sub<P>(A, rx, ry, rz, D);
-    float Q[NT];
-    Q[0] = nb.mass;
-    const float *qq = A.q + (size_t)db * A.nq;
+    R Q[NT];
+    if (sizeof(R) == 8) {
+        const double *dd = node_fp64(A, db);
+        Q[0] = (R)dd[3];
 #pragma unroll
-    for (int k = 4; k < NT; k++) Q[k] = __ldg(qq + k - 4);
-    const float mG = -(float)A.G;
+        for (int k = 4; k < NT; k++) Q[k] = (R)dd[k];
+    } else {
+        Q[0] = nb.mass;
+        const float *qq = A.q + (size_t)db * A.nq;
+#pragma unroll
+        for (int k = 4; k < NT; k++) Q[k] = __ldg(qq + k - 4);
+    }
+    const R mG = -(R)A.G;
 #pragma unroll
     for (int kn = 0; kn <= P; kn++)
 #pragma unroll
@@ -238,7 +253,7 @@ __device__ __forceinline__ void m2l_add(const FmmArgs &A, float *T, int db, cons
 #pragma unroll
             for (int kc = 0; kc <= kbc; kc++) {
                 const int ka = kn - kbc, kb = kbc - kc;
-                float s = Q[0] * D[g4_midx(ka, kb, kc)];
+                R s = Q[0] * D[g4_midx(ka, kb, kc)];
 #pragma unroll
                 for (int nn = 2; nn <= P - kn; nn++) {
                     if (nn == P && !A.keep_qp) continue;   // Q_p only shifts the potential
@@ -248,7 +263,7 @@ __device__ __forceinline__ void m2l_add(const FmmArgs &A, float *T, int db, cons
                         for (int nc = 0; nc <= nbc; nc++) {
                             const int na_ = nn - nbc, nb_ = nbc - nc;
                             s += Q[g4_midx(na_, nb_, nc)] * D[g4_midx(ka + na_, kb + nb_, kc + nc)] *
-                                 (1.0f / (float)(fact(na_) * fact(nb_) * fact(nc)));
+                                 (R(1) / (R)(fact(na_) * fact(nb_) * fact(nc)));
                         }
                 }
                 T[g4_midx(ka, kb, kc)] += ((kn & 1) ? -mG : mG) * s;
@@ -257,19 +272,18 @@ __device__ __forceinline__ void m2l_add(const FmmArgs &A, float *T, int db, cons
 
 // lane-private P2L: T += field of a point mass m at A's centre of mass, r = x - s_A
 // (the M2L with Q_0 = m only): T_k += -G (-1)^|k| m D_k(r)
-template <int P, bool TREEPM>
-__device__ __forceinline__ void p2l_add(const FmmArgs &A, float *T, float m, float rx, float ry,
-                                        float rz, float hs)
+template <int P, bool TREEPM, typename R>
+__device__ __forceinline__ void p2l_add(const FmmArgs &A, R *T, R m, R rx, R ry, R rz, R hs)
 {
     constexpr int NT = FT<P>::NT;
     if (!TREEPM) ewald_wrap(A, rx, ry, rz);
-    const float r2 = rx * rx + ry * ry + rz * rz;
-    float g[P + 1];
+    const R r2 = rx * rx + ry * ry + rz * rz;
+    R g[P + 1];
     fmm_gn<P, TREEPM>(A, r2, hs, g);
-    float D[NT];
-    dtensors<P, float>(rx, ry, rz, g, D);
+    R D[NT];
+    dtensors<P, R>(rx, ry, rz, g, D);
     if (!TREEPM) ewald_sub<P>(A, rx, ry, rz, D);
-    const float mG = -(float)A.G * m;
+    const R mG = -(R)A.G * m;
 #pragma unroll
     for (int kn = 0; kn <= P; kn++)
 #pragma unroll
@@ -284,21 +298,21 @@ __device__ __forceinline__ void p2l_add(const FmmArgs &A, float *T, float m, flo
 // M2P: field of node Z at particle x, r = s_Z - x (the mutual expansion evaluated on a cell of
 // side 0): sacc += sum_{n<P} Q_n . D_{n+1} / n!,  spot += sum_{n<P} Q_n . D_n / n! (plus Q_P
 // when keep_qp); the caller multiplies both by -G.
-template <int P, bool TREEPM>
-__device__ __forceinline__ void m2p_add(const FmmArgs &A, int dz, const G4Node &nz, float x, float y,
-                                        float z, float hs, float &sx, float &sy, float &sz,
-                                        float &sp)
+template <int P, bool TREEPM, typename R>
+__device__ __forceinline__ void m2p_add(const FmmArgs &A, int dz, const G4Node &nz, R x, R y, R z,
+                                        R hs, R &sx, R &sy, R &sz, R &sp)
 {
     if (!TREEPM) ewald_wrap(A, x, y, z);
-    const float r2 = x * x + y * y + z * z;
-    float g[P + 1];
+    const R r2 = x * x + y * y + z * z;
+    R g[P + 1];
     fmm_gn<P, TREEPM>(A, r2, hs, g);
-    float D[g4_nmono(P)];
-    dtensors<P, float>(x, y, z, g, D);
+    R D[g4_nmono(P)];
+    dtensors<P, R>(x, y, z, g, D);
     if (!TREEPM) ewald_sub<P>(A, x, y, z, D);
-    const float M = nz.mass;
-    float ax = M * D[g4_midx(1, 0, 0)], ay = M * D[g4_midx(0, 1, 0)], az = M * D[g4_midx(0, 0, 1)];
-    float ph = M * D[0];
+    const double *dd = sizeof(R) == 8 ? node_fp64(A, dz) : nullptr;
+    const R M = sizeof(R) == 8 ? (R)dd[3] : (R)nz.mass;
+    R ax = M * D[g4_midx(1, 0, 0)], ay = M * D[g4_midx(0, 1, 0)], az = M * D[g4_midx(0, 0, 1)];
+    R ph = M * D[0];
     const float *qq = A.q + (size_t)dz * A.nq;
 #pragma unroll
     for (int n = 2; n <= P; n++)
@@ -307,8 +321,8 @@ __device__ __forceinline__ void m2p_add(const FmmArgs &A, int dz, const G4Node &
 #pragma unroll
             for (int c = 0; c <= bc; c++) {
                 const int a = n - bc, b = bc - c;
-                const float w = __ldg(qq + g4_midx(a, b, c) - 4) *
-                                (1.0f / (float)(fact(a) * fact(b) * fact(c)));
+                const R qn = sizeof(R) == 8 ? (R)dd[g4_midx(a, b, c)] : (R)__ldg(qq + g4_midx(a, b, c) - 4);
+                const R w = qn * (R(1) / (R)(fact(a) * fact(b) * fact(c)));
                 if (n <= P - 1) {
                     ph += w * D[g4_midx(a, b, c)];
                     ax += w * D[g4_midx(a + 1, b, c)];
@@ -330,7 +344,8 @@ __device__ __forceinline__ int warp_sum_i(int v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ float warp_sum_f(float v)
+template <typename R>
+__device__ __forceinline__ R warp_sum_f(R v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -352,10 +367,11 @@ __device__ __forceinline__ int warp_excl_i(int v, int lane)
 // FP16x2 candidate tests, exact evaluation of each lane's candidates; in integer-grid units
 // for TreePM), the results added to the sinks' outputs.  An entry with lane mask 0 reaches
 // every sink of A; any other entry only the lanes of sink chunk `ic`.
-template <bool TREEPM>
+template <bool TREEPM, typename R>
 __device__ void p2p_flush(const FmmArgs &A, PPSmem<FMM_P2PBUF> &S, const G4Node &na, const int4 *buf,
                           int nbuf, int ic, int lane)
 {
+    constexpr bool INTU = TREEPM && sizeof(R) == 4;   // FP32 TreePM: integer-grid units
     const double gscale = A.scale;
     const float fscale = (float)gscale, figs = A.figs;
     const int nA = na.count;
@@ -391,12 +407,12 @@ __device__ void p2p_flush(const FmmArgs &A, PPSmem<FMM_P2PBUF> &S, const G4Node 
                     zr = (float)(int32_t)(zi - gcz) * fscale;
         __syncwarp();
         const float hi = A.h_cls[A.cls ? A.cls[i] : 0];
-        float ax = 0.f, ay = 0.f, az = 0.f, ap = 0.f;
+        R ax = R(0), ay = R(0), az = R(0), ap = R(0);
         uint32_t npp = 0;
-        pp_flush<float, TREEPM>(A, S, nbuf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, vmask,
-                                TREEPM ? hi * figs : hi, ax, ay, az, ap, npp, gscale, figs, A.pf,
-                                A.rc2i, 0, 1);
-        if (TREEPM) {
+        pp_flush<R, TREEPM>(A, S, nbuf, lane, i, xi, yi, zi, gcx, gcy, gcz, xr, yr, zr, vmask,
+                            INTU ? (R)(hi * figs) : (R)hi, ax, ay, az, ap, npp, gscale, figs, A.pf,
+                            A.rc2i, 0, 1);
+        if (INTU) {
             const float ca = figs * figs;
             ax *= ca;
             ay *= ca;
@@ -404,11 +420,11 @@ __device__ void p2p_flush(const FmmArgs &A, PPSmem<FMM_P2PBUF> &S, const G4Node 
             ap *= figs;
         }
         if (valid) {
-            const float mG = -(float)A.G;
-            A.acc[i] += mG * ax;
-            A.acc[A.n + i] += mG * ay;
-            A.acc[2 * A.n + i] += mG * az;
-            if (A.pot) A.pot[i] += mG * ap;
+            const R mG = -(R)A.G;
+            A.acc[i] = (float)((R)A.acc[i] + mG * ax);
+            A.acc[A.n + i] = (float)((R)A.acc[A.n + i] + mG * ay);
+            A.acc[2 * A.n + i] = (float)((R)A.acc[2 * A.n + i] + mG * az);
+            if (A.pot) A.pot[i] = (float)((R)A.pot[i] + mG * ap);
             if (A.counts) A.counts[i] += npp;
         }
         __syncwarp();
@@ -448,7 +464,7 @@ __device__ bool defer_p2p(const FmmArgs &A, int da, const int4 *buf, int nbuf, i
 
 // Deferred particle pairs: one warp per sink leaf, its chunks in the order they were found;
 // the results are added to the sink particles' outputs (zeroed by the dual walk)
-template <bool TREEPM>
+template <bool TREEPM, typename R>
 __global__ void __launch_bounds__(FMM_THREADS, 5) k_fmm_p2p(const FmmArgs A)
 {
     __shared__ PPSmem<FMM_P2PBUF> s_pp[FMM_WARPS];
@@ -462,7 +478,7 @@ __global__ void __launch_bounds__(FMM_THREADS, 5) k_fmm_p2p(const FmmArgs A)
         const G4Node na = load_node(A.node + da);
         for (int c = A.p2p_head[da]; c >= 0;) {
             const int4 ch = A.p2p_chunk[c];
-            p2p_flush<TREEPM>(A, s_pp[wib], na, A.p2p_src + ch.x, ch.y, ch.w, lane);
+            p2p_flush<TREEPM, R>(A, s_pp[wib], na, A.p2p_src + ch.x, ch.y, ch.w, lane);
             c = ch.z;
         }
     }
@@ -479,7 +495,40 @@ struct LeafSmem {
     int2 stack[FMM_STACK];
 };
 
-template <int P, bool TREEPM, bool GEOM>
+// Separations for the expansions.  FP32: the ones the decisions computed.  FP64 (R = double):
+// recomputed from the integer centres and the FP64 centre-of-mass offsets.
+template <bool TREEPM, typename R>
+__device__ __forceinline__ void sep_nodes(const FmmArgs &A, const G4Node &na, int da, const G4Node &nb,
+                                          int db, float fx, float fy, float fz, R &rx, R &ry, R &rz)
+{
+    if (sizeof(R) == 4) {
+        rx = fx; ry = fy; rz = fz;
+        return;
+    }
+    const double *a = node_fp64(A, da), *b = node_fp64(A, db);
+    rx = (R)((double)(int32_t)(nb.cx - na.cx) * A.scale + (b[0] - a[0]));
+    ry = (R)((double)(int32_t)(nb.cy - na.cy) * A.scale + (b[1] - a[1]));
+    rz = (R)((double)(int32_t)(nb.cz - na.cz) * A.scale + (b[2] - a[2]));
+    if (!TREEPM) periodic_wrap(A, rx, ry, rz);
+}
+// s_Z - x for node Z and particle x (fx.. = the decision's FP32 separation)
+template <bool TREEPM, typename R>
+__device__ __forceinline__ void sep_node_particle(const FmmArgs &A, const G4Node &nz, int dz,
+                                                  const PCell &x, float fx, float fy, float fz,
+                                                  R &rx, R &ry, R &rz)
+{
+    if (sizeof(R) == 4) {
+        rx = fx; ry = fy; rz = fz;
+        return;
+    }
+    const double *z = node_fp64(A, dz);
+    rx = (R)((double)(int32_t)(nz.cx - x.x) * A.scale + z[0]);
+    ry = (R)((double)(int32_t)(nz.cy - x.y) * A.scale + z[1]);
+    rz = (R)((double)(int32_t)(nz.cz - x.z) * A.scale + z[2]);
+    if (!TREEPM) periodic_wrap(A, rx, ry, rz);
+}
+
+template <int P, bool TREEPM, bool GEOM, typename R>
 __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(const FmmArgs A, int level)
 {
     constexpr int NT = FT<P>::NT;
@@ -508,9 +557,9 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
             cand = Din + A.Doff[na.parent];
             ncand = A.Dlen[na.parent];
         }
-        float T[NT];
+        R T[NT];
 #pragma unroll
-        for (int k = 0; k < NT; k++) T[k] = 0.f;
+        for (int k = 0; k < NT; k++) T[k] = R(0);
         int nm2l = 0;
         if (!leafA) {
             // pass 1: size of the list passed down to the daughters (a particle chunk always
@@ -556,8 +605,10 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                             const PCell x = load_pcell(A, p0 + bit);
                             const int d = fmm_decide_pn<P, TREEPM, GEOM>(A, na, x, rx, ry, rz);
                             if (d == D_ACCEPT) {
-                                p2l_add<P, TREEPM>(A, T, x.m, -rx, -ry, -rz,
-                                                   A.soft_nodes ? fmaxf(na.hmax, x.h) : 0.f);
+                                R qx, qy, qz;
+                                sep_node_particle<TREEPM, R>(A, na, da, x, rx, ry, rz, qx, qy, qz);
+                                p2l_add<P, TREEPM, R>(A, T, (R)x.m, -qx, -qy, -qz,
+                                                      (R)(A.soft_nodes ? fmaxf(na.hmax, x.h) : 0.f));
                             } else if (d == D_OPEN) {
                                 keep |= 1u << bit;
                             }
@@ -571,8 +622,10 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                     }
                 }
                 if (dec == D_ACCEPT) {
-                    m2l_add<P, TREEPM>(A, T, ce.x, nb, rx, ry, rz,
-                                       A.soft_nodes ? fmaxf(na.hmax, nb.hmax) : 0.f);
+                    R qx, qy, qz;
+                    sep_nodes<TREEPM, R>(A, na, da, nb, ce.x, rx, ry, rz, qx, qy, qz);
+                    m2l_add<P, TREEPM, R>(A, T, ce.x, nb, qx, qy, qz,
+                                          (R)(A.soft_nodes ? fmaxf(na.hmax, nb.hmax) : 0.f));
                     nm2l++;
                 }
                 const int pre = warp_excl_i(e, lane);
@@ -610,9 +663,9 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                     // each particle's own periodic images: + G m_i psi(0) (pure periodic FMM)
                     float p0 = 0.f;
                     if (!TREEPM && A.ewald) {
-                        float D0[1];
-                        ewald_dpsi<0, float>(A.ew, 0.f, 0.f, 0.f, D0);
-                        p0 = (float)A.G * A.mass[i] * D0[0];
+                        R D0[1];
+                        ewald_dpsi<0, R>(A.ew, R(0), R(0), R(0), D0);
+                        p0 = (float)((R)A.G * (R)A.mass[i] * D0[0]);
                     }
                     A.pot[i] = p0;
                 }
@@ -630,7 +683,7 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                 const unsigned vmask = __ballot_sync(0xffffffffu, valid);
                 const int i = na.first + 32 * ic + (valid ? lane : 0);
                 const PCell xs = load_pcell(A, i);
-                float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
+                R bx = R(0), by = R(0), bz = R(0), bp = R(0);
                 uint32_t npn = 0;
                 int sp = 0, nbuf = 0;
                 // appends one particle-pair entry per lane that has one
@@ -641,7 +694,7 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                     if (nbuf + k > FMM_P2PBUF) {
                         __syncwarp();
                         if (!defer_p2p(A, da, L.pp, nbuf, ic, lane, tail))
-                            p2p_flush<TREEPM>(A, s_pp[wib], na, L.pp, nbuf, ic, lane);
+                            p2p_flush<TREEPM, R>(A, s_pp[wib], na, L.pp, nbuf, ic, lane);
                         nbuf = 0;
                     }
                     if (has) L.pp[nbuf + __popc(bm & lt)] = ent;
@@ -663,8 +716,10 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                         if (dec == D_OPEN && !(nb.meta & 32u)) e = nb.nchild;   // B internal
                     }
                     if (ic == 0 && dec == D_ACCEPT) {
-                        m2l_add<P, TREEPM>(A, T, ce.x, nb, rx, ry, rz,
-                                           A.soft_nodes ? fmaxf(na.hmax, nb.hmax) : 0.f);
+                        R qx, qy, qz;
+                        sep_nodes<TREEPM, R>(A, na, da, nb, ce.x, rx, ry, rz, qx, qy, qz);
+                        m2l_add<P, TREEPM, R>(A, T, ce.x, nb, qx, qy, qz,
+                                              (R)(A.soft_nodes ? fmaxf(na.hmax, nb.hmax) : 0.f));
                         nm2l++;
                     }
                     // leaf pairs (A itself, or a leaf B that fails): all of A's particles
@@ -696,9 +751,12 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                                 const PCell x = load_pcell(A, y);
                                 float qx, qy, qz;
                                 const int d = fmm_decide_pn<P, TREEPM, GEOM>(A, na, x, qx, qy, qz);
-                                if (d == D_ACCEPT)
-                                    p2l_add<P, TREEPM>(A, T, x.m, -qx, -qy, -qz,
-                                                       A.soft_nodes ? fmaxf(na.hmax, x.h) : 0.f);
+                                if (d == D_ACCEPT) {
+                                    R ux, uy, uz;
+                                    sep_node_particle<TREEPM, R>(A, na, da, x, qx, qy, qz, ux, uy, uz);
+                                    p2l_add<P, TREEPM, R>(A, T, (R)x.m, -ux, -uy, -uz,
+                                                          (R)(A.soft_nodes ? fmaxf(na.hmax, x.h) : 0.f));
+                                }
                                 op = d == D_OPEN;
                             }
                             push_pp(op, make_int4(y, 1, 0, 0));
@@ -717,9 +775,11 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                         if (((unsigned)se.y >> lane) & 1u)
                             d = fmm_decide_pn<P, TREEPM, GEOM>(A, nz, xs, qx, qy, qz);
                         if (d == D_ACCEPT) {
-                            m2p_add<P, TREEPM>(A, se.x, nz, qx, qy, qz,
-                                               A.soft_nodes ? fmaxf(nz.hmax, xs.h) : 0.f, bx, by,
-                                               bz, bp);
+                            R ux, uy, uz;
+                            sep_node_particle<TREEPM, R>(A, nz, se.x, xs, qx, qy, qz, ux, uy, uz);
+                            m2p_add<P, TREEPM, R>(A, se.x, nz, ux, uy, uz,
+                                                  (R)(A.soft_nodes ? fmaxf(nz.hmax, xs.h) : 0.f), bx,
+                                                  by, bz, bp);
                             npn++;
                         }
                         const unsigned om = __ballot_sync(0xffffffffu, d == D_OPEN);
@@ -739,13 +799,13 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
                     }
                 }
                 if (nbuf > 0 && !defer_p2p(A, da, L.pp, nbuf, ic, lane, tail))
-                    p2p_flush<TREEPM>(A, s_pp[wib], na, L.pp, nbuf, ic, lane);
+                    p2p_flush<TREEPM, R>(A, s_pp[wib], na, L.pp, nbuf, ic, lane);
                 if (valid) {
-                    const float mG = -(float)A.G;
-                    A.acc[i] += mG * bx;
-                    A.acc[A.n + i] += mG * by;
-                    A.acc[2 * A.n + i] += mG * bz;
-                    if (A.pot) A.pot[i] += mG * bp;
+                    const R mG = -(R)A.G;
+                    A.acc[i] = (float)((R)A.acc[i] + mG * bx);
+                    A.acc[A.n + i] = (float)((R)A.acc[A.n + i] + mG * by);
+                    A.acc[2 * A.n + i] = (float)((R)A.acc[2 * A.n + i] + mG * bz);
+                    if (A.pot) A.pot[i] = (float)((R)A.pot[i] + mG * bp);
                     if (A.counts) A.counts[A.n + i] = npn;
                 }
                 __syncwarp();
@@ -754,8 +814,8 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
         // reduce the lane-private fields and store the node's own field
 #pragma unroll
         for (int k = 0; k < NT; k++) {
-            const float v = warp_sum_f(T[k]);
-            if (lane == 0) A.T_own[(size_t)da * NT + k] = v;
+            const R v = warp_sum_f(T[k]);
+            if (lane == 0) ((R *)A.T_own)[(size_t)da * NT + k] = v;
         }
         nm2l = warp_sum_i(nm2l);
         if (lane == 0) A.m2l_own[da] = (uint32_t)nm2l;
@@ -763,7 +823,7 @@ __global__ void __launch_bounds__(FMM_THREADS, G4_FMM_MIN_BLOCKS) k_fmm_level(co
 }
 
 // downward pass: T_tot = T_own + shifted parent field (L2L); leaves evaluate at particles (L2P)
-template <int P>
+template <int P, typename R>
 __global__ void __launch_bounds__(128) k_fmm_down(const FmmArgs A, int level)
 {
     constexpr int NT = FT<P>::NT;
@@ -771,29 +831,42 @@ __global__ void __launch_bounds__(128) k_fmm_down(const FmmArgs A, int level)
     const int32_t *off = A.lvl, *cnt = A.lvl + G4_NLEVELS + 1;
     const int o = off[level], c = cnt[level];
     const int total_nodes = off[G4_NLEVELS];
-    const float scale = (float)A.scale;
+    const R scale = (R)A.scale;
+    const R *Town = (const R *)A.T_own;
+    R *Ttot = (R *)A.T_tot;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < c; b += gridDim.x * blockDim.x) {
         const int d = A.b_dfs[o + b];
         if ((unsigned)d >= (unsigned)total_nodes) continue;
         const G4Node nd = load_node(A.node + d);
-        float T[NT];
+        // centre-of-mass offset (FP64 node data in the FP64 mode)
+        R ndx = nd.sx, ndy = nd.sy, ndz = nd.sz;
+        if (sizeof(R) == 8) {
+            const double *dd = node_fp64(A, d);
+            ndx = (R)dd[0]; ndy = (R)dd[1]; ndz = (R)dd[2];
+        }
+        R T[NT];
 #pragma unroll
-        for (int k = 0; k < NT; k++) T[k] = A.T_own[(size_t)d * NT + k];
+        for (int k = 0; k < NT; k++) T[k] = Town[(size_t)d * NT + k];
         uint32_t cum = A.m2l_own[d];
         if (nd.parent >= 0) {
             const G4Node np = load_node(A.node + nd.parent);
-            const float dx = (float)(int32_t)(nd.cx - np.cx) * scale + (nd.sx - np.sx);
-            const float dy = (float)(int32_t)(nd.cy - np.cy) * scale + (nd.sy - np.sy);
-            const float dz = (float)(int32_t)(nd.cz - np.cz) * scale + (nd.sz - np.sz);
-            float px[P + 1], py[P + 1], pz[P + 1];
-            px[0] = py[0] = pz[0] = 1.f;
+            R npx = np.sx, npy = np.sy, npz = np.sz;
+            if (sizeof(R) == 8) {
+                const double *dp = node_fp64(A, nd.parent);
+                npx = (R)dp[0]; npy = (R)dp[1]; npz = (R)dp[2];
+            }
+            const R dx = (R)(int32_t)(nd.cx - np.cx) * scale + (ndx - npx);
+            const R dy = (R)(int32_t)(nd.cy - np.cy) * scale + (ndy - npy);
+            const R dz = (R)(int32_t)(nd.cz - np.cz) * scale + (ndz - npz);
+            R px[P + 1], py[P + 1], pz[P + 1];
+            px[0] = py[0] = pz[0] = R(1);
 #pragma unroll
             for (int k = 1; k <= P; k++) {
                 px[k] = px[k - 1] * dx;
                 py[k] = py[k - 1] * dy;
                 pz[k] = pz[k - 1] * dz;
             }
-            const float *Tp = A.T_tot + (size_t)nd.parent * NT;
+            const R *Tp = Ttot + (size_t)nd.parent * NT;
 #pragma unroll
             for (int kn = 0; kn <= P; kn++)
 #pragma unroll
@@ -801,7 +874,7 @@ __global__ void __launch_bounds__(128) k_fmm_down(const FmmArgs A, int level)
 #pragma unroll
                     for (int kc = 0; kc <= kbc; kc++) {
                         const int ka = kn - kbc, kb = kbc - kc;
-                        float s = 0.f;
+                        R s = R(0);
 #pragma unroll
                         for (int mn = 0; mn <= P - kn; mn++)
 #pragma unroll
@@ -810,29 +883,29 @@ __global__ void __launch_bounds__(128) k_fmm_down(const FmmArgs A, int level)
                                 for (int mc = 0; mc <= mbc; mc++) {
                                     const int ma = mn - mbc, mb = mbc - mc;
                                     s += Tp[g4_midx(ka + ma, kb + mb, kc + mc)] * px[ma] * py[mb] *
-                                         pz[mc] * (1.0f / (float)(fact(ma) * fact(mb) * fact(mc)));
+                                         pz[mc] * (R(1) / (R)(fact(ma) * fact(mb) * fact(mc)));
                                 }
                         T[g4_midx(ka, kb, kc)] += s;
                     }
             cum += A.m2l_cum[nd.parent];
         }
 #pragma unroll
-        for (int k = 0; k < NT; k++) A.T_tot[(size_t)d * NT + k] = T[k];
+        for (int k = 0; k < NT; k++) Ttot[(size_t)d * NT + k] = T[k];
         A.m2l_cum[d] = cum;
         if (nd.meta & 32u) {
             for (int i = nd.first; i < nd.first + nd.count; i++) {
-                const float ax = (float)(int32_t)(A.pos[i] - nd.cx) * scale - nd.sx;
-                const float ay = (float)(int32_t)(A.pos[A.n + i] - nd.cy) * scale - nd.sy;
-                const float az = (float)(int32_t)(A.pos[2 * A.n + i] - nd.cz) * scale - nd.sz;
-                float px[P + 1], py[P + 1], pz[P + 1];
-                px[0] = py[0] = pz[0] = 1.f;
+                const R ax = (R)(int32_t)(A.pos[i] - nd.cx) * scale - ndx;
+                const R ay = (R)(int32_t)(A.pos[A.n + i] - nd.cy) * scale - ndy;
+                const R az = (R)(int32_t)(A.pos[2 * A.n + i] - nd.cz) * scale - ndz;
+                R px[P + 1], py[P + 1], pz[P + 1];
+                px[0] = py[0] = pz[0] = R(1);
 #pragma unroll
                 for (int k = 1; k <= P; k++) {
                     px[k] = px[k - 1] * ax;
                     py[k] = py[k - 1] * ay;
                     pz[k] = pz[k - 1] * az;
                 }
-                float phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                R phi = R(0), gx = R(0), gy = R(0), gz = R(0);
 #pragma unroll
                 for (int kn = 0; kn <= P; kn++)
 #pragma unroll
@@ -840,8 +913,8 @@ __global__ void __launch_bounds__(128) k_fmm_down(const FmmArgs A, int level)
 #pragma unroll
                         for (int kc = 0; kc <= kbc; kc++) {
                             const int ka = kn - kbc, kb = kbc - kc;
-                            const float w = px[ka] * py[kb] * pz[kc] *
-                                            (1.0f / (float)(fact(ka) * fact(kb) * fact(kc)));
+                            const R w = px[ka] * py[kb] * pz[kc] *
+                                        (R(1) / (R)(fact(ka) * fact(kb) * fact(kc)));
                             phi += T[g4_midx(ka, kb, kc)] * w;
                             if (kn < P) {
                                 gx += T[g4_midx(ka + 1, kb, kc)] * w;
@@ -849,17 +922,17 @@ __global__ void __launch_bounds__(128) k_fmm_down(const FmmArgs A, int level)
                                 gz += T[g4_midx(ka, kb, kc + 1)] * w;
                             }
                         }
-                A.acc[i] -= gx;
-                A.acc[A.n + i] -= gy;
-                A.acc[2 * A.n + i] -= gz;
-                if (A.pot) A.pot[i] += phi;
+                A.acc[i] = (float)((R)A.acc[i] - gx);
+                A.acc[A.n + i] = (float)((R)A.acc[A.n + i] - gy);
+                A.acc[2 * A.n + i] = (float)((R)A.acc[2 * A.n + i] - gz);
+                if (A.pot) A.pot[i] = (float)((R)A.pot[i] + phi);
                 if (A.counts) A.counts[2 * A.n + i] = cum;
             }
         }
     }
 }
 
-template <int P, bool TREEPM, bool GEOM>
+template <int P, bool TREEPM, bool GEOM, typename R>
 void run_fmm(const FmmArgs &A, cudaStream_t st)
 {
     const int nb = g4_num_sms() * 8;
@@ -868,19 +941,19 @@ void run_fmm(const FmmArgs &A, cudaStream_t st)
             // the list of level l-2 is no longer needed: its buffer is reused at level l
             cudaMemsetAsync(A.dcount + (l & 1), 0, sizeof(int32_t), st);
         }
-        k_fmm_level<P, TREEPM, GEOM><<<nb, FMM_THREADS, 0, st>>>(A, l);
+        k_fmm_level<P, TREEPM, GEOM, R><<<nb, FMM_THREADS, 0, st>>>(A, l);
     }
-    k_fmm_p2p<TREEPM><<<g4_num_sms() * 5, FMM_THREADS, 0, st>>>(A);
-    for (int l = 0; l <= G4_MAXLEVEL; l++) k_fmm_down<P><<<nb, 128, 0, st>>>(A, l);
+    k_fmm_p2p<TREEPM, R><<<g4_num_sms() * 5, FMM_THREADS, 0, st>>>(A);
+    for (int l = 0; l <= G4_MAXLEVEL; l++) k_fmm_down<P, R><<<nb, 128, 0, st>>>(A, l);
 }
 
 }  // namespace
 
 // The variant's launches: the dual walk level by level, the deferred particle pairs, the
 // downward pass.
-template <int P, bool TREEPM>
+template <int P, bool TREEPM, typename R>
 void g4fmm::run_variant(const FmmArgs &A, bool geom, cudaStream_t st)
 {
-    if (geom) run_fmm<P, TREEPM, true>(A, st);
-    else run_fmm<P, TREEPM, false>(A, st);
+    if (geom) run_fmm<P, TREEPM, true, R>(A, st);
+    else run_fmm<P, TREEPM, false, R>(A, st);
 }

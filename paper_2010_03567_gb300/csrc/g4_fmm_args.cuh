@@ -27,8 +27,10 @@ struct FmmArgs {
     const G4Node *node;
     const int32_t *kids;       // per depth-first node: its daughters' depth-first indices (8)
     const float *q;
+    const double *qd;          // FP64 node data (precision 1): (4 + nq) doubles per node --
+                               // centre-of-mass offset, mass, the moments of q
     int nq;
-    float *T_own, *T_tot;
+    void *T_own, *T_tot;       // field tensors, float or double (the interaction type)
     int2 *D0, *D1;             // pass-down candidate lists, by level parity: (node, 0) or
                                // (-(first particle) - 1, particle mask)
     int64_t dcap;
@@ -61,7 +63,9 @@ struct FmmArgs {
     int64_t p2p_cap, chunk_cap;
 };
 
-// one (order, TreePM) variant of the dual walk, defined in g4_fmm_variant.cu
-template <int P, bool TREEPM> void run_variant(const FmmArgs &A, bool geom, cudaStream_t st);
+// one (order, TreePM, interaction type) variant of the dual walk, defined in
+// g4_fmm_variant.cu; R = double is the FP64 reference mode (decisions as in FP32, every
+// expansion, field and particle pair in FP64 from the FP64 node data)
+template <int P, bool TREEPM, typename R> void run_variant(const FmmArgs &A, bool geom, cudaStream_t st);
 
 }  // namespace g4fmm

@@ -131,6 +131,57 @@ def test_fmm_parity_treepm_box_bench_leaf():
     assert rel < 1e-5, rel
 
 
+@pytest.mark.parametrize("case", ["plummer", "treepm_box"])
+def test_fmm_fp64_mode(case):
+    """The FP64 reference mode (precision 1: FP64 node data, expansions, fields and particle
+    pairs; decisions as in FP32): the same interactions as the oracle's FP64 FMM for >= 99% of
+    the particles, and there agreement to the FP32 rounding of the outputs; closer to the
+    oracle than the FP32 mode; momentum conserved to the outputs' rounding."""
+    if case == "plummer":
+        ps, q, box, aold, _ = _plummer(6000)
+        kw = dict(alpha=0.0025, order_p=4)
+        OP = oracle_params(ps, box, **kw)
+        leaf = 8
+    else:
+        L = 24 * 1.953125
+        ps = synth.zeldovich(24, L, 2.0, 1023)
+        q, box = int_coords(ps)
+        kw = dict(alpha=0.0025, order_p=4, r_s=1.25 * L / 48, r_cut_factor=4.5, leaf_max=32)
+        OP = oracle_params(ps, box, **kw)
+        ad, _ = oracle.direct(q, ps.mass, None, np.arange(ps.n), OP, r_max=OP.r_cut)
+        aold = np.linalg.norm(ad, axis=1).astype(np.float32)
+        leaf = 32
+    ao, po, co, pc = oracle_fmm(ps, q, OP, aold.astype(np.float64), leaf=leaf)
+    a32, _, c32, _ = gpu_fmm(ps, q, gpu_params(g4, ps, box, **kw), aold)
+    a64, p64, c64, mom = gpu_fmm(ps, q, gpu_params(g4, ps, box, precision=1, **kw), aold)
+    # FP32 decisions in both modes (on node records rounded from FP64 moments in this mode)
+    assert np.mean(np.all(c64 == c32, axis=1)) >= 0.999
+    assert same_counts(c64, pc)
+    same = (c64[:, 0] == pc[:, 0]) & (c64[:, 1] == pc[:, 1])
+    e64, e32 = relerr(a64, ao), relerr(a32, ao)
+    assert np.percentile(e64[same], 99) < 5e-7, np.percentile(e64[same], [50, 99, 100])
+    assert np.percentile(e64[same], 99) < 0.5 * np.percentile(e32[same], 99)
+    assert np.percentile(np.abs(p64 - po)[same] / np.abs(po[same]), 99) < 5e-7
+    rel = np.linalg.norm(mom) / np.sum(ps.mass * np.linalg.norm(a64, axis=1))
+    assert rel < 1e-6, rel
+
+
+def test_fmm_fp64_mode_needs_order4_and_fp64_moments():
+    ps, q, box, aold, _ = _plummer(2000)
+    tg = g4.TreeGravity(ps.n, gpu_params(g4, ps, box, alpha=0.0025, order_p=3))
+    P3 = gpu_params(g4, ps, box, alpha=0.0025, order_p=3, precision=1)
+    tg.prepare(u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32), None,
+               to_dev(torch, aold, torch.float32), P3)
+    with pytest.raises(g4.G4Error, match="order_p 4"):
+        tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, tg.aold_s, P3)
+    P4 = gpu_params(g4, ps, box, alpha=0.0025, order_p=4)
+    tg.prepare(u32_dev(torch, q), to_dev(torch, ps.mass, torch.float32), None,
+               to_dev(torch, aold, torch.float32), P4)           # FP32 multipoles only
+    P4d = gpu_params(g4, ps, box, alpha=0.0025, order_p=4, precision=1)
+    with pytest.raises(g4.G4Error, match="FP64 multipoles"):
+        tg.tree.gravity_fmm(tg.pos_s, tg.mass_s, None, tg.aold_s, P4d)
+
+
 def test_fmm_alpha0_is_direct_sum():
     ps, q, box, aold, ad = _plummer(3000)
     kw = dict(alpha=0.0, order_p=4)
