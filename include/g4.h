@@ -165,13 +165,12 @@ g4_status g4_keys_sort(const uint32_t *pos_int, int64_t n, uint64_t *keys_sorted
 /* Same result as g4_keys_sort, but allocation-free: the scratch memory is a fixed array inside
  * the library (about 16 MB of device memory on every GPU that loads libg4, held until the
  * process exits) instead of a caller workspace.  The paper has no counterpart; this entry
- * point exists for callers that cannot allocate device memory when they sort -- code running
- * during CUDA-graph capture, applications whose device memory belongs to another allocator,
- * plugins handed pointers but no allocator.  It calls no cudaMalloc/cudaFree.
+ * point exists for callers that cannot allocate device memory when they sort -- applications
+ * whose device memory belongs to another allocator, plugins handed pointers but no
+ * allocator.  It calls no cudaMalloc/cudaFree.
  *   - n is limited to 2^20 (1048576); larger n returns G4_ERR_INVALID_ARG with a message.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- *     with that device current) and caches it; make that first call before any stream
- *     capture.
+ *     with that device current) and caches it.
  *   - All calls share the array: calls that overlap on the GPU (other streams or threads)
  *     race on it and must be serialised.  Each call overwrites every scratch word it reads,
  *     so nothing needs clearing between calls.

@@ -510,8 +510,7 @@ g4_status g4_sort_pairs_u64(const uint64_t *keys_in, uint64_t *keys_out, int32_t
     p += align256(sizeof(uint32_t) * 256 * (size_t)ntiles);
     uint32_t *tot = (uint32_t *)p;
     // opt in to the tile's dynamic shared memory once per device (flags per device, set
-    // atomically, so that threads and devices do not repeat the call -- in particular not
-    // during a later stream capture)
+    // atomically, so that threads and devices do not repeat the call)
     static int smem_set[64] = {0};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
@@ -706,10 +705,10 @@ extern "C" g4_status g4_scatter(const int32_t *perm, int64_t n, const float *acc
 // -------------------------------------------------------------------------------------------
 // Allocation-free variant of g4_keys_sort.
 //
-// Some callers cannot allocate device memory at the time they need the sort: code running
-// while a CUDA graph is being captured, host applications whose device memory is owned by
-// another allocator (a pre-reserved arena) and that forbid cudaMalloc after start-up, and
-// plugins that are handed device pointers but no allocator.  This entry point takes its
+// Some callers cannot allocate device memory at the time they need the sort: host
+// applications whose device memory is owned by another allocator (a pre-reserved arena) and
+// that forbid cudaMalloc after start-up, and plugins that are handed device pointers but no
+// allocator.  This entry point takes its
 // scratch from a fixed file-scope device array instead of a caller-provided workspace.
 //
 // The array is part of the library image: every GPU that loads libg4 holds it (about 16 MB)

@@ -1,7 +1,7 @@
 """The allocation-free key sort (g4_keys_sort_noalloc) against the workspace version.
 
-Some callers cannot allocate device memory when they sort (for example code running during
-CUDA-graph capture, or an application whose device memory belongs to another allocator).
+Some callers cannot allocate device memory when they sort (for example an application whose
+device memory belongs to another allocator).
 The allocation-free entry point keeps its scratch in a fixed array inside the library.  This
 test calls it through the C ABI twice in a row -- the second call reuses the scratch left by
 the first -- and checks that keys and permutation are bit-identical to g4_keys_sort (the
