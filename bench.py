@@ -54,10 +54,10 @@ def fp32_peak_tflops():
 
 
 # DRAM bytes (read + write) of one k_walk launch of the headline workload: the single-pass ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed walk, 761,592,320 +
-# 762,985,984 bytes.  Reported as roofline.traffic for the default workload only; set to
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed walk, 762,177,280 +
+# 763,437,056 bytes.  Reported as roofline.traffic for the default workload only; set to
 # None whenever the walk kernel changes until it is captured again.
-WALK_DRAM_BYTES_256 = 1524578304
+WALK_DRAM_BYTES_256 = 1525614336
 
 
 def hbm_peak_gbs():

@@ -97,6 +97,12 @@ typedef struct g4_params {
                               cells, FP64 from the Ewald sums, built in the handle on first
                               use) by third-order Taylor expansion about the nearest cell
                               centre.  0: nearest images only. */
+    long long watchdog_cycles; /* tree walk work-queue watchdog: 0 none; > 0: a warp takes no
+                              further work once it has run that many SM clock cycles, the
+                              walk's results are then incomplete and g4_tree_status reports
+                              G4_ERR_TIMEOUT (until the next g4_tree_build clears the flags).
+                              A bounded run time for callers that must not wait on a
+                              runaway walk; nothing spins, the kernel ends normally. */
 } g4_params;
 
 typedef struct g4_tree_s *g4_tree;

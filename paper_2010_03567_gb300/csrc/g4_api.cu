@@ -84,5 +84,6 @@ extern "C" g4_status g4_params_default(g4_params *p)
     p->fmm_p2p_per_particle = 0;
     p->soft_nodes = 0;
     p->ewald = 0;
+    p->watchdog_cycles = 0;
     return G4_OK;
 }

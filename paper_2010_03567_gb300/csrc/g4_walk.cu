@@ -52,6 +52,7 @@ struct WalkArgs {
     int n_sys;
     const int32_t *group_order;   // optional schedule (longest predicted cost first)
     const int32_t *operm;         // optional output order: acc/pot of sorted sink i go to operm[i]
+    long long watchdog;           // > 0: a warp stops taking work after this many SM cycles
     const int4 *items;            // optional work items (first sink, count, part | parts << 8,
     const int32_t *n_items;       //   split slot); their number on the device
     int gs;                       // sinks per group (8, 16 or 32)
@@ -625,9 +626,17 @@ k_walk(const WalkArgs A)
             }
         }
     };
+    const long long t_start = clock64();
     for (;;) {
         int g = 0;
-        if (lane == 0) g = atomicAdd(A.work, uni ? UNION_G : 1);
+        if (lane == 0) {
+            if (A.watchdog > 0 && clock64() - t_start > A.watchdog) {
+                atomicOr(A.flags, G4_FLAG_TIMEOUT);   // reported by g4_tree_status
+                g = ngroups;
+            } else {
+                g = atomicAdd(A.work, uni ? UNION_G : 1);
+            }
+        }
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
         int ng = 1, ul_n = -1;
@@ -821,6 +830,8 @@ g4_status g4_check_params(const g4_params *P, const char *who)
         return g4_fail(G4_ERR_INVALID_ARG, "%s: group_size=%d (8, 16 or 32)", who, P->group_size);
     if (P->ewald && (!P->periodic || P->r_s > 0.0 || P->order_p > 5))
         return g4_fail(G4_ERR_INVALID_ARG, "%s: the Ewald correction needs periodic=1, r_s=0", who);
+    if (P->watchdog_cycles < 0)
+        return g4_fail(G4_ERR_INVALID_ARG, "%s: watchdog_cycles=%lld", who, P->watchdog_cycles);
     return G4_OK;
 }
 
@@ -882,6 +893,7 @@ static g4_status gravity_tree(g4_tree t, const uint32_t *pos_sorted, const float
     A.pot = pot;
     A.counts = counts;
     A.operm = out_perm;
+    A.watchdog = P->watchdog_cycles;
     A.work = t->d_flags + 1;
     A.flags = t->d_flags;
     A.sys_first = t->sys_first;

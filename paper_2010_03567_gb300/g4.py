@@ -34,7 +34,7 @@ class G4Params(C.Structure):
                 ("G", C.c_double), ("n_eps_classes", C.c_int),
                 ("eps_table", C.c_double * MAX_EPS), ("group_size", C.c_int),
                 ("fp64_count", C.c_int), ("keep_qp", C.c_int), ("fmm_p2p_per_particle", C.c_int),
-                ("soft_nodes", C.c_int), ("ewald", C.c_int)]
+                ("soft_nodes", C.c_int), ("ewald", C.c_int), ("watchdog_cycles", C.c_int64)]
 
     def copy(self) -> "G4Params":
         p = G4Params()

@@ -48,3 +48,36 @@ def test_state_and_argument_errors():
         t.gravity_tree(pos, m, None, m, g4.params())
     with pytest.raises(g4.G4Error, match="status 1"):      # order out of range
         t.gravity_tree(pos, m, None, m, g4.params(order_p=9))
+
+
+def test_walk_watchdog_times_out_cleanly():
+    """The tree walk's work-queue watchdog (watchdog_cycles): with a budget of one SM clock cycle
+    every warp stops taking groups, the call ends normally and g4_tree_status reports
+    G4_ERR_TIMEOUT; the next build clears the flag and the same handle then walks every group
+    (results equal to a walk on a fresh handle).  No spin, no trap: the device keeps working."""
+    ps = synth.plummer(20000, 7)
+    pos = torch.from_numpy(ps.pos).cuda()
+    q, frame = g4.g4_int_coords(pos, False)
+    mass = torch.from_numpy(ps.mass.astype(np.float32)).cuda()
+    P = g4.params(box_size=float(frame[3].item()), eps=[0.01], criterion=1, theta=0.5)
+    Pw = g4.params(box_size=float(frame[3].item()), eps=[0.01], criterion=1, theta=0.5,
+                   watchdog_cycles=1)
+    tg = g4.TreeGravity(ps.n, P)
+    tg.prepare(q, mass, None, None, P)
+    tg.walk(Pw, use_aold=False)
+    with pytest.raises(g4.G4Error, match="status 4"):      # G4_ERR_TIMEOUT
+        tg.tree.status()
+    # not every sink was reached: the groups no warp took still carry no interactions
+    cnt = tg.counts.to(torch.int64).sum(dim=0)
+    assert int((cnt == 0).sum().item()) > 0
+    acc, _ = tg.forces(q, mass, None, None, P)              # rebuild clears the flags
+    torch.cuda.synchronize()
+    tg.tree.status()
+    ref = g4.TreeGravity(ps.n, P)
+    acc_ref, _ = ref.forces(q, mass, None, None, P)
+    torch.cuda.synchronize()
+    assert torch.equal(acc, acc_ref)
+    with pytest.raises(g4.G4Error, match="status 1"):      # a negative budget is refused
+        tg.tree.gravity_tree(tg.pos_s, tg.mass_s, None, None,
+                             g4.params(box_size=float(frame[3].item()), eps=[0.01], criterion=1,
+                                       watchdog_cycles=-5))
