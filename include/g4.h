@@ -326,8 +326,8 @@ g4_status g4_gravity_tree_perm(g4_tree tree, const uint32_t *pos_sorted, const f
 g4_status g4_fmm_workspace(g4_tree tree, const g4_params *params, size_t *bytes);
 
 /* Forces for all n particles by the dual tree walk over pairs of cells, a cell being a node or
- * a single particle (Sec. 2.4: "interacting pairs of nodes or particles"; a particle is a cell
- * of side 0 with Q_0 = m).  A pair interacts by the symmetric expansion (fields added to both
+ * a single particle (Sec. 2.4: a pair's members are nodes or single particles; a particle is a
+ * cell of side 0 with Q_0 = m).  A pair interacts by the symmetric expansion (fields added to both
  * cells; at a particle the field is evaluated on the spot), or fails and is opened: both cells
  * ("open both"), a leaf into its particles, a particle never; two particles interact directly
  * (pair kernel).  A node paired with itself is replaced by all pairs of its daughters.

@@ -853,8 +853,9 @@ typedef struct {
 } or_fmm_ctx;
 
 /* A cell of the dual walk: a tree node, or a single particle.  Sec. 2.4 lets the walk pair
- * "nodes or particles"; a particle is a cell of side 0 centred on itself whose only moment is
- * Q_0 = m (its dipole and higher moments about its own position vanish). */
+ * nodes with nodes or with single particles; a particle is a cell of side 0 centred on itself
+ * whose only moment is Q_0 = m (its dipole and higher moments about its own position
+ * vanish). */
 typedef struct {
     int64_t k;   /* node index, or sorted particle index */
     int part;    /* 1: particle */
@@ -1077,7 +1078,7 @@ static int64_t or_daughters(const or_fmm_ctx *C, int64_t k, or_cell **out)
 /* Dual tree walk (Sec. 2.4) over cells A != B: a pair either interacts through the symmetric
  * expansion (fields added to both cells), or is opened.  Readings:
  *   - two particles always interact directly (pair kernel, softened);
- *   - a failing pair opens both cells ("open both"); a particle cannot be opened, so a
+ *   - a failing pair opens both of its cells; a particle cannot be opened, so a
  *     particle paired with a node opens the node only; a leaf opens into its particles, which
  *     then meet the other side's daughters as particle-node pairs (the cell-particle
  *     interactions of the method's second phase);

@@ -1,9 +1,9 @@
 // g4_fmm.cuh -- symmetric Cartesian fast multipole method (Sec. 2.4, Sec. 2.5).
 //
 // The paper's dual tree walk visits unordered pairs of cells, a cell being a node or a single
-// particle ("interacting pairs of nodes or particles").  A particle is a cell of side 0 whose
-// only moment is Q_0 = m.  A pair either interacts through the symmetric expansion, or fails
-// and is opened: both cells if both can be ("open both", Sec. 2.4), a leaf into its particles,
+// particle (Sec. 2.4).  A particle is a cell of side 0 whose only moment is Q_0 = m.  A pair
+// either interacts through the symmetric expansion, or fails and is opened: both cells if both
+// can be (Sec. 2.4 opens both), a leaf into its particles,
 // a particle never.  Two particles always interact directly.  The decisions are symmetric in
 // the two cells, so the same interactions are found by visiting ordered pairs (X, Y) -- sink X,
 // source Y -- where (X, Y) and (Y, X) receive the same decision.  That makes the walk
