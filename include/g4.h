@@ -120,7 +120,7 @@ int64_t g4_launch_count(void);
 /* Fills *p with the defaults: periodic=0, r_s=0, R_cut=4.5, pp_cut=1, alpha=0.0025,
  * theta=0.5, criterion=0, p=3, leaf_max=8, exclusion=1, precision=0, G=1, one class with
  * eps=0.01, group_size=32, fp64_count=4096, keep_qp=0, fmm_p2p_per_particle=0, soft_nodes=0,
- * ewald=0.
+ * ewald=0, watchdog_cycles=0.
  * Host-only, never fails for p!=NULL. */
 g4_status g4_params_default(g4_params *p);
 
