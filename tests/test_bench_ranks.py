@@ -62,3 +62,22 @@ def test_reference_arm_extra_ranks_exit_without_work(capsys):
         steps, warmup = 1, 0
     assert bench.run_reference(A(), 1, 2) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_fmm_baseline_leg_on_a_small_sample():
+    """The FMM's host baseline (the FP64 oracle FMM on a bounded sample of the headline's
+    spacing and split) reports forces/s on one core and names its sample."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.oracle_fmm_throughput(n_side_cpu=12)
+    assert r["value"] > 0 and r["cores"] == 1 and r["kind"] == "oracle" and r["unit"] == bench.UNIT
+    assert "12^3" in r["sample"] and "p = 4" in r["sample"]
+
+
+def test_params_defaults_include_the_watchdog_off():
+    """The binding's ctypes mirror carries the walk's watchdog budget, off (0) by default."""
+    sys.path.insert(0, ROOT)
+    from paper_2010_03567_gb300 import g4
+    p = g4.params()
+    assert p.watchdog_cycles == 0
+    assert g4.params(watchdog_cycles=1 << 40).watchdog_cycles == 1 << 40
