@@ -515,6 +515,10 @@ def extra_fmm(pos_int, mass, aold, wp, n, sample_ref, cpu=True):
            "pn_per_step": int(cnt[1].to(torch.int64).sum().item()),
            # node-node (M2L) fields acting on each particle through its ancestors, summed
            "nn_per_particle_sum": int(cnt[2].to(torch.int64).sum().item())}
+    # interactions per second by kind (ordered particle pairs, particle-node terms, node-node
+    # fields counted at the particles they reach)
+    res["interactions_per_s"] = {k: res[f"{k}_per_step"] / (ms * 1e-3) for k in ("pp", "pn")}
+    res["interactions_per_s"]["nn_per_particle"] = res["nn_per_particle_sum"] / (ms * 1e-3)
     if sample_ref is not None:
         sinks, ad = sample_ref
         ag = tg.acc.cpu().numpy().T[sinks].astype(np.float64)
