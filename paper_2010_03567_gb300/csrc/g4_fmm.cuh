@@ -3,8 +3,8 @@
 // The paper's dual tree walk visits unordered pairs of cells, a cell being a node or a single
 // particle (Sec. 2.4).  A particle is a cell of side 0 whose only moment is Q_0 = m.  A pair
 // either interacts through the symmetric expansion, or fails and is opened: both cells if both
-// can be (Sec. 2.4 opens both), a leaf into its particles,
-// a particle never.  Two particles always interact directly.  The decisions are symmetric in
+// can be (Sec. 2.4 opens both), a leaf into its particles, a particle never.  Two particles
+// always interact directly.  The decisions are symmetric in
 // the two cells, so the same interactions are found by visiting ordered pairs (X, Y) -- sink X,
 // source Y -- where (X, Y) and (Y, X) receive the same decision.  That makes the walk
 // sink-centric and free of write conflicts:
